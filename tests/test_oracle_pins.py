@@ -1,0 +1,601 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: a value the
+paper prints, a published constant, a closed form, an invariant, a library
+routine, or brute force on a tiny problem.  None of these needs a GPU.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_2502_14148_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    rows = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            parts = line.split()
+            rows.setdefault(parts[0], []).append(parts[1:])
+    return rows
+
+
+def _cell_averages(poly, cells):
+    """Exact cell averages over [n, n+1] of a polynomial given by numpy coefficients (highest first)."""
+    P = np.polyint(poly)
+    return np.array([np.polyval(P, n + 1) - np.polyval(P, n) for n in cells])
+
+
+def small_params(**over):
+    p = dict(Nx=8, Ny=8, Nz=8, Lx=8.0, Ly=8.0, Lz=8.0, stretch=None, weno_order=5, closure="none",
+             tracers=["b"], eos="buoyancy_tracer", f=0.0)
+    p.update(over)
+    if p.get("stretch"):
+        p["z_faces"] = inputs.tanh_faces(p["Nz"], p["Lz"], p["stretch"])
+    else:
+        p["z_faces"] = inputs.uniform_faces(p["Nz"], p["Lz"])
+    p.setdefault("top_flux", {})
+    p.setdefault("bottom_flux", {})
+    return p
+
+
+# ----------------------------------------------------------------------------- grid
+def test_xnodes_worked_example(oracle_mod):
+    """Appendix B, staggered-grid listing: faces [0,.2,.3,.7,1] -> centres [.1,.25,.5,.85]."""
+    g = _golden("xnodes_staggered_grid.txt")
+    faces = np.array([float(x) for x in g["faces"][0]])
+    centers = np.array([float(x) for x in g["centers"][0]])
+    p = small_params(Nx=4, Ny=4, Nz=4)
+    p["z_faces"] = faces
+    m = oracle_mod.OracleModel(p)
+    zc, dzc, dzf = m.grid_metrics()
+    np.testing.assert_allclose(zc, centers, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(dzc, np.diff(faces), atol=1e-15)
+    np.testing.assert_allclose(dzf[1:4], np.diff(centers), atol=1e-15)
+
+
+# ----------------------------------------------------------------------------- reconstruction
+def test_weno5_smoothness_indicators_textbook(oracle_mod):
+    """Jiang-Shu WENO5 indicators in their published 13/12, 1/4 form (golden file)."""
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        c = rng.standard_normal(6)          # c_{m-3} .. c_{m+2}
+        q, beta = oracle_mod.weno_parts(c, 3, +1.0)
+        a, b, cc, d, e = c[0], c[1], c[2], c[3], c[4]
+        ref = [13 / 12 * (a - 2 * b + cc) ** 2 + 0.25 * (a - 4 * b + 3 * cc) ** 2,
+               13 / 12 * (b - 2 * cc + d) ** 2 + 0.25 * (b - d) ** 2,
+               13 / 12 * (cc - 2 * d + e) ** 2 + 0.25 * (3 * cc - 4 * d + e) ** 2]
+        np.testing.assert_allclose(beta, ref, rtol=1e-13, atol=1e-13)
+        refq = [(2 * a - 7 * b + 11 * cc) / 6, (-b + 5 * cc + 2 * d) / 6, (2 * cc + 5 * d - e) / 6]
+        np.testing.assert_allclose(q, refq, rtol=1e-13, atol=1e-13)
+
+
+def test_upwind3_stencil_paper(oracle_mod):
+    """Paper Eq. upwind-biased: the order-3 upwind stencil (-c_{i-2}+5c_{i-1}+2c_i)/6 is
+    WENO3's linear combination; V-shaped data (beta_0 = beta_1) make WENO3 reduce to it."""
+    g = _golden("weno_published_constants.txt")
+    w = [float(Fraction(x)) for x in g["upwind3"][0]]
+    rng = np.random.default_rng(2)
+    for _ in range(10):
+        a, b = rng.standard_normal(2)
+        s = np.array([a + b, a, a + b, rng.standard_normal()])   # c_{i-2}, c_{i-1}, c_i, (unused) c_{i+1}
+        got = oracle_mod.weno(s, 2, +1.0)
+        np.testing.assert_allclose(got, w[0] * s[0] + w[1] * s[1] + w[2] * s[2], rtol=1e-14, atol=1e-14)
+        # mirror for u < 0: (2 c_{i-1} + 5 c_i - c_{i+1})/6 with c_{i-1} = c_{i+1}
+        s2 = np.array([rng.standard_normal(), a + b, a, a + b])
+        got2 = oracle_mod.weno(s2, 2, -1.0)
+        np.testing.assert_allclose(got2, (2 * s2[1] + 5 * s2[2] - s2[3]) / 6, rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("r", [2, 3, 4, 5])
+def test_weno_linear_limit_exact_on_symmetric_polynomials(oracle_mod, r):
+    """When the data are cell averages of a polynomial of degree <= 2r-2 that is mirror-symmetric
+    about the upwind cell, beta_0 = beta_{r-1} so the WENO-Z weights equal the linear weights, and the
+    linear combination is the upwind stencil of order 2r-1, exact for that degree (any error in the
+    substencils, linear weights or indicators breaks exactness)."""
+    cells = list(range(-r, r))
+    for deg in range(0, 2 * r - 1, 2):
+        poly = np.zeros(deg + 1); poly[0] = 1.0                  # (x + 1/2)^deg, symmetric about -1/2
+        poly = np.poly1d(np.poly1d([1.0, 0.5]) ** deg).coeffs
+        s = _cell_averages(poly, cells)
+        got = oracle_mod.weno(s, r, +1.0)
+        np.testing.assert_allclose(got, 0.5 ** deg, rtol=1e-12, atol=1e-12)
+
+
+def test_published_linear_weights(oracle_mod):
+    """Published optimal weights recombine the substencils into the single high-order upwind stencil
+    (checked through the oracle's substencil values on random data)."""
+    g = _golden("weno_published_constants.txt")
+    rng = np.random.default_rng(3)
+    for row in g["d"]:
+        r = int(row[0].split("=")[1])
+        d = np.array([float(Fraction(x)) for x in row[1:]])
+        for _ in range(5):
+            # cell averages of a random polynomial of degree 2r-2: the recombination must be exact
+            poly = rng.standard_normal(2 * r - 1)
+            s = _cell_averages(poly, range(-r, r))
+            q, _ = oracle_mod.weno_parts(s, r, +1.0)
+            exact = np.polyval(poly, 0.0)
+            np.testing.assert_allclose(d @ q, exact, rtol=1e-11, atol=1e-11)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6])
+def test_centered_exact_for_polynomials(oracle_mod, p):
+    """Centered reconstruction of order 2p (Eq. centered-reconstruction for p=1) is exact for
+    cell averages of polynomials of degree <= 2p-1."""
+    rng = np.random.default_rng(4)
+    for _ in range(5):
+        poly = rng.standard_normal(2 * p)
+        s = _cell_averages(poly, range(-p, p))
+        tol = 1e-13 * np.abs(s).max() * 4 ** p      # round-off of the averages of high-degree polynomials
+        np.testing.assert_allclose(oracle_mod.centered(s, p), np.polyval(poly, 0.0), rtol=0, atol=tol)
+    assert oracle_mod.centered([3.0, 5.0], 1) == 4.0      # the paper's (c_i + c_{i-1})/2
+
+
+def test_upwind1_decomposition(oracle_mod):
+    """Paper: u[c]^1 = u (c_i + c_{i-1})/2 - kappa_1 (c_i - c_{i-1})/dx, kappa_1 = |u| dx / 2."""
+    rng = np.random.default_rng(5)
+    dx = 0.37
+    for _ in range(10):
+        cm1, ci = rng.standard_normal(2)
+        for u in (1.7, -0.4):
+            lhs = u * oracle_mod.weno([cm1, ci], 1, u)
+            k1 = abs(u) * dx / 2
+            rhs = u * (ci + cm1) / 2 - k1 * (ci - cm1) / dx
+            assert abs(lhs - rhs) < 1e-14
+
+
+def test_upwind3_equals_centered4_plus_hyperdiffusion(oracle_mod):
+    """Paper: UpwindBiased(3) = Centered(4) flux + a fourth-order hyperdiffusive flux with
+    kappa_3 = |u| dx^3 / 12 acting on the third derivative (here its 4-point difference)."""
+    rng = np.random.default_rng(6)
+    for _ in range(10):
+        a, b, e = rng.standard_normal(3)
+        c = np.array([a + b, a, a + b, e])            # c_{i-2}, c_{i-1}, c_i, c_{i+1}; beta_0 = beta_1
+        u = 0.8
+        up3 = oracle_mod.weno(c, 2, u)
+        cen4 = oracle_mod.centered(c, 2)
+        d3 = c[3] - 3 * c[2] + 3 * c[1] - c[0]
+        assert abs(u * up3 - (u * cen4 + abs(u) * d3 / 12)) < 1e-14   # u c + kappa_3 d3c/dx3
+
+
+@pytest.mark.parametrize("r,order", [(3, 5), (5, 9)])
+def test_weno_convergence_order_on_smooth_data(oracle_mod, r, order):
+    """On smooth data WENO-Z keeps the design order 2r-1 (measured by refinement)."""
+    errs = []
+    Ns = [16, 32, 64] if r == 3 else [12, 16, 24]
+    for N in Ns:
+        h = 1.0 / N
+        k = 2 * math.pi
+        e = 0.0
+        for m in range(N):
+            x0 = m * h                             # interface position
+            cells = np.arange(m - r, m + r)
+            s = (np.cos(k * cells * h) - np.cos(k * (cells + 1) * h)) / (k * h)   # averages of sin
+            e = max(e, abs(oracle_mod.weno(s, r, 1.0) - math.sin(k * x0)))
+        errs.append(e)
+    rates = [math.log(errs[i] / errs[i + 1]) / math.log(Ns[i + 1] / Ns[i]) for i in range(len(Ns) - 1)]
+    assert min(rates) > order - 0.6, (errs, rates)
+
+
+# ----------------------------------------------------------------------------- FFT
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 8, 12, 16, 24, 32, 48, 96, 128])
+def test_fft_matches_numpy(oracle_mod, n):
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    np.testing.assert_allclose(oracle_mod.fft(x, -1), np.fft.fft(x), rtol=1e-12, atol=1e-12 * n)
+    np.testing.assert_allclose(oracle_mod.fft(x, +1), np.fft.ifft(x) * n, rtol=1e-12, atol=1e-12 * n)
+
+
+# ----------------------------------------------------------------------------- Poisson / projection
+def _dense_laplacian(Nx, Ny, zf, dx, dy):
+    """Assemble div(grad) with Neumann walls column by column, by applying discrete differences
+    (numpy) to unit vectors: a route independent of the spectral solver."""
+    zc = 0.5 * (zf[1:] + zf[:-1]); dzc = np.diff(zf); dzf = np.diff(zc)
+    Nz = len(zc)
+    N = Nx * Ny * Nz
+    A = np.zeros((N, N))
+    for n in range(N):
+        e = np.zeros(N); e[n] = 1.0
+        p = e.reshape(Nz, Ny, Nx)
+        gx = (p - np.roll(p, 1, axis=2)) / dx
+        gy = (p - np.roll(p, 1, axis=1)) / dy
+        gz = np.zeros((Nz + 1, Ny, Nx)); gz[1:Nz] = (p[1:] - p[:-1]) / dzf[:, None, None]
+        div = (np.roll(gx, -1, axis=2) - gx) / dx + (np.roll(gy, -1, axis=1) - gy) / dy + (gz[1:] - gz[:-1]) / dzc[:, None, None]
+        A[:, n] = div.ravel()
+    return A, dzc
+
+
+@pytest.mark.parametrize("stretch", [None, 1.5])
+def test_poisson_matches_dense_solve_8cubed(oracle_mod, stretch):
+    p = small_params(stretch=stretch)
+    m = oracle_mod.OracleModel(p)
+    rng = np.random.default_rng(7)
+    Nx, Ny, Nz = 8, 8, 8
+    rhs = rng.standard_normal((Nz, Ny, Nx))
+    A, dzc = _dense_laplacian(Nx, Ny, np.asarray(p["z_faces"]), 1.0, 1.0)
+    V = np.broadcast_to(dzc[:, None, None], (Nz, Ny, Nx)).ravel()
+    rhs -= (V @ rhs.ravel()) / V.sum()                     # compatible right-hand side
+    # gauge: zero volume-weighted mean (augment the singular system with that constraint)
+    Aug = np.vstack([A, V[None, :]])
+    sol = np.linalg.lstsq(Aug, np.concatenate([rhs.ravel(), [0.0]]), rcond=None)[0]
+    got = m.poisson(rhs)
+    np.testing.assert_allclose(got.ravel(), sol, rtol=0, atol=1e-12 * np.abs(sol).max())
+    np.testing.assert_allclose(A @ got.ravel(), rhs.ravel(), atol=1e-11)
+
+
+def _random_velocity_model(oracle_mod, stretch=1.5, **over):
+    p = small_params(stretch=stretch, Nx=12, Ny=8, Nz=6, Lx=12.0, **over)
+    m = oracle_mod.OracleModel(p)
+    st = inputs.random_state(p, seed=11)
+    m.set(**st)
+    return m, p, st
+
+
+def test_projection_divergence_free_and_idempotent(oracle_mod):
+    m, p, st = _random_velocity_model(oracle_mod)
+    assert np.abs(m.divergence()).max() > 0.1
+    m.project(0.7)
+    div = np.abs(m.divergence()).max()
+    umax = max(np.abs(m.get(x)).max() for x in "uvw")
+    assert div <= 1e-13 * umax / 0.5
+    u1 = {x: m.get(x) for x in "uvw"}
+    m.project(0.3)
+    for x in "uvw":
+        np.testing.assert_allclose(m.get(x), u1[x], atol=1e-13)
+
+
+def test_projection_removes_discrete_gradient(oracle_mod):
+    p = small_params(stretch=1.5, Nx=12, Ny=8, Nz=6, Lx=12.0)
+    m = oracle_mod.OracleModel(p)
+    phi = np.random.default_rng(8).standard_normal((6, 8, 12))
+    zc = 0.5 * (p["z_faces"][1:] + p["z_faces"][:-1])
+    u = phi - np.roll(phi, 1, axis=2)
+    v = phi - np.roll(phi, 1, axis=1)
+    w = np.zeros((7, 8, 12)); w[1:6] = (phi[1:] - phi[:-1]) / np.diff(zc)[:, None, None]
+    m.set(u=u, v=v, w=w)
+    m.project(1.0)
+    for x in "uvw":
+        assert np.abs(m.get(x)).max() < 1e-12
+
+
+# ----------------------------------------------------------------------------- RK3
+def _taylor3(z):
+    return 1 + z + z * z / 2 + z ** 3 / 6
+
+
+def test_rk3_inertial_oscillation_taylor_polynomial(oracle_mod):
+    """Eq. rk3 (gamma=(8/15,5/12,3/4), zeta=(0,17/60,5/12)) on uniform u, v with f != 0: the exact
+    linear system y' = A y, A = [[0,f],[-f,0]]; one step must equal the cubic Taylor polynomial."""
+    f, dt = 0.3, 0.7
+    p = small_params(f=f, closure="none", weno_order=5)
+    m = oracle_mod.OracleModel(p)
+    U0, V0 = 0.4, -1.1
+    m.set(u=np.full((8, 8, 8), U0), v=np.full((8, 8, 8), V0), w=np.zeros((9, 8, 8)), b=np.zeros((8, 8, 8)))
+    m.time_step(dt, 1)
+    A = np.array([[0.0, f], [-f, 0.0]]) * dt
+    P = np.eye(2) + A + A @ A / 2 + A @ A @ A / 6
+    exp = P @ np.array([U0, V0])
+    np.testing.assert_allclose(m.get("u"), exp[0], atol=1e-14)
+    np.testing.assert_allclose(m.get("v"), exp[1], atol=1e-14)
+
+
+def test_rk3_discrete_diffusion_eigenmode(oracle_mod):
+    """Constant-kappa diffusion of a sampled sine: an exact eigenvector of the periodic second
+    difference with eigenvalue -kappa (2 sin(pi/N)/dx)^2; one RK3 step multiplies it by the cubic
+    Taylor polynomial of dt*lambda."""
+    N, kappa, dt = 16, 0.05, 0.8
+    p = small_params(Nx=N, Ny=4, Nz=4, Lx=float(N), closure="scalar", nu=0.0, kappa=kappa, tracers=["b", "c"])
+    m = oracle_mod.OracleModel(p)
+    x = np.arange(N) + 0.5
+    c = np.broadcast_to(np.sin(2 * np.pi * x / N), (4, 4, N)).copy()
+    m.set(u=np.zeros((4, 4, N)), v=np.zeros((4, 4, N)), w=np.zeros((5, 4, N)), b=np.zeros((4, 4, N)), c=c)
+    m.time_step(dt, 1)
+    lam = -kappa * (2 * math.sin(math.pi / N)) ** 2
+    np.testing.assert_allclose(m.get("c"), _taylor3(dt * lam) * c, atol=1e-14)
+
+
+# ----------------------------------------------------------------------------- conservation
+@pytest.mark.parametrize("closure", ["none", "scalar", "amd", "smagorinsky"])
+def test_conservation_periodic_noflux(oracle_mod, closure):
+    """Flux form + periodic x,y + no-flux walls: sum V c, sum V u and sum V v (f=0) are invariant."""
+    p = small_params(stretch=1.5, Nx=12, Ny=8, Nz=6, Lx=12.0, closure=closure, nu=0.02, kappa=0.03)
+    m = oracle_mod.OracleModel(p)
+    st = inputs.random_state(p, seed=12, amp=0.3)
+    m.set(**st)
+    m.project(1.0)
+    d0 = m.diagnostics()
+    m.time_step(0.05, 3)
+    d1 = m.diagnostics()
+    assert d1["nonfinite"] == 0
+    scale_c = np.abs(st["b"]).sum() * 1.0
+    assert abs(d1["sum_b"] - d0["sum_b"]) < 1e-13 * scale_c
+    scale_u = np.abs(st["u"]).sum()
+    assert abs(d1["sum_u"] - d0["sum_u"]) < 1e-13 * scale_u
+    assert abs(d1["sum_v"] - d0["sum_v"]) < 1e-13 * scale_u
+
+
+def test_surface_flux_changes_budget_exactly(oracle_mod):
+    """With a top flux Q of b, sum V b changes by exactly -Q * A_top * dt per RK3 step (sum(gamma-zeta)=1)."""
+    Q, dt = 3e-3, 0.05
+    p = small_params(stretch=1.5, Nx=12, Ny=8, Nz=6, Lx=12.0, closure="amd", top_flux={"b": Q}, bottom_flux={"b": -Q / 3})
+    m = oracle_mod.OracleModel(p)
+    st = inputs.random_state(p, seed=13, amp=0.3)
+    m.set(**st)
+    m.project(1.0)
+    d0 = m.diagnostics()
+    m.time_step(dt, 2)
+    d1 = m.diagnostics()
+    A = 12.0 * 8.0
+    np.testing.assert_allclose(d1["sum_b"] - d0["sum_b"], -(Q + Q / 3) * A * dt * 2, rtol=1e-11)
+
+
+def test_coriolis_energy_neutral(oracle_mod):
+    """The discrete Coriolis force does no work: sum(u G_u^cor + v G_v^cor) V = 0."""
+    p0 = small_params(stretch=1.5, Nx=12, Ny=8, Nz=6, Lx=12.0, f=0.0)
+    p1 = dict(p0, f=1.3)
+    st = inputs.random_state(p0, seed=14)
+    m0 = oracle_mod.OracleModel(p0); m0.set(**st)
+    m1 = oracle_mod.OracleModel(p1); m1.set(**st)
+    G0, G1 = m0.tendencies(), m1.tendencies()
+    dzc = np.diff(p0["z_faces"])[:, None, None]
+    work = ((G1["u"] - G0["u"]) * st["u"] * dzc).sum() + ((G1["v"] - G0["v"]) * st["v"] * dzc).sum()
+    scale = (np.abs(G1["u"] - G0["u"]) * np.abs(st["u"]) * dzc).sum()
+    assert scale > 1.0
+    assert abs(work) < 1e-13 * scale
+
+
+# ----------------------------------------------------------------------------- closures
+def test_smagorinsky_on_pure_shear(oracle_mod):
+    """Linear shear u = S z, no stratification: nu_e = (C_s Delta)^2 S in the interior."""
+    S = 0.37
+    p = small_params(closure="smagorinsky", Cs=0.16, Cb=1.0, Pr=1.0, Nx=8, Ny=8, Nz=8, Lx=16.0, Ly=8.0)
+    m = oracle_mod.OracleModel(p)
+    zc = 0.5 * (p["z_faces"][1:] + p["z_faces"][:-1])
+    m.set(u=np.broadcast_to(S * zc[:, None, None], (8, 8, 8)).copy(), v=np.zeros((8, 8, 8)),
+          w=np.zeros((9, 8, 8)), b=np.zeros((8, 8, 8)))
+    Delta = (2.0 * 1.0 * 1.0) ** (1 / 3)
+    for k in range(1, 7):
+        assert abs(m.diffusivity_at(0, 3, 2, k) - (0.16 * Delta) ** 2 * S) < 1e-15
+
+
+def test_amd_zero_on_pure_shear_and_nonnegative(oracle_mod):
+    p = small_params(closure="amd", C_amd=1 / 12)
+    m = oracle_mod.OracleModel(p)
+    zc = 0.5 * (p["z_faces"][1:] + p["z_faces"][:-1])
+    m.set(u=np.broadcast_to(0.5 * zc[:, None, None], (8, 8, 8)).copy(), v=np.zeros((8, 8, 8)),
+          w=np.zeros((9, 8, 8)), b=np.broadcast_to(zc[:, None, None], (8, 8, 8)).copy())
+    for k in range(1, 7):
+        assert m.diffusivity_at(0, 1, 1, k) == 0.0
+    st = inputs.random_state(p, seed=15)
+    m.set(**st)
+    for closure in ("amd", "smagorinsky"):
+        mm = oracle_mod.OracleModel(dict(p, closure=closure))
+        mm.set(**st)
+        vals = [mm.diffusivity_at(w_, i, j, k) for w_ in (0, 1) for i in range(0, 8, 3) for j in range(0, 8, 3) for k in range(8)]
+        assert min(vals) >= 0.0 and max(vals) > 0.0
+
+
+# ----------------------------------------------------------------------------- solutions
+def test_resting_stratified_state_stays_at_rest(oracle_mod):
+    p = small_params(stretch=1.5, Nx=8, Ny=8, Nz=10, closure="amd", f=1e-4)
+    m = oracle_mod.OracleModel(p)
+    zc = 0.5 * (p["z_faces"][1:] + p["z_faces"][:-1])
+    m.set(u=np.zeros((10, 8, 8)), v=np.zeros((10, 8, 8)), w=np.zeros((11, 8, 8)),
+          b=np.broadcast_to(1e-2 * zc[:, None, None], (10, 8, 8)).copy())
+    m.time_step(0.5, 4)
+    for x in "uvw":
+        assert np.abs(m.get(x)).max() < 1e-14
+
+
+def _tg_amplitude(oracle_mod, N, steps, dt, nu):
+    p = inputs.config("taylor_green_32", Nx=N, Ny=N, Nz=4, Lz=1.0, init="taylor_green_2d", noise=0.0, nu=nu, kappa=nu)
+    m = oracle_mod.OracleModel(p)
+    st = inputs.initial_state(p)
+    m.set(**st)
+    m.project(1.0)
+    u0 = m.get("u")
+    m.time_step(dt, steps)
+    u1 = m.get("u")
+    return (u1 * u0).sum() / (u0 * u0).sum()
+
+
+def test_taylor_green_decay_closed_form(oracle_mod):
+    """2D Taylor-Green is an exact Navier-Stokes solution decaying as exp(-2 nu t).
+    (a) At 32^2 the decay factor matches the closed form within 2e-6.
+    (b) The sampled Taylor-Green mode is an exact eigenvector of the discrete Laplacian with
+    eigenvalue -2 (2 sin(d/2)/d)^2, so without advection error one RK3 step multiplies it by the cubic
+    Taylor polynomial of dt*nu*lambda.  The remaining difference is the WENO5 advection error, which
+    must shrink at fifth order under refinement (16 -> 32 -> 64)."""
+    nu, dt, steps = 1e-3, 1e-2, 20
+    exact = math.exp(-2 * nu * dt * steps)
+    res = {}
+    for N in (16, 32, 64):
+        a = _tg_amplitude(oracle_mod, N, steps, dt, nu)
+        d = 2 * math.pi / N
+        z = dt * (-2 * nu * (2 * math.sin(d / 2) / d) ** 2)
+        res[N] = (a - exact, a - _taylor3(z) ** steps)
+    assert abs(res[32][0]) < 2e-6
+    for N in (16, 32):
+        rate = math.log2(abs(res[N][1]) / abs(res[2 * N][1]))
+        assert rate > 4.6, (N, res)
+
+
+def test_sine_tracer_translation(oracle_mod):
+    """Uniform flow translates a sine tracer; after one period it returns to itself within the
+    scheme's error, which shrinks at high order under refinement (fixed CFL)."""
+    errs = []
+    for N in (16, 32):
+        U, L = 1.0, float(N)
+        dt = 0.25
+        p = small_params(Nx=N, Ny=4, Nz=4, Lx=L, Ly=4.0, Lz=4.0, weno_order=5, tracers=["b", "c"])
+        m = oracle_mod.OracleModel(p)
+        x = np.arange(N) + 0.5
+        k = 2 * np.pi / L
+        cavg = (np.cos(k * (x - 0.5)) - np.cos(k * (x + 0.5))) / k      # exact cell averages
+        c = np.broadcast_to(cavg, (4, 4, N)).copy()
+        m.set(u=np.full((4, 4, N), U), v=np.zeros((4, 4, N)), w=np.zeros((5, 4, N)), b=np.zeros((4, 4, N)), c=c)
+        m.time_step(dt, int(round(L / (U * dt))))
+        errs.append(np.abs(m.get("c") - c).max())
+        # constant fields stay exactly constant
+    assert errs[0] < 2e-3 and errs[1] < errs[0] / 6, errs
+    m2 = oracle_mod.OracleModel(small_params(Nx=8))
+    m2.set(u=np.full((8, 8, 8), 0.3), v=np.full((8, 8, 8), -0.2), w=np.zeros((9, 8, 8)), b=np.full((8, 8, 8), 2.5))
+    m2.time_step(0.3, 3)
+    assert np.abs(m2.get("b") - 2.5).max() < 1e-14
+
+
+@pytest.mark.parametrize("order", [5, 9])
+def test_advective_tendency_convergence(oracle_mod, order):
+    """For exact cell averages of a smooth tracer in uniform flow, the finite-volume tendency equals
+    the exact rate of change of the cell averages up to the reconstruction error, O(dx^(2r-1))."""
+    errs, Ns = [], ([16, 32, 64] if order == 5 else [12, 16, 24])
+    for N in Ns:
+        L, U = 1.0, 0.7
+        p = small_params(Nx=N, Ny=4, Nz=4, Lx=L, Ly=4.0, Lz=4.0, weno_order=order)
+        m = oracle_mod.OracleModel(p)
+        h = L / N
+        k = 2 * np.pi / L
+        xl = np.arange(N) * h
+        cavg = (np.cos(k * xl) - np.cos(k * (xl + h))) / (k * h)
+        exact = -U * (np.sin(k * (xl + h)) - np.sin(k * xl)) / h
+        m.set(u=np.full((4, 4, N), U), v=np.zeros((4, 4, N)), w=np.zeros((5, 4, N)),
+              b=np.broadcast_to(cavg, (4, 4, N)).copy())
+        G = m.tendencies()["b"]
+        errs.append(np.abs(G[1, 1] - exact).max())
+    rates = [math.log(errs[i] / errs[i + 1]) / math.log(Ns[i + 1] / Ns[i]) for i in range(len(Ns) - 1)]
+    assert min(rates) > order - 0.7, (errs, rates)
+
+
+# ----------------------------------------------------------------------------- more directions
+def _avg_sin(k, lo, h):
+    """Exact averages of sin(k x) over [lo, lo+h]."""
+    return (np.cos(k * lo) - np.cos(k * (lo + h))) / (k * h)
+
+
+@pytest.mark.parametrize("order", [5, 9])
+def test_tracer_tendency_convergence_y_and_z(oracle_mod, order):
+    """Same finite-volume consistency as in x, for the y (periodic) and z (bounded, interior cells
+    away from the walls, uniform interior w) directions."""
+    Ns = [16, 32, 64] if order == 5 else [16, 20, 24]
+    R = (order + 1) // 2
+    ey, ez = [], []
+    for N in Ns:
+        h, k, V = 1.0 / N, 2 * np.pi, 0.6
+        lo = np.arange(N) * h
+        cavg = _avg_sin(k, lo, h)
+        exact = -V * (np.sin(k * (lo + h)) - np.sin(k * lo)) / h
+        p = small_params(Nx=4, Ny=N, Nz=N, Lx=4.0, Ly=1.0, Lz=1.0, weno_order=order, tracers=["b", "c"])
+        m = oracle_mod.OracleModel(p)
+        zeros = np.zeros((N, N, 4))
+        m.set(u=zeros, v=np.full((N, N, 4), V), w=np.zeros((N + 1, N, 4)), b=zeros,
+              c=np.broadcast_to(cavg[None, :, None], (N, N, 4)).copy())
+        ey.append(np.abs(m.tendencies()["c"][N // 2, :, 1] - exact).max())
+        # z: uniform interior w, z-grid from -1 to 0 (cell n covers [-1 + n h, -1 + (n+1) h])
+        zlo = -1.0 + np.arange(N) * h
+        w = np.full((N + 1, N, 4), V); w[0] = 0.0; w[-1] = 0.0
+        m.set(v=zeros, w=w, c=np.broadcast_to(_avg_sin(k, zlo, h)[:, None, None], (N, N, 4)).copy())
+        Gz = m.tendencies()["c"][:, 3, 2]
+        exz = -V * (np.sin(k * (zlo + h)) - np.sin(k * zlo)) / h
+        ez.append(np.abs(Gz[R:N - R] - exz[R:N - R]).max())
+    for errs in (ey, ez):
+        rates = [math.log(errs[i] / errs[i + 1]) / math.log(Ns[i + 1] / Ns[i]) for i in range(len(Ns) - 1)]
+        assert min(rates) > order - 0.7, (errs, rates)
+
+
+def test_momentum_vertical_and_w_advection_convergence(oracle_mod):
+    """Momentum advection (Sec. B.2.1): u(z) carried by uniform interior w (u-equation z-flux),
+    w(x) carried by uniform u (w-equation x-flux) and w(z) self-advection (w-equation z-flux, order
+    limited by the order-4 centered advecting velocity) converge to the exact finite-volume rates."""
+    Ns = [16, 32, 64]
+    e_uz, e_wx, e_wz = [], [], []
+    for N in Ns:
+        h, k, W = 1.0 / N, 2 * np.pi, 0.45
+        p = small_params(Nx=N, Ny=4, Nz=N, Lx=1.0, Ly=4.0, Lz=1.0, weno_order=5)
+        m = oracle_mod.OracleModel(p)
+        zlo = -1.0 + np.arange(N) * h
+        w = np.full((N + 1, 4, N), W); w[0] = 0.0; w[-1] = 0.0
+        u = np.broadcast_to(_avg_sin(k, zlo, h)[:, None, None], (N, 4, N)).copy()
+        m.set(u=u, v=np.zeros((N, 4, N)), w=w, b=np.zeros((N, 4, N)))
+        Gu = m.tendencies()["u"][:, 1, 2]
+        ex = -W * (np.sin(k * (zlo + h)) - np.sin(k * zlo)) / h
+        e_uz.append(np.abs(Gu[3:N - 3] - ex[3:N - 3]).max())
+        # w(x) advected by uniform U: w-cells are centred on x-centres, x-faces at i h
+        U = 0.8
+        xlo = np.arange(N) * h - 0.5 * h           # w-control volume in x spans [x_c - h/2, x_c + h/2]
+        wx = np.zeros((N + 1, 4, N)); wx[1:N] = _avg_sin(k, xlo, h)[None, None, :]
+        # w's x-faces are at the u points i*h; the w control volume i spans [(i-1/2)h, (i+1/2)h]
+        m.set(u=np.full((N, 4, N), U), w=wx)
+        Gw = m.tendencies()["w"][N // 2, 1, :]
+        exw = -U * (np.sin(k * (xlo + h)) - np.sin(k * xlo)) / h
+        e_wx.append(np.abs(Gw - exw).max())
+        # w(z) self-advection, interior faces; the w control volume k spans [zc_{k-1}, zc_k]
+        zc = -1.0 + (np.arange(N) + 0.5) * h
+        a = 0.3
+        wz = np.zeros((N + 1, 4, N))
+        wz[1:N] = (a * _avg_sin(k, zc[:-1], h))[:, None, None]
+        m.set(u=np.zeros((N, 4, N)), w=wz)
+        Gwz = m.tendencies()["w"][:, 2, 3]
+        F = (a * np.sin(k * zc)) ** 2
+        exz = -(F[1:] - F[:-1]) / h                # faces 1..N-1
+        e_wz.append(np.abs(Gwz[4:N - 3] - exz[3:N - 4]).max())
+    for errs, order in ((e_uz, 5), (e_wx, 5), (e_wz, 4)):
+        rates = [math.log(errs[i] / errs[i + 1]) / math.log(Ns[i + 1] / Ns[i]) for i in range(len(Ns) - 1)]
+        assert min(rates) > order - 0.7, (errs, rates, order)
+
+
+def test_diffusion_eigenmodes_y_z(oracle_mod):
+    """ScalarDiffusivity (Laplacian form) acting on exact discrete eigenvectors: a periodic sine in y,
+    a Neumann cosine in z for tracers and u, and a Dirichlet sine in z for w."""
+    N, nu, kap = 12, 0.07, 0.03
+    p = small_params(Nx=4, Ny=N, Nz=N, Lx=4.0, Ly=float(N), Lz=float(N), closure="scalar", nu=nu, kappa=kap,
+                     tracers=["b", "c"], weno_order=1)
+    m = oracle_mod.OracleModel(p)
+    y = np.arange(N) + 0.5
+    z = np.arange(N) + 0.5
+    sy = np.broadcast_to(np.sin(2 * np.pi * y / N)[None, :, None], (N, N, 4)).copy()
+    cz = np.broadcast_to(np.cos(np.pi * z / N)[:, None, None], (N, N, 4)).copy()
+    wz = np.zeros((N + 1, N, 4)); wz[:, :, :] = np.sin(np.pi * np.arange(N + 1) / N)[:, None, None]
+    zero = np.zeros((N, N, 4))
+    lam_y = -(2 * math.sin(math.pi / N)) ** 2
+    lam_z = -(2 * math.sin(math.pi / (2 * N))) ** 2
+    # tracer: y eigenmode (no velocity, so no advection)
+    m.set(u=zero, v=zero, w=np.zeros((N + 1, N, 4)), b=zero, c=sy)
+    np.testing.assert_allclose(m.tendencies()["c"], kap * lam_y * sy, atol=1e-15)
+    m.set(c=cz)
+    np.testing.assert_allclose(m.tendencies()["c"], kap * lam_z * cz, atol=1e-15)
+    # momentum: u(z) with weno_order=1 still advects only by a zero velocity here
+    m.set(c=zero, u=cz)
+    np.testing.assert_allclose(m.tendencies()["u"], nu * lam_z * cz, atol=1e-15)
+    m.set(u=zero, w=wz)
+    Gw = m.tendencies()["w"]
+    # w is advected by itself; remove that by comparing against the nonlinear part at half amplitude
+    m.set(w=0.5 * wz)
+    Gw_half = m.tendencies()["w"]
+    lin = 2 * (2 * Gw_half - 0.5 * Gw)        # G(a) = a L + a^2 Q  ->  L = 2(2 G(1/2) - G(1)/2)
+    np.testing.assert_allclose(lin[1:N], (nu * lam_z * wz)[1:N], atol=1e-13)
+
+
+@pytest.mark.parametrize("closure", ["smagorinsky", "amd"])
+def test_eddy_viscosity_stress_dissipates_energy(oracle_mod, closure):
+    """With nu_e >= 0 at every location, the stress-form closure only removes kinetic energy:
+    sum over velocity cells of V (u . G_closure) <= 0 (discrete summation by parts)."""
+    p = small_params(stretch=1.5, Nx=12, Ny=8, Nz=6, Lx=12.0, closure=closure)
+    st = inputs.random_state(p, seed=16, amp=0.5)
+    m = oracle_mod.OracleModel(p); m.set(**st); m.project(1.0)
+    st = {x: m.get(x) for x in ("u", "v", "w", "b")}
+    m0 = oracle_mod.OracleModel(dict(p, closure="none")); m0.set(**st)
+    G1, G0 = m.tendencies(), m0.tendencies()
+    zf = np.asarray(p["z_faces"]); dzc = np.diff(zf)[:, None, None]
+    zc = 0.5 * (zf[1:] + zf[:-1]); dzf = np.diff(zc)[:, None, None]
+    work = ((G1["u"] - G0["u"]) * st["u"] * dzc).sum() + ((G1["v"] - G0["v"]) * st["v"] * dzc).sum() \
+        + ((G1["w"] - G0["w"])[1:-1] * st["w"][1:-1] * dzf).sum()
+    assert work < 0.0
