@@ -599,3 +599,103 @@ def test_eddy_viscosity_stress_dissipates_energy(oracle_mod, closure):
     work = ((G1["u"] - G0["u"]) * st["u"] * dzc).sum() + ((G1["v"] - G0["v"]) * st["v"] * dzc).sum() \
         + ((G1["w"] - G0["w"])[1:-1] * st["w"][1:-1] * dzf).sum()
     assert work < 0.0
+
+
+# ----------------------------------------------------------------------------- grid symmetries
+def _sym_params(closure, **over):
+    p = small_params(Nx=10, Ny=10, Nz=8, Lx=10.0, Ly=10.0, Lz=8.0, closure=closure, nu=0.03, kappa=0.02,
+                     weno_order=over.pop("weno_order", 5), tracers=["b", "c"], **over)
+    return p
+
+
+def _tendencies(oracle_mod, p, st):
+    m = oracle_mod.OracleModel(p)
+    m.set(**st)
+    return m.tendencies()
+
+
+@pytest.mark.parametrize("closure", ["scalar", "smagorinsky", "amd"])
+@pytest.mark.parametrize("order", [5, 9])
+def test_transpose_xy_equivariance(oracle_mod, closure, order):
+    """Swapping x and y (u <-> v, all fields transposed) is a symmetry of the equations on a square
+    grid; it reverses orientation, so f -> -f.  Every tendency must transform the same way."""
+    p = _sym_params(closure, weno_order=order, f=0.7)
+    st = inputs.random_state(p, seed=21, amp=0.5)
+    T = lambda a: np.ascontiguousarray(a.transpose(0, 2, 1))
+    st2 = {"u": T(st["v"]), "v": T(st["u"]), "w": T(st["w"]), "b": T(st["b"]), "c": T(st["c"])}
+    G1 = _tendencies(oracle_mod, p, st)
+    G2 = _tendencies(oracle_mod, dict(p, f=-0.7), st2)
+    for a, b in (("u", "v"), ("v", "u"), ("w", "w"), ("b", "b"), ("c", "c")):
+        np.testing.assert_allclose(G2[a], T(G1[b]), rtol=0, atol=1e-12 * np.abs(G1[b]).max())
+
+
+@pytest.mark.parametrize("closure", ["scalar", "smagorinsky", "amd"])
+def test_reflection_x_equivariance(oracle_mod, closure):
+    """x -> -x maps face i to face -i (u changes sign) and centre i to centre N-1-i; f -> -f."""
+    p = _sym_params(closure, f=0.4)
+    N = p["Nx"]
+    st = inputs.random_state(p, seed=22, amp=0.5)
+    fi = (N - np.arange(N)) % N
+    ci = N - 1 - np.arange(N)
+    st2 = {"u": -st["u"][:, :, fi], "v": st["v"][:, :, ci], "w": st["w"][:, :, ci],
+           "b": st["b"][:, :, ci], "c": st["c"][:, :, ci]}
+    G1 = _tendencies(oracle_mod, p, st)
+    G2 = _tendencies(oracle_mod, dict(p, f=-0.4), {k: np.ascontiguousarray(v) for k, v in st2.items()})
+    np.testing.assert_allclose(G2["u"], -G1["u"][:, :, fi], atol=1e-12 * np.abs(G1["u"]).max())
+    for name in ("v", "w", "b", "c"):
+        np.testing.assert_allclose(G2[name], G1[name][:, :, ci], atol=1e-12 * np.abs(G1[name]).max())
+
+
+@pytest.mark.parametrize("closure", ["scalar", "smagorinsky", "amd"])
+def test_reflection_z_equivariance(oracle_mod, closure):
+    """On a uniform z-grid, z -> -z maps level k to Nz-1-k, face k to Nz-k, w and b change sign
+    (gravity points the other way relative to the grid) and top and bottom fluxes trade places
+    with opposite sign."""
+    p = _sym_params(closure, f=0.3, top_flux={"u": 0.02, "c": -0.01}, bottom_flux={"v": 0.03, "b": 0.01})
+    Nz = p["Nz"]
+    p2 = dict(p, top_flux={"v": -0.03, "b": 0.01}, bottom_flux={"u": -0.02, "c": 0.01})
+    st = inputs.random_state(p, seed=23, amp=0.5)
+    ck = Nz - 1 - np.arange(Nz)
+    fk = Nz - np.arange(Nz + 1)
+    st2 = {"u": st["u"][ck], "v": st["v"][ck], "w": -st["w"][fk], "b": -st["b"][ck], "c": st["c"][ck]}
+    G1 = _tendencies(oracle_mod, p, st)
+    G2 = _tendencies(oracle_mod, p2, {k: np.ascontiguousarray(v) for k, v in st2.items()})
+    for name, sgn, idx in (("u", 1, ck), ("v", 1, ck), ("w", -1, fk), ("b", -1, ck), ("c", 1, ck)):
+        np.testing.assert_allclose(G2[name], sgn * G1[name][idx], atol=1e-12 * np.abs(G1[name]).max())
+
+
+def test_uniform_velocity_exact_at_every_face(oracle_mod):
+    """A uniform velocity is reproduced exactly by every centered interpolation, including the
+    wall-reduced ones, so w(x) carried by uniform u has the exact finite-volume tendency at every
+    interior w face, next to the walls as well."""
+    N, U = 24, 0.8
+    p = small_params(Nx=N, Ny=4, Nz=8, Lx=1.0, Ly=4.0, Lz=8.0, weno_order=9)
+    m = oracle_mod.OracleModel(p)
+    h, k = 1.0 / N, 2 * np.pi
+    xlo = np.arange(N) * h - 0.5 * h
+    w = np.zeros((9, 4, N)); w[1:8] = _avg_sin(k, xlo, h)[None, None, :]
+    m.set(u=np.zeros((8, 4, N)), v=np.zeros((8, 4, N)), w=w, b=np.zeros((8, 4, N)))
+    G0 = m.tendencies()["w"]                       # w self-advection only
+    m.set(u=np.full((8, 4, N), U))
+    Gw = m.tendencies()["w"] - G0                  # the x-flux part, carried by u
+    exw = -U * (np.sin(k * (xlo + h)) - np.sin(k * xlo)) / h
+    err = np.abs(Gw[1:8, 2, :] - exw[None, :]).max()
+    ref = np.abs(Gw[4, 2, :] - exw).max()            # interior face: the pure WENO9 error
+    assert err <= 1.0000001 * ref and ref < 1e-6
+
+
+def test_buoyancy_interpolated_to_w_faces_second_order(oracle_mod):
+    """The buoyancy term of the w equation is b interpolated to the w face: for cell averages of a
+    smooth b(z), G_w (no flow) approaches b at the face at second order."""
+    errs, Ns = [], [8, 16, 32]
+    for N in Ns:
+        h = 1.0 / N
+        p = small_params(Nx=4, Ny=4, Nz=N, Lx=4.0, Ly=4.0, Lz=1.0)
+        m = oracle_mod.OracleModel(p)
+        zlo = -1.0 + np.arange(N) * h
+        b = np.broadcast_to((np.sin(3 * (zlo + h)) - np.sin(3 * zlo))[:, None, None] / (3 * h), (N, 4, 4)).copy()
+        m.set(u=np.zeros((N, 4, 4)), v=np.zeros((N, 4, 4)), w=np.zeros((N + 1, 4, 4)), b=b)
+        Gw = m.tendencies()["w"][1:N, 1, 1]
+        errs.append(np.abs(Gw - np.cos(3 * (-1.0 + np.arange(1, N) * h))).max())
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(len(Ns) - 1)]
+    assert min(rates) > 1.8, (errs, rates)
