@@ -1,0 +1,185 @@
+/*
+ * ocn.h -- C ABI of the GB300 (sm_103a) nonhydrostatic Boussinesq RK3 substep.
+ *
+ * The library advances the incompressible Boussinesq equations on a staggered
+ * C-grid (arXiv 2502.14148):
+ *   momentum   Sec. 3.1.1, Eq. nonhydrotatic-momentum-equations, in flux form
+ *              (Eq. flux-form-advection), without Stokes drift, background
+ *              fields or user forcing;
+ *   tracers    Sec. 3.1.2, Eq. nonhydrostatic-tracer-equation (advection +
+ *              closure + boundary fluxes);
+ *   time       low-storage RK3, Appendix A.1 Eq. rk3;
+ *   pressure   fractional step, Appendix A.2, Eqs. predictor-velocity,
+ *              pressure-correction and pressure-poisson, solved by an FFT in
+ *              x and y and a tridiagonal solve in z (the eigenfunction
+ *              expansion of the discrete Laplacian described there);
+ *   space      finite volumes, Appendix B: Eq. flux-divergence, WENO
+ *              reconstruction (Eq. fifth-order-weno generalised to order
+ *              2r-1 with WENO-Z weights), centered advecting velocities for
+ *              momentum (Sec. B.2.1).
+ *
+ * Grid: x and y periodic and uniform, z bounded (impenetrable, free-slip,
+ * no-flux walls unless a boundary flux is given) with arbitrary ascending face
+ * heights.  Face index i is left of cell index i (Appendix B.1).
+ *
+ * Layout of every field in device or host memory: x fastest, then y, then z.
+ *   u (Face,Center,Center), v (Center,Face,Center), tracers, p: [Nz][Ny][Nx]
+ *   w (Center,Center,Face): [Nz+1][Ny][Nx]; w[0] and w[Nz] (the walls) are 0.
+ * Element type: float when the model precision is 32, double when it is 64.
+ *
+ * Ownership: the library never allocates device memory.  The caller obtains
+ * the size of the model's device arena with ocn_model_arena_bytes(), allocates
+ * it (for example as a PyTorch tensor), and binds it with
+ * ocn_model_bind_arena() before any other call that touches fields.  The
+ * arena must stay valid until ocn_model_destroy(); the library never frees it.
+ * Host buffers passed to ocn_set_field/ocn_get_field are read or written
+ * during the call only (pinned host memory gives the fastest copies).
+ *
+ * Streams: all work of a model is issued on the cudaStream_t given at
+ * creation (NULL selects the legacy default stream; graph capture of the time
+ * step then stays off).  Calls return after enqueueing, except
+ * ocn_get_field to host memory and ocn_diagnostics, which synchronise the
+ * stream.
+ *
+ * Errors: every call returns an ocn_status.  OCN_OK is 0; failures are
+ * negative.  ocn_last_error() returns a thread-local description of the last
+ * failure on the calling thread.  Nothing aborts, traps or exits.
+ */
+#ifndef OCN_H
+#define OCN_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OCN_ABI_VERSION 1
+#define OCN_MAX_TRACERS 4
+
+typedef enum {
+  OCN_OK = 0,
+  OCN_ERR_ARG = -1,          /* invalid argument (null pointer, size mismatch, unknown id) */
+  OCN_ERR_CUDA = -2,         /* a CUDA runtime call or kernel launch failed */
+  OCN_ERR_OOM = -3,          /* host allocation failed */
+  OCN_ERR_NONFINITE = -4,    /* diagnostics found a NaN or Inf */
+  OCN_ERR_CFL = -5,          /* diagnostics found an advective CFL number above 1 */
+  OCN_ERR_TIMEOUT = -6,      /* a bounded device-side wait gave up */
+  OCN_ERR_UNSUPPORTED = -7,  /* valid but not built (e.g. a WENO order without a kernel) */
+  OCN_ERR_STATE = -8         /* call order violated (e.g. arena not bound) */
+} ocn_status;
+
+enum { OCN_CLOSURE_NONE = 0, OCN_CLOSURE_SCALAR = 1, OCN_CLOSURE_SMAGORINSKY = 2, OCN_CLOSURE_AMD = 3 };
+enum { OCN_EOS_BUOYANCY_TRACER = 0, OCN_EOS_LINEAR_TS = 1 };
+
+/* Field ids for ocn_set_field / ocn_get_field. */
+enum {
+  OCN_FIELD_U = 0, OCN_FIELD_V = 1, OCN_FIELD_W = 2,
+  OCN_FIELD_TRACER0 = 3,     /* tracer n is OCN_FIELD_TRACER0 + n */
+  OCN_FIELD_P = 10,          /* kinematic pressure of the last projection, zero volume mean */
+  OCN_FIELD_G = 20,          /* tendency G of field f is OCN_FIELD_G + f (G^{m-1} after a step) */
+  OCN_FIELD_NU_E = 30        /* eddy viscosity at cell centres (Smagorinsky-Lilly, AMD) */
+};
+
+/* Grid (paper listing "RectilinearGrid(...)"): x in [0,Lx), y in [0,Ly) periodic,
+ * uniform; z bounded with Nz+1 ascending face heights. */
+typedef struct {
+  int Nx, Ny, Nz;            /* Nx, Ny even and of the form 2^a 3^b, >= 4; Nz >= 1 */
+  double Lx, Ly;             /* > 0 */
+  const double* z_faces;     /* Nz+1 strictly ascending heights; copied by ocn_grid_create */
+} ocn_grid_desc;
+
+/* Model (paper listing "NonhydrostaticModel(; grid, advection, closure, coriolis,
+ * buoyancy, tracers, boundary_conditions)"). */
+typedef struct {
+  int precision;             /* 32 (FP32 state and tendencies) or 64 (FP64) */
+  int weno_order;            /* 5 or 9; momentum advecting velocities use centered order weno_order-1 */
+  int closure;               /* OCN_CLOSURE_* */
+  double nu, kappa;          /* ScalarDiffusivity: constant viscosity and tracer diffusivity */
+  double Cs, Cb, Pr;         /* Smagorinsky-Lilly: nu_e = (Cs D)^2 |S| sqrt(max(0, 1 - Cb N^2/(Pr |S|^2))), kappa_e = nu_e/Pr */
+  double C_amd;              /* AMD Poincare constant (1/12 for second-order differences) */
+  double f;                  /* FPlane Coriolis parameter */
+  int n_tracers;             /* 1..OCN_MAX_TRACERS */
+  int eos;                   /* OCN_EOS_BUOYANCY_TRACER: tracer 0 is b.  OCN_EOS_LINEAR_TS: tracers 0,1 are T,S */
+  double g, alpha, beta, T0, S0;   /* linear EOS: b = g (alpha (T - T0) - beta (S - S0)) */
+  double top_flux[2 + OCN_MAX_TRACERS];     /* upward flux of u, v, tracer 0.. through the top face */
+  double bottom_flux[2 + OCN_MAX_TRACERS];  /* upward flux of u, v, tracer 0.. through the bottom face */
+  int fp64_pivots;           /* tridiagonal pivots in FP64: 1 yes, 0 no, -1 when the z-grid is stretched */
+} ocn_model_desc;
+
+typedef struct ocn_grid ocn_grid;
+typedef struct ocn_model ocn_model;
+
+/* ABI version the library was built with (OCN_ABI_VERSION). */
+int ocn_abi_version(void);
+
+/* Thread-local text of the last failure ("" if none). Owned by the library. */
+const char* ocn_last_error(void);
+
+/* Create a grid from *desc.  *out receives a new handle (free with ocn_grid_destroy).
+ * Errors: OCN_ERR_ARG for a null pointer, a size that is not even 2^a 3^b >= 4,
+ * non-positive lengths or non-ascending faces; OCN_ERR_OOM. */
+ocn_status ocn_grid_create(const ocn_grid_desc* desc, ocn_grid** out);
+void ocn_grid_destroy(ocn_grid* grid);
+
+/* Create a model on a grid (the grid must outlive the model).  stream is a
+ * cudaStream_t (NULL: legacy default stream).  Selects the CUDA device that is
+ * current on the calling thread.
+ * Errors: OCN_ERR_ARG (bad precision, tracer count, closure, eos),
+ * OCN_ERR_UNSUPPORTED (weno_order other than 5 or 9), OCN_ERR_CUDA, OCN_ERR_OOM. */
+ocn_status ocn_model_create(const ocn_grid* grid, const ocn_model_desc* desc, void* stream, ocn_model** out);
+void ocn_model_destroy(ocn_model* model);
+
+/* Bytes of device memory the model needs (state, tendencies, pressure,
+ * diffusivities, spectral work space, metrics). */
+ocn_status ocn_model_arena_bytes(const ocn_model* model, size_t* bytes);
+
+/* Bind caller-owned device memory of at least ocn_model_arena_bytes() bytes,
+ * 256-byte aligned.  Uploads the grid metrics and clears all fields to 0.
+ * Errors: OCN_ERR_ARG (null, too small, misaligned), OCN_ERR_CUDA. */
+ocn_status ocn_model_bind_arena(ocn_model* model, void* device_ptr, size_t bytes);
+
+/* Copy a field in (set) or out (get).  nbytes must equal the field's size in
+ * the model precision.  src/dst is device memory when *_is_device != 0, host
+ * memory otherwise.  Setting w forces w = 0 on the wall faces.  Setting a
+ * field does not project the velocity (call ocn_project).
+ * Errors: OCN_ERR_ARG, OCN_ERR_STATE (no arena), OCN_ERR_CUDA. */
+ocn_status ocn_set_field(ocn_model* model, int field, const void* src, size_t nbytes, int src_is_device);
+ocn_status ocn_get_field(ocn_model* model, int field, void* dst, size_t nbytes, int dst_is_device);
+
+/* Enforce incompressibility of the current velocity: solve the discrete
+ * Poisson problem lap p = div u (Eq. pressure-poisson with dt = 1) and set
+ * u -= grad p (Eq. pressure-correction).  Errors: OCN_ERR_STATE, OCN_ERR_CUDA. */
+ocn_status ocn_project(ocn_model* model);
+
+/* Advance nsteps full RK3 steps of size dt (three substages each; Appendix A.1
+ * Eq. rk3 and Appendix A.2).  Each substage: eddy diffusivities, fused
+ * tendency + RK update, then the pressure projection with step
+ * (gamma_m - zeta_m) dt.  Errors: OCN_ERR_ARG (nsteps < 0, dt not finite),
+ * OCN_ERR_STATE, OCN_ERR_CUDA. */
+ocn_status ocn_time_step(ocn_model* model, double dt, int nsteps);
+
+/* Evaluate the tendencies G of every prognostic field at the current state
+ * (no stepping; readable as OCN_FIELD_G + f).  Errors: OCN_ERR_STATE, OCN_ERR_CUDA. */
+ocn_status ocn_compute_tendencies(ocn_model* model);
+
+/* Diagnostics in FP64 (synchronises the stream).  out[0..n_tracers-1] = sum V c_n;
+ * then sum V u, sum V v, sum V w, max |div u|, dt * max(|u|/dx, |v|/dy, |w|/dz),
+ * count of non-finite values: nout must be >= n_tracers + 6.
+ * Returns OCN_ERR_NONFINITE if any value is not finite and OCN_ERR_CFL if the
+ * CFL number exceeds 1 (the values are written in both cases). */
+ocn_status ocn_diagnostics(ocn_model* model, double dt, double* out, int nout);
+
+/* Options.  OCN_OPT_GRAPHS: 1 (default) replays each time step from a CUDA
+ * graph captured on first use per dt; 0 launches kernels directly.
+ * OCN_OPT_SYNC_CHECK: 1 synchronises and checks for errors after every kernel. */
+enum { OCN_OPT_GRAPHS = 1, OCN_OPT_SYNC_CHECK = 2 };
+ocn_status ocn_set_option(ocn_model* model, int option, long long value);
+
+/* Number of kernel launches the last ocn_time_step issued per RK3 step. */
+ocn_status ocn_launches_per_step(const ocn_model* model, int* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OCN_H */

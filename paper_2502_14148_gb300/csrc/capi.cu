@@ -1,0 +1,612 @@
+// C ABI (include/ocn.h): grid and model objects, the device arena layout, the
+// RK3 substage sequence and its CUDA-graph replay.
+//
+// One RK3 substage m (Appendix A.1 Eq. rk3, Appendix A.2):
+//   1. eddy diffusivities (Smagorinsky-Lilly / AMD)            k_closure
+//   2. tendencies, u~ = u + dt(gamma G^m - zeta G^{m-1}),
+//      tracers c^{m+1} likewise, G^{m-1} <- G^m              k_tendency
+//   3. projection with the stage step (gamma-zeta) dt        k_div_fftx ... k_correct
+// The state is double buffered (the tendency stencil reads neighbours of the
+// old state while the new one is written); every substage swaps buffers.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ocn_internal.cuh"
+
+using namespace ocn;
+
+namespace {
+
+thread_local std::string g_err;
+
+ocn_status fail(ocn_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+ocn_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(OCN_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bool is_2a3b(int n) {
+  if (n < 1) return false;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  return n == 1;
+}
+
+FftPlan make_plan(int n) {
+  FftPlan p;
+  memset(&p, 0, sizeof(p));
+  p.n = n;
+  int m = n;
+  while (m % 8 == 0 && p.npass < kMaxFftPasses) { p.radix[p.npass++] = 8; m /= 8; }
+  while (m % 4 == 0 && p.npass < kMaxFftPasses) { p.radix[p.npass++] = 4; m /= 4; }
+  while (m % 2 == 0 && p.npass < kMaxFftPasses) { p.radix[p.npass++] = 2; m /= 2; }
+  while (m % 3 == 0 && p.npass < kMaxFftPasses) { p.radix[p.npass++] = 3; m /= 3; }
+  return p;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int now = -1;
+    if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+  }
+};
+
+std::mutex g_tab_mu;
+bool g_tab_ready = false;
+WenoTables<double> g_tab;
+uint64_t g_tab_devices = 0;
+
+cudaError_t ensure_tables(int dev) {
+  std::lock_guard<std::mutex> lk(g_tab_mu);
+  if (!g_tab_ready) { derive_weno_tables(&g_tab); g_tab_ready = true; }
+  if (dev < 64 && (g_tab_devices >> dev) & 1ull) return cudaSuccess;
+  cudaError_t e = upload_weno_tables(g_tab);
+  if (e == cudaSuccess && dev < 64) g_tab_devices |= (1ull << dev);
+  return e;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct ocn_grid {
+  int Nx, Ny, Nz;
+  double Lx, Ly;
+  std::vector<double> zf, zc, dzc, dzf;
+  bool stretched;
+};
+
+struct ocn_model {
+  const ocn_grid* g = nullptr;
+  ocn_model_desc d;
+  cudaStream_t stream = nullptr;
+  int dev = 0;
+  int R = 3;
+  int es = 4;                       // element size
+  int nf = 4;                       // prognostic fields: u, v, w, tracers
+  bool fp64_piv = false;
+  // arena layout (byte offsets)
+  size_t bytes = 0;
+  size_t off_state[2][3 + OCN_MAX_TRACERS];
+  size_t off_G[3 + OCN_MAX_TRACERS];
+  size_t off_p = 0, off_nu = 0, off_kap[OCN_MAX_TRACERS], off_spec = 0, off_cpiv = 0;
+  size_t off_dzc = 0, off_rdzc = 0, off_dzf = 0, off_rdzf = 0, off_lamx = 0, off_lamy = 0, off_twx = 0, off_twy = 0;
+  size_t off_partial = 0, off_diag = 0;
+  char* arena = nullptr;
+  int cur = 0;
+  bool graphs = true, sync_check = false;
+  std::map<std::pair<uint64_t, int>, cudaGraphExec_t> graph_cache;
+  int launches_per_step = 0;
+  FftPlan px, py;
+  // Linear-EOS tracers are stored as anomalies about (T0, S0): the arithmetic is
+  // unchanged (the EOS only sees differences, and the advection of a constant
+  // by a divergence-free velocity vanishes) while FP32 keeps ~20x more digits.
+  double cref[OCN_MAX_TRACERS] = {0, 0, 0, 0};
+};
+
+namespace {
+
+size_t field_elems(const ocn_model* m, int f) {
+  size_t plane = (size_t)m->g->Nx * m->g->Ny;
+  return plane * (size_t)(f == OCN_FIELD_W ? m->g->Nz + 1 : m->g->Nz);
+}
+
+template <typename T>
+T* at(const ocn_model* m, size_t off) { return reinterpret_cast<T*>(m->arena + off); }
+
+template <typename T>
+StatePtrs<T> state_ptrs(const ocn_model* m, int which) {
+  StatePtrs<T> s;
+  s.u = at<T>(m, m->off_state[which][0]);
+  s.v = at<T>(m, m->off_state[which][1]);
+  s.w = at<T>(m, m->off_state[which][2]);
+  for (int t = 0; t < kMaxTracers; ++t) s.c[t] = (t < m->d.n_tracers) ? at<T>(m, m->off_state[which][3 + t]) : nullptr;
+  return s;
+}
+
+template <typename T>
+StatePtrs<T> g_ptrs(const ocn_model* m) {
+  StatePtrs<T> s;
+  s.u = at<T>(m, m->off_G[0]);
+  s.v = at<T>(m, m->off_G[1]);
+  s.w = at<T>(m, m->off_G[2]);
+  for (int t = 0; t < kMaxTracers; ++t) s.c[t] = (t < m->d.n_tracers) ? at<T>(m, m->off_G[3 + t]) : nullptr;
+  return s;
+}
+
+void layout(ocn_model* m) {
+  const ocn_grid* g = m->g;
+  const size_t plane = (size_t)g->Nx * g->Ny;
+  const size_t Nc = plane * g->Nz, Nw = plane * (g->Nz + 1);
+  const size_t es = (size_t)m->es;
+  size_t o = 0;
+  auto take = [&](size_t nbytes) { size_t at_ = o; o = align256(o + nbytes); return at_; };
+  for (int b = 0; b < 2; ++b)
+    for (int f = 0; f < m->nf; ++f) m->off_state[b][f] = take(es * (f == 2 ? Nw : Nc));
+  for (int f = 0; f < m->nf; ++f) m->off_G[f] = take(es * (f == 2 ? Nw : Nc));
+  m->off_p = take(es * Nc);
+  const bool stress = m->d.closure == OCN_CLOSURE_SMAGORINSKY || m->d.closure == OCN_CLOSURE_AMD;
+  m->off_nu = stress ? take(es * Nc) : 0;
+  for (int t = 0; t < OCN_MAX_TRACERS; ++t)
+    m->off_kap[t] = (m->d.closure == OCN_CLOSURE_AMD && t < m->d.n_tracers) ? take(es * Nc) : 0;
+  const size_t S = (size_t)(g->Nx / 2 + 1) * g->Ny * g->Nz;
+  m->off_spec = take(2 * es * S);
+  m->off_cpiv = take(es * S);
+  m->off_dzc = take(es * g->Nz);
+  m->off_rdzc = take(es * g->Nz);
+  m->off_dzf = take(es * (g->Nz + 1));
+  m->off_rdzf = take(es * (g->Nz + 1));
+  m->off_lamx = take(es * (g->Nx / 2 + 1));
+  m->off_lamy = take(es * g->Ny);
+  m->off_twx = take(2 * es * g->Nx);
+  m->off_twy = take(2 * es * g->Ny);
+  m->off_partial = take(sizeof(double) * (size_t)diag_blocks() * (OCN_MAX_TRACERS + 6));
+  m->off_diag = take(sizeof(double) * 16);
+  m->bytes = o;
+}
+
+template <typename T>
+std::vector<char> metrics_blob(const ocn_model* m) {
+  // host images of the metric tables, placed at their arena offsets relative to off_dzc
+  const ocn_grid* g = m->g;
+  std::vector<char> blob(m->off_twy + 2 * sizeof(T) * g->Ny - m->off_dzc, 0);
+  auto put = [&](size_t off, size_t idx, T v) { memcpy(blob.data() + (off - m->off_dzc) + idx * sizeof(T), &v, sizeof(T)); };
+  for (int k = 0; k < g->Nz; ++k) { put(m->off_dzc, k, (T)g->dzc[k]); put(m->off_rdzc, k, (T)(1.0 / g->dzc[k])); }
+  for (int k = 0; k <= g->Nz; ++k) {
+    put(m->off_dzf, k, (T)g->dzf[k]);
+    put(m->off_rdzf, k, (T)((k >= 1 && k < g->Nz) ? 1.0 / g->dzf[k] : 0.0));
+  }
+  const double dx = g->Lx / g->Nx, dy = g->Ly / g->Ny;
+  for (int kx = 0; kx <= g->Nx / 2; ++kx) { double s = 2.0 * sin(M_PI * kx / g->Nx) / dx; put(m->off_lamx, kx, (T)(-s * s)); }
+  for (int ky = 0; ky < g->Ny; ++ky) { double s = 2.0 * sin(M_PI * ky / g->Ny) / dy; put(m->off_lamy, ky, (T)(-s * s)); }
+  for (int t = 0; t < g->Nx; ++t) {
+    double th = -2.0 * M_PI * (double)t / g->Nx;
+    put(m->off_twx, 2 * t, (T)cos(th)); put(m->off_twx, 2 * t + 1, (T)sin(th));
+  }
+  for (int t = 0; t < g->Ny; ++t) {
+    double th = -2.0 * M_PI * (double)t / g->Ny;
+    put(m->off_twy, 2 * t, (T)cos(th)); put(m->off_twy, 2 * t + 1, (T)sin(th));
+  }
+  return blob;
+}
+
+template <typename T>
+PoissonArgs<T> poisson_args(const ocn_model* m, int which, double dts) {
+  const ocn_grid* g = m->g;
+  PoissonArgs<T> a;
+  memset(&a, 0, sizeof(a));
+  StatePtrs<T> s = state_ptrs<T>(m, which);
+  a.u = s.u; a.v = s.v; a.w = s.w;
+  a.p = at<T>(m, m->off_p);
+  a.spec = at<T>(m, m->off_spec);
+  a.cpiv = at<T>(m, m->off_cpiv);
+  a.rdzc = at<T>(m, m->off_rdzc); a.rdzf = at<T>(m, m->off_rdzf); a.dzc = at<T>(m, m->off_dzc);
+  a.lamx = at<T>(m, m->off_lamx); a.lamy = at<T>(m, m->off_lamy);
+  a.twx = at<T>(m, m->off_twx); a.twy = at<T>(m, m->off_twy);
+  a.Nx = g->Nx; a.Ny = g->Ny; a.Nz = g->Nz; a.Mx = g->Nx / 2;
+  a.rdx = (T)(g->Nx / g->Lx); a.rdy = (T)(g->Ny / g->Ly);
+  a.inv_dt = (T)(1.0 / dts); a.dt = (T)dts;
+  a.scale = (T)(1.0 / ((double)(g->Nx / 2) * g->Ny));
+  a.Htot = (T)(g->zf[g->Nz] - g->zf[0]);
+  a.fp64_pivots = m->fp64_piv ? 1 : 0;
+  a.px = m->px; a.py = m->py;
+  return a;
+}
+
+template <typename T>
+cudaError_t enqueue_closure(ocn_model* m, int which) {
+  const ocn_grid* g = m->g;
+  if (!(m->d.closure == OCN_CLOSURE_SMAGORINSKY || m->d.closure == OCN_CLOSURE_AMD)) return cudaSuccess;
+  ClosureArgs<T> c;
+  memset(&c, 0, sizeof(c));
+  c.cur = state_ptrs<T>(m, which);
+  c.nu = at<T>(m, m->off_nu);
+  for (int t = 0; t < kMaxTracers; ++t) c.kap[t] = m->off_kap[t] ? at<T>(m, m->off_kap[t]) : nullptr;
+  c.dzc = at<T>(m, m->off_dzc); c.rdzc = at<T>(m, m->off_rdzc); c.rdzf = at<T>(m, m->off_rdzf);
+  c.Nx = g->Nx; c.Ny = g->Ny; c.Nz = g->Nz; c.nt = m->d.n_tracers;
+  c.dx = (T)(g->Lx / g->Nx); c.dy = (T)(g->Ly / g->Ny); c.rdx = (T)(g->Nx / g->Lx); c.rdy = (T)(g->Ny / g->Ly);
+  c.closure = m->d.closure;
+  c.Cs = (T)m->d.Cs; c.Cb = (T)m->d.Cb; c.inv_Pr = (T)(1.0 / m->d.Pr); c.C_amd = (T)m->d.C_amd;
+  c.eos = m->d.eos;
+  c.g_alpha = (T)(m->d.g * m->d.alpha); c.g_beta = (T)(m->d.g * m->d.beta);
+  c.T0 = (T)(m->d.T0 - m->cref[0]); c.S0 = (T)(m->d.S0 - m->cref[1]);
+  return launch_closure<T>(c, m->stream);
+}
+
+template <typename T>
+cudaError_t enqueue_tendency(ocn_model* m, int which, double dt_gamma, double dt_zeta, int mode) {
+  const ocn_grid* g = m->g;
+  TendencyArgs<T> a;
+  memset(&a, 0, sizeof(a));
+  a.cur = state_ptrs<T>(m, which);
+  a.nxt = state_ptrs<T>(m, 1 - which);
+  a.G = g_ptrs<T>(m);
+  a.nu = m->off_nu ? at<T>(m, m->off_nu) : nullptr;
+  for (int t = 0; t < kMaxTracers; ++t) a.kap[t] = m->off_kap[t] ? at<T>(m, m->off_kap[t]) : nullptr;
+  a.rdzc = at<T>(m, m->off_rdzc); a.rdzf = at<T>(m, m->off_rdzf);
+  a.Nx = g->Nx; a.Ny = g->Ny; a.Nz = g->Nz; a.nt = m->d.n_tracers;
+  a.rdx = (T)(g->Nx / g->Lx); a.rdy = (T)(g->Ny / g->Ly);
+  a.closure = m->d.closure;
+  a.nu0 = (T)m->d.nu; a.kappa0 = (T)m->d.kappa; a.inv_Pr = (T)(1.0 / m->d.Pr);
+  a.f = (T)m->d.f;
+  a.eos = m->d.eos;
+  a.g_alpha = (T)(m->d.g * m->d.alpha); a.g_beta = (T)(m->d.g * m->d.beta);
+  a.T0 = (T)(m->d.T0 - m->cref[0]); a.S0 = (T)(m->d.S0 - m->cref[1]);
+  for (int n = 0; n < 2 + kMaxTracers; ++n) { a.top[n] = (T)m->d.top_flux[n]; a.bot[n] = (T)m->d.bottom_flux[n]; }
+  a.dt_gamma = (T)dt_gamma; a.dt_zeta = (T)dt_zeta;
+  a.mode = mode;
+  return launch_tendency<T>(a, m->R, m->stream);
+}
+
+cudaError_t check_sync(ocn_model* m, cudaError_t e) {
+  if (e != cudaSuccess || !m->sync_check) return e;
+  return cudaStreamSynchronize(m->stream);
+}
+
+// Enqueue one full RK3 step starting from buffer `which`; returns the final buffer.
+template <typename T>
+cudaError_t enqueue_step(ocn_model* m, double dt, int* which, int* nlaunch) {
+  static const double gam[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
+  static const double zet[3] = {0.0, 17.0 / 60.0, 5.0 / 12.0};
+  int n = 0;
+  for (int st = 0; st < 3; ++st) {
+    cudaError_t e = check_sync(m, enqueue_closure<T>(m, *which));
+    if (e != cudaSuccess) return e;
+    if (m->off_nu) ++n;
+    e = check_sync(m, enqueue_tendency<T>(m, *which, gam[st] * dt, zet[st] * dt, 0));
+    if (e != cudaSuccess) return e;
+    ++n;
+    int np = 0;
+    e = check_sync(m, launch_projection<T>(poisson_args<T>(m, 1 - *which, (gam[st] - zet[st]) * dt), m->stream, &np));
+    if (e != cudaSuccess) return e;
+    n += np;
+    *which = 1 - *which;
+  }
+  if (nlaunch) *nlaunch = n;
+  return cudaSuccess;
+}
+
+template <typename T>
+ocn_status time_step_t(ocn_model* m, double dt, int nsteps) {
+  const bool use_graph = m->graphs && m->stream != nullptr && !m->sync_check;
+  for (int s = 0; s < nsteps; ++s) {
+    if (!use_graph) {
+      int w = m->cur, nl = 0;
+      cudaError_t e = enqueue_step<T>(m, dt, &w, &nl);
+      if (e != cudaSuccess) return cuda_fail(e, "time step launch");
+      m->cur = w;
+      m->launches_per_step = nl;
+      continue;
+    }
+    uint64_t key;
+    memcpy(&key, &dt, sizeof(key));
+    auto it = m->graph_cache.find({key, m->cur});
+    cudaGraphExec_t exec = nullptr;
+    int w = m->cur;
+    if (it == m->graph_cache.end()) {
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+      int nl = 0;
+      cudaError_t el = enqueue_step<T>(m, dt, &w, &nl);
+      e = cudaStreamEndCapture(m->stream, &graph);
+      if (el != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(el, "capture step"); }
+      if (e != cudaSuccess) return cuda_fail(e, "end capture");
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+      m->graph_cache[{key, m->cur}] = exec;
+      m->launches_per_step = nl;
+    } else {
+      exec = it->second;
+      w = (m->cur + 3) & 1;
+    }
+    cudaError_t e = cudaGraphLaunch(exec, m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    m->cur = w;
+  }
+  return OCN_OK;
+}
+
+void drop_graphs(ocn_model* m) {
+  for (auto& kv : m->graph_cache) cudaGraphExecDestroy(kv.second);
+  m->graph_cache.clear();
+}
+
+bool field_valid(const ocn_model* m, int field) {
+  if (field == OCN_FIELD_U || field == OCN_FIELD_V || field == OCN_FIELD_W || field == OCN_FIELD_P) return true;
+  if (field >= OCN_FIELD_TRACER0 && field < OCN_FIELD_TRACER0 + m->d.n_tracers) return true;
+  if (field >= OCN_FIELD_G && field < OCN_FIELD_G + m->nf) return true;
+  if (field == OCN_FIELD_NU_E && m->off_nu) return true;
+  return false;
+}
+
+char* field_ptr(const ocn_model* m, int field, size_t* elems) {
+  if (field >= OCN_FIELD_G && field < OCN_FIELD_G + m->nf) {
+    *elems = field_elems(m, field - OCN_FIELD_G);
+    return m->arena + m->off_G[field - OCN_FIELD_G];
+  }
+  if (field == OCN_FIELD_P) { *elems = field_elems(m, OCN_FIELD_U); return m->arena + m->off_p; }
+  if (field == OCN_FIELD_NU_E) { *elems = field_elems(m, OCN_FIELD_U); return m->arena + m->off_nu; }
+  *elems = field_elems(m, field);
+  return m->arena + m->off_state[m->cur][field];
+}
+
+}  // namespace
+
+extern "C" {
+
+int ocn_abi_version(void) { return OCN_ABI_VERSION; }
+
+const char* ocn_last_error(void) { return g_err.c_str(); }
+
+ocn_status ocn_grid_create(const ocn_grid_desc* desc, ocn_grid** out) {
+  if (!desc || !out) return fail(OCN_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (desc->Nx < 4 || desc->Ny < 4 || (desc->Nx % 2) || (desc->Ny % 2) || !is_2a3b(desc->Nx) || !is_2a3b(desc->Ny))
+    return fail(OCN_ERR_ARG, "Nx and Ny must be even, >= 4 and of the form 2^a 3^b");
+  if (desc->Nz < 1) return fail(OCN_ERR_ARG, "Nz must be >= 1");
+  if (!(desc->Lx > 0) || !(desc->Ly > 0)) return fail(OCN_ERR_ARG, "Lx and Ly must be positive");
+  if (!desc->z_faces) return fail(OCN_ERR_ARG, "z_faces is null");
+  for (int k = 0; k < desc->Nz; ++k)
+    if (!(desc->z_faces[k + 1] > desc->z_faces[k])) return fail(OCN_ERR_ARG, "z_faces must be strictly ascending");
+  ocn_grid* g = new (std::nothrow) ocn_grid;
+  if (!g) return fail(OCN_ERR_OOM, "grid allocation");
+  g->Nx = desc->Nx; g->Ny = desc->Ny; g->Nz = desc->Nz; g->Lx = desc->Lx; g->Ly = desc->Ly;
+  g->zf.assign(desc->z_faces, desc->z_faces + desc->Nz + 1);
+  g->zc.resize(g->Nz); g->dzc.resize(g->Nz); g->dzf.assign(g->Nz + 1, 0.0);
+  for (int k = 0; k < g->Nz; ++k) { g->zc[k] = 0.5 * (g->zf[k] + g->zf[k + 1]); g->dzc[k] = g->zf[k + 1] - g->zf[k]; }
+  for (int k = 1; k < g->Nz; ++k) g->dzf[k] = g->zc[k] - g->zc[k - 1];
+  g->dzf[0] = g->dzc[0]; g->dzf[g->Nz] = g->dzc[g->Nz - 1];
+  g->stretched = false;
+  for (int k = 1; k < g->Nz; ++k)
+    if (fabs(g->dzc[k] - g->dzc[0]) > 1e-12 * fabs(g->dzc[0])) g->stretched = true;
+  *out = g;
+  return OCN_OK;
+}
+
+void ocn_grid_destroy(ocn_grid* grid) { delete grid; }
+
+ocn_status ocn_model_create(const ocn_grid* grid, const ocn_model_desc* desc, void* stream, ocn_model** out) {
+  if (!grid || !desc || !out) return fail(OCN_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (desc->precision != 32 && desc->precision != 64) return fail(OCN_ERR_ARG, "precision must be 32 or 64");
+  if (desc->n_tracers < 1 || desc->n_tracers > OCN_MAX_TRACERS) return fail(OCN_ERR_ARG, "n_tracers must be 1..4");
+  if (desc->closure < OCN_CLOSURE_NONE || desc->closure > OCN_CLOSURE_AMD) return fail(OCN_ERR_ARG, "unknown closure");
+  if (desc->eos != OCN_EOS_BUOYANCY_TRACER && desc->eos != OCN_EOS_LINEAR_TS) return fail(OCN_ERR_ARG, "unknown eos");
+  if (desc->eos == OCN_EOS_LINEAR_TS && desc->n_tracers < 2) return fail(OCN_ERR_ARG, "linear T,S EOS needs 2 tracers");
+  if (desc->closure == OCN_CLOSURE_SMAGORINSKY && !(desc->Pr > 0)) return fail(OCN_ERR_ARG, "Pr must be positive");
+  if (desc->weno_order != 5 && desc->weno_order != 9) return fail(OCN_ERR_UNSUPPORTED, "weno_order must be 5 or 9");
+  if (desc->n_tracers > 2) return fail(OCN_ERR_UNSUPPORTED, "the CUDA tendency kernel is built for 1 or 2 tracers");
+  ocn_model* m = new (std::nothrow) ocn_model;
+  if (!m) return fail(OCN_ERR_OOM, "model allocation");
+  m->g = grid;
+  m->d = *desc;
+  m->stream = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaGetDevice(&m->dev);
+  if (e != cudaSuccess) { delete m; return cuda_fail(e, "cudaGetDevice"); }
+  m->R = (desc->weno_order + 1) / 2;
+  m->es = desc->precision / 8;
+  m->nf = 3 + desc->n_tracers;
+  m->fp64_piv = desc->fp64_pivots > 0 || (desc->fp64_pivots < 0 && grid->stretched);
+  if (desc->eos == OCN_EOS_LINEAR_TS) { m->cref[0] = desc->T0; m->cref[1] = desc->S0; }
+  m->px = make_plan(grid->Nx / 2);
+  m->py = make_plan(grid->Ny);
+  layout(m);
+  *out = m;
+  return OCN_OK;
+}
+
+void ocn_model_destroy(ocn_model* model) {
+  if (!model) return;
+  {
+    DeviceGuard dg(model->dev);
+    drop_graphs(model);
+  }
+  delete model;
+}
+
+ocn_status ocn_model_arena_bytes(const ocn_model* model, size_t* bytes) {
+  if (!model || !bytes) return fail(OCN_ERR_ARG, "null argument");
+  *bytes = model->bytes;
+  return OCN_OK;
+}
+
+ocn_status ocn_model_bind_arena(ocn_model* m, void* device_ptr, size_t bytes) {
+  if (!m || !device_ptr) return fail(OCN_ERR_ARG, "null argument");
+  if (bytes < m->bytes) return fail(OCN_ERR_ARG, "arena smaller than ocn_model_arena_bytes()");
+  if (reinterpret_cast<uintptr_t>(device_ptr) % 256) return fail(OCN_ERR_ARG, "arena must be 256-byte aligned");
+  DeviceGuard dg(m->dev);
+  cudaError_t e = ensure_tables(m->dev);
+  if (e != cudaSuccess) return cuda_fail(e, "upload reconstruction tables");
+  drop_graphs(m);
+  m->arena = reinterpret_cast<char*>(device_ptr);
+  m->cur = 0;
+  e = cudaMemsetAsync(m->arena, 0, m->bytes, m->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "clear arena");
+  std::vector<char> blob = (m->es == 4) ? metrics_blob<float>(m) : metrics_blob<double>(m);
+  e = cudaMemcpyAsync(m->arena + m->off_dzc, blob.data(), blob.size(), cudaMemcpyHostToDevice, m->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "upload metrics");
+  e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bind synchronise");
+  return OCN_OK;
+}
+
+ocn_status ocn_set_field(ocn_model* m, int field, const void* src, size_t nbytes, int src_is_device) {
+  if (!m || !src) return fail(OCN_ERR_ARG, "null argument");
+  if (!m->arena) return fail(OCN_ERR_STATE, "arena not bound");
+  if (!field_valid(m, field) || field == OCN_FIELD_NU_E) return fail(OCN_ERR_ARG, "invalid field id for set");
+  DeviceGuard dg(m->dev);
+  size_t elems = 0;
+  char* dst = field_ptr(m, field, &elems);
+  if (nbytes != elems * (size_t)m->es) return fail(OCN_ERR_ARG, "byte count does not match the field size");
+  cudaError_t e = cudaMemcpyAsync(dst, src, nbytes, src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, m->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "set field copy");
+  const int tr = field - OCN_FIELD_TRACER0;
+  if (tr >= 0 && tr < m->d.n_tracers && m->cref[tr] != 0.0) {
+    e = (m->es == 4) ? launch_shift<float>(reinterpret_cast<float*>(dst), elems, (float)-m->cref[tr], m->stream)
+                     : launch_shift<double>(reinterpret_cast<double*>(dst), elems, -m->cref[tr], m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "tracer reference shift");
+  }
+  if (field == OCN_FIELD_W || field == OCN_FIELD_G + OCN_FIELD_W) {
+    size_t pb = (size_t)m->g->Nx * m->g->Ny * m->es;
+    e = cudaMemsetAsync(dst, 0, pb, m->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dst + (size_t)m->g->Nz * pb, 0, pb, m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "wall faces");
+  }
+  if (!src_is_device) {
+    e = cudaStreamSynchronize(m->stream);   // the host buffer is only borrowed for the call
+    if (e != cudaSuccess) return cuda_fail(e, "set field synchronise");
+  }
+  return OCN_OK;
+}
+
+ocn_status ocn_get_field(ocn_model* m, int field, void* dst, size_t nbytes, int dst_is_device) {
+  if (!m || !dst) return fail(OCN_ERR_ARG, "null argument");
+  if (!m->arena) return fail(OCN_ERR_STATE, "arena not bound");
+  if (!field_valid(m, field)) return fail(OCN_ERR_ARG, "invalid field id");
+  DeviceGuard dg(m->dev);
+  size_t elems = 0;
+  char* src = field_ptr(m, field, &elems);
+  if (nbytes != elems * (size_t)m->es) return fail(OCN_ERR_ARG, "byte count does not match the field size");
+  const int tr = field - OCN_FIELD_TRACER0;
+  if (tr >= 0 && tr < m->d.n_tracers && m->cref[tr] != 0.0) {
+    // add the reference back in the spectral work space (at least one field large)
+    char* scratch = m->arena + m->off_spec;
+    cudaError_t e = cudaMemcpyAsync(scratch, src, nbytes, cudaMemcpyDeviceToDevice, m->stream);
+    if (e == cudaSuccess)
+      e = (m->es == 4) ? launch_shift<float>(reinterpret_cast<float*>(scratch), elems, (float)m->cref[tr], m->stream)
+                       : launch_shift<double>(reinterpret_cast<double*>(scratch), elems, m->cref[tr], m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "tracer reference shift");
+    src = scratch;
+  }
+  cudaError_t e = cudaMemcpyAsync(dst, src, nbytes, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "get field copy");
+  if (!dst_is_device) {
+    e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "get field synchronise");
+  }
+  return OCN_OK;
+}
+
+ocn_status ocn_project(ocn_model* m) {
+  if (!m) return fail(OCN_ERR_ARG, "null argument");
+  if (!m->arena) return fail(OCN_ERR_STATE, "arena not bound");
+  DeviceGuard dg(m->dev);
+  cudaError_t e = (m->es == 4) ? launch_projection<float>(poisson_args<float>(m, m->cur, 1.0), m->stream, nullptr)
+                               : launch_projection<double>(poisson_args<double>(m, m->cur, 1.0), m->stream, nullptr);
+  e = check_sync(m, e);
+  if (e != cudaSuccess) return cuda_fail(e, "projection");
+  return OCN_OK;
+}
+
+ocn_status ocn_time_step(ocn_model* m, double dt, int nsteps) {
+  if (!m) return fail(OCN_ERR_ARG, "null argument");
+  if (!m->arena) return fail(OCN_ERR_STATE, "arena not bound");
+  if (nsteps < 0 || !isfinite(dt)) return fail(OCN_ERR_ARG, "nsteps must be >= 0 and dt finite");
+  DeviceGuard dg(m->dev);
+  return (m->es == 4) ? time_step_t<float>(m, dt, nsteps) : time_step_t<double>(m, dt, nsteps);
+}
+
+ocn_status ocn_compute_tendencies(ocn_model* m) {
+  if (!m) return fail(OCN_ERR_ARG, "null argument");
+  if (!m->arena) return fail(OCN_ERR_STATE, "arena not bound");
+  DeviceGuard dg(m->dev);
+  cudaError_t e;
+  if (m->es == 4) {
+    e = check_sync(m, enqueue_closure<float>(m, m->cur));
+    if (e == cudaSuccess) e = check_sync(m, enqueue_tendency<float>(m, m->cur, 0.0, 0.0, 1));
+  } else {
+    e = check_sync(m, enqueue_closure<double>(m, m->cur));
+    if (e == cudaSuccess) e = check_sync(m, enqueue_tendency<double>(m, m->cur, 0.0, 0.0, 1));
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "tendencies");
+  return OCN_OK;
+}
+
+ocn_status ocn_diagnostics(ocn_model* m, double dt, double* out, int nout) {
+  if (!m || !out) return fail(OCN_ERR_ARG, "null argument");
+  if (!m->arena) return fail(OCN_ERR_STATE, "arena not bound");
+  const int nt = m->d.n_tracers;
+  if (nout < nt + 6) return fail(OCN_ERR_ARG, "nout must be >= n_tracers + 6");
+  DeviceGuard dg(m->dev);
+  const ocn_grid* g = m->g;
+  cudaError_t e;
+  auto fill = [&](auto tag) {
+    typedef decltype(tag) T;
+    DiagArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.cur = state_ptrs<T>(m, m->cur);
+    a.dzc = at<T>(m, m->off_dzc); a.dzf = at<T>(m, m->off_dzf); a.rdzc = at<T>(m, m->off_rdzc); a.rdzf = at<T>(m, m->off_rdzf);
+    a.Nx = g->Nx; a.Ny = g->Ny; a.Nz = g->Nz; a.nt = nt;
+    a.dx = (T)(g->Lx / g->Nx); a.dy = (T)(g->Ly / g->Ny); a.rdx = (T)(g->Nx / g->Lx); a.rdy = (T)(g->Ny / g->Ly);
+    a.partial = at<double>(m, m->off_partial);
+    a.out = at<double>(m, m->off_diag);
+    a.nblocks = diag_blocks();
+    return launch_diagnostics<T>(a, m->stream);
+  };
+  e = (m->es == 4) ? fill(0.0f) : fill(0.0);
+  if (e != cudaSuccess) return cuda_fail(e, "diagnostics launch");
+  double vals[OCN_MAX_TRACERS + 6];
+  e = cudaMemcpyAsync(vals, m->arena + m->off_diag, sizeof(double) * (nt + 6), cudaMemcpyDeviceToHost, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "diagnostics read");
+  for (int v = 0; v < nt + 6; ++v) out[v] = vals[v];
+  const double volume = g->Lx * g->Ly * (g->zf[g->Nz] - g->zf[0]);
+  for (int t = 0; t < nt; ++t) out[t] += m->cref[t] * volume;
+  out[nt + 4] *= dt;
+  if (out[nt + 5] > 0 || !isfinite(out[nt + 3])) return fail(OCN_ERR_NONFINITE, "non-finite values in the state");
+  if (out[nt + 4] > 1.0) return fail(OCN_ERR_CFL, "advective CFL number above 1");
+  return OCN_OK;
+}
+
+ocn_status ocn_set_option(ocn_model* m, int option, long long value) {
+  if (!m) return fail(OCN_ERR_ARG, "null argument");
+  if (option == OCN_OPT_GRAPHS) { m->graphs = value != 0; return OCN_OK; }
+  if (option == OCN_OPT_SYNC_CHECK) { m->sync_check = value != 0; return OCN_OK; }
+  return fail(OCN_ERR_ARG, "unknown option");
+}
+
+ocn_status ocn_launches_per_step(const ocn_model* m, int* launches) {
+  if (!m || !launches) return fail(OCN_ERR_ARG, "null argument");
+  *launches = m->launches_per_step;
+  return OCN_OK;
+}
+
+}  // extern "C"

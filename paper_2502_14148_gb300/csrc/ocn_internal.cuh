@@ -1,0 +1,126 @@
+// Internal declarations shared by the translation units of the CUDA library.
+// Nothing here is part of the public ABI (include/ocn.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/ocn.h"
+
+namespace ocn {
+
+constexpr int kMaxTracers = OCN_MAX_TRACERS;
+constexpr int kMaxR = 5;          // WENO order up to 9
+constexpr int kMaxFftPasses = 12;
+
+// Reconstruction tables in the kernel's precision (uploaded to __constant__).
+template <typename T>
+struct WenoTables {
+  T sub[kMaxR + 1][kMaxR][kMaxR];          // [r][s][n]: substencil s of WENO(2r-1), weight of cell -r+s+n
+  T d[kMaxR + 1][kMaxR];                   // linear weights
+  T beta[kMaxR + 1][kMaxR][kMaxR][kMaxR];  // symmetric smoothness forms
+  T cen[kMaxR + 1][2 * kMaxR];             // centered order 2p: weight of cell -p+n
+};
+
+// Host-side derivation of the tables (coeffs.cpp).
+void derive_weno_tables(WenoTables<double>* out);
+// Upload to the tendency TU's constant memory.
+cudaError_t upload_weno_tables(const WenoTables<double>& t);
+
+// Fields of one prognostic state.
+template <typename T>
+struct StatePtrs {
+  T* u;
+  T* v;
+  T* w;
+  T* c[kMaxTracers];
+};
+
+template <typename T>
+struct TendencyArgs {
+  StatePtrs<T> cur;       // state at the start of the substage (read)
+  StatePtrs<T> nxt;       // new state (u~, tracers at m+1) (written)
+  StatePtrs<T> G;         // G^{m-1} (read when zeta != 0), overwritten with G^m
+  const T* nu;            // eddy viscosity at centres (closure SMAG/AMD)
+  const T* kap[kMaxTracers];  // AMD tracer diffusivities
+  const T* rdzc;          // 1/dz_c[k], k < Nz
+  const T* rdzf;          // 1/dz_f[k], 1 <= k < Nz (entries 0, Nz unused)
+  int Nx, Ny, Nz, nt;
+  T rdx, rdy;
+  int closure;
+  T nu0, kappa0;          // scalar diffusivity
+  T inv_Pr;
+  T f;
+  int eos;
+  T g_alpha, g_beta, T0, S0;
+  T top[2 + kMaxTracers], bot[2 + kMaxTracers];
+  T dt_gamma, dt_zeta;    // RK coefficients times dt
+  int mode;               // 0: RK update + G;  1: G only
+};
+
+template <typename T>
+struct ClosureArgs {
+  StatePtrs<T> cur;
+  T* nu;
+  T* kap[kMaxTracers];
+  const T* dzc;
+  const T* rdzc;
+  const T* rdzf;
+  int Nx, Ny, Nz, nt;
+  T dx, dy, rdx, rdy;
+  int closure;
+  T Cs, Cb, inv_Pr, C_amd;
+  int eos;
+  T g_alpha, g_beta, T0, S0;
+};
+
+// FFT plan for one line length (the half length for the real transform in x).
+struct FftPlan {
+  int n;                       // line length
+  int npass;
+  int radix[kMaxFftPasses];
+};
+
+template <typename T>
+struct PoissonArgs {
+  T* u; T* v; T* w;            // velocity to project (in place)
+  T* p;                        // pressure out
+  T* spec;                     // complex [Nz][Ny][Nx/2+1] interleaved (re, im)
+  T* cpiv;                     // Thomas pivots [Nz][Ny][Nx/2+1] (when fp64 pivots: double storage)
+  const T* rdzc; const T* rdzf; const T* dzc;
+  const T* lamx;               // [Nx/2+1]
+  const T* lamy;               // [Ny]
+  const T* twx;                // e^{-2 pi i t/Nx}, t < Nx (complex interleaved)
+  const T* twy;                // e^{-2 pi i t/Ny}, t < Ny
+  int Nx, Ny, Nz, Mx;          // Mx = Nx/2
+  T rdx, rdy;
+  T inv_dt;                    // 1 / (stage dt)
+  T dt;                        // stage dt
+  T scale;                     // 1 / (Mx * Ny) for the inverse transforms
+  T Htot;                      // total depth (for the gauge mean)
+  int fp64_pivots;
+  FftPlan px, py;
+};
+
+template <typename T>
+struct DiagArgs {
+  StatePtrs<T> cur;
+  const T* dzc; const T* dzf; const T* rdzc; const T* rdzf;
+  int Nx, Ny, Nz, nt;
+  T dx, dy, rdx, rdy;
+  double* partial;             // [nblocks][nvals]
+  double* out;                 // [nvals]
+  int nblocks;
+};
+
+// Launchers (return the launch error; kernels are enqueued on `s`).
+template <typename T> cudaError_t launch_closure(const ClosureArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_tendency(const TendencyArgs<T>& a, int weno_r, cudaStream_t s);
+template <typename T> cudaError_t launch_projection(const PoissonArgs<T>& a, cudaStream_t s, int* nlaunch);
+template <typename T> cudaError_t launch_diagnostics(const DiagArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_fill(T* p, size_t n, T v, cudaStream_t s);
+template <typename T> cudaError_t launch_shift(T* p, size_t n, T v, cudaStream_t s);
+int diag_blocks();
+
+}  // namespace ocn

@@ -1,0 +1,360 @@
+// Pressure projection (Appendix A.2): rhs = div(u~)/dt, lap p = rhs solved by
+// the eigenfunction expansion of the discrete Laplacian -- FFT in the periodic,
+// equispaced x and y directions and a tridiagonal (Thomas) solve down each
+// vertical column of the possibly stretched z grid -- then u = u~ - dt grad p
+// (Eqs. pressure-poisson, pressure-correction).
+//
+// Kernels:
+//   k_div_fftx : divergence of each x-row fused with its real-to-complex FFT
+//                (half-length complex FFT + split), written to the half
+//                spectrum [Nz][Ny][Nx/2+1];
+//   k_fft_y    : complex FFT along y for tiles of kx columns (forward/inverse);
+//   k_tridiag  : one thread per (kx, ky) column; coalesced across kx;
+//                Neumann walls; the (0,0) mode is pinned by p_0 = 0;
+//   k_gauge    : one warp removes the volume mean of the (0,0) column;
+//   k_ifftx    : complex-to-real inverse FFT along x -> p;
+//   k_correct  : u -= dt grad p on every non-wall face.
+// FFTs are shared-memory Stockham passes of radix 8/4/2/3 with host-built
+// twiddle tables, so every size 2^a 3^b is handled.
+#include <cuda_runtime.h>
+
+#include "ocn_internal.cuh"
+
+namespace ocn {
+
+template <typename T> struct CT;
+template <> struct CT<float> { typedef float2 type; };
+template <> struct CT<double> { typedef double2 type; };
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return {a.x + b.x, a.y + b.y}; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return {a.x - b.x, a.y - b.y}; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+template <typename C> __device__ __forceinline__ C cconj(C a) { return {a.x, -a.y}; }
+template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) { return {a.x * s, a.y * s}; }
+// multiply by s*i
+template <typename C> __device__ __forceinline__ C cmuli(C a, int s) { return s > 0 ? C{-a.y, a.x} : C{a.y, -a.x}; }
+
+// In-place DFT of length R on v (sign s = -1 forward, +1 inverse).
+template <typename C, typename T, int R>
+__device__ __forceinline__ void dft(C* v, int s) {
+  if constexpr (R == 2) {
+    C a = v[0], b = v[1];
+    v[0] = cadd(a, b); v[1] = csub(a, b);
+  } else if constexpr (R == 3) {
+    const T h = T(0.86602540378443864676);
+    C t = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+    C m = csub(v[0], cscale(t, T(0.5)));
+    C r = cmuli(cscale(d, h), s);
+    v[0] = cadd(v[0], t); v[1] = cadd(m, r); v[2] = csub(m, r);
+  } else if constexpr (R == 4) {
+    C t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+    C t2 = cadd(v[1], v[3]), t3 = cmuli(csub(v[1], v[3]), s);
+    v[0] = cadd(t0, t2); v[2] = csub(t0, t2); v[1] = cadd(t1, t3); v[3] = csub(t1, t3);
+  } else if constexpr (R == 8) {
+    C e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+    dft<C, T, 4>(e, s);
+    dft<C, T, 4>(o, s);
+    const T h = T(0.70710678118654752440);
+    // twiddles e^{s 2 pi i k / 8}, k = 0..3
+    C w1 = {h, T(s) * h}, w3 = {-h, T(s) * h};
+    C o1 = cmul(o[1], w1), o2 = cmuli(o[2], s), o3 = cmul(o[3], w3);
+    v[0] = cadd(e[0], o[0]); v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], o1);   v[5] = csub(e[1], o1);
+    v[2] = cadd(e[2], o2);   v[6] = csub(e[2], o2);
+    v[3] = cadd(e[3], o3);   v[7] = csub(e[3], o3);
+  }
+}
+
+// One Stockham pass of radix R over `nlines` lines of length N held in `src`,
+// written to `dst`.  Element e of line l lives at l*sl + e*se.  The twiddle
+// table holds e^{-2 pi i t / (N*tws)} for t < N*tws (tws = stride into it).
+template <typename C, typename T, int R>
+__device__ __forceinline__ void stockham_pass(const C* src, C* dst, int N, int Ns, int nlines, int sl, int se,
+                                              const C* tw, int tws, int s, bool line_fast) {
+  const int nb = N / R;
+  const int total = nlines * nb;
+  const int twstep = N / (Ns * R);
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    int l, j;
+    if (line_fast) { l = idx % nlines; j = idx / nlines; }
+    else { j = idx % nb; l = idx / nb; }
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[l * sl + (j + r * nb) * se];
+    const int k = j % Ns;
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        int t = (r * k * twstep) % N;
+        C w = tw[t * tws];
+        if (s > 0) w.y = -w.y;
+        v[r] = cmul(v[r], w);
+      }
+    }
+    dft<C, T, R>(v, s);
+    const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[l * sl + (base + r * Ns) * se] = v[r];
+  }
+}
+
+// Full FFT; the data start in a and the result ends in a or b (returned).
+template <typename C, typename T>
+__device__ C* block_fft(C* a, C* b, const FftPlan& plan, int nlines, int sl, int se, const C* tw, int tws, int s,
+                        bool line_fast) {
+  int Ns = 1;
+  for (int p = 0; p < plan.npass; ++p) {
+    const int R = plan.radix[p];
+    switch (R) {
+      case 8: stockham_pass<C, T, 8>(a, b, plan.n, Ns, nlines, sl, se, tw, tws, s, line_fast); break;
+      case 4: stockham_pass<C, T, 4>(a, b, plan.n, Ns, nlines, sl, se, tw, tws, s, line_fast); break;
+      case 3: stockham_pass<C, T, 3>(a, b, plan.n, Ns, nlines, sl, se, tw, tws, s, line_fast); break;
+      default: stockham_pass<C, T, 2>(a, b, plan.n, Ns, nlines, sl, se, tw, tws, s, line_fast); break;
+    }
+    __syncthreads();
+    Ns *= R;
+    C* t = a; a = b; b = t;
+  }
+  return a;
+}
+
+// ---------------------------------------------------------------------------
+// divergence + real FFT along x.  Each block handles LR consecutive rows.
+template <typename T>
+__global__ void __launch_bounds__(256) k_div_fftx(const PoissonArgs<T> a, int LR) {
+  typedef typename CT<T>::type C;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C* A = reinterpret_cast<C*>(sm_raw);
+  const int M = a.Mx, Nx = a.Nx, Ny = a.Ny, Nz = a.Nz;
+  C* B = A + LR * M;
+  const size_t plane = (size_t)Nx * Ny;
+  const int row0 = blockIdx.x * LR;
+  const int nrows = min(LR, Ny * Nz - row0);
+  for (int idx = threadIdx.x; idx < nrows * M; idx += blockDim.x) {
+    const int l = idx / M, n = idx % M;
+    const int row = row0 + l;
+    const int j = row % Ny, k = row / Ny;
+    const int jp = (j + 1 == Ny) ? 0 : j + 1;
+    const T rdz = __ldg(a.rdzc + k);
+    T val[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = 2 * n + h;
+      const int ip = (i + 1 == Nx) ? 0 : i + 1;
+      const size_t o = (size_t)k * plane + (size_t)j * Nx;
+      const T div = (a.u[o + ip] - a.u[o + i]) * a.rdx + (a.v[(size_t)k * plane + (size_t)jp * Nx + i] - a.v[o + i]) * a.rdy +
+                    (a.w[o + plane + i] - a.w[o + i]) * rdz;
+      val[h] = div * a.inv_dt;
+    }
+    A[l * M + n] = C{val[0], val[1]};
+  }
+  __syncthreads();
+  C* Z = block_fft<C, T>(A, B, a.px, nrows, M, 1, reinterpret_cast<const C*>(a.twx), 2, -1, false);
+  // split: X[kx] = E + W^kx O, E = (Z[kx] + conj Z[M-kx])/2, O = (Z[kx] - conj Z[M-kx])/(2i)
+  const int S = M + 1;
+  for (int idx = threadIdx.x; idx < nrows * S; idx += blockDim.x) {
+    const int l = idx / S, kx = idx % S;
+    const C z1 = Z[l * M + (kx % M)];
+    const C z2 = cconj(Z[l * M + ((M - kx) % M)]);
+    const C E = cscale(cadd(z1, z2), T(0.5));
+    const C D = cscale(csub(z1, z2), T(0.5));
+    const C O = {D.y, -D.x};                   // D / i
+    const C w = reinterpret_cast<const C*>(a.twx)[kx % Nx];
+    const C X = cadd(E, cmul(w, O));
+    const int row = row0 + l;
+    reinterpret_cast<C*>(a.spec)[(size_t)row * S + kx] = X;
+  }
+}
+
+// complex-to-real inverse FFT along x -> p (scaled by a.scale).
+template <typename T>
+__global__ void __launch_bounds__(256) k_ifftx(const PoissonArgs<T> a, int LR) {
+  typedef typename CT<T>::type C;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C* A = reinterpret_cast<C*>(sm_raw);
+  const int M = a.Mx, Nx = a.Nx, Ny = a.Ny, Nz = a.Nz;
+  C* B = A + LR * M;
+  const int S = M + 1;
+  const int row0 = blockIdx.x * LR;
+  const int nrows = min(LR, Ny * Nz - row0);
+  const C* spec = reinterpret_cast<const C*>(a.spec);
+  const C* tw = reinterpret_cast<const C*>(a.twx);
+  for (int idx = threadIdx.x; idx < nrows * M; idx += blockDim.x) {
+    const int l = idx / M, kx = idx % M;
+    const size_t ro = (size_t)(row0 + l) * S;
+    const C x1 = spec[ro + kx];
+    const C x2 = cconj(spec[ro + (M - kx)]);
+    const C E = cscale(cadd(x1, x2), T(0.5));
+    C w = tw[kx];
+    w.y = -w.y;                                 // e^{+2 pi i kx / Nx}
+    const C O = cmul(cscale(csub(x1, x2), T(0.5)), w);
+    const C Zk = cscale(cadd(E, cmuli(O, 1)), a.scale);
+    A[l * M + kx] = Zk;
+  }
+  __syncthreads();
+  C* z = block_fft<C, T>(A, B, a.px, nrows, M, 1, tw, 2, +1, false);
+  const size_t plane = (size_t)Nx * Ny;
+  (void)plane;
+  for (int idx = threadIdx.x; idx < nrows * M; idx += blockDim.x) {
+    const int l = idx / M, n = idx % M;
+    const int row = row0 + l;
+    const C v = z[l * M + n];
+    a.p[(size_t)row * Nx + 2 * n] = v.x;
+    a.p[(size_t)row * Nx + 2 * n + 1] = v.y;
+  }
+}
+
+// FFT along y of a tile of CW kx-columns in one z-plane, in place.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fft_y(const PoissonArgs<T> a, int CW, int sign) {
+  typedef typename CT<T>::type C;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C* A = reinterpret_cast<C*>(sm_raw);
+  const int Ny = a.Ny, S = a.Mx + 1;
+  C* B = A + Ny * CW;
+  const int kx0 = blockIdx.x * CW, k = blockIdx.y;
+  const int ncol = min(CW, S - kx0);
+  C* spec = reinterpret_cast<C*>(a.spec) + (size_t)k * Ny * S;
+  for (int idx = threadIdx.x; idx < Ny * CW; idx += blockDim.x) {
+    const int c = idx % CW, j = idx / CW;
+    if (c < ncol) A[j * CW + c] = spec[(size_t)j * S + kx0 + c];
+  }
+  __syncthreads();
+  C* r = block_fft<C, T>(A, B, a.py, CW, 1, CW, reinterpret_cast<const C*>(a.twy), 1, sign, true);
+  for (int idx = threadIdx.x; idx < Ny * CW; idx += blockDim.x) {
+    const int c = idx % CW, j = idx / CW;
+    if (c < ncol) spec[(size_t)j * S + kx0 + c] = r[j * CW + c];
+  }
+}
+
+// Thomas algorithm per horizontal wavenumber.  a_k p_{k-1} + b_k p_k + c_k p_{k+1} = r_k,
+// a_k = 1/(dzc_k dzf_k), c_k = 1/(dzc_k dzf_{k+1}) (zero at the walls: Neumann),
+// b_k = -(a_k + c_k) + lambda_x + lambda_y.
+template <typename T, typename P>
+__global__ void __launch_bounds__(256) k_tridiag(const PoissonArgs<T> a) {
+  typedef typename CT<T>::type C;
+  const int S = a.Mx + 1, Ny = a.Ny, Nz = a.Nz;
+  const int kx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ky = blockIdx.y;
+  if (kx >= S) return;
+  const size_t pl = (size_t)Ny * S;
+  C* x = reinterpret_cast<C*>(a.spec) + (size_t)ky * S + kx;
+  T* cp = a.cpiv + (size_t)ky * S + kx;
+  const P lam = (P)__ldg(a.lamx + kx) + (P)__ldg(a.lamy + ky);
+  const bool gauge = (kx == 0 && ky == 0);
+  P cprev = P(0);
+  C dprev = {T(0), T(0)};
+  for (int k = 0; k < Nz; ++k) {
+    const P rz = (P)__ldg(a.rdzc + k);
+    P ak = (k > 0) ? rz * (P)__ldg(a.rdzf + k) : P(0);
+    P ck = (k < Nz - 1) ? rz * (P)__ldg(a.rdzf + k + 1) : P(0);
+    P bk = -(ak + ck) + lam;
+    C r = x[(size_t)k * pl];
+    if (gauge && k == 0) { ak = P(0); bk = P(1); ck = P(0); r = C{T(0), T(0)}; }
+    const P inv = P(1) / (bk - ak * cprev);
+    cprev = ck * inv;
+    const T ti = (T)inv, ta = (T)ak;
+    C d = {(r.x - ta * dprev.x) * ti, (r.y - ta * dprev.y) * ti};
+    x[(size_t)k * pl] = d;
+    cp[(size_t)k * pl] = (T)cprev;
+    dprev = d;
+  }
+  C pn = dprev;
+  for (int k = Nz - 2; k >= 0; --k) {
+    const T c = cp[(size_t)k * pl];
+    C d = x[(size_t)k * pl];
+    d.x -= c * pn.x;
+    d.y -= c * pn.y;
+    x[(size_t)k * pl] = d;
+    pn = d;
+  }
+}
+
+// zero volume mean of the (kx,ky) = (0,0) column (one warp)
+template <typename T>
+__global__ void k_gauge(const PoissonArgs<T> a) {
+  typedef typename CT<T>::type C;
+  const size_t pl = (size_t)a.Ny * (a.Mx + 1);
+  C* x = reinterpret_cast<C*>(a.spec);
+  double sr = 0.0, si = 0.0;
+  for (int k = threadIdx.x; k < a.Nz; k += 32) {
+    const double dz = (double)a.dzc[k];
+    sr += dz * (double)x[(size_t)k * pl].x;
+    si += dz * (double)x[(size_t)k * pl].y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+  }
+  const T mr = (T)(sr / (double)a.Htot), mi = (T)(si / (double)a.Htot);
+  for (int k = threadIdx.x; k < a.Nz; k += 32) {
+    C v = x[(size_t)k * pl];
+    v.x -= mr;
+    v.y -= mi;
+    x[(size_t)k * pl] = v;
+  }
+}
+
+// u = u~ - dt grad p (walls untouched)
+template <typename T>
+__global__ void __launch_bounds__(256) k_correct(const PoissonArgs<T> a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  const int k = blockIdx.z;
+  const int Nx = a.Nx, Ny = a.Ny;
+  if (i >= Nx) return;
+  const size_t plane = (size_t)Nx * Ny;
+  const size_t id = (size_t)k * plane + (size_t)j * Nx + i;
+  const int im = (i == 0) ? Nx - 1 : i - 1;
+  const int jm = (j == 0) ? Ny - 1 : j - 1;
+  const T pc = a.p[id];
+  a.u[id] -= a.dt * (pc - a.p[(size_t)k * plane + (size_t)j * Nx + im]) * a.rdx;
+  a.v[id] -= a.dt * (pc - a.p[(size_t)k * plane + (size_t)jm * Nx + i]) * a.rdy;
+  if (k >= 1) a.w[id] -= a.dt * (pc - a.p[id - plane]) * __ldg(a.rdzf + k);
+}
+
+static int rows_per_block(int M) { return M >= 2048 ? 1 : 2048 / M; }
+
+template <typename T>
+cudaError_t launch_projection(const PoissonArgs<T>& a, cudaStream_t s, int* nlaunch) {
+  typedef typename CT<T>::type C;
+  cudaError_t e;
+  int n = 0;
+  const int M = a.Mx;
+  const int LR = rows_per_block(M);
+  const size_t smx = 2 * (size_t)LR * M * sizeof(C);
+  const int rows = a.Ny * a.Nz;
+  e = cudaFuncSetAttribute(k_div_fftx<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_ifftx<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx);
+  if (e != cudaSuccess) return e;
+  k_div_fftx<T><<<(rows + LR - 1) / LR, 256, smx, s>>>(a, LR);
+  ++n;
+  const int CW = (sizeof(T) == 4) ? 8 : 4;
+  const size_t smy = 2 * (size_t)a.Ny * CW * sizeof(C);
+  e = cudaFuncSetAttribute(k_fft_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smy);
+  if (e != cudaSuccess) return e;
+  dim3 gy((a.Mx + 1 + CW - 1) / CW, a.Nz);
+  k_fft_y<T><<<gy, 256, smy, s>>>(a, CW, -1);
+  ++n;
+  dim3 gt((a.Mx + 1 + 127) / 128, a.Ny);
+  if (a.fp64_pivots) k_tridiag<T, double><<<gt, 128, 0, s>>>(a);
+  else k_tridiag<T, T><<<gt, 128, 0, s>>>(a);
+  ++n;
+  k_gauge<T><<<1, 32, 0, s>>>(a);
+  ++n;
+  k_fft_y<T><<<gy, 256, smy, s>>>(a, CW, +1);
+  ++n;
+  k_ifftx<T><<<(rows + LR - 1) / LR, 256, smx, s>>>(a, LR);
+  ++n;
+  dim3 gc((a.Nx + 255) / 256, a.Ny, a.Nz);
+  k_correct<T><<<gc, 256, 0, s>>>(a);
+  ++n;
+  if (nlaunch) *nlaunch = n;
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_projection<float>(const PoissonArgs<float>&, cudaStream_t, int*);
+template cudaError_t launch_projection<double>(const PoissonArgs<double>&, cudaStream_t, int*);
+
+}  // namespace ocn

@@ -1,0 +1,131 @@
+// Diagnostics: FP64 volume integrals (sum V c for every tracer, sum V u,
+// sum V v, sum V w), max |div u|, the largest advective rate |u|/dx, |v|/dy,
+// |w|/dz_f, and a count of non-finite values.  Conservation of the volume
+// integrals in periodic, no-flux domains follows from the flux form
+// (Eq. flux-divergence, Appendix B); div u = 0 from the projection (Eq.
+// continuity, Appendix A.2).
+// Two stages with a fixed reduction order (per-block partials, then one
+// block), so the result is bitwise reproducible run to run.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "ocn_internal.cuh"
+
+namespace ocn {
+
+constexpr int kDiagBlocks = 1216;   // 8 x 152 SMs
+constexpr int kDiagThreads = 256;
+constexpr int kDiagVals = OCN_MAX_TRACERS + 6;
+
+int diag_blocks() { return kDiagBlocks; }
+
+template <typename T>
+__global__ void __launch_bounds__(kDiagThreads) k_diag(const DiagArgs<T> a) {
+  const int Nx = a.Nx, Ny = a.Ny, Nz = a.Nz, nt = a.nt;
+  const size_t plane = (size_t)Nx * Ny;
+  const size_t N = plane * Nz;
+  double acc[kDiagVals];
+#pragma unroll
+  for (int v = 0; v < kDiagVals; ++v) acc[v] = 0.0;
+  const double A = (double)a.dx * (double)a.dy;
+  for (size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x; id < N; id += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(id / plane);
+    const size_t r = id - (size_t)k * plane;
+    const int j = (int)(r / Nx), i = (int)(r - (size_t)j * Nx);
+    const int ip = (i + 1 == Nx) ? 0 : i + 1, jp = (j + 1 == Ny) ? 0 : j + 1;
+    const double V = A * (double)a.dzc[k];
+    double bad = 0.0;
+#pragma unroll
+    for (int t = 0; t < OCN_MAX_TRACERS; ++t) {
+      if (t < nt) {
+        const double c = (double)a.cur.c[t][id];
+        acc[t] += V * c;
+        if (!isfinite(c)) bad += 1.0;
+      }
+    }
+    const double u = (double)a.cur.u[id], v = (double)a.cur.v[id], w = (double)a.cur.w[id];
+    acc[nt] += V * u;
+    acc[nt + 1] += V * v;
+    const double div = ((double)a.cur.u[id - i + ip] - u) * (double)a.rdx +
+                       ((double)a.cur.v[(size_t)k * plane + (size_t)jp * Nx + i] - v) * (double)a.rdy +
+                       ((double)a.cur.w[id + plane] - w) * (double)a.rdzc[k];
+    acc[nt + 3] = fmax(acc[nt + 3], fabs(div));
+    double rate = fmax(fabs(u) * (double)a.rdx, fabs(v) * (double)a.rdy);
+    if (k >= 1) {
+      acc[nt + 2] += A * (double)a.dzf[k] * w;
+      rate = fmax(rate, fabs(w) * (double)a.rdzf[k]);
+    }
+    acc[nt + 4] = fmax(acc[nt + 4], rate);
+    if (!isfinite(u) || !isfinite(v) || !isfinite(w)) bad += 1.0;
+    acc[nt + 5] += bad;
+  }
+  __shared__ double red[kDiagThreads / 32][kDiagVals];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int v = 0; v < kDiagVals; ++v) {
+    double x = acc[v];
+    const bool ismax = (v == nt + 3 || v == nt + 4);
+    for (int o = 16; o > 0; o >>= 1) {
+      const double y = __shfl_down_sync(0xffffffffu, x, o);
+      x = ismax ? fmax(x, y) : x + y;
+    }
+    if (lane == 0) red[wid][v] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < kDiagVals) {
+    const int v = threadIdx.x;
+    const bool ismax = (v == nt + 3 || v == nt + 4);
+    double x = red[0][v];
+    for (int w = 1; w < kDiagThreads / 32; ++w) x = ismax ? fmax(x, red[w][v]) : x + red[w][v];
+    a.partial[(size_t)blockIdx.x * kDiagVals + v] = x;
+  }
+}
+
+template <typename T>
+__global__ void k_diag_final(const DiagArgs<T> a) {
+  const int v = threadIdx.x;
+  if (v >= kDiagVals) return;
+  const int nt = a.nt;
+  const bool ismax = (v == nt + 3 || v == nt + 4);
+  double x = a.partial[v];
+  for (int b = 1; b < a.nblocks; ++b) {
+    const double y = a.partial[(size_t)b * kDiagVals + v];
+    x = ismax ? fmax(x, y) : x + y;
+  }
+  a.out[v] = x;
+}
+
+template <typename T>
+cudaError_t launch_diagnostics(const DiagArgs<T>& a, cudaStream_t s) {
+  k_diag<T><<<a.nblocks, kDiagThreads, 0, s>>>(a);
+  k_diag_final<T><<<1, 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_fill(T* p, size_t n, T v) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
+}
+template <typename T>
+__global__ void k_shift(T* p, size_t n, T v) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] += v;
+}
+template <typename T>
+cudaError_t launch_fill(T* p, size_t n, T v, cudaStream_t s) {
+  k_fill<T><<<1216, 256, 0, s>>>(p, n, v);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_shift(T* p, size_t n, T v, cudaStream_t s) {
+  k_shift<T><<<1216, 256, 0, s>>>(p, n, v);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_diagnostics<float>(const DiagArgs<float>&, cudaStream_t);
+template cudaError_t launch_diagnostics<double>(const DiagArgs<double>&, cudaStream_t);
+template cudaError_t launch_fill<float>(float*, size_t, float, cudaStream_t);
+template cudaError_t launch_fill<double>(double*, size_t, double, cudaStream_t);
+template cudaError_t launch_shift<float>(float*, size_t, float, cudaStream_t);
+template cudaError_t launch_shift<double>(double*, size_t, double, cudaStream_t);
+
+}  // namespace ocn

@@ -1,0 +1,739 @@
+// Fused tendency + RK3 substage update, and the eddy-diffusivity kernel.
+//
+// Physics (arXiv 2502.14148): flux-form advection (Eq. flux-form-advection,
+// Eq. advection-flux-divergence) with WENO-Z reconstruction of the advected
+// quantity (Eq. fifth-order-weno, order 2R-1) and, for momentum, a centered
+// advecting velocity of order 2R-2 (Sec. B.2.1); closure fluxes (Sec. 3.1.1:
+// ScalarDiffusivity in Laplacian form, Smagorinsky-Lilly / AMD in stress
+// form); f-plane Coriolis; buoyancy b z_hat (Eq. buoyancy, linear EOS);
+// prescribed top/bottom fluxes; finite-volume flux divergence
+// (Eq. flux-divergence); RK3 substage (Eq. rk3).
+//
+// Kernel layout (GB300, one CTA per TX x TY column tile, marching up in z):
+//  * The current level of every field, with an R-wide halo, is staged in
+//    shared memory by cp.async (periodic wrap done by the gather), double or
+//    triple buffered so that level k+1 streams in while level k is computed.
+//  * Each thread also keeps its own column's 2R nearest levels of every field
+//    in registers: the z-stencils come from there, with no shared traffic.
+//  * Each thread computes the fluxes through the west, south and top faces of
+//    its control volumes; the tile's east column and north row of faces are
+//    computed by two "ghost" warps.  x/y fluxes meet through shared memory,
+//    z fluxes are carried in registers from one level to the next, so every
+//    face flux is reconstructed exactly once.
+//  * The epilogue forms G, applies u~ = u + dt (gamma G - zeta G_prev) and
+//    writes the new state and G (the G_prev of the next substage).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ocn_internal.cuh"
+
+namespace ocn {
+
+__constant__ WenoTables<float> cWf;
+__constant__ WenoTables<double> cWd;
+
+cudaError_t upload_weno_tables(const WenoTables<double>& t) {
+  // Pack beta as upper triangle with doubled off-diagonal terms.
+  WenoTables<double> d = t;
+  for (int r = 1; r <= kMaxR; ++r)
+    for (int s = 0; s < r; ++s)
+      for (int a = 0; a < r; ++a)
+        for (int b = 0; b < r; ++b) d.beta[r][s][a][b] = (b > a) ? 2.0 * t.beta[r][s][a][b] : (b == a ? t.beta[r][s][a][b] : 0.0);
+  WenoTables<float> f;
+  const double* src = reinterpret_cast<const double*>(&d);
+  float* dst = reinterpret_cast<float*>(&f);
+  static_assert(sizeof(WenoTables<double>) == 2 * sizeof(WenoTables<float>), "table layout");
+  for (size_t n = 0; n < sizeof(WenoTables<float>) / sizeof(float); ++n) dst[n] = (float)src[n];
+  cudaError_t e = cudaMemcpyToSymbol(cWd, &d, sizeof(d));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(cWf, &f, sizeof(f));
+}
+
+template <typename T> struct Tab;
+template <> struct Tab<float> {
+  static __device__ __forceinline__ float sub(int r, int s, int n) { return cWf.sub[r][s][n]; }
+  static __device__ __forceinline__ float d(int r, int s) { return cWf.d[r][s]; }
+  static __device__ __forceinline__ float beta(int r, int s, int a, int b) { return cWf.beta[r][s][a][b]; }
+  static __device__ __forceinline__ float cen(int p, int n) { return cWf.cen[p][n]; }
+};
+template <> struct Tab<double> {
+  static __device__ __forceinline__ double sub(int r, int s, int n) { return cWd.sub[r][s][n]; }
+  static __device__ __forceinline__ double d(int r, int s) { return cWd.d[r][s]; }
+  static __device__ __forceinline__ double beta(int r, int s, int a, int b) { return cWd.beta[r][s][a][b]; }
+  static __device__ __forceinline__ double cen(int p, int n) { return cWd.cen[p][n]; }
+};
+
+__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+
+// WENO(2r-1) at the interface between s[r-1] and s[r] (s holds cells m-r .. m+r-1),
+// upwinded by the sign of vel (the branch for vel >= 0 when vel == 0).
+// The upwind cell value is subtracted before the linear algebra (the
+// reconstruction weights sum to one and the indicators are shift invariant),
+// which keeps FP32 accurate for fields with a large mean.
+template <typename T, int r>
+__device__ __forceinline__ T weno(const T* s, T vel) {
+  T t[2 * r];
+  const bool pos = vel >= T(0);
+#pragma unroll
+  for (int n = 0; n < 2 * r; ++n) t[n] = pos ? s[n] : s[2 * r - 1 - n];
+  if constexpr (r == 1) {
+    return t[0];
+  } else {
+    const T ref = t[r - 1];
+#pragma unroll
+    for (int n = 0; n < 2 * r; ++n) t[n] -= ref;
+    T q[r], b[r];
+#pragma unroll
+    for (int k = 0; k < r; ++k) {
+      T acc = T(0);
+#pragma unroll
+      for (int n = 0; n < r; ++n) acc = fma(Tab<T>::sub(r, k, n), t[k + n], acc);
+      q[k] = acc;
+      T bb = T(0);
+#pragma unroll
+      for (int a = 0; a < r; ++a) {
+        T inner = Tab<T>::beta(r, k, a, a) * t[k + a];
+#pragma unroll
+        for (int c = a + 1; c < r; ++c) inner = fma(Tab<T>::beta(r, k, a, c), t[k + c], inner);
+        bb = fma(inner, t[k + a], bb);
+      }
+      b[k] = bb;
+    }
+    const T tau = fabs(b[0] - b[r - 1]);
+    T num = T(0), den = T(0);
+#pragma unroll
+    for (int k = 0; k < r; ++k) {
+      const T ratio = tau * rcp(b[k] + T(1e-8));
+      const T alpha = Tab<T>::d(r, k) * fma(ratio, ratio, T(1));
+      num = fma(alpha, q[k], num);
+      den += alpha;
+    }
+    return ref + num * rcp(den);
+  }
+}
+
+// Centered reconstruction of order 2p at the interface between s[p-1] and s[p].
+template <typename T, int p>
+__device__ __forceinline__ T centered(const T* s) {
+  T acc = T(0);
+#pragma unroll
+  for (int n = 0; n < p; ++n) acc = fma(Tab<T>::cen(p, n), s[n] + s[2 * p - 1 - n], acc);
+  return acc;
+}
+
+// Wall-reduced variants: a ring holding levels m-R .. m+R-1 around interface m.
+template <typename T, int R>
+__device__ __forceinline__ T weno_reduced(const T* ring, int r, T vel) {
+  if (r >= R) return weno<T, R>(ring, vel);
+  if constexpr (R > 4) { if (r == 4) return weno<T, 4>(ring + R - 4, vel); }
+  if constexpr (R > 3) { if (r == 3) return weno<T, 3>(ring + R - 3, vel); }
+  if constexpr (R > 2) { if (r == 2) return weno<T, 2>(ring + R - 2, vel); }
+  if (r == 1) return weno<T, 1>(ring + R - 1, vel);
+  return T(0);
+}
+// Centered interpolation at the interface between ring[R-1-SHIFT] and ring[R-SHIFT],
+// of order 2p (p <= R-1), for a ring of 2R values.
+template <typename T, int R, int SHIFT>
+__device__ __forceinline__ T centered_reduced(const T* ring, int p) {
+  constexpr int P = R - 1;
+  if (p >= P) return centered<T, P>(ring + R - SHIFT - P);
+  if constexpr (P > 3) { if (p == 3) return centered<T, 3>(ring + R - SHIFT - 3); }
+  if constexpr (P > 2) { if (p == 2) return centered<T, 2>(ring + R - SHIFT - 2); }
+  if constexpr (P > 1) { if (p == 1) return centered<T, 1>(ring + R - SHIFT - 1); }
+  return T(0);
+}
+
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if (bytes == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
+
+template <typename T>
+__device__ __forceinline__ T buoyancy(const TendencyArgs<T>& a, T c0, T c1) {
+  return a.eos == OCN_EOS_LINEAR_TS ? a.g_alpha * (c0 - a.T0) - a.g_beta * (c1 - a.S0) : c0;
+}
+
+template <int TX, int TY>
+struct TileGeom {
+  static constexpr int NMAIN = TX * TY;
+  static constexpr int NTHREADS = ((TX * TY + TX + TY) + 31) / 32 * 32;
+};
+
+template <typename T, int R, int NTR, int TX, int TY>
+__global__ void __launch_bounds__(TileGeom<TX, TY>::NTHREADS, 1)
+k_tendency(const TendencyArgs<T> a) {
+  constexpr int P = R - 1;          // advecting-velocity half width
+  constexpr int H = R;              // plane halo
+  constexpr int PW = TX + 2 * H;
+  constexpr int PH = TY + 2 * H;
+  constexpr int PLANE = PW * PH;
+  constexpr int NT_ = TileGeom<TX, TY>::NTHREADS;
+  constexpr int FXS = TY * (TX + 1);
+  constexpr int FYS = (TY + 1) * TX;
+
+  const int Nx = a.Nx, Ny = a.Ny, Nz = a.Nz;
+  constexpr int nt = NTR;
+  constexpr int nf = 3 + nt;
+  const size_t plane = (size_t)Nx * Ny;
+  const bool stress = (a.closure == OCN_CLOSURE_SMAGORINSKY || a.closure == OCN_CLOSURE_AMD);
+  const bool amd = (a.closure == OCN_CLOSURE_AMD);
+  const bool scalar = (a.closure == OCN_CLOSURE_SCALAR);
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  T* sU = sm;                             // 2 slots
+  T* sV = sU + 2 * PLANE;                 // 2 slots
+  T* sW = sV + 2 * PLANE;                 // 3 slots (faces k, k+1, prefetch)
+  T* sC = sW + 3 * PLANE;                 // nt x 2 slots
+  T* sNu = sC + 2 * nt * PLANE;           // 4 slots (levels k-1, k, k+1, prefetch) if stress
+  T* sK = sNu + (stress ? 4 : 0) * PLANE; // nt x 3 slots if amd
+  T* FX = sK + (amd ? 3 * nt : 0) * PLANE;
+  T* FY = FX + nf * FXS;
+  int* gi_tab = reinterpret_cast<int*>(FY + nf * FYS);
+  int* gj_tab = gi_tab + PW;
+
+  const int tid = threadIdx.x;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int Wt = min(TX, Nx - i0), Ht = min(TY, Ny - j0);
+
+  // roles: main (TX*TY), north ghost row (TX), east ghost column (TY), idle
+  int role, lx, ly;
+  if (tid < TX * TY) { role = 0; lx = tid % TX; ly = tid / TX; }
+  else if (tid < TX * TY + TX) { role = 1; lx = tid - TX * TY; ly = Ht; }
+  else if (tid < TX * TY + TX + TY) { role = 2; lx = Wt; ly = tid - TX * TY - TX; }
+  else { role = 3; lx = 0; ly = 0; }
+  const bool active = (role == 0) ? (lx < Wt && ly < Ht) : (role == 1 ? lx < Wt : (role == 2 ? ly < Ht : false));
+
+  for (int e = tid; e < PW; e += NT_) { int g = (i0 + e - H) % Nx; gi_tab[e] = g < 0 ? g + Nx : g; }
+  for (int e = tid; e < PH; e += NT_) { int g = (j0 + e - H) % Ny; gj_tab[e] = g < 0 ? g + Ny : g; }
+  __syncthreads();
+
+  auto load_plane = [&](T* dst, const T* field, int level) {
+    const T* base = field + (size_t)level * plane;
+    for (int e = tid; e < PLANE; e += NT_) {
+      const int yy = e / PW, xx = e - yy * PW;
+      cp_async(dst + e, base + (size_t)gj_tab[yy] * Nx + gi_tab[xx], (int)sizeof(T));
+    }
+  };
+  auto load_level = [&](int k) {  // u, v, tracers at level k (slot k&1)
+    if (k >= Nz) return;
+    load_plane(sU + (k & 1) * PLANE, a.cur.u, k);
+    load_plane(sV + (k & 1) * PLANE, a.cur.v, k);
+    for (int n = 0; n < nt; ++n) load_plane(sC + (2 * n + (k & 1)) * PLANE, a.cur.c[n], k);
+  };
+  auto load_wface = [&](int f) { if (f <= Nz) load_plane(sW + (f % 3) * PLANE, a.cur.w, f); };
+  auto load_diff = [&](int l) {
+    if (l < 0 || l >= Nz) return;
+    if (stress) load_plane(sNu + (l & 3) * PLANE, a.nu, l);
+    if (amd) for (int n = 0; n < nt; ++n) load_plane(sK + (3 * n + l % 3) * PLANE, a.kap[n], l);
+  };
+
+  // own column (periodic)
+  const int ci = (i0 + lx) % Nx, cj = (j0 + ly) % Ny;
+  const size_t col = (size_t)cj * Nx + ci;
+  auto ld_c = [&](const T* f, int level) -> T { return (level >= 0 && level < Nz) ? __ldg(f + (size_t)level * plane + col) : T(0); };
+  auto ld_w = [&](int face) -> T { return (face >= 0 && face <= Nz) ? __ldg(a.cur.w + (size_t)face * plane + col) : T(0); };
+
+  // register rings: level (or face) k+1-R+n at index n
+  T ru[2 * R], rv[2 * R], rw[2 * R], rc[NTR][2 * R];
+#pragma unroll
+  for (int n = 0; n < 2 * R; ++n) {
+    ru[n] = ld_c(a.cur.u, 1 - R + n);
+    rv[n] = ld_c(a.cur.v, 1 - R + n);
+    rw[n] = ld_w(1 - R + n);
+  }
+#pragma unroll
+  for (int t = 0; t < NTR; ++t)
+#pragma unroll
+    for (int n = 0; n < 2 * R; ++n) rc[t][n] = ld_c(a.cur.c[t], 1 - R + n);
+
+  load_level(0);
+  load_wface(0);
+  load_wface(1);
+  load_diff(0);
+  load_diff(1);
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+
+  // carried z fluxes through the bottom face of the current control volumes
+  T fz_u = a.bot[0], fz_v = a.bot[1], fz_w = T(0);
+  T fz_c[NTR];
+#pragma unroll
+  for (int t = 0; t < NTR; ++t) fz_c[t] = a.bot[2 + t];
+
+  const int rowc = (ly + H) * PW + (lx + H);   // this thread's plane index
+
+  for (int k = 0; k < Nz; ++k) {
+    // ---- prefetch the next level's planes
+    load_level(k + 1);
+    load_wface(k + 2);
+    load_diff(k + 2);
+    cp_async_commit();
+    // next ring entries (level k+1+R)
+    T nu_ = ld_c(a.cur.u, k + 1 + R), nv_ = ld_c(a.cur.v, k + 1 + R), nw_ = ld_w(k + 1 + R);
+    T nc_[NTR];
+#pragma unroll
+    for (int t = 0; t < NTR; ++t) nc_[t] = ld_c(a.cur.c[t], k + 1 + R);
+
+    const T* pU = sU + (k & 1) * PLANE;
+    const T* pV = sV + (k & 1) * PLANE;
+    const T* pW0 = sW + (k % 3) * PLANE;        // face k
+    const T* pW1 = sW + ((k + 1) % 3) * PLANE;  // face k+1
+    const T* pNm = sNu + ((k + 3) & 3) * PLANE; // level k-1
+    const T* pN0 = sNu + (k & 3) * PLANE;       // level k
+    const T* pN1 = sNu + ((k + 1) & 3) * PLANE; // level k+1
+    const T rdzc_k = __ldg(a.rdzc + k);
+    const T rdzf_k = (k >= 1) ? __ldg(a.rdzf + k) : T(0);
+    const T rdzf_k1 = (k + 1 < Nz) ? __ldg(a.rdzf + k + 1) : T(0);
+    const T rdx = a.rdx, rdy = a.rdy;
+
+    // ================= x fluxes (main threads and the east ghost column)
+    if (role == 0 || role == 2) {
+      T s[2 * R];
+      // u: advecting U = centered_x(u), advected WENO_x(u), interface lx (centre lx-1)
+#pragma unroll
+      for (int n = 0; n < 2 * R; ++n) s[n] = pU[rowc - R + n];
+      {
+        const T U = centered<T, P>(s + R - P);
+        T F = U * weno<T, R>(s, U);
+        const T du = (s[R] - s[R - 1]) * rdx;
+        if (scalar) F -= a.nu0 * du;
+        else if (stress) F -= T(2) * pN0[rowc - 1] * du;
+        if (active) FX[0 * FXS + ly * (TX + 1) + lx] = F;
+      }
+      // v at (face i, face j): advecting centered_y(u), advected WENO_x(v)
+      {
+        T cu[2 * P];
+#pragma unroll
+        for (int n = 0; n < 2 * P; ++n) cu[n] = pU[rowc + (n - P) * PW];
+        const T U = centered<T, P>(cu);
+        T sv[2 * R];
+#pragma unroll
+        for (int n = 0; n < 2 * R; ++n) sv[n] = pV[rowc - R + n];
+        T F = U * weno<T, R>(sv, U);
+        const T dvdx = (sv[R] - sv[R - 1]) * rdx;
+        if (scalar) F -= a.nu0 * dvdx;
+        else if (stress) {
+          const T nuf = T(0.25) * (pN0[rowc - 1 - PW] + pN0[rowc - PW] + pN0[rowc - 1] + pN0[rowc]);
+          const T S12 = T(0.5) * ((pU[rowc] - pU[rowc - PW]) * rdy + dvdx);
+          F -= T(2) * nuf * S12;
+        }
+        if (active) FX[1 * FXS + ly * (TX + 1) + lx] = F;
+      }
+      // w at (face i, face k): advecting centered_z(u) (own column), advected WENO_x(w)
+      {
+        T F = T(0);
+        if (k >= 1) {
+          const int p = min(P, min(k, Nz - k));
+          const T U = centered_reduced<T, R, 1>(ru, p);   // ru-1: levels k-R .. k+R-1 around face k
+          T sw[2 * R];
+#pragma unroll
+          for (int n = 0; n < 2 * R; ++n) sw[n] = pW0[rowc - R + n];
+          F = U * weno<T, R>(sw, U);
+          const T dwdx = (sw[R] - sw[R - 1]) * rdx;
+          if (scalar) F -= a.nu0 * dwdx;
+          else if (stress) {
+            const T nuf = T(0.25) * (pNm[rowc - 1] + pNm[rowc] + pN0[rowc - 1] + pN0[rowc]);
+            const T S13 = T(0.5) * ((ru[R - 1] - ru[R - 2]) * rdzf_k + dwdx);
+            F -= T(2) * nuf * S13;
+          }
+        }
+        if (active) FX[2 * FXS + ly * (TX + 1) + lx] = F;
+      }
+      // tracers at face i: U = u, advected WENO_x(c)
+#pragma unroll
+      for (int t = 0; t < NTR; ++t) {
+        const T* pC = sC + (2 * t + (k & 1)) * PLANE;
+        T sc[2 * R];
+#pragma unroll
+        for (int n = 0; n < 2 * R; ++n) sc[n] = pC[rowc - R + n];
+        const T U = pU[rowc];
+        T F = U * weno<T, R>(sc, U);
+        const T dc = (sc[R] - sc[R - 1]) * rdx;
+        if (scalar) F -= a.kappa0 * dc;
+        else if (amd) { const T* pK = sK + (3 * t + k % 3) * PLANE; F -= T(0.5) * (pK[rowc - 1] + pK[rowc]) * dc; }
+        else if (stress) F -= T(0.5) * a.inv_Pr * (pN0[rowc - 1] + pN0[rowc]) * dc;
+        if (active) FX[(3 + t) * FXS + ly * (TX + 1) + lx] = F;
+      }
+    }
+
+    // ================= y fluxes (main threads and the north ghost row)
+    if (role == 0 || role == 1) {
+      // u at (face i, face j): advecting centered_x(v), advected WENO_y(u)
+      {
+        T cv[2 * P];
+#pragma unroll
+        for (int n = 0; n < 2 * P; ++n) cv[n] = pV[rowc - P + n];
+        const T V = centered<T, P>(cv);
+        T su[2 * R];
+#pragma unroll
+        for (int n = 0; n < 2 * R; ++n) su[n] = pU[rowc + (n - R) * PW];
+        T F = V * weno<T, R>(su, V);
+        const T dudy = (su[R] - su[R - 1]) * rdy;
+        if (scalar) F -= a.nu0 * dudy;
+        else if (stress) {
+          const T nuf = T(0.25) * (pN0[rowc - 1 - PW] + pN0[rowc - PW] + pN0[rowc - 1] + pN0[rowc]);
+          const T S12 = T(0.5) * (dudy + (pV[rowc] - pV[rowc - 1]) * rdx);
+          F -= T(2) * nuf * S12;
+        }
+        if (active) FY[0 * FYS + ly * TX + lx] = F;
+      }
+      // v: advecting centered_y(v), advected WENO_y(v), interface ly (centre ly-1)
+      {
+        T sv[2 * R];
+#pragma unroll
+        for (int n = 0; n < 2 * R; ++n) sv[n] = pV[rowc + (n - R) * PW];
+        const T V = centered<T, P>(sv + R - P);
+        T F = V * weno<T, R>(sv, V);
+        const T dv = (sv[R] - sv[R - 1]) * rdy;
+        if (scalar) F -= a.nu0 * dv;
+        else if (stress) F -= T(2) * pN0[rowc - PW] * dv;
+        if (active) FY[1 * FYS + ly * TX + lx] = F;
+      }
+      // w at (face j, face k): advecting centered_z(v) (own column), advected WENO_y(w)
+      {
+        T F = T(0);
+        if (k >= 1) {
+          const int p = min(P, min(k, Nz - k));
+          const T V = centered_reduced<T, R, 1>(rv, p);
+          T sw[2 * R];
+#pragma unroll
+          for (int n = 0; n < 2 * R; ++n) sw[n] = pW0[rowc + (n - R) * PW];
+          F = V * weno<T, R>(sw, V);
+          const T dwdy = (sw[R] - sw[R - 1]) * rdy;
+          if (scalar) F -= a.nu0 * dwdy;
+          else if (stress) {
+            const T nuf = T(0.25) * (pNm[rowc - PW] + pNm[rowc] + pN0[rowc - PW] + pN0[rowc]);
+            const T S23 = T(0.5) * ((rv[R - 1] - rv[R - 2]) * rdzf_k + dwdy);
+            F -= T(2) * nuf * S23;
+          }
+        }
+        if (active) FY[2 * FYS + ly * TX + lx] = F;
+      }
+#pragma unroll
+      for (int t = 0; t < NTR; ++t) {
+        const T* pC = sC + (2 * t + (k & 1)) * PLANE;
+        T sc[2 * R];
+#pragma unroll
+        for (int n = 0; n < 2 * R; ++n) sc[n] = pC[rowc + (n - R) * PW];
+        const T V = pV[rowc];
+        T F = V * weno<T, R>(sc, V);
+        const T dc = (sc[R] - sc[R - 1]) * rdy;
+        if (scalar) F -= a.kappa0 * dc;
+        else if (amd) { const T* pK = sK + (3 * t + k % 3) * PLANE; F -= T(0.5) * (pK[rowc - PW] + pK[rowc]) * dc; }
+        else if (stress) F -= T(0.5) * a.inv_Pr * (pN0[rowc - PW] + pN0[rowc]) * dc;
+        if (active) FY[(3 + t) * FYS + ly * TX + lx] = F;
+      }
+    }
+
+    // ================= z fluxes through the top faces (main threads), registers only
+    T nz_u = T(0), nz_v = T(0), nz_w = T(0);
+    T nz_c[NTR];
+#pragma unroll
+    for (int t = 0; t < NTR; ++t) nz_c[t] = T(0);
+    if (role == 0) {
+      const bool top = (k + 1 == Nz);
+      const int r = min(R, min(k + 1, Nz - k - 1));        // centre fields at face k+1
+      // u at (face i, face k+1): advecting centered_x(w at face k+1)
+      if (top) nz_u = a.top[0];
+      else {
+        T cw[2 * P];
+#pragma unroll
+        for (int n = 0; n < 2 * P; ++n) cw[n] = pW1[rowc - P + n];
+        const T Wv = centered<T, P>(cw);
+        T F = Wv * weno_reduced<T, R>(ru, r, Wv);
+        const T dudz = (ru[R] - ru[R - 1]) * rdzf_k1;
+        if (scalar) F -= a.nu0 * dudz;
+        else if (stress) {
+          const T nuf = T(0.25) * (pN0[rowc - 1] + pN0[rowc] + pN1[rowc - 1] + pN1[rowc]);
+          const T S13 = T(0.5) * (dudz + (pW1[rowc] - pW1[rowc - 1]) * rdx);
+          F -= T(2) * nuf * S13;
+        }
+        nz_u = F;
+      }
+      if (top) nz_v = a.top[1];
+      else {
+        T cw[2 * P];
+#pragma unroll
+        for (int n = 0; n < 2 * P; ++n) cw[n] = pW1[rowc + (n - P) * PW];
+        const T Wv = centered<T, P>(cw);
+        T F = Wv * weno_reduced<T, R>(rv, r, Wv);
+        const T dvdz = (rv[R] - rv[R - 1]) * rdzf_k1;
+        if (scalar) F -= a.nu0 * dvdz;
+        else if (stress) {
+          const T nuf = T(0.25) * (pN0[rowc - PW] + pN0[rowc] + pN1[rowc - PW] + pN1[rowc]);
+          const T S23 = T(0.5) * (dvdz + (pW1[rowc] - pW1[rowc - PW]) * rdy);
+          F -= T(2) * nuf * S23;
+        }
+        nz_v = F;
+      }
+#pragma unroll
+      for (int t = 0; t < NTR; ++t) {
+        if (top) { nz_c[t] = a.top[2 + t]; continue; }
+        const T Wv = rw[R];
+        T F = Wv * weno_reduced<T, R>(rc[t], r, Wv);
+        const T dc = (rc[t][R] - rc[t][R - 1]) * rdzf_k1;
+        if (scalar) F -= a.kappa0 * dc;
+        else if (amd) {
+          const T* pK0 = sK + (3 * t + k % 3) * PLANE;
+          const T* pK1 = sK + (3 * t + (k + 1) % 3) * PLANE;
+          F -= T(0.5) * (pK0[rowc] + pK1[rowc]) * dc;
+        } else if (stress) F -= T(0.5) * a.inv_Pr * (pN0[rowc] + pN1[rowc]) * dc;
+        nz_c[t] = F;
+      }
+      // w through centre k (w interface k+1; valid faces 0..Nz)
+      {
+        const int rw_ = min(R, min(k + 1, Nz - k));
+        const int pw_ = min(P, min(k + 1, Nz - k));
+        const T Wv = centered_reduced<T, R, 0>(rw, pw_);
+        T F = Wv * weno_reduced<T, R>(rw, rw_, Wv);
+        const T dw = (rw[R] - rw[R - 1]) * rdzc_k;
+        if (scalar) F -= a.nu0 * dw;
+        else if (stress) F -= T(2) * pN0[rowc] * dw;
+        nz_w = F;
+      }
+    }
+
+    __syncthreads();
+
+    // ================= tendencies and RK update
+    if (role == 0 && active) {
+      const size_t id = (size_t)k * plane + col;
+      const T* FXu = FX + ly * (TX + 1) + lx;
+      const T* FYu = FY + ly * TX + lx;
+      // u
+      {
+        const T vbar = T(0.25) * (pV[rowc - 1] + pV[rowc] + pV[rowc - 1 + PW] + pV[rowc + PW]);
+        const T G = -(FXu[1] - FXu[0]) * rdx - (FYu[TX] - FYu[0]) * rdy - (nz_u - fz_u) * rdzc_k + a.f * vbar;
+        if (a.mode == 0) {
+          T upd = fma(a.dt_gamma, G, ru[R - 1]);
+          if (a.dt_zeta != T(0)) upd = fma(-a.dt_zeta, a.G.u[id], upd);
+          a.nxt.u[id] = upd;
+        }
+        a.G.u[id] = G;
+      }
+      // v
+      {
+        const T ubar = T(0.25) * (pU[rowc - PW] + pU[rowc + 1 - PW] + pU[rowc] + pU[rowc + 1]);
+        const T G = -(FXu[FXS + 1] - FXu[FXS]) * rdx - (FYu[FYS + TX] - FYu[FYS]) * rdy - (nz_v - fz_v) * rdzc_k - a.f * ubar;
+        if (a.mode == 0) {
+          T upd = fma(a.dt_gamma, G, rv[R - 1]);
+          if (a.dt_zeta != T(0)) upd = fma(-a.dt_zeta, a.G.v[id], upd);
+          a.nxt.v[id] = upd;
+        }
+        a.G.v[id] = G;
+      }
+      // w at face k
+      {
+        T G = T(0);
+        if (k >= 1) {
+          const T bk = buoyancy(a, rc[0][R - 1], rc[NTR > 1 ? 1 : 0][R - 1]);
+          const T bkm = buoyancy(a, rc[0][R - 2], rc[NTR > 1 ? 1 : 0][R - 2]);
+          G = -(FXu[2 * FXS + 1] - FXu[2 * FXS]) * rdx - (FYu[2 * FYS + TX] - FYu[2 * FYS]) * rdy
+              - (nz_w - fz_w) * rdzf_k + T(0.5) * (bkm + bk);
+        }
+        if (a.mode == 0) {
+          T upd = T(0);
+          if (k >= 1) {
+            upd = fma(a.dt_gamma, G, rw[R - 1]);
+            if (a.dt_zeta != T(0)) upd = fma(-a.dt_zeta, a.G.w[id], upd);
+          }
+          a.nxt.w[id] = upd;
+          if (k == Nz - 1) a.nxt.w[id + plane] = T(0);
+        }
+        a.G.w[id] = G;
+        if (k == Nz - 1) a.G.w[id + plane] = T(0);
+      }
+#pragma unroll
+      for (int t = 0; t < NTR; ++t) {
+        const T G = -(FXu[(3 + t) * FXS + 1] - FXu[(3 + t) * FXS]) * rdx - (FYu[(3 + t) * FYS + TX] - FYu[(3 + t) * FYS]) * rdy
+                    - (nz_c[t] - fz_c[t]) * rdzc_k;
+        if (a.mode == 0) {
+          T upd = fma(a.dt_gamma, G, rc[t][R - 1]);
+          if (a.dt_zeta != T(0)) upd = fma(-a.dt_zeta, a.G.c[t][id], upd);
+          a.nxt.c[t][id] = upd;
+        }
+        a.G.c[t][id] = G;
+      }
+    }
+
+    // ---- advance: carry z fluxes, shift rings
+    fz_u = nz_u; fz_v = nz_v; fz_w = nz_w;
+#pragma unroll
+    for (int t = 0; t < NTR; ++t) fz_c[t] = nz_c[t];
+#pragma unroll
+    for (int n = 0; n < 2 * R - 1; ++n) { ru[n] = ru[n + 1]; rv[n] = rv[n + 1]; rw[n] = rw[n + 1]; }
+    ru[2 * R - 1] = nu_; rv[2 * R - 1] = nv_; rw[2 * R - 1] = nw_;
+#pragma unroll
+    for (int t = 0; t < NTR; ++t) {
+#pragma unroll
+      for (int n = 0; n < 2 * R - 1; ++n) rc[t][n] = rc[t][n + 1];
+      rc[t][2 * R - 1] = nc_[t];
+    }
+    cp_async_wait_all();
+    __syncthreads();
+  }
+}
+
+template <typename T, int R, int TX, int TY>
+static size_t tendency_smem(const TendencyArgs<T>& a) {
+  constexpr int H = R;
+  constexpr int PLANE = (TX + 2 * H) * (TY + 2 * H);
+  const bool stress = (a.closure == OCN_CLOSURE_SMAGORINSKY || a.closure == OCN_CLOSURE_AMD);
+  const bool amd = (a.closure == OCN_CLOSURE_AMD);
+  const int nf = 3 + a.nt;
+  size_t planes = 2 + 2 + 3 + 2 * a.nt + (stress ? 4 : 0) + (amd ? 3 * a.nt : 0);
+  size_t bytes = sizeof(T) * (planes * PLANE + (size_t)nf * (TY * (TX + 1) + (TY + 1) * TX));
+  bytes += sizeof(int) * ((TX + 2 * H) + (TY + 2 * H));
+  return bytes;
+}
+
+template <typename T, int R, int NTR>
+static cudaError_t launch_tendency_rn(const TendencyArgs<T>& a, cudaStream_t s) {
+  constexpr int TX = 32, TY = 8;
+  auto kern = k_tendency<T, R, NTR, TX, TY>;
+  size_t smem = tendency_smem<T, R, TX, TY>(a);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.Nx + TX - 1) / TX, (a.Ny + TY - 1) / TY);
+  kern<<<grid, TileGeom<TX, TY>::NTHREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int R>
+static cudaError_t launch_tendency_r(const TendencyArgs<T>& a, cudaStream_t s) {
+  switch (a.nt) {
+    case 1: return launch_tendency_rn<T, R, 1>(a, s);
+    case 2: return launch_tendency_rn<T, R, 2>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
+cudaError_t launch_tendency(const TendencyArgs<T>& a, int weno_r, cudaStream_t s) {
+  switch (weno_r) {
+    case 3: return launch_tendency_r<T, 3>(a, s);
+    case 5: return launch_tendency_r<T, 5>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// --------------------------------------------------------------------------
+// Eddy diffusivities at cell centres (Sec. 3.1.1): Smagorinsky-Lilly and AMD.
+// One thread per cell; neighbours come through the read-only cache.
+template <typename T>
+__global__ void __launch_bounds__(256) k_closure(const ClosureArgs<T> a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  const int Nx = a.Nx, Ny = a.Ny, Nz = a.Nz;
+  if (i >= Nx || j >= Ny) return;
+  const size_t plane = (size_t)Nx * Ny;
+  const int ip = (i + 1 == Nx) ? 0 : i + 1, im = (i == 0) ? Nx - 1 : i - 1;
+  const int jp = (j + 1 == Ny) ? 0 : j + 1, jm = (j == 0) ? Ny - 1 : j - 1;
+  auto U = [&](int ii, int jj, int kk) { return __ldg(a.cur.u + (size_t)kk * plane + (size_t)jj * Nx + ii); };
+  auto V = [&](int ii, int jj, int kk) { return __ldg(a.cur.v + (size_t)kk * plane + (size_t)jj * Nx + ii); };
+  auto Wf = [&](int ii, int jj, int kk) { return __ldg(a.cur.w + (size_t)kk * plane + (size_t)jj * Nx + ii); };
+  const T rdx = a.rdx, rdy = a.rdy;
+  const T rdzc = __ldg(a.rdzc + k);
+  const T rdzf0 = (k >= 1) ? __ldg(a.rdzf + k) : T(0);
+  const T rdzf1 = (k + 1 < Nz) ? __ldg(a.rdzf + k + 1) : T(0);
+  // natural-location derivatives around the centre
+  auto dudy_ffc = [&](int ii, int jj) { return (U(ii, jj, k) - U(ii, jj == 0 ? Ny - 1 : jj - 1, k)) * rdy; };
+  auto dvdx_ffc = [&](int ii, int jj) { return (V(ii, jj, k) - V(ii == 0 ? Nx - 1 : ii - 1, jj, k)) * rdx; };
+  auto dudz_fcf = [&](int ii, int kk, T rz) { return (kk <= 0 || kk >= Nz) ? T(0) : (U(ii, j, kk) - U(ii, j, kk - 1)) * rz; };
+  auto dvdz_cff = [&](int jj, int kk, T rz) { return (kk <= 0 || kk >= Nz) ? T(0) : (V(i, jj, kk) - V(i, jj, kk - 1)) * rz; };
+  auto dwdx_fcf = [&](int ii, int kk) { return (Wf(ii, j, kk) - Wf(ii == 0 ? Nx - 1 : ii - 1, j, kk)) * rdx; };
+  auto dwdy_cff = [&](int jj, int kk) { return (Wf(i, jj, kk) - Wf(i, jj == 0 ? Ny - 1 : jj - 1, kk)) * rdy; };
+
+  const T ux = (U(ip, j, k) - U(i, j, k)) * rdx;
+  const T vy = (V(i, jp, k) - V(i, j, k)) * rdy;
+  const T wz = (Wf(i, j, k + 1) - Wf(i, j, k)) * rdzc;
+  const T uy = T(0.25) * (dudy_ffc(i, j) + dudy_ffc(ip, j) + dudy_ffc(i, jp) + dudy_ffc(ip, jp));
+  const T vx = T(0.25) * (dvdx_ffc(i, j) + dvdx_ffc(ip, j) + dvdx_ffc(i, jp) + dvdx_ffc(ip, jp));
+  const T uz = T(0.25) * (dudz_fcf(i, k, rdzf0) + dudz_fcf(ip, k, rdzf0) + dudz_fcf(i, k + 1, rdzf1) + dudz_fcf(ip, k + 1, rdzf1));
+  const T wx = T(0.25) * (dwdx_fcf(i, k) + dwdx_fcf(ip, k) + dwdx_fcf(i, k + 1) + dwdx_fcf(ip, k + 1));
+  const T vz = T(0.25) * (dvdz_cff(j, k, rdzf0) + dvdz_cff(jp, k, rdzf0) + dvdz_cff(j, k + 1, rdzf1) + dvdz_cff(jp, k + 1, rdzf1));
+  const T wy = T(0.25) * (dwdy_cff(j, k) + dwdy_cff(jp, k) + dwdy_cff(j, k + 1) + dwdy_cff(jp, k + 1));
+  const size_t id = (size_t)k * plane + (size_t)j * Nx + i;
+  const T dz = __ldg(a.dzc + k);
+
+  auto bof = [&](int kk) -> T {
+    const size_t o = (size_t)kk * plane + (size_t)j * Nx + i;
+    if (a.eos == OCN_EOS_LINEAR_TS) return a.g_alpha * (__ldg(a.cur.c[0] + o) - a.T0) - a.g_beta * (__ldg(a.cur.c[1] + o) - a.S0);
+    return __ldg(a.cur.c[0] + o);
+  };
+
+  if (a.closure == OCN_CLOSURE_SMAGORINSKY) {
+    const T S12 = T(0.5) * (uy + vx), S13 = T(0.5) * (uz + wx), S23 = T(0.5) * (vz + wy);
+    const T SS = T(2) * (ux * ux + vy * vy + wz * wz + T(2) * (S12 * S12 + S13 * S13 + S23 * S23));
+    T nu = T(0);
+    if (SS > T(0)) {
+      const T b0 = bof(k);
+      const T dbb = (k >= 1) ? (b0 - bof(k - 1)) * rdzf0 : T(0);
+      const T dbt = (k + 1 < Nz) ? (bof(k + 1) - b0) * rdzf1 : T(0);
+      const T N2 = T(0.5) * (dbb + dbt);
+      const T Delta = cbrt(a.dx * a.dy * dz);
+      const T CD = a.Cs * Delta;
+      T stab = T(1) - a.Cb * N2 * a.inv_Pr / SS;
+      stab = stab > T(0) ? stab : T(0);
+      nu = CD * CD * sqrt(SS) * sqrt(stab);
+    }
+    a.nu[id] = nu;
+  } else {  // AMD
+    const T G[3][3] = {{ux, uy, uz}, {vx, vy, vz}, {wx, wy, wz}};
+    const T D2[3] = {a.dx * a.dx, a.dy * a.dy, dz * dz};
+    T num = T(0), den = T(0);
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const T Spq = T(0.5) * (G[p][q] + G[q][p]);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) num += D2[m] * G[p][m] * G[q][m] * Spq;
+        den += G[p][q] * G[p][q];
+      }
+    T nu = (den > T(0)) ? -a.C_amd * num / den : T(0);
+    a.nu[id] = nu > T(0) ? nu : T(0);
+    for (int t = 0; t < a.nt; ++t) {
+      const T* c = a.cur.c[t];
+      auto C = [&](int ii, int jj, int kk) { return __ldg(c + (size_t)kk * plane + (size_t)jj * Nx + ii); };
+      const T c0 = C(i, j, k);
+      T dc[3];
+      dc[0] = T(0.5) * ((c0 - C(im, j, k)) + (C(ip, j, k) - c0)) * rdx;
+      dc[1] = T(0.5) * ((c0 - C(i, jm, k)) + (C(i, jp, k) - c0)) * rdy;
+      const T dcb = (k >= 1) ? (c0 - C(i, j, k - 1)) * rdzf0 : T(0);
+      const T dct = (k + 1 < Nz) ? (C(i, j, k + 1) - c0) * rdzf1 : T(0);
+      dc[2] = T(0.5) * (dcb + dct);
+      T cn = T(0), cd = T(0);
+#pragma unroll
+      for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int p = 0; p < 3; ++p) cn += D2[m] * G[p][m] * dc[m] * dc[p];
+#pragma unroll
+      for (int p = 0; p < 3; ++p) cd += dc[p] * dc[p];
+      T kap = (cd > T(0)) ? -a.C_amd * cn / cd : T(0);
+      a.kap[t][id] = kap > T(0) ? kap : T(0);
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_closure(const ClosureArgs<T>& a, cudaStream_t s) {
+  dim3 blk(32, 8);
+  dim3 grid((a.Nx + 31) / 32, (a.Ny + 7) / 8, a.Nz);
+  k_closure<T><<<grid, blk, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_tendency<float>(const TendencyArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_tendency<double>(const TendencyArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_closure<float>(const ClosureArgs<float>&, cudaStream_t);
+template cudaError_t launch_closure<double>(const ClosureArgs<double>&, cudaStream_t);
+
+}  // namespace ocn

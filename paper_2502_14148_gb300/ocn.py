@@ -1,0 +1,252 @@
+"""Thin ctypes binding of the C ABI in ``include/ocn.h``.
+
+Argument marshalling only: every step of the time integration runs in the CUDA
+kernels of ``_lib/libocn.so``.  PyTorch supplies the device arena and the CUDA
+stream.  There is no CPU fallback: if the library or a GPU is missing, the
+constructors raise.
+
+The parameter dictionary uses the keys of :mod:`paper_2502_14148_gb300.inputs`
+(the names follow the paper's ``RectilinearGrid`` / ``NonhydrostaticModel``
+keywords: size, extent, advection order, closure, coriolis, buoyancy, tracers,
+boundary fluxes).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libocn.so")
+
+OCN_FIELD_U, OCN_FIELD_V, OCN_FIELD_W, OCN_FIELD_TRACER0 = 0, 1, 2, 3
+OCN_FIELD_P, OCN_FIELD_G, OCN_FIELD_NU_E = 10, 20, 30
+OCN_OPT_GRAPHS, OCN_OPT_SYNC_CHECK = 1, 2
+MAX_TRACERS = 4
+CLOSURES = {"none": 0, "scalar": 1, "smagorinsky": 2, "amd": 3}
+EOS = {"buoyancy_tracer": 0, "linear_ts": 1}
+STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_NONFINITE", -5: "ERR_CFL",
+          -6: "ERR_TIMEOUT", -7: "ERR_UNSUPPORTED", -8: "ERR_STATE"}
+
+# Entry points declared in include/ocn.h (checked by the CPU test suite).
+EXPORTS = ["ocn_abi_version", "ocn_last_error", "ocn_grid_create", "ocn_grid_destroy", "ocn_model_create",
+           "ocn_model_destroy", "ocn_model_arena_bytes", "ocn_model_bind_arena", "ocn_set_field", "ocn_get_field",
+           "ocn_project", "ocn_time_step", "ocn_compute_tendencies", "ocn_diagnostics", "ocn_set_option",
+           "ocn_launches_per_step"]
+
+
+class OcnError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("Nx", C.c_int), ("Ny", C.c_int), ("Nz", C.c_int), ("Lx", C.c_double), ("Ly", C.c_double),
+                ("z_faces", C.POINTER(C.c_double))]
+
+
+class ModelDesc(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int), ("weno_order", C.c_int), ("closure", C.c_int),
+        ("nu", C.c_double), ("kappa", C.c_double),
+        ("Cs", C.c_double), ("Cb", C.c_double), ("Pr", C.c_double),
+        ("C_amd", C.c_double), ("f", C.c_double),
+        ("n_tracers", C.c_int), ("eos", C.c_int),
+        ("g", C.c_double), ("alpha", C.c_double), ("beta", C.c_double), ("T0", C.c_double), ("S0", C.c_double),
+        ("top_flux", C.c_double * (2 + MAX_TRACERS)), ("bottom_flux", C.c_double * (2 + MAX_TRACERS)),
+        ("fp64_pivots", C.c_int),
+    ]
+
+
+_lib = None
+
+
+def lib(path: str = LIB_PATH):
+    """Load libocn.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -m paper_2502_14148_gb300.build`")
+    L = C.CDLL(path)
+    vp, sz = C.c_void_p, C.c_size_t
+    L.ocn_abi_version.restype = C.c_int
+    L.ocn_last_error.restype = C.c_char_p
+    L.ocn_grid_create.argtypes = [C.POINTER(GridDesc), C.POINTER(vp)]
+    L.ocn_grid_destroy.argtypes = [vp]
+    L.ocn_model_create.argtypes = [vp, C.POINTER(ModelDesc), vp, C.POINTER(vp)]
+    L.ocn_model_destroy.argtypes = [vp]
+    L.ocn_model_arena_bytes.argtypes = [vp, C.POINTER(sz)]
+    L.ocn_model_bind_arena.argtypes = [vp, vp, sz]
+    L.ocn_set_field.argtypes = [vp, C.c_int, vp, sz, C.c_int]
+    L.ocn_get_field.argtypes = [vp, C.c_int, vp, sz, C.c_int]
+    L.ocn_project.argtypes = [vp]
+    L.ocn_time_step.argtypes = [vp, C.c_double, C.c_int]
+    L.ocn_compute_tendencies.argtypes = [vp]
+    L.ocn_diagnostics.argtypes = [vp, C.c_double, C.POINTER(C.c_double), C.c_int]
+    L.ocn_set_option.argtypes = [vp, C.c_int, C.c_longlong]
+    L.ocn_launches_per_step.argtypes = [vp, C.POINTER(C.c_int)]
+    for name in EXPORTS:
+        if name not in ("ocn_abi_version", "ocn_last_error", "ocn_grid_destroy", "ocn_model_destroy"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        raise OcnError(st, where, lib().ocn_last_error().decode())
+
+
+class Grid:
+    """RectilinearGrid: x, y periodic and uniform, z bounded with given face heights."""
+
+    def __init__(self, Nx: int, Ny: int, Nz: int, Lx: float, Ly: float, z_faces):
+        self.Nx, self.Ny, self.Nz, self.Lx, self.Ly = int(Nx), int(Ny), int(Nz), float(Lx), float(Ly)
+        self._zf = np.ascontiguousarray(z_faces, dtype=np.float64)
+        d = GridDesc(self.Nx, self.Ny, self.Nz, self.Lx, self.Ly, self._zf.ctypes.data_as(C.POINTER(C.c_double)))
+        h = C.c_void_p()
+        _check(lib().ocn_grid_create(C.byref(d), C.byref(h)), "ocn_grid_create")
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().ocn_grid_destroy(self._h)
+            self._h = None
+
+
+class Model:
+    """NonhydrostaticModel on the GPU.  ``params``: a workload dict (see inputs.config)."""
+
+    def __init__(self, params: dict, device=None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (the library has no CPU path)")
+        p = dict(params)
+        self.params = p
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.tracers = list(p.get("tracers", ["b"]))
+        self.precision = int(p.get("precision", 32))
+        self.dtype = torch.float32 if self.precision == 32 else torch.float64
+        self.np_dtype = np.float32 if self.precision == 32 else np.float64
+        self.grid = Grid(p["Nx"], p["Ny"], p["Nz"], p["Lx"], p["Ly"], p["z_faces"])
+        self.Nx, self.Ny, self.Nz = self.grid.Nx, self.grid.Ny, self.grid.Nz
+        d = ModelDesc()
+        d.precision = self.precision
+        d.weno_order = int(p.get("weno_order", 5))
+        d.closure = CLOSURES[p.get("closure", "none")]
+        d.nu, d.kappa = float(p.get("nu", 0.0)), float(p.get("kappa", 0.0))
+        d.Cs, d.Cb, d.Pr = float(p.get("Cs", 0.16)), float(p.get("Cb", 1.0)), float(p.get("Pr", 1.0))
+        d.C_amd = float(p.get("C_amd", 1.0 / 12.0))
+        d.f = float(p.get("f", 0.0))
+        d.n_tracers = len(self.tracers)
+        d.eos = EOS[p.get("eos", "buoyancy_tracer")]
+        d.g, d.alpha, d.beta = float(p.get("g", 9.81)), float(p.get("alpha", 2e-4)), float(p.get("beta", 8e-4))
+        d.T0, d.S0 = float(p.get("T0", 20.0)), float(p.get("S0", 35.0))
+        for n, name in enumerate(["u", "v"] + self.tracers):
+            d.top_flux[n] = float(p.get("top_flux", {}).get(name, 0.0))
+            d.bottom_flux[n] = float(p.get("bottom_flux", {}).get(name, 0.0))
+        d.fp64_pivots = int(p.get("fp64_pivots", -1))
+        self._desc = d
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+            h = C.c_void_p()
+            _check(lib().ocn_model_create(self.grid._h, C.byref(d), C.c_void_p(self.stream.cuda_stream), C.byref(h)),
+                   "ocn_model_create")
+            self._h = h
+            nbytes = C.c_size_t()
+            _check(lib().ocn_model_arena_bytes(self._h, C.byref(nbytes)), "ocn_model_arena_bytes")
+            self.arena_bytes = nbytes.value
+            with torch.cuda.stream(self.stream):
+                self.arena = torch.empty(self.arena_bytes, dtype=torch.uint8, device=self.device)
+            _check(lib().ocn_model_bind_arena(self._h, C.c_void_p(self.arena.data_ptr()), self.arena_bytes),
+                   "ocn_model_bind_arena")
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().ocn_model_destroy(self._h)
+            self._h = None
+
+    # ------------------------------------------------------------------ fields
+    def fid(self, name: str) -> int:
+        if name.startswith("G_"):
+            return OCN_FIELD_G + self.fid(name[2:])
+        table = {"u": OCN_FIELD_U, "v": OCN_FIELD_V, "w": OCN_FIELD_W, "p": OCN_FIELD_P, "nu_e": OCN_FIELD_NU_E}
+        if name in table:
+            return table[name]
+        return OCN_FIELD_TRACER0 + self.tracers.index(name)
+
+    def shape(self, name: str):
+        base = name[2:] if name.startswith("G_") else name
+        return (self.Nz + 1 if base == "w" else self.Nz, self.Ny, self.Nx)
+
+    def set(self, project: bool = True, **fields):
+        """set!: copy fields in (numpy or torch); projects the velocity unless project=False."""
+        import torch
+        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+            for name, arr in fields.items():
+                t = torch.as_tensor(arr).to(device=self.device, dtype=self.dtype).contiguous()
+                assert tuple(t.shape) == self.shape(name), (name, tuple(t.shape))
+                _check(lib().ocn_set_field(self._h, self.fid(name), C.c_void_p(t.data_ptr()),
+                                           t.numel() * t.element_size(), 1), "ocn_set_field")
+                self.stream.synchronize()
+        if project and any(k in fields for k in ("u", "v", "w")):
+            self.project()
+
+    def get(self, name: str):
+        """A device tensor copy of a field."""
+        import torch
+        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+            out = torch.empty(self.shape(name), dtype=self.dtype, device=self.device)
+            _check(lib().ocn_get_field(self._h, self.fid(name), C.c_void_p(out.data_ptr()),
+                                       out.numel() * out.element_size(), 1), "ocn_get_field")
+        self.stream.synchronize()
+        return out
+
+    def get_numpy(self, name: str) -> np.ndarray:
+        return self.get(name).cpu().numpy()
+
+    def set_host(self, name: str, host_tensor):
+        """Copy from (pinned) host memory through the C ABI's host path."""
+        _check(lib().ocn_set_field(self._h, self.fid(name), C.c_void_p(host_tensor.data_ptr()),
+                                   host_tensor.numel() * host_tensor.element_size(), 0), "ocn_set_field")
+
+    def get_host(self, name: str, host_tensor):
+        _check(lib().ocn_get_field(self._h, self.fid(name), C.c_void_p(host_tensor.data_ptr()),
+                                   host_tensor.numel() * host_tensor.element_size(), 0), "ocn_get_field")
+
+    # ------------------------------------------------------------------ stepping
+    def project(self):
+        _check(lib().ocn_project(self._h), "ocn_project")
+
+    def time_step(self, dt: float, nsteps: int = 1):
+        """time_step!: nsteps RK3 steps (enqueued on the model stream)."""
+        _check(lib().ocn_time_step(self._h, float(dt), int(nsteps)), "ocn_time_step")
+
+    def compute_tendencies(self) -> dict:
+        _check(lib().ocn_compute_tendencies(self._h), "ocn_compute_tendencies")
+        return {n: self.get("G_" + n) for n in ["u", "v", "w"] + self.tracers}
+
+    def diagnostics(self, dt: float = 0.0, check: bool = False) -> dict:
+        nt = len(self.tracers)
+        out = (C.c_double * (nt + 6))()
+        st = lib().ocn_diagnostics(self._h, float(dt), out, nt + 6)
+        if check or st not in (0, -4, -5):
+            _check(st, "ocn_diagnostics")
+        d = {f"sum_{t}": out[n] for n, t in enumerate(self.tracers)}
+        d.update(sum_u=out[nt], sum_v=out[nt + 1], sum_w=out[nt + 2], max_div=out[nt + 3], cfl=out[nt + 4],
+                 nonfinite=int(out[nt + 5]), status=STATUS.get(st, st))
+        return d
+
+    def set_option(self, option: int, value: int):
+        _check(lib().ocn_set_option(self._h, int(option), int(value)), "ocn_set_option")
+
+    def launches_per_step(self) -> int:
+        n = C.c_int()
+        _check(lib().ocn_launches_per_step(self._h, C.byref(n)), "ocn_launches_per_step")
+        return n.value
+
+    def synchronize(self):
+        self.stream.synchronize()

@@ -1,0 +1,61 @@
+"""The C-ABI library builds, loads and exports every entry point include/ocn.h declares.
+
+No compute calls are made (this runs on machines without a GPU); only pure
+host-side entry points (version, argument validation of the grid) are invoked.
+"""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "ocn.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ocn_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libocn():
+    from paper_2502_14148_gb300 import build, ocn
+    build.build()
+    return ocn.lib()
+
+
+def test_every_declared_symbol_is_exported(libocn):
+    from paper_2502_14148_gb300 import ocn
+    names = _declared()
+    assert len(names) >= 16
+    for n in names:
+        assert hasattr(libocn, n), n
+    assert sorted(ocn.EXPORTS) == names
+
+
+def test_abi_version_and_grid_validation(libocn):
+    from paper_2502_14148_gb300 import ocn
+    assert libocn.ocn_abi_version() == 1
+    zf = np.linspace(-1, 0, 9)
+    g = ocn.Grid(16, 12, 8, 1.0, 1.0, zf)          # host-only call
+    assert g._h
+    for bad in [(15, 12, 8), (10, 12, 8), (16, 12, 0), (2, 12, 8)]:
+        with pytest.raises(ocn.OcnError) as ei:
+            ocn.Grid(*bad, 1.0, 1.0, np.linspace(-1, 0, max(bad[2], 0) + 1))
+        assert ei.value.status == -1
+    with pytest.raises(ocn.OcnError):
+        ocn.Grid(16, 12, 8, 1.0, 1.0, zf[::-1])       # descending faces
+    assert "ascending" in libocn.ocn_last_error().decode()
+
+
+def test_no_oracle_in_the_product_path():
+    """The CUDA library and its binding never import, link or call the oracle."""
+    pat = re.compile(r"(from|import)\s+oracle|liboracle|ocn_oracle|\borc_[a-z_]+\s*\(")
+    pkg = os.path.join(ROOT, "paper_2502_14148_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
+                txt = open(os.path.join(dirpath, f), encoding="utf-8").read()
+                assert not pat.search(txt), f
