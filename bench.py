@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Benchmark: cell-RK3-substeps/s of the nonhydrostatic Boussinesq RK3 step.
+
+Workload (default ``les_512``): 512 x 512 x 256 cells, FP32, WENO9 advection,
+Smagorinsky-Lilly closure, T and S with a linear EOS, f = 1e-4, surface stress
+and heat flux, dt = 2 s, seeded synthetic initial state.  A "step" is one full
+RK3 step (three substages of closure + fused tendency + pressure projection).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank advances its own replica on its own GPU (the
+single-domain LES has no data-parallel split without halo and transpose
+exchanges); the value is the aggregate over ranks.  The model state (1.3 GB)
+is larger than L2, so no L2 flush is needed between steps.  One JSON line is
+printed by rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+CPU_SAMPLE = dict(Nx=128, Ny=128, Nz=64)     # bounded oracle sample, same spacing and physics
+
+
+# ------------------------------------------------------------------ algorithmic counts
+def weno_flops(r: int) -> int:
+    """Floating-point operations of one WENO(2r-1) reconstruction as the method states it
+    (an FMA counts 2): r substencil dot products (2r^2), r smoothness quadratic forms evaluated
+    as sum_a t_a (sum_{b>=a} C_ab t_b) (r(r+1) + 2r each), WENO-Z weights (tau: 2; per
+    substencil: +eps, reciprocal, ratio, square+1, times d: 6), sum of weights (r), weighted sum
+    (2r), final normalisation (2)."""
+    return 2 * r * r + r * (r * (r + 1) + 2 * r) + 2 + 6 * r + r + 2 * r + 2
+
+
+def tendency_flops_per_cell(p: dict) -> int:
+    """Algorithmic FP operations of the fused tendency + RK update per cell (one substage)."""
+    r = (p["weno_order"] + 1) // 2
+    P = r - 1
+    nt = len(p["tracers"])
+    nrec = 9 + 3 * nt                       # 3 momentum components x 3 directions + tracers x 3
+    flops = nrec * weno_flops(r)
+    flops += 9 * 3 * P                      # centered advecting velocities (symmetric form)
+    flops += nrec                           # flux = velocity x reconstruction
+    flops += (3 + nt) * 9                   # flux divergence: 3 differences + 3 scaled sums per field
+    closure = p.get("closure", "none")
+    if closure in ("smagorinsky", "amd"):
+        flops += 9 * 11 + 3 * nt * 5         # eddy stress fluxes (edge averages, strain, flux) + tracer fluxes
+    elif closure == "scalar":
+        flops += nrec * 3
+    flops += 2 * 5                          # Coriolis
+    flops += 2 * 4 + 6                      # hydrostatic pressure gradient + column integral
+    flops += (3 + nt) * 4                   # RK3 update
+    return flops
+
+
+def substep_bytes_per_cell(p: dict) -> int:
+    """Algorithmic HBM bytes of one RK3 substage per cell: (4n + 9) words, n = 3 + tracers
+    (state in, G^{m-1} in, G^m out, state out; projection: read u~ for div, write the spectrum,
+    tridiagonal read/write, inverse read/write, read p for the correction)."""
+    n = 3 + len(p["tracers"])
+    w = 4 if p.get("precision", 32) == 32 else 8
+    return (4 * n + 9) * w
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(MEASURED_PEAKS) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured", "sm_max_mhz": float(d.get("sm_max_mhz", SM_MAX_MHZ))}
+    except Exception:
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "source": "fallback", "sm_max_mhz": SM_MAX_MHZ}
+
+
+def profiled_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, valid only while the kernel
+    source hash recorded there matches the current source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
+    src = os.path.join(ROOT, "paper_2502_14148_gb300", "csrc", "tendency.cu" if kernel == "tendency" else "poisson.cu")
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        fields = {}
+        for line in open(path):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                fields[k.strip()] = v.strip()
+        if fields.get("source_sha256_16") != h:
+            return None
+        return float(fields["dram_bytes_per_full_launch"])
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs (our own child process)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.rows = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(index)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        if not self.rows:
+            return None
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------ distributed (replicas)
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        try:
+            import torch
+            if not torch.cuda.is_available():
+                backend = "gloo"
+            else:
+                torch.cuda.set_device(local)
+        except Exception:
+            backend = "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ oracle legs
+def oracle_rate(workload: str, steps: int, warmup: int = 0):
+    """Time the FP64 oracle (as it stands) on the bounded sample; returns (cell-substeps/s, s/step, cores)."""
+    from oracle import oracle
+    from paper_2502_14148_gb300 import inputs
+    cores = os.cpu_count() or 1
+    p = inputs.config(workload, **CPU_SAMPLE)
+    p["nthreads"] = cores
+    m = oracle.OracleModel(p)
+    m.set(**inputs.initial_state(p))
+    m.project(1.0)
+    if warmup:
+        m.time_step(p["dt"], warmup)
+    t0 = time.perf_counter()
+    m.time_step(p["dt"], steps)
+    dt = time.perf_counter() - t0
+    cells = p["Nx"] * p["Ny"] * p["Nz"]
+    return cells * 3 * steps / dt, dt / steps, cores, f"{p['Nx']}x{p['Ny']}x{p['Nz']} cells of the {workload} physics and spacing, {steps} RK3 step(s), FP64 oracle"
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    from paper_2502_14148_gb300 import inputs
+    p = inputs.config(args.workload)
+    rate, sps, cores, sample = oracle_rate(args.workload, args.steps, args.warmup)
+    line = {"metric": "cell-RK3-substeps/sec", "value": rate, "unit": "cell-substeps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": workload_desc(p), "sample": sample},
+            "cpu_baseline": {"value": rate, "unit": "cell-substeps/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": rate, "unit": "cell-substeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_desc(p: dict) -> str:
+    return (f"{p['name']}: {p['Nx']}x{p['Ny']}x{p['Nz']} FP{p['precision']}, WENO{p['weno_order']}, {p['closure']}, "
+            f"tracers {','.join(p['tracers'])}, f={p.get('f', 0)}, dt={p['dt']} s")
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_2502_14148_gb300 import build, inputs, ocn
+
+    if rank == 0 or world == 1:
+        build.build()
+    barrier(world)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    p = inputs.config(args.workload)
+    cells = p["Nx"] * p["Ny"] * p["Nz"]
+    st = inputs.initial_state(p, seed=inputs.SEED + rank)
+    model = ocn.Model(p, device=dev)
+    model.set(**st)
+    dt = p["dt"]
+
+    model.time_step(dt, args.warmup)              # warm-up (graph capture, clocks)
+    model.synchronize()
+    # ---- timed region: K steps, kernel events on the model stream
+    model.set_option(ocn.OCN_OPT_KERNEL_TIMING, 1)
+    clocks = ClockSampler(local)
+    time.sleep(0.4)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(model.stream)
+    model.time_step(dt, args.steps)
+    e1.record(model.stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    ck = clocks.stop()
+    ms_local = e0.elapsed_time(e1)
+    ktimes = model.kernel_times()
+    model.set_option(ocn.OCN_OPT_KERNEL_TIMING, 0)
+    launches = sum(c for c, _ in ktimes.values())
+    ms = max_over_ranks(ms_local, world)
+    value = cells * 3 * args.steps * world / (ms * 1e-3)
+    d = model.diagnostics(dt)
+
+    # ---- e2e: through the C ABI with pinned host buffers, copies inside the timed region
+    names = ["u", "v", "w"] + model.tracers
+    host_in = {n: torch.from_numpy(np.ascontiguousarray(st[n], dtype=np.float32)).pin_memory() for n in names}
+    host_out = {n: torch.empty(model.shape(n), dtype=torch.float32).pin_memory() for n in names}
+    h2d = sum(t.numel() * t.element_size() for t in host_in.values())
+    d2h = sum(t.numel() * t.element_size() for t in host_out.values())
+    k_e2e = max(1, min(args.steps, 5))
+    model.set_option(ocn.OCN_OPT_GRAPHS, 1)
+    for n in names:                                # warm the e2e path once
+        model.set_host(n, host_in[n])
+    model.time_step(dt, 1)
+    for n in names:
+        model.get_host(n, host_out[n])
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        for n in names:
+            model.set_host(n, host_in[n])
+        model.time_step(dt, 1)
+        for n in names:
+            model.get_host(n, host_out[n])
+    t_e2e = max_over_ranks(time.perf_counter() - t0, world)
+    e2e_value = cells * 3 * k_e2e * world / t_e2e
+
+    if rank != 0:
+        return 0
+    peaks = measured_peaks()
+    # dominant kernel and its roofline
+    per_class = {k: {"launches": c, "ms_total": t, "ms_per_launch": (t / c if c else None),
+                     "share": (t / sum(x for _, x in ktimes.values()))} for k, (c, t) in ktimes.items() if c}
+    dom = max(per_class, key=lambda k: per_class[k]["ms_total"])
+    flops_cell = tendency_flops_per_cell(p)
+    clock_mhz = peaks["sm_max_mhz"]
+    if dom == "tendency":
+        t_launch = per_class["tendency"]["ms_per_launch"] * 1e-3
+        achieved = flops_cell * cells / t_launch / 1e12
+        peak = SMS * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
+        traffic = profiled_traffic("tendency", p["name"])
+        roof = {"bound": "alu", "kernel": "k_tendency", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "algorithmic": f"{flops_cell} FP32 flops per cell (FMA = 2) x {cells} cells per launch",
+                "peak_source": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 x {clock_mhz:.0f} MHz"}
+    else:
+        roof = None
+    sub_bytes = substep_bytes_per_cell(p) * cells
+    t_sub = ms / args.steps / 3 * 1e-3
+    line = {
+        "metric": "cell-RK3-substeps/sec", "value": value, "unit": "cell-substeps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if p["precision"] == 32 else "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_desc(p), "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (model state 1.3 GB)", "graphs": False,
+                   "kernel_events": True},
+        "roofline": roof,
+        "substep_hbm": {"achieved": sub_bytes / t_sub / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": sub_bytes / t_sub / 1e9 / peaks["hbm_gbs"], "peak_source": peaks["source"],
+                        "algorithmic": f"{substep_bytes_per_cell(p)} B per cell per substage"},
+        "kernels": per_class,
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_value, "unit": "cell-substeps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": k_e2e, "path": "ocn_set_field/ocn_time_step/ocn_get_field with pinned host buffers"},
+        "clocks": ck,
+        "checks": {"max_div": d["max_div"], "cfl": d["cfl"], "nonfinite": d["nonfinite"]},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        rate, sps, cores, sample = oracle_rate(args.workload, 1)
+        line["cpu_baseline"] = {"value": rate, "unit": "cell-substeps/s", "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="les_512")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    try:
+        if args.impl == "reference":
+            return run_reference(args, world, rank)
+        return run_ours(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -76,7 +76,9 @@ enum { OCN_EOS_BUOYANCY_TRACER = 0, OCN_EOS_LINEAR_TS = 1 };
 enum {
   OCN_FIELD_U = 0, OCN_FIELD_V = 1, OCN_FIELD_W = 2,
   OCN_FIELD_TRACER0 = 3,     /* tracer n is OCN_FIELD_TRACER0 + n */
-  OCN_FIELD_P = 10,          /* kinematic pressure of the last projection, zero volume mean */
+  OCN_FIELD_P = 10,          /* pressure of the last projection, zero volume mean: after ocn_project the
+                                kinematic pressure; after ocn_time_step the nonhydrostatic part p_nh of the
+                                last substage (Eq. pressure-decomposition), scaled by 1/((gamma-zeta) dt) */
   OCN_FIELD_G = 20,          /* tendency G of field f is OCN_FIELD_G + f (G^{m-1} after a step) */
   OCN_FIELD_NU_E = 30        /* eddy viscosity at cell centres (Smagorinsky-Lilly, AMD) */
 };
@@ -155,12 +157,17 @@ ocn_status ocn_project(ocn_model* model);
 /* Advance nsteps full RK3 steps of size dt (three substages each; Appendix A.1
  * Eq. rk3 and Appendix A.2).  Each substage: eddy diffusivities, fused
  * tendency + RK update, then the pressure projection with step
- * (gamma_m - zeta_m) dt.  Errors: OCN_ERR_ARG (nsteps < 0, dt not finite),
+ * (gamma_m - zeta_m) dt.  Buoyancy enters through the hydrostatic split of
+ * Eq. pressure-decomposition: -grad_h p_hy in the horizontal momentum
+ * equations, p_hy integrated up each column, the w equation without b (the
+ * result equals the unsplit form up to rounding, since the two differ by a
+ * discrete gradient that the projection removes).  Errors: OCN_ERR_ARG (nsteps < 0, dt not finite),
  * OCN_ERR_STATE, OCN_ERR_CUDA. */
 ocn_status ocn_time_step(ocn_model* model, double dt, int nsteps);
 
 /* Evaluate the tendencies G of every prognostic field at the current state
- * (no stepping; readable as OCN_FIELD_G + f).  Errors: OCN_ERR_STATE, OCN_ERR_CUDA. */
+ * (no stepping; readable as OCN_FIELD_G + f), in the unsplit form: b
+ * interpolated to the w faces appears in G_w.  Errors: OCN_ERR_STATE, OCN_ERR_CUDA. */
 ocn_status ocn_compute_tendencies(ocn_model* model);
 
 /* Diagnostics in FP64 (synchronises the stream).  out[0..n_tracers-1] = sum V c_n;
@@ -172,9 +179,29 @@ ocn_status ocn_diagnostics(ocn_model* model, double dt, double* out, int nout);
 
 /* Options.  OCN_OPT_GRAPHS: 1 (default) replays each time step from a CUDA
  * graph captured on first use per dt; 0 launches kernels directly.
- * OCN_OPT_SYNC_CHECK: 1 synchronises and checks for errors after every kernel. */
-enum { OCN_OPT_GRAPHS = 1, OCN_OPT_SYNC_CHECK = 2 };
+ * OCN_OPT_SYNC_CHECK: 1 synchronises and checks for errors after every kernel.
+ * OCN_OPT_KERNEL_TIMING: 1 launches directly and brackets every kernel with
+ * CUDA events on the model stream (read with ocn_kernel_times); 0 (default) off. */
+enum { OCN_OPT_GRAPHS = 1, OCN_OPT_SYNC_CHECK = 2, OCN_OPT_KERNEL_TIMING = 3 };
 ocn_status ocn_set_option(ocn_model* model, int option, long long value);
+
+/* Kernel classes reported by ocn_kernel_times. */
+enum {
+  OCN_K_CLOSURE = 0,     /* eddy diffusivities */
+  OCN_K_TENDENCY = 1,    /* fused tendency + RK update */
+  OCN_K_DIV_FFTX = 2,    /* divergence + real FFT in x */
+  OCN_K_FFT_Y = 3,       /* complex FFT in y (forward and inverse) */
+  OCN_K_TRIDIAG = 4,     /* tridiagonal solve in z */
+  OCN_K_GAUGE = 5,       /* pressure gauge */
+  OCN_K_IFFTX = 6,       /* inverse real FFT in x */
+  OCN_K_CORRECT = 7,     /* velocity correction */
+  OCN_K_COUNT = 8
+};
+
+/* Launch counts and summed device milliseconds per kernel class, accumulated
+ * since OCN_OPT_KERNEL_TIMING was last set to 1; synchronises the stream.
+ * counts and ms must hold OCN_K_COUNT entries.  Errors: OCN_ERR_ARG, OCN_ERR_CUDA. */
+ocn_status ocn_kernel_times(ocn_model* model, int* counts, double* ms);
 
 /* Number of kernel launches the last ocn_time_step issued per RK3 step. */
 ocn_status ocn_launches_per_step(const ocn_model* model, int* launches);

@@ -118,9 +118,35 @@ struct ocn_model {
   // unchanged (the EOS only sees differences, and the advection of a constant
   // by a divergence-free velocity vanishes) while FP32 keeps ~20x more digits.
   double cref[OCN_MAX_TRACERS] = {0, 0, 0, 0};
+  // kernel timing (OCN_OPT_KERNEL_TIMING)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  struct Rec { int kclass; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  cudaEvent_t ev_open = nullptr;
+  LaunchHook hook;
 };
 
 namespace {
+
+cudaEvent_t take_event(ocn_model* m) {
+  if (!m->ev_pool.empty()) { cudaEvent_t e = m->ev_pool.back(); m->ev_pool.pop_back(); return e; }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+void hook_before(void* ctx, int) {
+  ocn_model* m = static_cast<ocn_model*>(ctx);
+  m->ev_open = take_event(m);
+  cudaEventRecord(m->ev_open, m->stream);
+}
+void hook_after(void* ctx, int kclass) {
+  ocn_model* m = static_cast<ocn_model*>(ctx);
+  cudaEvent_t b = take_event(m);
+  cudaEventRecord(b, m->stream);
+  m->recs.push_back({kclass, m->ev_open, b});
+  m->ev_open = nullptr;
+}
 
 size_t field_elems(const ocn_model* m, int f) {
   size_t plane = (size_t)m->g->Nx * m->g->Ny;
@@ -246,7 +272,10 @@ cudaError_t enqueue_closure(ocn_model* m, int which) {
   c.eos = m->d.eos;
   c.g_alpha = (T)(m->d.g * m->d.alpha); c.g_beta = (T)(m->d.g * m->d.beta);
   c.T0 = (T)(m->d.T0 - m->cref[0]); c.S0 = (T)(m->d.S0 - m->cref[1]);
-  return launch_closure<T>(c, m->stream);
+  m->hook.pre(OCN_K_CLOSURE);
+  cudaError_t e = launch_closure<T>(c, m->stream);
+  m->hook.post(OCN_K_CLOSURE);
+  return e;
 }
 
 template <typename T>
@@ -259,9 +288,10 @@ cudaError_t enqueue_tendency(ocn_model* m, int which, double dt_gamma, double dt
   a.G = g_ptrs<T>(m);
   a.nu = m->off_nu ? at<T>(m, m->off_nu) : nullptr;
   for (int t = 0; t < kMaxTracers; ++t) a.kap[t] = m->off_kap[t] ? at<T>(m, m->off_kap[t]) : nullptr;
-  a.rdzc = at<T>(m, m->off_rdzc); a.rdzf = at<T>(m, m->off_rdzf);
+  a.rdzc = at<T>(m, m->off_rdzc); a.rdzf = at<T>(m, m->off_rdzf); a.dzf = at<T>(m, m->off_dzf);
   a.Nx = g->Nx; a.Ny = g->Ny; a.Nz = g->Nz; a.nt = m->d.n_tracers;
   a.rdx = (T)(g->Nx / g->Lx); a.rdy = (T)(g->Ny / g->Ly);
+  for (int t = 0; t < kMaxTracers; ++t) a.cref[t] = (T)m->cref[t];
   a.closure = m->d.closure;
   a.nu0 = (T)m->d.nu; a.kappa0 = (T)m->d.kappa; a.inv_Pr = (T)(1.0 / m->d.Pr);
   a.f = (T)m->d.f;
@@ -271,7 +301,10 @@ cudaError_t enqueue_tendency(ocn_model* m, int which, double dt_gamma, double dt
   for (int n = 0; n < 2 + kMaxTracers; ++n) { a.top[n] = (T)m->d.top_flux[n]; a.bot[n] = (T)m->d.bottom_flux[n]; }
   a.dt_gamma = (T)dt_gamma; a.dt_zeta = (T)dt_zeta;
   a.mode = mode;
-  return launch_tendency<T>(a, m->R, m->stream);
+  m->hook.pre(OCN_K_TENDENCY);
+  cudaError_t e = launch_tendency<T>(a, m->R, m->stream);
+  m->hook.post(OCN_K_TENDENCY);
+  return e;
 }
 
 cudaError_t check_sync(ocn_model* m, cudaError_t e) {
@@ -293,7 +326,7 @@ cudaError_t enqueue_step(ocn_model* m, double dt, int* which, int* nlaunch) {
     if (e != cudaSuccess) return e;
     ++n;
     int np = 0;
-    e = check_sync(m, launch_projection<T>(poisson_args<T>(m, 1 - *which, (gam[st] - zet[st]) * dt), m->stream, &np));
+    e = check_sync(m, launch_projection<T>(poisson_args<T>(m, 1 - *which, (gam[st] - zet[st]) * dt), m->stream, &np, m->hook));
     if (e != cudaSuccess) return e;
     n += np;
     *which = 1 - *which;
@@ -304,7 +337,7 @@ cudaError_t enqueue_step(ocn_model* m, double dt, int* which, int* nlaunch) {
 
 template <typename T>
 ocn_status time_step_t(ocn_model* m, double dt, int nsteps) {
-  const bool use_graph = m->graphs && m->stream != nullptr && !m->sync_check;
+  const bool use_graph = m->graphs && m->stream != nullptr && !m->sync_check && !m->timing;
   for (int s = 0; s < nsteps; ++s) {
     if (!use_graph) {
       int w = m->cur, nl = 0;
@@ -347,6 +380,11 @@ ocn_status time_step_t(ocn_model* m, double dt, int nsteps) {
 void drop_graphs(ocn_model* m) {
   for (auto& kv : m->graph_cache) cudaGraphExecDestroy(kv.second);
   m->graph_cache.clear();
+}
+
+void drop_events(ocn_model* m) {
+  for (auto& r : m->recs) { m->ev_pool.push_back(r.a); m->ev_pool.push_back(r.b); }
+  m->recs.clear();
 }
 
 bool field_valid(const ocn_model* m, int field) {
@@ -438,6 +476,10 @@ void ocn_model_destroy(ocn_model* model) {
   {
     DeviceGuard dg(model->dev);
     drop_graphs(model);
+    cudaStreamSynchronize(model->stream);
+    drop_events(model);
+    for (cudaEvent_t e : model->ev_pool) cudaEventDestroy(e);
+    model->ev_pool.clear();
   }
   delete model;
 }
@@ -600,7 +642,31 @@ ocn_status ocn_set_option(ocn_model* m, int option, long long value) {
   if (!m) return fail(OCN_ERR_ARG, "null argument");
   if (option == OCN_OPT_GRAPHS) { m->graphs = value != 0; return OCN_OK; }
   if (option == OCN_OPT_SYNC_CHECK) { m->sync_check = value != 0; return OCN_OK; }
+  if (option == OCN_OPT_KERNEL_TIMING) {
+    DeviceGuard dg(m->dev);
+    cudaStreamSynchronize(m->stream);
+    drop_events(m);
+    m->timing = value != 0;
+    m->hook = LaunchHook();
+    if (m->timing) { m->hook.before = hook_before; m->hook.after = hook_after; m->hook.ctx = m; }
+    return OCN_OK;
+  }
   return fail(OCN_ERR_ARG, "unknown option");
+}
+
+ocn_status ocn_kernel_times(ocn_model* m, int* counts, double* ms) {
+  if (!m || !counts || !ms) return fail(OCN_ERR_ARG, "null argument");
+  DeviceGuard dg(m->dev);
+  cudaError_t e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel timing synchronise");
+  for (int k = 0; k < OCN_K_COUNT; ++k) { counts[k] = 0; ms[k] = 0.0; }
+  for (const auto& r : m->recs) {
+    float t = 0.0f;
+    e = cudaEventElapsedTime(&t, r.a, r.b);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel timing read");
+    if (r.kclass >= 0 && r.kclass < OCN_K_COUNT) { counts[r.kclass] += 1; ms[r.kclass] += t; }
+  }
+  return OCN_OK;
 }
 
 ocn_status ocn_launches_per_step(const ocn_model* m, int* launches) {

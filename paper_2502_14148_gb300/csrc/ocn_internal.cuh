@@ -46,8 +46,10 @@ struct TendencyArgs {
   const T* kap[kMaxTracers];  // AMD tracer diffusivities
   const T* rdzc;          // 1/dz_c[k], k < Nz
   const T* rdzf;          // 1/dz_f[k], 1 <= k < Nz (entries 0, Nz unused)
+  const T* dzf;           // dz_f[k]
   int Nx, Ny, Nz, nt;
   T rdx, rdy;
+  T cref[kMaxTracers];    // tracers are stored as c - cref: G gains -cref div(u)
   int closure;
   T nu0, kappa0;          // scalar diffusivity
   T inv_Pr;
@@ -114,10 +116,20 @@ struct DiagArgs {
   int nblocks;
 };
 
+// Optional per-launch hook (kernel timing): called around every kernel launch.
+struct LaunchHook {
+  void (*before)(void* ctx, int kclass) = nullptr;
+  void (*after)(void* ctx, int kclass) = nullptr;
+  void* ctx = nullptr;
+  void pre(int k) const { if (before) before(ctx, k); }
+  void post(int k) const { if (after) after(ctx, k); }
+};
+
 // Launchers (return the launch error; kernels are enqueued on `s`).
 template <typename T> cudaError_t launch_closure(const ClosureArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_tendency(const TendencyArgs<T>& a, int weno_r, cudaStream_t s);
-template <typename T> cudaError_t launch_projection(const PoissonArgs<T>& a, cudaStream_t s, int* nlaunch);
+template <typename T> cudaError_t launch_projection(const PoissonArgs<T>& a, cudaStream_t s, int* nlaunch,
+                                                    const LaunchHook& hook = LaunchHook());
 template <typename T> cudaError_t launch_diagnostics(const DiagArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_fill(T* p, size_t n, T v, cudaStream_t s);
 template <typename T> cudaError_t launch_shift(T* p, size_t n, T v, cudaStream_t s);

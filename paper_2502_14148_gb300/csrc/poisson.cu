@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(256) k_correct(const PoissonArgs<T> a) {
 static int rows_per_block(int M) { return M >= 2048 ? 1 : 2048 / M; }
 
 template <typename T>
-cudaError_t launch_projection(const PoissonArgs<T>& a, cudaStream_t s, int* nlaunch) {
+cudaError_t launch_projection(const PoissonArgs<T>& a, cudaStream_t s, int* nlaunch, const LaunchHook& hook) {
   typedef typename CT<T>::type C;
   cudaError_t e;
   int n = 0;
@@ -328,33 +328,47 @@ cudaError_t launch_projection(const PoissonArgs<T>& a, cudaStream_t s, int* nlau
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_ifftx<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx);
   if (e != cudaSuccess) return e;
+  hook.pre(OCN_K_DIV_FFTX);
   k_div_fftx<T><<<(rows + LR - 1) / LR, 256, smx, s>>>(a, LR);
+  hook.post(OCN_K_DIV_FFTX);
   ++n;
   const int CW = (sizeof(T) == 4) ? 8 : 4;
   const size_t smy = 2 * (size_t)a.Ny * CW * sizeof(C);
   e = cudaFuncSetAttribute(k_fft_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smy);
   if (e != cudaSuccess) return e;
   dim3 gy((a.Mx + 1 + CW - 1) / CW, a.Nz);
+  hook.pre(OCN_K_FFT_Y);
   k_fft_y<T><<<gy, 256, smy, s>>>(a, CW, -1);
+  hook.post(OCN_K_FFT_Y);
   ++n;
   dim3 gt((a.Mx + 1 + 127) / 128, a.Ny);
+  hook.pre(OCN_K_TRIDIAG);
   if (a.fp64_pivots) k_tridiag<T, double><<<gt, 128, 0, s>>>(a);
   else k_tridiag<T, T><<<gt, 128, 0, s>>>(a);
+  hook.post(OCN_K_TRIDIAG);
   ++n;
+  hook.pre(OCN_K_GAUGE);
   k_gauge<T><<<1, 32, 0, s>>>(a);
+  hook.post(OCN_K_GAUGE);
   ++n;
+  hook.pre(OCN_K_FFT_Y);
   k_fft_y<T><<<gy, 256, smy, s>>>(a, CW, +1);
+  hook.post(OCN_K_FFT_Y);
   ++n;
+  hook.pre(OCN_K_IFFTX);
   k_ifftx<T><<<(rows + LR - 1) / LR, 256, smx, s>>>(a, LR);
+  hook.post(OCN_K_IFFTX);
   ++n;
   dim3 gc((a.Nx + 255) / 256, a.Ny, a.Nz);
+  hook.pre(OCN_K_CORRECT);
   k_correct<T><<<gc, 256, 0, s>>>(a);
+  hook.post(OCN_K_CORRECT);
   ++n;
   if (nlaunch) *nlaunch = n;
   return cudaGetLastError();
 }
 
-template cudaError_t launch_projection<float>(const PoissonArgs<float>&, cudaStream_t, int*);
-template cudaError_t launch_projection<double>(const PoissonArgs<double>&, cudaStream_t, int*);
+template cudaError_t launch_projection<float>(const PoissonArgs<float>&, cudaStream_t, int*, const LaunchHook&);
+template cudaError_t launch_projection<double>(const PoissonArgs<double>&, cudaStream_t, int*, const LaunchHook&);
 
 }  // namespace ocn

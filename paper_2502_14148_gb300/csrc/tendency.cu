@@ -193,7 +193,8 @@ k_tendency(const TendencyArgs<T> a) {
   T* sK = sNu + (stress ? 4 : 0) * PLANE; // nt x 3 slots if amd
   T* FX = sK + (amd ? 3 * nt : 0) * PLANE;
   T* FY = FX + nf * FXS;
-  int* gi_tab = reinterpret_cast<int*>(FY + nf * FYS);
+  T* PHs = FY + nf * FYS;                 // hydrostatic pressure anomaly, [TY+1][TX+1] (offset -1)
+  int* gi_tab = reinterpret_cast<int*>(PHs + (TY + 1) * (TX + 1));
   int* gj_tab = gi_tab + PW;
 
   const int tid = threadIdx.x;
@@ -267,6 +268,21 @@ k_tendency(const TendencyArgs<T> a) {
   for (int t = 0; t < NTR; ++t) fz_c[t] = a.bot[2 + t];
 
   const int rowc = (ly + H) * PW + (lx + H);   // this thread's plane index
+
+  // Hydrostatic split (Eq. pressure-decomposition), used when stepping: b leaves
+  // the w equation and u, v feel -grad_h p_hy with d p_hy/dz = b.  p_hy is
+  // integrated up each column along the z march from the buoyancy anomaly
+  // relative to column (0,0), whose horizontally uniform part has no horizontal
+  // gradient; the difference from the unsplit form is an exact discrete
+  // gradient, removed by the projection.  Main threads integrate their own
+  // column, the east ghosts the west halo column, the north ghosts the south
+  // halo row.
+  const bool split = (a.mode == 0);
+  T phy = T(0), anom_prev = T(0);
+  int hidx = -1, phw = -1;               // SMEM plane index of the integrated column, PH slot written
+  if (role == 0) { hidx = rowc; phw = (active ? (ly + 1) * (TX + 1) + lx + 1 : -1); }
+  else if (role == 2) { hidx = (ly + H) * PW + (H - 1); phw = (ly < Ht) ? (ly + 1) * (TX + 1) : -1; }
+  else if (role == 1) { hidx = (H - 1) * PW + (lx + H); phw = (lx < Wt) ? lx + 1 : -1; }
 
   for (int k = 0; k < Nz; ++k) {
     // ---- prefetch the next level's planes
@@ -499,6 +515,16 @@ k_tendency(const TendencyArgs<T> a) {
       }
     }
 
+    if (split && hidx >= 0) {
+      const T* pC0 = sC + (k & 1) * PLANE;
+      const T* pC1 = sC + (2 * (NTR > 1 ? 1 : 0) + (k & 1)) * PLANE;
+      const T bref = buoyancy(a, __ldg(a.cur.c[0] + (size_t)k * plane), __ldg(a.cur.c[NTR > 1 ? 1 : 0] + (size_t)k * plane));
+      const T anom = buoyancy(a, pC0[hidx], pC1[hidx]) - bref;
+      if (k >= 1) phy = fma(__ldg(a.dzf + k) * T(0.5), anom_prev + anom, phy);
+      anom_prev = anom;
+      if (phw >= 0) PHs[phw] = phy;
+    }
+
     __syncthreads();
 
     // ================= tendencies and RK update
@@ -509,7 +535,8 @@ k_tendency(const TendencyArgs<T> a) {
       // u
       {
         const T vbar = T(0.25) * (pV[rowc - 1] + pV[rowc] + pV[rowc - 1 + PW] + pV[rowc + PW]);
-        const T G = -(FXu[1] - FXu[0]) * rdx - (FYu[TX] - FYu[0]) * rdy - (nz_u - fz_u) * rdzc_k + a.f * vbar;
+        T G = -(FXu[1] - FXu[0]) * rdx - (FYu[TX] - FYu[0]) * rdy - (nz_u - fz_u) * rdzc_k + a.f * vbar;
+        if (split) G -= (PHs[(ly + 1) * (TX + 1) + lx + 1] - PHs[(ly + 1) * (TX + 1) + lx]) * rdx;
         if (a.mode == 0) {
           T upd = fma(a.dt_gamma, G, ru[R - 1]);
           if (a.dt_zeta != T(0)) upd = fma(-a.dt_zeta, a.G.u[id], upd);
@@ -520,7 +547,8 @@ k_tendency(const TendencyArgs<T> a) {
       // v
       {
         const T ubar = T(0.25) * (pU[rowc - PW] + pU[rowc + 1 - PW] + pU[rowc] + pU[rowc + 1]);
-        const T G = -(FXu[FXS + 1] - FXu[FXS]) * rdx - (FYu[FYS + TX] - FYu[FYS]) * rdy - (nz_v - fz_v) * rdzc_k - a.f * ubar;
+        T G = -(FXu[FXS + 1] - FXu[FXS]) * rdx - (FYu[FYS + TX] - FYu[FYS]) * rdy - (nz_v - fz_v) * rdzc_k - a.f * ubar;
+        if (split) G -= (PHs[(ly + 1) * (TX + 1) + lx + 1] - PHs[ly * (TX + 1) + lx + 1]) * rdy;
         if (a.mode == 0) {
           T upd = fma(a.dt_gamma, G, rv[R - 1]);
           if (a.dt_zeta != T(0)) upd = fma(-a.dt_zeta, a.G.v[id], upd);
@@ -532,10 +560,13 @@ k_tendency(const TendencyArgs<T> a) {
       {
         T G = T(0);
         if (k >= 1) {
-          const T bk = buoyancy(a, rc[0][R - 1], rc[NTR > 1 ? 1 : 0][R - 1]);
-          const T bkm = buoyancy(a, rc[0][R - 2], rc[NTR > 1 ? 1 : 0][R - 2]);
           G = -(FXu[2 * FXS + 1] - FXu[2 * FXS]) * rdx - (FYu[2 * FYS + TX] - FYu[2 * FYS]) * rdy
-              - (nz_w - fz_w) * rdzf_k + T(0.5) * (bkm + bk);
+              - (nz_w - fz_w) * rdzf_k;
+          if (!split) {   // unsplit form (tendency output): + b interpolated to the w face
+            const T bk = buoyancy(a, rc[0][R - 1], rc[NTR > 1 ? 1 : 0][R - 1]);
+            const T bkm = buoyancy(a, rc[0][R - 2], rc[NTR > 1 ? 1 : 0][R - 2]);
+            G += T(0.5) * (bkm + bk);
+          }
         }
         if (a.mode == 0) {
           T upd = T(0);
@@ -551,8 +582,12 @@ k_tendency(const TendencyArgs<T> a) {
       }
 #pragma unroll
       for (int t = 0; t < NTR; ++t) {
-        const T G = -(FXu[(3 + t) * FXS + 1] - FXu[(3 + t) * FXS]) * rdx - (FYu[(3 + t) * FYS + TX] - FYu[(3 + t) * FYS]) * rdy
-                    - (nz_c[t] - fz_c[t]) * rdzc_k;
+        T G = -(FXu[(3 + t) * FXS + 1] - FXu[(3 + t) * FXS]) * rdx - (FYu[(3 + t) * FYS + TX] - FYu[(3 + t) * FYS]) * rdy
+              - (nz_c[t] - fz_c[t]) * rdzc_k;
+        if (a.cref[t] != T(0)) {   // stored as c - cref: restore -cref div(u) of the flux form
+          const T div = (pU[rowc + 1] - pU[rowc]) * rdx + (pV[rowc + PW] - pV[rowc]) * rdy + (rw[R] - rw[R - 1]) * rdzc_k;
+          G -= a.cref[t] * div;
+        }
         if (a.mode == 0) {
           T upd = fma(a.dt_gamma, G, rc[t][R - 1]);
           if (a.dt_zeta != T(0)) upd = fma(-a.dt_zeta, a.G.c[t][id], upd);
@@ -589,6 +624,7 @@ static size_t tendency_smem(const TendencyArgs<T>& a) {
   const int nf = 3 + a.nt;
   size_t planes = 2 + 2 + 3 + 2 * a.nt + (stress ? 4 : 0) + (amd ? 3 * a.nt : 0);
   size_t bytes = sizeof(T) * (planes * PLANE + (size_t)nf * (TY * (TX + 1) + (TY + 1) * TX));
+  bytes += sizeof(T) * (TY + 1) * (TX + 1);
   bytes += sizeof(int) * ((TX + 2 * H) + (TY + 2 * H));
   return bytes;
 }

@@ -22,7 +22,8 @@ LIB_PATH = os.path.join(HERE, "_lib", "libocn.so")
 
 OCN_FIELD_U, OCN_FIELD_V, OCN_FIELD_W, OCN_FIELD_TRACER0 = 0, 1, 2, 3
 OCN_FIELD_P, OCN_FIELD_G, OCN_FIELD_NU_E = 10, 20, 30
-OCN_OPT_GRAPHS, OCN_OPT_SYNC_CHECK = 1, 2
+OCN_OPT_GRAPHS, OCN_OPT_SYNC_CHECK, OCN_OPT_KERNEL_TIMING = 1, 2, 3
+KERNEL_CLASSES = ["closure", "tendency", "div_fftx", "fft_y", "tridiag", "gauge", "ifftx", "correct"]
 MAX_TRACERS = 4
 CLOSURES = {"none": 0, "scalar": 1, "smagorinsky": 2, "amd": 3}
 EOS = {"buoyancy_tracer": 0, "linear_ts": 1}
@@ -33,7 +34,7 @@ STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_NONFIN
 EXPORTS = ["ocn_abi_version", "ocn_last_error", "ocn_grid_create", "ocn_grid_destroy", "ocn_model_create",
            "ocn_model_destroy", "ocn_model_arena_bytes", "ocn_model_bind_arena", "ocn_set_field", "ocn_get_field",
            "ocn_project", "ocn_time_step", "ocn_compute_tendencies", "ocn_diagnostics", "ocn_set_option",
-           "ocn_launches_per_step"]
+           "ocn_launches_per_step", "ocn_kernel_times"]
 
 
 class OcnError(RuntimeError):
@@ -88,6 +89,7 @@ def lib(path: str = LIB_PATH):
     L.ocn_diagnostics.argtypes = [vp, C.c_double, C.POINTER(C.c_double), C.c_int]
     L.ocn_set_option.argtypes = [vp, C.c_int, C.c_longlong]
     L.ocn_launches_per_step.argtypes = [vp, C.POINTER(C.c_int)]
+    L.ocn_kernel_times.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_double)]
     for name in EXPORTS:
         if name not in ("ocn_abi_version", "ocn_last_error", "ocn_grid_destroy", "ocn_model_destroy"):
             getattr(L, name).restype = C.c_int
@@ -247,6 +249,14 @@ class Model:
         n = C.c_int()
         _check(lib().ocn_launches_per_step(self._h, C.byref(n)), "ocn_launches_per_step")
         return n.value
+
+    def kernel_times(self) -> dict:
+        """{kernel class: (launches, summed ms)} recorded while OCN_OPT_KERNEL_TIMING is on."""
+        n = len(KERNEL_CLASSES)
+        counts = (C.c_int * n)()
+        ms = (C.c_double * n)()
+        _check(lib().ocn_kernel_times(self._h, counts, ms), "ocn_kernel_times")
+        return {k: (counts[i], ms[i]) for i, k in enumerate(KERNEL_CLASSES)}
 
     def synchronize(self):
         self.stream.synchronize()
