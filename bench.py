@@ -226,6 +226,13 @@ def workload_desc(p: dict) -> str:
 
 
 # ------------------------------------------------------------------ our arm
+def size_override(args) -> dict:
+    if not args.size:
+        return {}
+    nx, ny, nz = (int(x) for x in args.size.lower().split("x"))
+    return dict(Nx=nx, Ny=ny, Nz=nz)
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -236,7 +243,7 @@ def run_ours(args, world, rank, local):
     barrier(world)
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    p = inputs.config(args.workload)
+    p = inputs.config(args.workload, **size_override(args))
     cells = p["Nx"] * p["Ny"] * p["Nz"]
     st = inputs.initial_state(p, seed=inputs.SEED + rank)
     model = ocn.Model(p, device=dev)
@@ -332,6 +339,8 @@ def run_ours(args, world, rank, local):
         "clocks": ck,
         "checks": {"max_div": d["max_div"], "cfl": d["cfl"], "nonfinite": d["nonfinite"]},
     }
+    if args.size:
+        line["config"]["workload"] += " (resized for profiling, not a bench line)"
     if world == 1 and not args.no_cpu_baseline:
         rate, sps, cores, sample = oracle_rate(args.workload, 1)
         line["cpu_baseline"] = {"value": rate, "unit": "cell-substeps/s", "cores": cores, "kind": "oracle",
@@ -348,6 +357,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="les_512")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--size", default=None, help="NxxNyxNz: the workload's physics and spacing on another grid (profiling)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     try:

@@ -114,10 +114,14 @@ struct ocn_model {
   std::map<std::pair<uint64_t, int>, cudaGraphExec_t> graph_cache;
   int launches_per_step = 0;
   FftPlan px, py;
-  // Linear-EOS tracers are stored as anomalies about (T0, S0): the arithmetic is
-  // unchanged (the EOS only sees differences, and the advection of a constant
-  // by a divergence-free velocity vanishes) while FP32 keeps ~20x more digits.
-  double cref[OCN_MAX_TRACERS] = {0, 0, 0, 0};
+  // Tracers are stored as anomalies about a per-level reference profile (their
+  // horizontal mean when set).  The kernels add the profile back wherever the
+  // full value enters the arithmetic (z stencils, EOS, vertical gradients) and
+  // use shift invariance elsewhere, so results are unchanged while FP32 state
+  // storage keeps the digits of the dynamic part rather than of the mean
+  // stratification.
+  size_t off_cref[OCN_MAX_TRACERS] = {0, 0, 0, 0};
+  std::vector<double> cref_host[OCN_MAX_TRACERS];
   // kernel timing (OCN_OPT_KERNEL_TIMING)
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -202,6 +206,7 @@ void layout(ocn_model* m) {
   m->off_lamy = take(es * g->Ny);
   m->off_twx = take(2 * es * g->Nx);
   m->off_twy = take(2 * es * g->Ny);
+  for (int t = 0; t < OCN_MAX_TRACERS; ++t) m->off_cref[t] = (t < m->d.n_tracers) ? take(es * g->Nz) : 0;
   m->off_partial = take(sizeof(double) * (size_t)diag_blocks() * (OCN_MAX_TRACERS + 6));
   m->off_diag = take(sizeof(double) * 16);
   m->bytes = o;
@@ -262,6 +267,7 @@ cudaError_t enqueue_closure(ocn_model* m, int which) {
   ClosureArgs<T> c;
   memset(&c, 0, sizeof(c));
   c.cur = state_ptrs<T>(m, which);
+  for (int t = 0; t < kMaxTracers; ++t) c.cref[t] = m->off_cref[t] ? at<T>(m, m->off_cref[t]) : nullptr;
   c.nu = at<T>(m, m->off_nu);
   for (int t = 0; t < kMaxTracers; ++t) c.kap[t] = m->off_kap[t] ? at<T>(m, m->off_kap[t]) : nullptr;
   c.dzc = at<T>(m, m->off_dzc); c.rdzc = at<T>(m, m->off_rdzc); c.rdzf = at<T>(m, m->off_rdzf);
@@ -270,8 +276,7 @@ cudaError_t enqueue_closure(ocn_model* m, int which) {
   c.closure = m->d.closure;
   c.Cs = (T)m->d.Cs; c.Cb = (T)m->d.Cb; c.inv_Pr = (T)(1.0 / m->d.Pr); c.C_amd = (T)m->d.C_amd;
   c.eos = m->d.eos;
-  c.g_alpha = (T)(m->d.g * m->d.alpha); c.g_beta = (T)(m->d.g * m->d.beta);
-  c.T0 = (T)(m->d.T0 - m->cref[0]); c.S0 = (T)(m->d.S0 - m->cref[1]);
+  c.g_alpha = (T)(m->d.g * m->d.alpha); c.g_beta = (T)(m->d.g * m->d.beta); c.T0 = (T)m->d.T0; c.S0 = (T)m->d.S0;
   m->hook.pre(OCN_K_CLOSURE);
   cudaError_t e = launch_closure<T>(c, m->stream);
   m->hook.post(OCN_K_CLOSURE);
@@ -291,13 +296,12 @@ cudaError_t enqueue_tendency(ocn_model* m, int which, double dt_gamma, double dt
   a.rdzc = at<T>(m, m->off_rdzc); a.rdzf = at<T>(m, m->off_rdzf); a.dzf = at<T>(m, m->off_dzf);
   a.Nx = g->Nx; a.Ny = g->Ny; a.Nz = g->Nz; a.nt = m->d.n_tracers;
   a.rdx = (T)(g->Nx / g->Lx); a.rdy = (T)(g->Ny / g->Ly);
-  for (int t = 0; t < kMaxTracers; ++t) a.cref[t] = (T)m->cref[t];
+  for (int t = 0; t < kMaxTracers; ++t) a.cref[t] = m->off_cref[t] ? at<T>(m, m->off_cref[t]) : nullptr;
   a.closure = m->d.closure;
   a.nu0 = (T)m->d.nu; a.kappa0 = (T)m->d.kappa; a.inv_Pr = (T)(1.0 / m->d.Pr);
   a.f = (T)m->d.f;
   a.eos = m->d.eos;
-  a.g_alpha = (T)(m->d.g * m->d.alpha); a.g_beta = (T)(m->d.g * m->d.beta);
-  a.T0 = (T)(m->d.T0 - m->cref[0]); a.S0 = (T)(m->d.S0 - m->cref[1]);
+  a.g_alpha = (T)(m->d.g * m->d.alpha); a.g_beta = (T)(m->d.g * m->d.beta); a.T0 = (T)m->d.T0; a.S0 = (T)m->d.S0;
   for (int n = 0; n < 2 + kMaxTracers; ++n) { a.top[n] = (T)m->d.top_flux[n]; a.bot[n] = (T)m->d.bottom_flux[n]; }
   a.dt_gamma = (T)dt_gamma; a.dt_zeta = (T)dt_zeta;
   a.mode = mode;
@@ -463,7 +467,7 @@ ocn_status ocn_model_create(const ocn_grid* grid, const ocn_model_desc* desc, vo
   m->es = desc->precision / 8;
   m->nf = 3 + desc->n_tracers;
   m->fp64_piv = desc->fp64_pivots > 0 || (desc->fp64_pivots < 0 && grid->stretched);
-  if (desc->eos == OCN_EOS_LINEAR_TS) { m->cref[0] = desc->T0; m->cref[1] = desc->S0; }
+  for (int t = 0; t < desc->n_tracers; ++t) m->cref_host[t].assign(grid->Nz, 0.0);
   m->px = make_plan(grid->Nx / 2);
   m->py = make_plan(grid->Ny);
   layout(m);
@@ -500,6 +504,7 @@ ocn_status ocn_model_bind_arena(ocn_model* m, void* device_ptr, size_t bytes) {
   drop_graphs(m);
   m->arena = reinterpret_cast<char*>(device_ptr);
   m->cur = 0;
+  for (int t = 0; t < m->d.n_tracers; ++t) m->cref_host[t].assign(m->g->Nz, 0.0);
   e = cudaMemsetAsync(m->arena, 0, m->bytes, m->stream);
   if (e != cudaSuccess) return cuda_fail(e, "clear arena");
   std::vector<char> blob = (m->es == 4) ? metrics_blob<float>(m) : metrics_blob<double>(m);
@@ -521,10 +526,24 @@ ocn_status ocn_set_field(ocn_model* m, int field, const void* src, size_t nbytes
   cudaError_t e = cudaMemcpyAsync(dst, src, nbytes, src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, m->stream);
   if (e != cudaSuccess) return cuda_fail(e, "set field copy");
   const int tr = field - OCN_FIELD_TRACER0;
-  if (tr >= 0 && tr < m->d.n_tracers && m->cref[tr] != 0.0) {
-    e = (m->es == 4) ? launch_shift<float>(reinterpret_cast<float*>(dst), elems, (float)-m->cref[tr], m->stream)
-                     : launch_shift<double>(reinterpret_cast<double*>(dst), elems, -m->cref[tr], m->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "tracer reference shift");
+  if (tr >= 0 && tr < m->d.n_tracers) {
+    // new reference profile = the horizontal mean of each level; store the anomaly
+    const size_t plane = (size_t)m->g->Nx * m->g->Ny;
+    char* ref = m->arena + m->off_cref[tr];
+    if (m->es == 4) {
+      e = launch_level_mean<float>(reinterpret_cast<float*>(dst), plane, m->g->Nz, reinterpret_cast<float*>(ref), m->stream);
+      if (e == cudaSuccess) e = launch_level_shift<float>(reinterpret_cast<float*>(dst), plane, m->g->Nz, reinterpret_cast<float*>(ref), -1.0f, m->stream);
+    } else {
+      e = launch_level_mean<double>(reinterpret_cast<double*>(dst), plane, m->g->Nz, reinterpret_cast<double*>(ref), m->stream);
+      if (e == cudaSuccess) e = launch_level_shift<double>(reinterpret_cast<double*>(dst), plane, m->g->Nz, reinterpret_cast<double*>(ref), -1.0, m->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "tracer reference profile");
+    std::vector<char> hb((size_t)m->g->Nz * m->es);
+    e = cudaMemcpyAsync(hb.data(), ref, hb.size(), cudaMemcpyDeviceToHost, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "tracer reference profile read");
+    for (int k = 0; k < m->g->Nz; ++k)
+      m->cref_host[tr][k] = (m->es == 4) ? (double)reinterpret_cast<float*>(hb.data())[k] : reinterpret_cast<double*>(hb.data())[k];
   }
   if (field == OCN_FIELD_W || field == OCN_FIELD_G + OCN_FIELD_W) {
     size_t pb = (size_t)m->g->Nx * m->g->Ny * m->es;
@@ -548,14 +567,16 @@ ocn_status ocn_get_field(ocn_model* m, int field, void* dst, size_t nbytes, int 
   char* src = field_ptr(m, field, &elems);
   if (nbytes != elems * (size_t)m->es) return fail(OCN_ERR_ARG, "byte count does not match the field size");
   const int tr = field - OCN_FIELD_TRACER0;
-  if (tr >= 0 && tr < m->d.n_tracers && m->cref[tr] != 0.0) {
-    // add the reference back in the spectral work space (at least one field large)
+  if (tr >= 0 && tr < m->d.n_tracers) {
+    // add the reference profile back in the spectral work space (larger than one field)
     char* scratch = m->arena + m->off_spec;
+    const size_t plane = (size_t)m->g->Nx * m->g->Ny;
+    const char* ref = m->arena + m->off_cref[tr];
     cudaError_t e = cudaMemcpyAsync(scratch, src, nbytes, cudaMemcpyDeviceToDevice, m->stream);
     if (e == cudaSuccess)
-      e = (m->es == 4) ? launch_shift<float>(reinterpret_cast<float*>(scratch), elems, (float)m->cref[tr], m->stream)
-                       : launch_shift<double>(reinterpret_cast<double*>(scratch), elems, m->cref[tr], m->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "tracer reference shift");
+      e = (m->es == 4) ? launch_level_shift<float>(reinterpret_cast<float*>(scratch), plane, m->g->Nz, reinterpret_cast<const float*>(ref), 1.0f, m->stream)
+                       : launch_level_shift<double>(reinterpret_cast<double*>(scratch), plane, m->g->Nz, reinterpret_cast<const double*>(ref), 1.0, m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "tracer reference profile");
     src = scratch;
   }
   cudaError_t e = cudaMemcpyAsync(dst, src, nbytes, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream);
@@ -630,8 +651,8 @@ ocn_status ocn_diagnostics(ocn_model* m, double dt, double* out, int nout) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
   if (e != cudaSuccess) return cuda_fail(e, "diagnostics read");
   for (int v = 0; v < nt + 6; ++v) out[v] = vals[v];
-  const double volume = g->Lx * g->Ly * (g->zf[g->Nz] - g->zf[0]);
-  for (int t = 0; t < nt; ++t) out[t] += m->cref[t] * volume;
+  for (int t = 0; t < nt; ++t)
+    for (int k = 0; k < g->Nz; ++k) out[t] += m->cref_host[t][k] * g->Lx * g->Ly * g->dzc[k];
   out[nt + 4] *= dt;
   if (out[nt + 5] > 0 || !isfinite(out[nt + 3])) return fail(OCN_ERR_NONFINITE, "non-finite values in the state");
   if (out[nt + 4] > 1.0) return fail(OCN_ERR_CFL, "advective CFL number above 1");

@@ -49,7 +49,7 @@ struct TendencyArgs {
   const T* dzf;           // dz_f[k]
   int Nx, Ny, Nz, nt;
   T rdx, rdy;
-  T cref[kMaxTracers];    // tracers are stored as c - cref: G gains -cref div(u)
+  const T* cref[kMaxTracers];  // per-level reference profiles: tracer n is stored as c - cref[n][k] (or null)
   int closure;
   T nu0, kappa0;          // scalar diffusivity
   T inv_Pr;
@@ -64,6 +64,7 @@ struct TendencyArgs {
 template <typename T>
 struct ClosureArgs {
   StatePtrs<T> cur;
+  const T* cref[kMaxTracers];  // per-level tracer reference profiles (or null)
   T* nu;
   T* kap[kMaxTracers];
   const T* dzc;
@@ -133,6 +134,10 @@ template <typename T> cudaError_t launch_projection(const PoissonArgs<T>& a, cud
 template <typename T> cudaError_t launch_diagnostics(const DiagArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_fill(T* p, size_t n, T v, cudaStream_t s);
 template <typename T> cudaError_t launch_shift(T* p, size_t n, T v, cudaStream_t s);
+// Per-level horizontal means of a [Nz][plane] field (FP64 accumulation) into ref[Nz],
+// and p[k][.] += sign * ref[k].
+template <typename T> cudaError_t launch_level_mean(const T* p, size_t plane, int Nz, T* ref, cudaStream_t s);
+template <typename T> cudaError_t launch_level_shift(T* p, size_t plane, int Nz, const T* ref, T sign, cudaStream_t s);
 int diag_blocks();
 
 }  // namespace ocn

@@ -121,6 +121,43 @@ cudaError_t launch_shift(T* p, size_t n, T v, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_level_mean(const T* p, size_t plane, T* ref) {
+  const int k = blockIdx.x;
+  const T* q = p + (size_t)k * plane;
+  double acc = 0.0;
+  for (size_t i = threadIdx.x; i < plane; i += blockDim.x) acc += (double)q[i];
+  __shared__ double red[8];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    ref[k] = (T)(t / (double)plane);
+  }
+}
+template <typename T>
+__global__ void k_level_shift(T* p, size_t plane, int Nz, const T* ref, T sign) {
+  const size_t n = plane * (size_t)Nz;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    p[i] += sign * ref[i / plane];
+}
+template <typename T>
+cudaError_t launch_level_mean(const T* p, size_t plane, int Nz, T* ref, cudaStream_t s) {
+  k_level_mean<T><<<Nz, 256, 0, s>>>(p, plane, ref);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_level_shift(T* p, size_t plane, int Nz, const T* ref, T sign, cudaStream_t s) {
+  k_level_shift<T><<<1216, 256, 0, s>>>(p, plane, Nz, ref, sign);
+  return cudaGetLastError();
+}
+template cudaError_t launch_level_mean<float>(const float*, size_t, int, float*, cudaStream_t);
+template cudaError_t launch_level_mean<double>(const double*, size_t, int, double*, cudaStream_t);
+template cudaError_t launch_level_shift<float>(float*, size_t, int, const float*, float, cudaStream_t);
+template cudaError_t launch_level_shift<double>(double*, size_t, int, const double*, double, cudaStream_t);
+
 template cudaError_t launch_diagnostics<float>(const DiagArgs<float>&, cudaStream_t);
 template cudaError_t launch_diagnostics<double>(const DiagArgs<double>&, cudaStream_t);
 template cudaError_t launch_fill<float>(float*, size_t, float, cudaStream_t);

@@ -237,6 +237,13 @@ k_tendency(const TendencyArgs<T> a) {
   const int ci = (i0 + lx) % Nx, cj = (j0 + ly) % Ny;
   const size_t col = (size_t)cj * Nx + ci;
   auto ld_c = [&](const T* f, int level) -> T { return (level >= 0 && level < Nz) ? __ldg(f + (size_t)level * plane + col) : T(0); };
+  // full tracer value: stored anomaly + the level's reference profile
+  auto ld_tr = [&](int t, int level) -> T {
+    if (level < 0 || level >= Nz) return T(0);
+    const T ref = a.cref[t] ? __ldg(a.cref[t] + level) : T(0);
+    return __ldg(a.cur.c[t] + (size_t)level * plane + col) + ref;
+  };
+  auto cref_at = [&](int t, int level) -> T { return a.cref[t] ? __ldg(a.cref[t] + level) : T(0); };
   auto ld_w = [&](int face) -> T { return (face >= 0 && face <= Nz) ? __ldg(a.cur.w + (size_t)face * plane + col) : T(0); };
 
   // register rings: level (or face) k+1-R+n at index n
@@ -250,7 +257,7 @@ k_tendency(const TendencyArgs<T> a) {
 #pragma unroll
   for (int t = 0; t < NTR; ++t)
 #pragma unroll
-    for (int n = 0; n < 2 * R; ++n) rc[t][n] = ld_c(a.cur.c[t], 1 - R + n);
+    for (int n = 0; n < 2 * R; ++n) rc[t][n] = ld_tr(t, 1 - R + n);
 
   load_level(0);
   load_wface(0);
@@ -294,7 +301,10 @@ k_tendency(const TendencyArgs<T> a) {
     T nu_ = ld_c(a.cur.u, k + 1 + R), nv_ = ld_c(a.cur.v, k + 1 + R), nw_ = ld_w(k + 1 + R);
     T nc_[NTR];
 #pragma unroll
-    for (int t = 0; t < NTR; ++t) nc_[t] = ld_c(a.cur.c[t], k + 1 + R);
+    for (int t = 0; t < NTR; ++t) nc_[t] = ld_tr(t, k + 1 + R);
+    T crk[NTR];                                  // reference profile at this level
+#pragma unroll
+    for (int t = 0; t < NTR; ++t) crk[t] = cref_at(t, k);
 
     const T* pU = sU + (k & 1) * PLANE;
     const T* pV = sV + (k & 1) * PLANE;
@@ -369,7 +379,7 @@ k_tendency(const TendencyArgs<T> a) {
 #pragma unroll
         for (int n = 0; n < 2 * R; ++n) sc[n] = pC[rowc - R + n];
         const T U = pU[rowc];
-        T F = U * weno<T, R>(sc, U);
+        T F = U * (weno<T, R>(sc, U) + crk[t]);    // reconstruction commutes with the level's constant shift
         const T dc = (sc[R] - sc[R - 1]) * rdx;
         if (scalar) F -= a.kappa0 * dc;
         else if (amd) { const T* pK = sK + (3 * t + k % 3) * PLANE; F -= T(0.5) * (pK[rowc - 1] + pK[rowc]) * dc; }
@@ -438,7 +448,7 @@ k_tendency(const TendencyArgs<T> a) {
 #pragma unroll
         for (int n = 0; n < 2 * R; ++n) sc[n] = pC[rowc + (n - R) * PW];
         const T V = pV[rowc];
-        T F = V * weno<T, R>(sc, V);
+        T F = V * (weno<T, R>(sc, V) + crk[t]);
         const T dc = (sc[R] - sc[R - 1]) * rdy;
         if (scalar) F -= a.kappa0 * dc;
         else if (amd) { const T* pK = sK + (3 * t + k % 3) * PLANE; F -= T(0.5) * (pK[rowc - PW] + pK[rowc]) * dc; }
@@ -518,8 +528,11 @@ k_tendency(const TendencyArgs<T> a) {
     if (split && hidx >= 0) {
       const T* pC0 = sC + (k & 1) * PLANE;
       const T* pC1 = sC + (2 * (NTR > 1 ? 1 : 0) + (k & 1)) * PLANE;
-      const T bref = buoyancy(a, __ldg(a.cur.c[0] + (size_t)k * plane), __ldg(a.cur.c[NTR > 1 ? 1 : 0] + (size_t)k * plane));
-      const T anom = buoyancy(a, pC0[hidx], pC1[hidx]) - bref;
+      constexpr int t1 = NTR > 1 ? 1 : 0;
+      const T bref = buoyancy(a, __ldg(a.cur.c[0] + (size_t)k * plane) + crk[0], __ldg(a.cur.c[t1] + (size_t)k * plane) + crk[t1]);
+      const T bhere = (role == 0) ? buoyancy(a, rc[0][R - 1], rc[t1][R - 1])
+                                  : buoyancy(a, pC0[hidx] + crk[0], pC1[hidx] + crk[t1]);
+      const T anom = bhere - bref;
       if (k >= 1) phy = fma(__ldg(a.dzf + k) * T(0.5), anom_prev + anom, phy);
       anom_prev = anom;
       if (phw >= 0) PHs[phw] = phy;
@@ -584,12 +597,8 @@ k_tendency(const TendencyArgs<T> a) {
       for (int t = 0; t < NTR; ++t) {
         T G = -(FXu[(3 + t) * FXS + 1] - FXu[(3 + t) * FXS]) * rdx - (FYu[(3 + t) * FYS + TX] - FYu[(3 + t) * FYS]) * rdy
               - (nz_c[t] - fz_c[t]) * rdzc_k;
-        if (a.cref[t] != T(0)) {   // stored as c - cref: restore -cref div(u) of the flux form
-          const T div = (pU[rowc + 1] - pU[rowc]) * rdx + (pV[rowc + PW] - pV[rowc]) * rdy + (rw[R] - rw[R - 1]) * rdzc_k;
-          G -= a.cref[t] * div;
-        }
         if (a.mode == 0) {
-          T upd = fma(a.dt_gamma, G, rc[t][R - 1]);
+          T upd = fma(a.dt_gamma, G, sC[(2 * t + (k & 1)) * PLANE + rowc]);   // the stored anomaly
           if (a.dt_zeta != T(0)) upd = fma(-a.dt_zeta, a.G.c[t][id], upd);
           a.nxt.c[t][id] = upd;
         }
@@ -699,10 +708,13 @@ __global__ void __launch_bounds__(256) k_closure(const ClosureArgs<T> a) {
   const size_t id = (size_t)k * plane + (size_t)j * Nx + i;
   const T dz = __ldg(a.dzc + k);
 
+  // tracers are stored about per-level reference profiles: add them back where levels mix
+  auto cref = [&](int t, int kk) -> T { return a.cref[t] ? __ldg(a.cref[t] + kk) : T(0); };
   auto bof = [&](int kk) -> T {
     const size_t o = (size_t)kk * plane + (size_t)j * Nx + i;
-    if (a.eos == OCN_EOS_LINEAR_TS) return a.g_alpha * (__ldg(a.cur.c[0] + o) - a.T0) - a.g_beta * (__ldg(a.cur.c[1] + o) - a.S0);
-    return __ldg(a.cur.c[0] + o);
+    if (a.eos == OCN_EOS_LINEAR_TS)
+      return a.g_alpha * (__ldg(a.cur.c[0] + o) + cref(0, kk) - a.T0) - a.g_beta * (__ldg(a.cur.c[1] + o) + cref(1, kk) - a.S0);
+    return __ldg(a.cur.c[0] + o) + cref(0, kk);
   };
 
   if (a.closure == OCN_CLOSURE_SMAGORINSKY) {
@@ -743,8 +755,8 @@ __global__ void __launch_bounds__(256) k_closure(const ClosureArgs<T> a) {
       T dc[3];
       dc[0] = T(0.5) * ((c0 - C(im, j, k)) + (C(ip, j, k) - c0)) * rdx;
       dc[1] = T(0.5) * ((c0 - C(i, jm, k)) + (C(i, jp, k) - c0)) * rdy;
-      const T dcb = (k >= 1) ? (c0 - C(i, j, k - 1)) * rdzf0 : T(0);
-      const T dct = (k + 1 < Nz) ? (C(i, j, k + 1) - c0) * rdzf1 : T(0);
+      const T dcb = (k >= 1) ? ((c0 - C(i, j, k - 1)) + (cref(t, k) - cref(t, k - 1))) * rdzf0 : T(0);
+      const T dct = (k + 1 < Nz) ? ((C(i, j, k + 1) - c0) + (cref(t, k + 1) - cref(t, k))) * rdzf1 : T(0);
       dc[2] = T(0.5) * (dcb + dct);
       T cn = T(0), cd = T(0);
 #pragma unroll

@@ -2,7 +2,7 @@
 
 Inputs always come from the seeded generators in paper_2502_14148_gb300.inputs;
 no oracle input or expected value comes from the GPU.  Tolerances:
-  FP64 runs       max|a-o| / max|o| <= 1e-11 per field (one evaluation: 1e-12)
+  FP64            max|a-o| / max|o| <= 1e-11 per field
   FP32 runs       ||a-o||_2 / ||o||_2 <= 1e-4 per field after 100 steps
   FP32 one call   max|a-o| / max|o| <= 2e-5 (inputs rounded to FP32 on both sides)
 """
@@ -69,7 +69,7 @@ def test_projection_parity(ocn, oracle_mod, precision, dims):
     o = oracle_mod.OracleModel(p)
     o.set(**st)
     o.project(1.0)
-    tol = 1e-12 if precision == 64 else 2e-5
+    tol = 1e-11 if precision == 64 else 2e-5
     for name in ("u", "v", "w", "p"):
         assert rel_max(g.get_numpy(name), o.get(name)) < tol, name
     d = g.diagnostics()
@@ -110,7 +110,7 @@ def _tendency_pair(ocn, oracle_mod, case, precision, seed=41, **over):
 def test_tendency_parity_fp64(ocn, oracle_mod, case):
     G, O, p = _tendency_pair(ocn, oracle_mod, case, 64)
     for name in O:
-        assert rel_max(G[name], O[name]) < 1e-12, name
+        assert rel_max(G[name], O[name]) < 1e-11, name
 
 
 @pytest.mark.parametrize("case", CASES, ids=[f"weno{c['weno_order']}-{c['closure']}-{len(c.get('tracers', ['b']))}tr" for c in CASES])
@@ -130,7 +130,7 @@ def test_tendency_parity_edge_sizes(ocn, oracle_mod, dims):
                     top_flux={"u": 1e-2, "T": 2e-3})
         G, O, _ = _tendency_pair(ocn, oracle_mod, case, 64, Nx=Nx, Ny=Ny, Nz=Nz, Lx=float(Nx), Ly=float(Ny), Lz=float(Nz))
         for name in O:
-            assert rel_max(G[name], O[name]) < 1e-12, (order, name)
+            assert rel_max(G[name], O[name]) < 1e-11, (order, name)
 
 
 # ----------------------------------------------------------------------------- time stepping
