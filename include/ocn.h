@@ -80,8 +80,16 @@ enum {
                                 kinematic pressure; after ocn_time_step the nonhydrostatic part p_nh of the
                                 last substage (Eq. pressure-decomposition), scaled by 1/((gamma-zeta) dt) */
   OCN_FIELD_G = 20,          /* tendency G of field f is OCN_FIELD_G + f (G^{m-1} after a step) */
-  OCN_FIELD_NU_E = 30        /* eddy viscosity at cell centres (Smagorinsky-Lilly, AMD) */
+  OCN_FIELD_NU_E = 30,       /* eddy viscosity at cell centres (Smagorinsky-Lilly, AMD) */
+  OCN_FIELD_TRACER_REF0 = 40, /* reference profile of tracer n ([Nz] values) is OCN_FIELD_TRACER_REF0 + n */
+  OCN_FIELD_RAW = 0x100      /* OR'ed with a tracer id: the stored anomaly c - ref[k] itself */
 };
+/* Tracers are stored as anomalies about a per-level reference profile.  Setting
+ * a tracer (without OCN_FIELD_RAW) makes its reference the horizontal mean of
+ * each level and stores the anomaly; getting it returns anomaly + reference.
+ * For a bitwise checkpoint, save u, v, w, every tracer with OCN_FIELD_RAW and
+ * every OCN_FIELD_TRACER_REF0 + n; restore the same fields (setting a raw
+ * tracer or a reference profile copies it as is). */
 
 /* Grid (paper listing "RectilinearGrid(...)"): x in [0,Lx), y in [0,Ly) periodic,
  * uniform; z bounded with Nz+1 ascending face heights. */

@@ -392,6 +392,11 @@ void drop_events(ocn_model* m) {
 }
 
 bool field_valid(const ocn_model* m, int field) {
+  if (field & OCN_FIELD_RAW) {
+    const int f = field & ~OCN_FIELD_RAW;
+    return f >= OCN_FIELD_TRACER0 && f < OCN_FIELD_TRACER0 + m->d.n_tracers;
+  }
+  if (field >= OCN_FIELD_TRACER_REF0 && field < OCN_FIELD_TRACER_REF0 + m->d.n_tracers) return true;
   if (field == OCN_FIELD_U || field == OCN_FIELD_V || field == OCN_FIELD_W || field == OCN_FIELD_P) return true;
   if (field >= OCN_FIELD_TRACER0 && field < OCN_FIELD_TRACER0 + m->d.n_tracers) return true;
   if (field >= OCN_FIELD_G && field < OCN_FIELD_G + m->nf) return true;
@@ -400,6 +405,11 @@ bool field_valid(const ocn_model* m, int field) {
 }
 
 char* field_ptr(const ocn_model* m, int field, size_t* elems) {
+  field &= ~OCN_FIELD_RAW;
+  if (field >= OCN_FIELD_TRACER_REF0 && field < OCN_FIELD_TRACER_REF0 + m->d.n_tracers) {
+    *elems = (size_t)m->g->Nz;
+    return m->arena + m->off_cref[field - OCN_FIELD_TRACER_REF0];
+  }
   if (field >= OCN_FIELD_G && field < OCN_FIELD_G + m->nf) {
     *elems = field_elems(m, field - OCN_FIELD_G);
     return m->arena + m->off_G[field - OCN_FIELD_G];
@@ -525,7 +535,16 @@ ocn_status ocn_set_field(ocn_model* m, int field, const void* src, size_t nbytes
   if (nbytes != elems * (size_t)m->es) return fail(OCN_ERR_ARG, "byte count does not match the field size");
   cudaError_t e = cudaMemcpyAsync(dst, src, nbytes, src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, m->stream);
   if (e != cudaSuccess) return cuda_fail(e, "set field copy");
-  const int tr = field - OCN_FIELD_TRACER0;
+  const int tr = (field & OCN_FIELD_RAW) ? -1 : field - OCN_FIELD_TRACER0;
+  const int rf = field - OCN_FIELD_TRACER_REF0;
+  if (rf >= 0 && rf < m->d.n_tracers) {   // a reference profile set as is: refresh the host mirror
+    std::vector<char> hb(nbytes);
+    e = cudaMemcpyAsync(hb.data(), dst, nbytes, cudaMemcpyDeviceToHost, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "reference profile read");
+    for (int k = 0; k < m->g->Nz; ++k)
+      m->cref_host[rf][k] = (m->es == 4) ? (double)reinterpret_cast<float*>(hb.data())[k] : reinterpret_cast<double*>(hb.data())[k];
+  }
   if (tr >= 0 && tr < m->d.n_tracers) {
     // new reference profile = the horizontal mean of each level; store the anomaly
     const size_t plane = (size_t)m->g->Nx * m->g->Ny;
@@ -566,7 +585,7 @@ ocn_status ocn_get_field(ocn_model* m, int field, void* dst, size_t nbytes, int 
   size_t elems = 0;
   char* src = field_ptr(m, field, &elems);
   if (nbytes != elems * (size_t)m->es) return fail(OCN_ERR_ARG, "byte count does not match the field size");
-  const int tr = field - OCN_FIELD_TRACER0;
+  const int tr = (field & OCN_FIELD_RAW) ? -1 : field - OCN_FIELD_TRACER0;
   if (tr >= 0 && tr < m->d.n_tracers) {
     // add the reference profile back in the spectral work space (larger than one field)
     char* scratch = m->arena + m->off_spec;

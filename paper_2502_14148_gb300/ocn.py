@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libocn.so")
 
 OCN_FIELD_U, OCN_FIELD_V, OCN_FIELD_W, OCN_FIELD_TRACER0 = 0, 1, 2, 3
 OCN_FIELD_P, OCN_FIELD_G, OCN_FIELD_NU_E = 10, 20, 30
+OCN_FIELD_TRACER_REF0, OCN_FIELD_RAW = 40, 0x100
 OCN_OPT_GRAPHS, OCN_OPT_SYNC_CHECK, OCN_OPT_KERNEL_TIMING = 1, 2, 3
 KERNEL_CLASSES = ["closure", "tendency", "div_fftx", "fft_y", "tridiag", "gauge", "ifftx", "correct"]
 MAX_TRACERS = 4
@@ -175,12 +176,20 @@ class Model:
     def fid(self, name: str) -> int:
         if name.startswith("G_"):
             return OCN_FIELD_G + self.fid(name[2:])
+        if name.startswith("raw_"):
+            return OCN_FIELD_RAW | self.fid(name[4:])
+        if name.startswith("ref_"):
+            return OCN_FIELD_TRACER_REF0 + self.tracers.index(name[4:])
         table = {"u": OCN_FIELD_U, "v": OCN_FIELD_V, "w": OCN_FIELD_W, "p": OCN_FIELD_P, "nu_e": OCN_FIELD_NU_E}
         if name in table:
             return table[name]
         return OCN_FIELD_TRACER0 + self.tracers.index(name)
 
     def shape(self, name: str):
+        if name.startswith("ref_"):
+            return (self.Nz,)
+        if name.startswith("raw_"):
+            name = name[4:]
         base = name[2:] if name.startswith("G_") else name
         return (self.Nz + 1 if base == "w" else self.Nz, self.Ny, self.Nx)
 
@@ -218,6 +227,14 @@ class Model:
     def get_host(self, name: str, host_tensor):
         _check(lib().ocn_get_field(self._h, self.fid(name), C.c_void_p(host_tensor.data_ptr()),
                                    host_tensor.numel() * host_tensor.element_size(), 0), "ocn_get_field")
+
+    def checkpoint(self) -> dict:
+        """Device copies of everything a bitwise restart needs (state, raw tracer anomalies, profiles)."""
+        names = ["u", "v", "w"] + [f"raw_{t}" for t in self.tracers] + [f"ref_{t}" for t in self.tracers]
+        return {n: self.get(n).clone() for n in names}
+
+    def restore(self, ckpt: dict):
+        self.set(project=False, **ckpt)
 
     # ------------------------------------------------------------------ stepping
     def project(self):

@@ -247,8 +247,9 @@ def test_checkpoint_resume_bitwise(ocn):
     st = inputs.initial_state(p)
     a = ocn.Model(p); a.set(**st); a.time_step(p["dt"], 6)
     b = ocn.Model(p); b.set(**st); b.time_step(p["dt"], 3)
-    saved = {n: b.get(n).clone() for n in ("u", "v", "w", "b")}
-    c = ocn.Model(p); c.set(project=False, **saved); c.time_step(p["dt"], 3)
+    saved = b.checkpoint()
+    del b
+    c = ocn.Model(p); c.restore(saved); c.time_step(p["dt"], 3)
     for name in ("u", "v", "w", "b"):
         assert np.array_equal(a.get_numpy(name), c.get_numpy(name)), name
 
