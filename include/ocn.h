@@ -214,6 +214,38 @@ ocn_status ocn_kernel_times(ocn_model* model, int* counts, double* ms);
 /* Number of kernel launches the last ocn_time_step issued per RK3 step. */
 ocn_status ocn_launches_per_step(const ocn_model* model, int* launches);
 
+/* No-allocation projection.  Some callers cannot call cudaMalloc: plug-ins
+ * whose host application owns every device allocation through its own pool
+ * allocator, and loops that must not allocate once they are running.  This
+ * entry point gives them the projection of ocn_project -- lap p = div u with
+ * Neumann walls and a zero-volume-mean gauge, then u -= grad p -- for a
+ * velocity (u, v, w) and pressure p that the caller already holds, with every
+ * other work array (spectrum, pivots, metrics, twiddles) inside a fixed device
+ * array of about 6.3 MB that the library declares at file scope.  The paper has
+ * no counterpart: it is a deployment variant of the projection, not a step of
+ * the method.
+ *   precision  32 (float arrays) or 64 (double arrays)
+ *   Nx, Ny, Nz, Lx, Ly, z_faces   the grid, as in ocn_grid_desc (z_faces in host memory)
+ *   u, v, w, p device arrays in the layouts above; u, v, w are corrected in place,
+ *              p receives the pressure
+ *   stream     cudaStream_t for all work (NULL: legacy default stream); the call
+ *              returns after enqueueing
+ *   error      if not NULL, receives a static description of a failure ("" on success)
+ * Limits: Nx, Ny, Nz <= OCN_NOALLOC_MAX_N and (Nx/2+1)*Ny*Nz <= OCN_NOALLOC_MAX_MODES,
+ * else OCN_ERR_ARG (so are the grid rules of ocn_grid_create).
+ * The call allocates no device memory (no cudaMalloc, cudaFree or allocating
+ * library routine).  The first call on each device looks up the device address
+ * of the array and keeps it; make that first call before any stream capture.
+ * Every call on a device shares the one array and leaves its contents behind
+ * (each call rewrites all it reads, so nothing needs clearing), so calls whose
+ * work overlaps on the GPU, e.g. on two streams at once, race and must be
+ * serialised by the caller.  Every device that loads the library holds the
+ * array until the process exits. */
+#define OCN_NOALLOC_MAX_N 4096
+#define OCN_NOALLOC_MAX_MODES 262144
+ocn_status ocn_project_noalloc(int precision, int Nx, int Ny, int Nz, double Lx, double Ly, const double* z_faces,
+                               void* u, void* v, void* w, void* p, void* stream, const char** error);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libocn.so")
-SOURCES = ["capi.cu", "coeffs.cpp", "tendency.cu", "poisson.cu", "reduce.cu"]
+SOURCES = ["capi.cu", "coeffs.cpp", "tendency.cu", "poisson.cu", "reduce.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -35,7 +35,7 @@ STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_NONFIN
 EXPORTS = ["ocn_abi_version", "ocn_last_error", "ocn_grid_create", "ocn_grid_destroy", "ocn_model_create",
            "ocn_model_destroy", "ocn_model_arena_bytes", "ocn_model_bind_arena", "ocn_set_field", "ocn_get_field",
            "ocn_project", "ocn_time_step", "ocn_compute_tendencies", "ocn_diagnostics", "ocn_set_option",
-           "ocn_launches_per_step", "ocn_kernel_times"]
+           "ocn_launches_per_step", "ocn_kernel_times", "ocn_project_noalloc"]
 
 
 class OcnError(RuntimeError):
@@ -91,6 +91,8 @@ def lib(path: str = LIB_PATH):
     L.ocn_set_option.argtypes = [vp, C.c_int, C.c_longlong]
     L.ocn_launches_per_step.argtypes = [vp, C.POINTER(C.c_int)]
     L.ocn_kernel_times.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    L.ocn_project_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                      C.POINTER(C.c_double), vp, vp, vp, vp, vp, C.POINTER(C.c_char_p)]
     for name in EXPORTS:
         if name not in ("ocn_abi_version", "ocn_last_error", "ocn_grid_destroy", "ocn_model_destroy"):
             getattr(L, name).restype = C.c_int
