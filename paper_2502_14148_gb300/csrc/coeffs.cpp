@@ -109,6 +109,27 @@ void derive_weno_tables(WenoTables<double>* out) {
           out->beta[r][s][a][b] = (double)acc;
         }
     }
+    // Difference form.  With d_m = t_{m+1} - t_m, t_j - t_{r-1} is a signed sum of the d between
+    // r-1 and j, so q_s - t_{r-1} is linear in the r-1 differences inside substencil s; and since
+    // beta_s is shift invariant (its form annihilates constants), beta_s = d^T (L^T B L) d with
+    // t_local = t_local[0] + L d_local, L[n][a] = 1 for a < n.
+    for (int s = 0; s < r; ++s) {
+      for (int a = 0; a < r - 1; ++a) out->gq[r][s][a] = 0.0;
+      for (int n = 0; n < r; ++n) {
+        const int j = s + n;              // cell index in the upwind frame (0 .. 2r-2)
+        const ld c = sub[s][n];
+        if (j > r - 1) for (int m = r - 1; m < j; ++m) out->gq[r][s][m - s] += (double)c;
+        if (j < r - 1) for (int m = j; m < r - 1; ++m) out->gq[r][s][m - s] -= (double)c;
+      }
+      for (int a = 0; a < r - 1; ++a)
+        for (int b = 0; b < r - 1; ++b) {
+          ld acc = 0.0L;
+          for (int n = 0; n < r; ++n)
+            for (int n2 = 0; n2 < r; ++n2)
+              if (a < n && b < n2) acc += (ld)out->beta[r][s][n][n2];
+          out->dbeta[r][s][a][b] = (double)acc;
+        }
+    }
     // linear weights: normal equations of the (2r-1) x r system
     ld full[kMaxN];
     reconstruction(-r, 2 * r - 1, full);

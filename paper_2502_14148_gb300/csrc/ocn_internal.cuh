@@ -21,6 +21,9 @@ struct WenoTables {
   T d[kMaxR + 1][kMaxR];                   // linear weights
   T beta[kMaxR + 1][kMaxR][kMaxR][kMaxR];  // symmetric smoothness forms
   T cen[kMaxR + 1][2 * kMaxR];             // centered order 2p: weight of cell -p+n
+  // Difference form used by the kernels (d_m = t_{m+1} - t_m in the upwind frame, m = 0..2r-3):
+  T gq[kMaxR + 1][kMaxR][kMaxR - 1];       // q_s - t_{r-1} = sum_a gq[r][s][a] d_{s+a}
+  T dbeta[kMaxR + 1][kMaxR][kMaxR - 1][kMaxR - 1];  // beta_s = sum_ab dbeta[r][s][a][b] d_{s+a} d_{s+b}
 };
 
 // Host-side derivation of the tables (coeffs.cpp).

@@ -36,9 +36,13 @@ cudaError_t upload_weno_tables(const WenoTables<double>& t) {
   // Pack beta as upper triangle with doubled off-diagonal terms.
   WenoTables<double> d = t;
   for (int r = 1; r <= kMaxR; ++r)
-    for (int s = 0; s < r; ++s)
+    for (int s = 0; s < r; ++s) {
       for (int a = 0; a < r; ++a)
         for (int b = 0; b < r; ++b) d.beta[r][s][a][b] = (b > a) ? 2.0 * t.beta[r][s][a][b] : (b == a ? t.beta[r][s][a][b] : 0.0);
+      for (int a = 0; a < r - 1; ++a)
+        for (int b = 0; b < r - 1; ++b)
+          d.dbeta[r][s][a][b] = (b > a) ? 2.0 * t.dbeta[r][s][a][b] : (b == a ? t.dbeta[r][s][a][b] : 0.0);
+    }
   WenoTables<float> f;
   const double* src = reinterpret_cast<const double*>(&d);
   float* dst = reinterpret_cast<float*>(&f);
@@ -55,12 +59,16 @@ template <> struct Tab<float> {
   static __device__ __forceinline__ float d(int r, int s) { return cWf.d[r][s]; }
   static __device__ __forceinline__ float beta(int r, int s, int a, int b) { return cWf.beta[r][s][a][b]; }
   static __device__ __forceinline__ float cen(int p, int n) { return cWf.cen[p][n]; }
+  static __device__ __forceinline__ float gq(int r, int s, int a) { return cWf.gq[r][s][a]; }
+  static __device__ __forceinline__ float db(int r, int s, int a, int b) { return cWf.dbeta[r][s][a][b]; }
 };
 template <> struct Tab<double> {
   static __device__ __forceinline__ double sub(int r, int s, int n) { return cWd.sub[r][s][n]; }
   static __device__ __forceinline__ double d(int r, int s) { return cWd.d[r][s]; }
   static __device__ __forceinline__ double beta(int r, int s, int a, int b) { return cWd.beta[r][s][a][b]; }
   static __device__ __forceinline__ double cen(int p, int n) { return cWd.cen[p][n]; }
+  static __device__ __forceinline__ double gq(int r, int s, int a) { return cWd.gq[r][s][a]; }
+  static __device__ __forceinline__ double db(int r, int s, int a, int b) { return cWd.dbeta[r][s][a][b]; }
 };
 
 __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
@@ -68,35 +76,40 @@ __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 
 // WENO(2r-1) at the interface between s[r-1] and s[r] (s holds cells m-r .. m+r-1),
 // upwinded by the sign of vel (the branch for vel >= 0 when vel == 0).
-// The upwind cell value is subtracted before the linear algebra (the
-// reconstruction weights sum to one and the indicators are shift invariant),
-// which keeps FP32 accurate for fields with a large mean.
+// Evaluated in difference form: with d_m = t_{m+1} - t_m in the upwind frame,
+// each substencil value is t_{r-1} + (linear form in its r-1 differences) and
+// each Jiang-Shu indicator a quadratic form in them (both exact rewritings of
+// the cell-value forms, the tables derived on the host).  Mirroring the
+// stencil for vel < 0 reverses and negates the differences; the indicators are
+// even in d, so only the final correction carries the sign.
 template <typename T, int r>
 __device__ __forceinline__ T weno(const T* s, T vel) {
-  T t[2 * r];
   const bool pos = vel >= T(0);
-#pragma unroll
-  for (int n = 0; n < 2 * r; ++n) t[n] = pos ? s[n] : s[2 * r - 1 - n];
   if constexpr (r == 1) {
-    return t[0];
+    return pos ? s[0] : s[1];
   } else {
-    const T ref = t[r - 1];
+    T ds[2 * r - 1];
 #pragma unroll
-    for (int n = 0; n < 2 * r; ++n) t[n] -= ref;
+    for (int n = 0; n < 2 * r - 1; ++n) ds[n] = s[n + 1] - s[n];
+    T d[2 * r - 2];                       // |upwind-frame differences| up to a common sign
+#pragma unroll
+    for (int m = 0; m < 2 * r - 2; ++m) d[m] = pos ? ds[m] : ds[2 * r - 2 - m];
+    const T ref = pos ? s[r - 1] : s[r];
+    const T sgn = pos ? T(1) : T(-1);
     T q[r], b[r];
 #pragma unroll
     for (int k = 0; k < r; ++k) {
-      T acc = T(0);
+      T acc = Tab<T>::gq(r, k, 0) * d[k];
 #pragma unroll
-      for (int n = 0; n < r; ++n) acc = fma(Tab<T>::sub(r, k, n), t[k + n], acc);
+      for (int a = 1; a < r - 1; ++a) acc = fma(Tab<T>::gq(r, k, a), d[k + a], acc);
       q[k] = acc;
       T bb = T(0);
 #pragma unroll
-      for (int a = 0; a < r; ++a) {
-        T inner = Tab<T>::beta(r, k, a, a) * t[k + a];
+      for (int a = 0; a < r - 1; ++a) {
+        T inner = Tab<T>::db(r, k, a, a) * d[k + a];
 #pragma unroll
-        for (int c = a + 1; c < r; ++c) inner = fma(Tab<T>::beta(r, k, a, c), t[k + c], inner);
-        bb = fma(inner, t[k + a], bb);
+        for (int c = a + 1; c < r - 1; ++c) inner = fma(Tab<T>::db(r, k, a, c), d[k + c], inner);
+        bb = fma(inner, d[k + a], bb);
       }
       b[k] = bb;
     }
@@ -109,7 +122,7 @@ __device__ __forceinline__ T weno(const T* s, T vel) {
       num = fma(alpha, q[k], num);
       den += alpha;
     }
-    return ref + num * rcp(den);
+    return fma(sgn, num * rcp(den), ref);
   }
 }
 
@@ -291,7 +304,17 @@ k_tendency(const TendencyArgs<T> a) {
   else if (role == 2) { hidx = (ly + H) * PW + (H - 1); phw = (ly < Ht) ? (ly + 1) * (TX + 1) : -1; }
   else if (role == 1) { hidx = (H - 1) * PW + (lx + H); phw = (lx < Wt) ? lx + 1 : -1; }
 
-  for (int k = 0; k < Nz; ++k) {
+  // Three segments of the z march: bottom levels, interior levels (every z
+  // stencil at full order, no wall), top levels.  The segment loop is unrolled,
+  // so the interior copy of the level body is compiled without wall branches.
+  const int kb = min(R - 1, Nz);
+  const int ke = max(kb, Nz - R);
+#pragma unroll
+  for (int seg = 0; seg < 3; ++seg) {
+  const bool INT = (seg == 1);
+  const int k0 = (seg == 0) ? 0 : (seg == 1 ? kb : ke);
+  const int k1 = (seg == 0) ? kb : (seg == 1 ? ke : Nz);
+  for (int k = k0; k < k1; ++k) {
     // ---- prefetch the next level's planes
     load_level(k + 1);
     load_wface(k + 2);
@@ -302,6 +325,16 @@ k_tendency(const TendencyArgs<T> a) {
     T nc_[NTR];
 #pragma unroll
     for (int t = 0; t < NTR; ++t) nc_[t] = ld_tr(t, k + 1 + R);
+    // G^{m-1} of this thread's points, loaded early (used by the update at the end of the level)
+    T gp_u = T(0), gp_v = T(0), gp_w = T(0), gp_c[NTR];
+#pragma unroll
+    for (int t = 0; t < NTR; ++t) gp_c[t] = T(0);
+    if (a.mode == 0 && a.dt_zeta != T(0) && role == 0 && active) {
+      const size_t id = (size_t)k * plane + col;
+      gp_u = a.G.u[id]; gp_v = a.G.v[id]; gp_w = a.G.w[id];
+#pragma unroll
+      for (int t = 0; t < NTR; ++t) gp_c[t] = a.G.c[t][id];
+    }
     T crk[NTR];                                  // reference profile at this level
 #pragma unroll
     for (int t = 0; t < NTR; ++t) crk[t] = cref_at(t, k);
@@ -314,7 +347,7 @@ k_tendency(const TendencyArgs<T> a) {
     const T* pN0 = sNu + (k & 3) * PLANE;       // level k
     const T* pN1 = sNu + ((k + 1) & 3) * PLANE; // level k+1
     const T rdzc_k = __ldg(a.rdzc + k);
-    const T rdzf_k = (k >= 1) ? __ldg(a.rdzf + k) : T(0);
+    const T rdzf_k = (INT || k >= 1) ? __ldg(a.rdzf + k) : T(0);
     const T rdzf_k1 = (k + 1 < Nz) ? __ldg(a.rdzf + k + 1) : T(0);
     const T rdx = a.rdx, rdy = a.rdy;
 
@@ -354,8 +387,8 @@ k_tendency(const TendencyArgs<T> a) {
       // w at (face i, face k): advecting centered_z(u) (own column), advected WENO_x(w)
       {
         T F = T(0);
-        if (k >= 1) {
-          const int p = min(P, min(k, Nz - k));
+        if (INT || k >= 1) {
+          const int p = INT ? P : min(P, min(k, Nz - k));
           const T U = centered_reduced<T, R, 1>(ru, p);   // ru-1: levels k-R .. k+R-1 around face k
           T sw[2 * R];
 #pragma unroll
@@ -424,8 +457,8 @@ k_tendency(const TendencyArgs<T> a) {
       // w at (face j, face k): advecting centered_z(v) (own column), advected WENO_y(w)
       {
         T F = T(0);
-        if (k >= 1) {
-          const int p = min(P, min(k, Nz - k));
+        if (INT || k >= 1) {
+          const int p = INT ? P : min(P, min(k, Nz - k));
           const T V = centered_reduced<T, R, 1>(rv, p);
           T sw[2 * R];
 #pragma unroll
@@ -463,8 +496,8 @@ k_tendency(const TendencyArgs<T> a) {
 #pragma unroll
     for (int t = 0; t < NTR; ++t) nz_c[t] = T(0);
     if (role == 0) {
-      const bool top = (k + 1 == Nz);
-      const int r = min(R, min(k + 1, Nz - k - 1));        // centre fields at face k+1
+      const bool top = !INT && (k + 1 == Nz);
+      const int r = INT ? R : min(R, min(k + 1, Nz - k - 1));        // centre fields at face k+1
       // u at (face i, face k+1): advecting centered_x(w at face k+1)
       if (top) nz_u = a.top[0];
       else {
@@ -514,8 +547,8 @@ k_tendency(const TendencyArgs<T> a) {
       }
       // w through centre k (w interface k+1; valid faces 0..Nz)
       {
-        const int rw_ = min(R, min(k + 1, Nz - k));
-        const int pw_ = min(P, min(k + 1, Nz - k));
+        const int rw_ = INT ? R : min(R, min(k + 1, Nz - k));
+        const int pw_ = INT ? P : min(P, min(k + 1, Nz - k));
         const T Wv = centered_reduced<T, R, 0>(rw, pw_);
         T F = Wv * weno_reduced<T, R>(rw, rw_, Wv);
         const T dw = (rw[R] - rw[R - 1]) * rdzc_k;
@@ -533,7 +566,7 @@ k_tendency(const TendencyArgs<T> a) {
       const T bhere = (role == 0) ? buoyancy(a, rc[0][R - 1], rc[t1][R - 1])
                                   : buoyancy(a, pC0[hidx] + crk[0], pC1[hidx] + crk[t1]);
       const T anom = bhere - bref;
-      if (k >= 1) phy = fma(__ldg(a.dzf + k) * T(0.5), anom_prev + anom, phy);
+      if (INT || k >= 1) phy = fma(__ldg(a.dzf + k) * T(0.5), anom_prev + anom, phy);
       anom_prev = anom;
       if (phw >= 0) PHs[phw] = phy;
     }
@@ -552,7 +585,7 @@ k_tendency(const TendencyArgs<T> a) {
         if (split) G -= (PHs[(ly + 1) * (TX + 1) + lx + 1] - PHs[(ly + 1) * (TX + 1) + lx]) * rdx;
         if (a.mode == 0) {
           T upd = fma(a.dt_gamma, G, ru[R - 1]);
-          if (a.dt_zeta != T(0)) upd = fma(-a.dt_zeta, a.G.u[id], upd);
+          if (a.dt_zeta != T(0)) upd = fma(-a.dt_zeta, gp_u, upd);
           a.nxt.u[id] = upd;
         }
         a.G.u[id] = G;
@@ -564,7 +597,7 @@ k_tendency(const TendencyArgs<T> a) {
         if (split) G -= (PHs[(ly + 1) * (TX + 1) + lx + 1] - PHs[ly * (TX + 1) + lx + 1]) * rdy;
         if (a.mode == 0) {
           T upd = fma(a.dt_gamma, G, rv[R - 1]);
-          if (a.dt_zeta != T(0)) upd = fma(-a.dt_zeta, a.G.v[id], upd);
+          if (a.dt_zeta != T(0)) upd = fma(-a.dt_zeta, gp_v, upd);
           a.nxt.v[id] = upd;
         }
         a.G.v[id] = G;
@@ -572,7 +605,7 @@ k_tendency(const TendencyArgs<T> a) {
       // w at face k
       {
         T G = T(0);
-        if (k >= 1) {
+        if (INT || k >= 1) {
           G = -(FXu[2 * FXS + 1] - FXu[2 * FXS]) * rdx - (FYu[2 * FYS + TX] - FYu[2 * FYS]) * rdy
               - (nz_w - fz_w) * rdzf_k;
           if (!split) {   // unsplit form (tendency output): + b interpolated to the w face
@@ -583,15 +616,15 @@ k_tendency(const TendencyArgs<T> a) {
         }
         if (a.mode == 0) {
           T upd = T(0);
-          if (k >= 1) {
+          if (INT || k >= 1) {
             upd = fma(a.dt_gamma, G, rw[R - 1]);
-            if (a.dt_zeta != T(0)) upd = fma(-a.dt_zeta, a.G.w[id], upd);
+            if (a.dt_zeta != T(0)) upd = fma(-a.dt_zeta, gp_w, upd);
           }
           a.nxt.w[id] = upd;
-          if (k == Nz - 1) a.nxt.w[id + plane] = T(0);
+          if (!INT && k == Nz - 1) a.nxt.w[id + plane] = T(0);
         }
         a.G.w[id] = G;
-        if (k == Nz - 1) a.G.w[id + plane] = T(0);
+        if (!INT && k == Nz - 1) a.G.w[id + plane] = T(0);
       }
 #pragma unroll
       for (int t = 0; t < NTR; ++t) {
@@ -599,7 +632,7 @@ k_tendency(const TendencyArgs<T> a) {
               - (nz_c[t] - fz_c[t]) * rdzc_k;
         if (a.mode == 0) {
           T upd = fma(a.dt_gamma, G, sC[(2 * t + (k & 1)) * PLANE + rowc]);   // the stored anomaly
-          if (a.dt_zeta != T(0)) upd = fma(-a.dt_zeta, a.G.c[t][id], upd);
+          if (a.dt_zeta != T(0)) upd = fma(-a.dt_zeta, gp_c[t], upd);
           a.nxt.c[t][id] = upd;
         }
         a.G.c[t][id] = G;
@@ -621,6 +654,7 @@ k_tendency(const TendencyArgs<T> a) {
     }
     cp_async_wait_all();
     __syncthreads();
+  }
   }
 }
 
@@ -670,111 +704,133 @@ cudaError_t launch_tendency(const TendencyArgs<T>& a, int weno_r, cudaStream_t s
 
 // --------------------------------------------------------------------------
 // Eddy diffusivities at cell centres (Sec. 3.1.1): Smagorinsky-Lilly and AMD.
-// One thread per cell; neighbours come through the read-only cache.
+// One thread per (i, j) column marching up in z: the values on face / level
+// k+1 loaded for one level are reused as the k values of the next, so each cell
+// costs about twenty loads (horizontal neighbours come through L1).
 template <typename T>
 __global__ void __launch_bounds__(256) k_closure(const ClosureArgs<T> a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
   const int Nx = a.Nx, Ny = a.Ny, Nz = a.Nz;
   if (i >= Nx || j >= Ny) return;
   const size_t plane = (size_t)Nx * Ny;
   const int ip = (i + 1 == Nx) ? 0 : i + 1, im = (i == 0) ? Nx - 1 : i - 1;
   const int jp = (j + 1 == Ny) ? 0 : j + 1, jm = (j == 0) ? Ny - 1 : j - 1;
-  auto U = [&](int ii, int jj, int kk) { return __ldg(a.cur.u + (size_t)kk * plane + (size_t)jj * Nx + ii); };
-  auto V = [&](int ii, int jj, int kk) { return __ldg(a.cur.v + (size_t)kk * plane + (size_t)jj * Nx + ii); };
-  auto Wf = [&](int ii, int jj, int kk) { return __ldg(a.cur.w + (size_t)kk * plane + (size_t)jj * Nx + ii); };
+  // column offsets inside a level
+  const size_t c00 = (size_t)j * Nx + i, cp0 = (size_t)j * Nx + ip, cm0 = (size_t)j * Nx + im;
+  const size_t c0p = (size_t)jp * Nx + i, c0m = (size_t)jm * Nx + i;
+  const size_t cpp = (size_t)jp * Nx + ip, cpm = (size_t)jm * Nx + ip, cmp = (size_t)jp * Nx + im;
   const T rdx = a.rdx, rdy = a.rdy;
-  const T rdzc = __ldg(a.rdzc + k);
-  const T rdzf0 = (k >= 1) ? __ldg(a.rdzf + k) : T(0);
-  const T rdzf1 = (k + 1 < Nz) ? __ldg(a.rdzf + k + 1) : T(0);
-  // natural-location derivatives around the centre
-  auto dudy_ffc = [&](int ii, int jj) { return (U(ii, jj, k) - U(ii, jj == 0 ? Ny - 1 : jj - 1, k)) * rdy; };
-  auto dvdx_ffc = [&](int ii, int jj) { return (V(ii, jj, k) - V(ii == 0 ? Nx - 1 : ii - 1, jj, k)) * rdx; };
-  auto dudz_fcf = [&](int ii, int kk, T rz) { return (kk <= 0 || kk >= Nz) ? T(0) : (U(ii, j, kk) - U(ii, j, kk - 1)) * rz; };
-  auto dvdz_cff = [&](int jj, int kk, T rz) { return (kk <= 0 || kk >= Nz) ? T(0) : (V(i, jj, kk) - V(i, jj, kk - 1)) * rz; };
-  auto dwdx_fcf = [&](int ii, int kk) { return (Wf(ii, j, kk) - Wf(ii == 0 ? Nx - 1 : ii - 1, j, kk)) * rdx; };
-  auto dwdy_cff = [&](int jj, int kk) { return (Wf(i, jj, kk) - Wf(i, jj == 0 ? Ny - 1 : jj - 1, kk)) * rdy; };
-
-  const T ux = (U(ip, j, k) - U(i, j, k)) * rdx;
-  const T vy = (V(i, jp, k) - V(i, j, k)) * rdy;
-  const T wz = (Wf(i, j, k + 1) - Wf(i, j, k)) * rdzc;
-  const T uy = T(0.25) * (dudy_ffc(i, j) + dudy_ffc(ip, j) + dudy_ffc(i, jp) + dudy_ffc(ip, jp));
-  const T vx = T(0.25) * (dvdx_ffc(i, j) + dvdx_ffc(ip, j) + dvdx_ffc(i, jp) + dvdx_ffc(ip, jp));
-  const T uz = T(0.25) * (dudz_fcf(i, k, rdzf0) + dudz_fcf(ip, k, rdzf0) + dudz_fcf(i, k + 1, rdzf1) + dudz_fcf(ip, k + 1, rdzf1));
-  const T wx = T(0.25) * (dwdx_fcf(i, k) + dwdx_fcf(ip, k) + dwdx_fcf(i, k + 1) + dwdx_fcf(ip, k + 1));
-  const T vz = T(0.25) * (dvdz_cff(j, k, rdzf0) + dvdz_cff(jp, k, rdzf0) + dvdz_cff(j, k + 1, rdzf1) + dvdz_cff(jp, k + 1, rdzf1));
-  const T wy = T(0.25) * (dwdy_cff(j, k) + dwdy_cff(jp, k) + dwdy_cff(j, k + 1) + dwdy_cff(jp, k + 1));
-  const size_t id = (size_t)k * plane + (size_t)j * Nx + i;
-  const T dz = __ldg(a.dzc + k);
-
-  // tracers are stored about per-level reference profiles: add them back where levels mix
+  const T* U = a.cur.u;
+  const T* V = a.cur.v;
+  const T* W = a.cur.w;
   auto cref = [&](int t, int kk) -> T { return a.cref[t] ? __ldg(a.cref[t] + kk) : T(0); };
-  auto bof = [&](int kk) -> T {
-    const size_t o = (size_t)kk * plane + (size_t)j * Nx + i;
+  auto buoy = [&](int kk) -> T {   // b at (i, j, kk), tracers stored about their profiles
+    const size_t o = (size_t)kk * plane + c00;
     if (a.eos == OCN_EOS_LINEAR_TS)
       return a.g_alpha * (__ldg(a.cur.c[0] + o) + cref(0, kk) - a.T0) - a.g_beta * (__ldg(a.cur.c[1] + o) + cref(1, kk) - a.S0);
     return __ldg(a.cur.c[0] + o) + cref(0, kk);
   };
-
-  if (a.closure == OCN_CLOSURE_SMAGORINSKY) {
-    const T S12 = T(0.5) * (uy + vx), S13 = T(0.5) * (uz + wx), S23 = T(0.5) * (vz + wy);
-    const T SS = T(2) * (ux * ux + vy * vy + wz * wz + T(2) * (S12 * S12 + S13 * S13 + S23 * S23));
-    T nu = T(0);
-    if (SS > T(0)) {
-      const T b0 = bof(k);
-      const T dbb = (k >= 1) ? (b0 - bof(k - 1)) * rdzf0 : T(0);
-      const T dbt = (k + 1 < Nz) ? (bof(k + 1) - b0) * rdzf1 : T(0);
-      const T N2 = T(0.5) * (dbb + dbt);
-      const T Delta = cbrt(a.dx * a.dy * dz);
-      const T CD = a.Cs * Delta;
-      T stab = T(1) - a.Cb * N2 * a.inv_Pr / SS;
-      stab = stab > T(0) ? stab : T(0);
-      nu = CD * CD * sqrt(SS) * sqrt(stab);
-    }
-    a.nu[id] = nu;
-  } else {  // AMD
-    const T G[3][3] = {{ux, uy, uz}, {vx, vy, vz}, {wx, wy, wz}};
-    const T D2[3] = {a.dx * a.dx, a.dy * a.dy, dz * dz};
-    T num = T(0), den = T(0);
-#pragma unroll
-    for (int p = 0; p < 3; ++p)
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const T Spq = T(0.5) * (G[p][q] + G[q][p]);
-#pragma unroll
-        for (int m = 0; m < 3; ++m) num += D2[m] * G[p][m] * G[q][m] * Spq;
-        den += G[p][q] * G[p][q];
+  // carried from level to level: u at (i|ip, j) and v at (i, j|jp) on the current level, w on face k,
+  // the two lower-face z-derivatives, b below
+  T u0 = __ldg(U + c00), u1 = __ldg(U + cp0);
+  T v0 = __ldg(V + c00), v1 = __ldg(V + c0p);
+  T w00 = __ldg(W + c00), wm0 = __ldg(W + cm0), wp0 = __ldg(W + cp0), w0m = __ldg(W + c0m), w0p = __ldg(W + c0p);
+  T dudz_lo0 = T(0), dudz_lo1 = T(0), dvdz_lo0 = T(0), dvdz_lo1 = T(0);   // faces at k (walls: 0)
+  T b_prev = T(0), b_cur = (a.closure == OCN_CLOSURE_SMAGORINSKY) ? buoy(0) : T(0);
+  for (int k = 0; k < Nz; ++k) {
+    const size_t L = (size_t)k * plane, L1 = L + plane;
+    const T rdzc = __ldg(a.rdzc + k);
+    const T rdzf1 = (k + 1 < Nz) ? __ldg(a.rdzf + k + 1) : T(0);
+    const T dz = __ldg(a.dzc + k);
+    // next level (k+1) of the carried columns, and face k+1 of w
+    T un0 = T(0), un1 = T(0), vn0 = T(0), vn1 = T(0);
+    if (k + 1 < Nz) { un0 = __ldg(U + L1 + c00); un1 = __ldg(U + L1 + cp0); vn0 = __ldg(V + L1 + c00); vn1 = __ldg(V + L1 + c0p); }
+    const T w01 = __ldg(W + L1 + c00), wm1 = __ldg(W + L1 + cm0), wp1 = __ldg(W + L1 + cp0);
+    const T w0m1 = __ldg(W + L1 + c0m), w0p1 = __ldg(W + L1 + c0p);
+    // horizontal neighbours on level k
+    const T u_0m = __ldg(U + L + c0m), u_1m = __ldg(U + L + cpm), u_0p = __ldg(U + L + c0p), u_1p = __ldg(U + L + cpp);
+    const T v_m0 = __ldg(V + L + cm0), v_p0 = __ldg(V + L + cp0), v_mp = __ldg(V + L + cmp), v_pp = __ldg(V + L + cpp);
+    const T ux = (u1 - u0) * rdx;
+    const T vy = (v1 - v0) * rdy;
+    const T wz = (w01 - w00) * rdzc;
+    // d u/dy at the four (f, f) edges around the centre, d v/dx likewise
+    const T uy = T(0.25) * ((u0 - u_0m) + (u1 - u_1m) + (u_0p - u0) + (u_1p - u1)) * rdy;
+    const T vx = T(0.25) * ((v0 - v_m0) + (v_p0 - v0) + (v1 - v_mp) + (v_pp - v1)) * rdx;
+    // z-derivatives on face k+1 (walls: 0), averaged with face k
+    const T dudz_hi0 = (k + 1 < Nz) ? (un0 - u0) * rdzf1 : T(0);
+    const T dudz_hi1 = (k + 1 < Nz) ? (un1 - u1) * rdzf1 : T(0);
+    const T dvdz_hi0 = (k + 1 < Nz) ? (vn0 - v0) * rdzf1 : T(0);
+    const T dvdz_hi1 = (k + 1 < Nz) ? (vn1 - v1) * rdzf1 : T(0);
+    const T uz = T(0.25) * (dudz_lo0 + dudz_lo1 + dudz_hi0 + dudz_hi1);
+    const T vz = T(0.25) * (dvdz_lo0 + dvdz_lo1 + dvdz_hi0 + dvdz_hi1);
+    const T wx = T(0.25) * ((w00 - wm0) + (wp0 - w00) + (w01 - wm1) + (wp1 - w01)) * rdx;
+    const T wy = T(0.25) * ((w00 - w0m) + (w0p - w00) + (w01 - w0m1) + (w0p1 - w01)) * rdy;
+    const size_t id = L + c00;
+    if (a.closure == OCN_CLOSURE_SMAGORINSKY) {
+      const T b_next = (k + 1 < Nz) ? buoy(k + 1) : T(0);
+      const T S12 = T(0.5) * (uy + vx), S13 = T(0.5) * (uz + wx), S23 = T(0.5) * (vz + wy);
+      const T SS = T(2) * (ux * ux + vy * vy + wz * wz + T(2) * (S12 * S12 + S13 * S13 + S23 * S23));
+      T nu = T(0);
+      if (SS > T(0)) {
+        const T dbb = (k >= 1) ? (b_cur - b_prev) * __ldg(a.rdzf + k) : T(0);
+        const T dbt = (k + 1 < Nz) ? (b_next - b_cur) * rdzf1 : T(0);
+        const T N2 = T(0.5) * (dbb + dbt);
+        const T Delta = cbrt(a.dx * a.dy * dz);
+        const T CD = a.Cs * Delta;
+        T stab = T(1) - a.Cb * N2 * a.inv_Pr / SS;
+        stab = stab > T(0) ? stab : T(0);
+        nu = CD * CD * sqrt(SS) * sqrt(stab);
       }
-    T nu = (den > T(0)) ? -a.C_amd * num / den : T(0);
-    a.nu[id] = nu > T(0) ? nu : T(0);
-    for (int t = 0; t < a.nt; ++t) {
-      const T* c = a.cur.c[t];
-      auto C = [&](int ii, int jj, int kk) { return __ldg(c + (size_t)kk * plane + (size_t)jj * Nx + ii); };
-      const T c0 = C(i, j, k);
-      T dc[3];
-      dc[0] = T(0.5) * ((c0 - C(im, j, k)) + (C(ip, j, k) - c0)) * rdx;
-      dc[1] = T(0.5) * ((c0 - C(i, jm, k)) + (C(i, jp, k) - c0)) * rdy;
-      const T dcb = (k >= 1) ? ((c0 - C(i, j, k - 1)) + (cref(t, k) - cref(t, k - 1))) * rdzf0 : T(0);
-      const T dct = (k + 1 < Nz) ? ((C(i, j, k + 1) - c0) + (cref(t, k + 1) - cref(t, k))) * rdzf1 : T(0);
-      dc[2] = T(0.5) * (dcb + dct);
-      T cn = T(0), cd = T(0);
+      a.nu[id] = nu;
+      b_prev = b_cur;
+      b_cur = b_next;
+    } else {  // AMD
+      const T G[3][3] = {{ux, uy, uz}, {vx, vy, vz}, {wx, wy, wz}};
+      const T D2[3] = {a.dx * a.dx, a.dy * a.dy, dz * dz};
+      T num = T(0), den = T(0);
 #pragma unroll
-      for (int m = 0; m < 3; ++m)
+      for (int p = 0; p < 3; ++p)
 #pragma unroll
-        for (int p = 0; p < 3; ++p) cn += D2[m] * G[p][m] * dc[m] * dc[p];
+        for (int q = 0; q < 3; ++q) {
+          const T Spq = T(0.5) * (G[p][q] + G[q][p]);
 #pragma unroll
-      for (int p = 0; p < 3; ++p) cd += dc[p] * dc[p];
-      T kap = (cd > T(0)) ? -a.C_amd * cn / cd : T(0);
-      a.kap[t][id] = kap > T(0) ? kap : T(0);
+          for (int m = 0; m < 3; ++m) num += D2[m] * G[p][m] * G[q][m] * Spq;
+          den += G[p][q] * G[p][q];
+        }
+      T nu = (den > T(0)) ? -a.C_amd * num / den : T(0);
+      a.nu[id] = nu > T(0) ? nu : T(0);
+      for (int t = 0; t < a.nt; ++t) {
+        const T* c = a.cur.c[t];
+        const T c0 = __ldg(c + id);
+        T dc[3];
+        dc[0] = T(0.5) * ((c0 - __ldg(c + L + cm0)) + (__ldg(c + L + cp0) - c0)) * rdx;
+        dc[1] = T(0.5) * ((c0 - __ldg(c + L + c0m)) + (__ldg(c + L + c0p) - c0)) * rdy;
+        const T dcb = (k >= 1) ? ((c0 - __ldg(c + id - plane)) + (cref(t, k) - cref(t, k - 1))) * __ldg(a.rdzf + k) : T(0);
+        const T dct = (k + 1 < Nz) ? ((__ldg(c + id + plane) - c0) + (cref(t, k + 1) - cref(t, k))) * rdzf1 : T(0);
+        dc[2] = T(0.5) * (dcb + dct);
+        T cn = T(0), cd = T(0);
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+#pragma unroll
+          for (int p = 0; p < 3; ++p) cn += D2[m] * G[p][m] * dc[m] * dc[p];
+#pragma unroll
+        for (int p = 0; p < 3; ++p) cd += dc[p] * dc[p];
+        T kap = (cd > T(0)) ? -a.C_amd * cn / cd : T(0);
+        a.kap[t][id] = kap > T(0) ? kap : T(0);
+      }
     }
+    // advance
+    u0 = un0; u1 = un1; v0 = vn0; v1 = vn1;
+    w00 = w01; wm0 = wm1; wp0 = wp1; w0m = w0m1; w0p = w0p1;
+    dudz_lo0 = dudz_hi0; dudz_lo1 = dudz_hi1; dvdz_lo0 = dvdz_hi0; dvdz_lo1 = dvdz_hi1;
   }
 }
 
 template <typename T>
 cudaError_t launch_closure(const ClosureArgs<T>& a, cudaStream_t s) {
   dim3 blk(32, 8);
-  dim3 grid((a.Nx + 31) / 32, (a.Ny + 7) / 8, a.Nz);
+  dim3 grid((a.Nx + 31) / 32, (a.Ny + 7) / 8);
   k_closure<T><<<grid, blk, 0, s>>>(a);
   return cudaGetLastError();
 }
