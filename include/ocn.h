@@ -190,8 +190,20 @@ ocn_status ocn_diagnostics(ocn_model* model, double dt, double* out, int nout);
  * OCN_OPT_SYNC_CHECK: 1 synchronises and checks for errors after every kernel.
  * OCN_OPT_KERNEL_TIMING: 1 launches directly and brackets every kernel with
  * CUDA events on the model stream (read with ocn_kernel_times); 0 (default) off. */
-enum { OCN_OPT_GRAPHS = 1, OCN_OPT_SYNC_CHECK = 2, OCN_OPT_KERNEL_TIMING = 3 };
+enum { OCN_OPT_GRAPHS = 1, OCN_OPT_SYNC_CHECK = 2, OCN_OPT_KERNEL_TIMING = 3, OCN_OPT_TENDENCY_VARIANT = 4 };
 ocn_status ocn_set_option(ocn_model* model, int option, long long value);
+
+/* Tile variants of the FP32 tendency kernel (OCN_OPT_TENDENCY_VARIANT): 0 = 32x8
+ * columns per CTA, one CTA per SM (default); 1 = 32x8, two CTAs per SM; 2 = 32x16;
+ * 3 = 32x4, three CTAs per SM.  All compute the same values. */
+#define OCN_TENDENCY_VARIANTS 4
+
+/* Autotuner: times every tendency variant on the model's current state (tendency
+ * only: the state is not advanced; G is overwritten), selects the fastest and
+ * returns its index in *best and the milliseconds per launch of every variant in
+ * ms[OCN_TENDENCY_VARIANTS] (either may be NULL).  Synchronises the stream.
+ * Errors: OCN_ERR_STATE (no arena), OCN_ERR_CUDA. */
+ocn_status ocn_autotune(ocn_model* model, int* best, double* ms);
 
 /* Kernel classes reported by ocn_kernel_times. */
 enum {

@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libocn.so")
-SOURCES = ["capi.cu", "coeffs.cpp", "tendency.cu", "poisson.cu", "reduce.cu", "noalloc.cu"]
+SOURCES = ["capi.cu", "coeffs.cpp", "tendency_f32_r5.cu", "tendency_f32_r3.cu", "tendency_f64.cu", "closure.cu",
+           "poisson.cu", "reduce.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -44,7 +45,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     os.makedirs(OBJ, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
-    headers = [os.path.join(CSRC, "ocn_internal.cuh"), os.path.join(ROOT, "include", "ocn.h")]
+    headers = [os.path.join(CSRC, "ocn_internal.cuh"), os.path.join(CSRC, "tendency_kernel.cuh"),
+               os.path.join(ROOT, "include", "ocn.h")]
     flags = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
              "-I" + os.path.join(ROOT, "include")] + ARCH
     if verbose:

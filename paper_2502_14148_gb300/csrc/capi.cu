@@ -111,6 +111,7 @@ struct ocn_model {
   char* arena = nullptr;
   int cur = 0;
   bool graphs = true, sync_check = false;
+  int variant = 0;                  // FP32 tendency tile variant
   std::map<std::pair<uint64_t, int>, cudaGraphExec_t> graph_cache;
   int launches_per_step = 0;
   FftPlan px, py;
@@ -305,6 +306,7 @@ cudaError_t enqueue_tendency(ocn_model* m, int which, double dt_gamma, double dt
   for (int n = 0; n < 2 + kMaxTracers; ++n) { a.top[n] = (T)m->d.top_flux[n]; a.bot[n] = (T)m->d.bottom_flux[n]; }
   a.dt_gamma = (T)dt_gamma; a.dt_zeta = (T)dt_zeta;
   a.mode = mode;
+  a.variant = m->variant;
   m->hook.pre(OCN_K_TENDENCY);
   cudaError_t e = launch_tendency<T>(a, m->R, m->stream);
   m->hook.post(OCN_K_TENDENCY);
@@ -682,6 +684,13 @@ ocn_status ocn_set_option(ocn_model* m, int option, long long value) {
   if (!m) return fail(OCN_ERR_ARG, "null argument");
   if (option == OCN_OPT_GRAPHS) { m->graphs = value != 0; return OCN_OK; }
   if (option == OCN_OPT_SYNC_CHECK) { m->sync_check = value != 0; return OCN_OK; }
+  if (option == OCN_OPT_TENDENCY_VARIANT) {
+    if (value < 0 || value >= kTendencyVariants) return fail(OCN_ERR_ARG, "tendency variant out of range");
+    DeviceGuard dg(m->dev);
+    if (m->variant != (int)value) drop_graphs(m);
+    m->variant = (int)value;
+    return OCN_OK;
+  }
   if (option == OCN_OPT_KERNEL_TIMING) {
     DeviceGuard dg(m->dev);
     cudaStreamSynchronize(m->stream);
@@ -692,6 +701,50 @@ ocn_status ocn_set_option(ocn_model* m, int option, long long value) {
     return OCN_OK;
   }
   return fail(OCN_ERR_ARG, "unknown option");
+}
+
+ocn_status ocn_autotune(ocn_model* m, int* best, double* ms) {
+  if (!m) return fail(OCN_ERR_ARG, "null argument");
+  if (!m->arena) return fail(OCN_ERR_STATE, "arena not bound");
+  DeviceGuard dg(m->dev);
+  const int nv = (m->es == 4) ? kTendencyVariants : 1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune events");
+  const int saved = m->variant;
+  const bool saved_timing = m->timing;
+  const LaunchHook saved_hook = m->hook;
+  m->timing = false;
+  m->hook = LaunchHook();
+  int arg = 0;
+  float bestms = 1e30f;
+  for (int v = 0; v < kTendencyVariants; ++v) {
+    float t = 1e30f;
+    if (v < nv) {
+      m->variant = v;
+      e = (m->es == 4) ? enqueue_tendency<float>(m, m->cur, 0.0, 0.0, 1) : enqueue_tendency<double>(m, m->cur, 0.0, 0.0, 1);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, m->stream);
+      for (int r = 0; r < 2 && e == cudaSuccess; ++r)
+        e = (m->es == 4) ? enqueue_tendency<float>(m, m->cur, 0.0, 0.0, 1) : enqueue_tendency<double>(m, m->cur, 0.0, 0.0, 1);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, m->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+      if (e != cudaSuccess) break;
+      t *= 0.5f;
+      if (t < bestms) { bestms = t; arg = v; }
+    }
+    if (ms) ms[v] = (v < nv) ? (double)t : -1.0;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  m->timing = saved_timing;
+  m->hook = saved_hook;
+  if (e != cudaSuccess) { m->variant = saved; return cuda_fail(e, "autotune"); }
+  if (arg != saved) drop_graphs(m);
+  m->variant = arg;
+  if (best) *best = arg;
+  return OCN_OK;
 }
 
 ocn_status ocn_kernel_times(ocn_model* m, int* counts, double* ms) {

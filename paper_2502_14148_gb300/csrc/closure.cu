@@ -1,0 +1,143 @@
+// Eddy diffusivities (Smagorinsky-Lilly, AMD) at cell centres.
+#include <cuda_runtime.h>
+
+#include "ocn_internal.cuh"
+
+namespace ocn {
+
+// Eddy diffusivities at cell centres (Sec. 3.1.1): Smagorinsky-Lilly and AMD.
+// One thread per (i, j) column marching up in z: the values on face / level
+// k+1 loaded for one level are reused as the k values of the next, so each cell
+// costs about twenty loads (horizontal neighbours come through L1).
+template <typename T>
+__global__ void __launch_bounds__(256) k_closure(const ClosureArgs<T> a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int Nx = a.Nx, Ny = a.Ny, Nz = a.Nz;
+  if (i >= Nx || j >= Ny) return;
+  const size_t plane = (size_t)Nx * Ny;
+  const int ip = (i + 1 == Nx) ? 0 : i + 1, im = (i == 0) ? Nx - 1 : i - 1;
+  const int jp = (j + 1 == Ny) ? 0 : j + 1, jm = (j == 0) ? Ny - 1 : j - 1;
+  // column offsets inside a level
+  const size_t c00 = (size_t)j * Nx + i, cp0 = (size_t)j * Nx + ip, cm0 = (size_t)j * Nx + im;
+  const size_t c0p = (size_t)jp * Nx + i, c0m = (size_t)jm * Nx + i;
+  const size_t cpp = (size_t)jp * Nx + ip, cpm = (size_t)jm * Nx + ip, cmp = (size_t)jp * Nx + im;
+  const T rdx = a.rdx, rdy = a.rdy;
+  const T* U = a.cur.u;
+  const T* V = a.cur.v;
+  const T* W = a.cur.w;
+  auto cref = [&](int t, int kk) -> T { return a.cref[t] ? __ldg(a.cref[t] + kk) : T(0); };
+  auto buoy = [&](int kk) -> T {   // b at (i, j, kk), tracers stored about their profiles
+    const size_t o = (size_t)kk * plane + c00;
+    if (a.eos == OCN_EOS_LINEAR_TS)
+      return a.g_alpha * (__ldg(a.cur.c[0] + o) + cref(0, kk) - a.T0) - a.g_beta * (__ldg(a.cur.c[1] + o) + cref(1, kk) - a.S0);
+    return __ldg(a.cur.c[0] + o) + cref(0, kk);
+  };
+  // carried from level to level: u at (i|ip, j) and v at (i, j|jp) on the current level, w on face k,
+  // the two lower-face z-derivatives, b below
+  T u0 = __ldg(U + c00), u1 = __ldg(U + cp0);
+  T v0 = __ldg(V + c00), v1 = __ldg(V + c0p);
+  T w00 = __ldg(W + c00), wm0 = __ldg(W + cm0), wp0 = __ldg(W + cp0), w0m = __ldg(W + c0m), w0p = __ldg(W + c0p);
+  T dudz_lo0 = T(0), dudz_lo1 = T(0), dvdz_lo0 = T(0), dvdz_lo1 = T(0);   // faces at k (walls: 0)
+  T b_prev = T(0), b_cur = (a.closure == OCN_CLOSURE_SMAGORINSKY) ? buoy(0) : T(0);
+  for (int k = 0; k < Nz; ++k) {
+    const size_t L = (size_t)k * plane, L1 = L + plane;
+    const T rdzc = __ldg(a.rdzc + k);
+    const T rdzf1 = (k + 1 < Nz) ? __ldg(a.rdzf + k + 1) : T(0);
+    const T dz = __ldg(a.dzc + k);
+    // next level (k+1) of the carried columns, and face k+1 of w
+    T un0 = T(0), un1 = T(0), vn0 = T(0), vn1 = T(0);
+    if (k + 1 < Nz) { un0 = __ldg(U + L1 + c00); un1 = __ldg(U + L1 + cp0); vn0 = __ldg(V + L1 + c00); vn1 = __ldg(V + L1 + c0p); }
+    const T w01 = __ldg(W + L1 + c00), wm1 = __ldg(W + L1 + cm0), wp1 = __ldg(W + L1 + cp0);
+    const T w0m1 = __ldg(W + L1 + c0m), w0p1 = __ldg(W + L1 + c0p);
+    // horizontal neighbours on level k
+    const T u_0m = __ldg(U + L + c0m), u_1m = __ldg(U + L + cpm), u_0p = __ldg(U + L + c0p), u_1p = __ldg(U + L + cpp);
+    const T v_m0 = __ldg(V + L + cm0), v_p0 = __ldg(V + L + cp0), v_mp = __ldg(V + L + cmp), v_pp = __ldg(V + L + cpp);
+    const T ux = (u1 - u0) * rdx;
+    const T vy = (v1 - v0) * rdy;
+    const T wz = (w01 - w00) * rdzc;
+    // d u/dy at the four (f, f) edges around the centre, d v/dx likewise
+    const T uy = T(0.25) * ((u0 - u_0m) + (u1 - u_1m) + (u_0p - u0) + (u_1p - u1)) * rdy;
+    const T vx = T(0.25) * ((v0 - v_m0) + (v_p0 - v0) + (v1 - v_mp) + (v_pp - v1)) * rdx;
+    // z-derivatives on face k+1 (walls: 0), averaged with face k
+    const T dudz_hi0 = (k + 1 < Nz) ? (un0 - u0) * rdzf1 : T(0);
+    const T dudz_hi1 = (k + 1 < Nz) ? (un1 - u1) * rdzf1 : T(0);
+    const T dvdz_hi0 = (k + 1 < Nz) ? (vn0 - v0) * rdzf1 : T(0);
+    const T dvdz_hi1 = (k + 1 < Nz) ? (vn1 - v1) * rdzf1 : T(0);
+    const T uz = T(0.25) * (dudz_lo0 + dudz_lo1 + dudz_hi0 + dudz_hi1);
+    const T vz = T(0.25) * (dvdz_lo0 + dvdz_lo1 + dvdz_hi0 + dvdz_hi1);
+    const T wx = T(0.25) * ((w00 - wm0) + (wp0 - w00) + (w01 - wm1) + (wp1 - w01)) * rdx;
+    const T wy = T(0.25) * ((w00 - w0m) + (w0p - w00) + (w01 - w0m1) + (w0p1 - w01)) * rdy;
+    const size_t id = L + c00;
+    if (a.closure == OCN_CLOSURE_SMAGORINSKY) {
+      const T b_next = (k + 1 < Nz) ? buoy(k + 1) : T(0);
+      const T S12 = T(0.5) * (uy + vx), S13 = T(0.5) * (uz + wx), S23 = T(0.5) * (vz + wy);
+      const T SS = T(2) * (ux * ux + vy * vy + wz * wz + T(2) * (S12 * S12 + S13 * S13 + S23 * S23));
+      T nu = T(0);
+      if (SS > T(0)) {
+        const T dbb = (k >= 1) ? (b_cur - b_prev) * __ldg(a.rdzf + k) : T(0);
+        const T dbt = (k + 1 < Nz) ? (b_next - b_cur) * rdzf1 : T(0);
+        const T N2 = T(0.5) * (dbb + dbt);
+        const T Delta = cbrt(a.dx * a.dy * dz);
+        const T CD = a.Cs * Delta;
+        T stab = T(1) - a.Cb * N2 * a.inv_Pr / SS;
+        stab = stab > T(0) ? stab : T(0);
+        nu = CD * CD * sqrt(SS) * sqrt(stab);
+      }
+      a.nu[id] = nu;
+      b_prev = b_cur;
+      b_cur = b_next;
+    } else {  // AMD
+      const T G[3][3] = {{ux, uy, uz}, {vx, vy, vz}, {wx, wy, wz}};
+      const T D2[3] = {a.dx * a.dx, a.dy * a.dy, dz * dz};
+      T num = T(0), den = T(0);
+#pragma unroll
+      for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const T Spq = T(0.5) * (G[p][q] + G[q][p]);
+#pragma unroll
+          for (int m = 0; m < 3; ++m) num += D2[m] * G[p][m] * G[q][m] * Spq;
+          den += G[p][q] * G[p][q];
+        }
+      T nu = (den > T(0)) ? -a.C_amd * num / den : T(0);
+      a.nu[id] = nu > T(0) ? nu : T(0);
+      for (int t = 0; t < a.nt; ++t) {
+        const T* c = a.cur.c[t];
+        const T c0 = __ldg(c + id);
+        T dc[3];
+        dc[0] = T(0.5) * ((c0 - __ldg(c + L + cm0)) + (__ldg(c + L + cp0) - c0)) * rdx;
+        dc[1] = T(0.5) * ((c0 - __ldg(c + L + c0m)) + (__ldg(c + L + c0p) - c0)) * rdy;
+        const T dcb = (k >= 1) ? ((c0 - __ldg(c + id - plane)) + (cref(t, k) - cref(t, k - 1))) * __ldg(a.rdzf + k) : T(0);
+        const T dct = (k + 1 < Nz) ? ((__ldg(c + id + plane) - c0) + (cref(t, k + 1) - cref(t, k))) * rdzf1 : T(0);
+        dc[2] = T(0.5) * (dcb + dct);
+        T cn = T(0), cd = T(0);
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+#pragma unroll
+          for (int p = 0; p < 3; ++p) cn += D2[m] * G[p][m] * dc[m] * dc[p];
+#pragma unroll
+        for (int p = 0; p < 3; ++p) cd += dc[p] * dc[p];
+        T kap = (cd > T(0)) ? -a.C_amd * cn / cd : T(0);
+        a.kap[t][id] = kap > T(0) ? kap : T(0);
+      }
+    }
+    // advance
+    u0 = un0; u1 = un1; v0 = vn0; v1 = vn1;
+    w00 = w01; wm0 = wm1; wp0 = wp1; w0m = w0m1; w0p = w0p1;
+    dudz_lo0 = dudz_hi0; dudz_lo1 = dudz_hi1; dvdz_lo0 = dvdz_hi0; dvdz_lo1 = dvdz_hi1;
+  }
+}
+
+template <typename T>
+cudaError_t launch_closure(const ClosureArgs<T>& a, cudaStream_t s) {
+  dim3 blk(32, 8);
+  dim3 grid((a.Nx + 31) / 32, (a.Ny + 7) / 8);
+  k_closure<T><<<grid, blk, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_closure<float>(const ClosureArgs<float>&, cudaStream_t);
+template cudaError_t launch_closure<double>(const ClosureArgs<double>&, cudaStream_t);
+
+}  // namespace ocn

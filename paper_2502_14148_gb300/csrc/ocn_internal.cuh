@@ -28,8 +28,11 @@ struct WenoTables {
 
 // Host-side derivation of the tables (coeffs.cpp).
 void derive_weno_tables(WenoTables<double>* out);
-// Upload to the tendency TU's constant memory.
+// Upload to the constant memory of every tendency translation unit.
 cudaError_t upload_weno_tables(const WenoTables<double>& t);
+cudaError_t upload_tables_f32_r5(const WenoTables<double>& t);
+cudaError_t upload_tables_f32_r3(const WenoTables<double>& t);
+cudaError_t upload_tables_f64(const WenoTables<double>& t);
 
 // Fields of one prognostic state.
 template <typename T>
@@ -62,6 +65,7 @@ struct TendencyArgs {
   T top[2 + kMaxTracers], bot[2 + kMaxTracers];
   T dt_gamma, dt_zeta;    // RK coefficients times dt
   int mode;               // 0: RK update + G;  1: G only
+  int variant;            // tile variant of the FP32 kernel (0: 32x8 one CTA/SM, 1: 32x8 two, 2: 32x16, 3: 32x4 three)
 };
 
 template <typename T>
@@ -132,6 +136,11 @@ struct LaunchHook {
 // Launchers (return the launch error; kernels are enqueued on `s`).
 template <typename T> cudaError_t launch_closure(const ClosureArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_tendency(const TendencyArgs<T>& a, int weno_r, cudaStream_t s);
+template <> cudaError_t launch_tendency<float>(const TendencyArgs<float>& a, int weno_r, cudaStream_t s);
+template <> cudaError_t launch_tendency<double>(const TendencyArgs<double>& a, int weno_r, cudaStream_t s);
+cudaError_t launch_tendency_f32_r5(const TendencyArgs<float>& a, cudaStream_t s);
+cudaError_t launch_tendency_f32_r3(const TendencyArgs<float>& a, cudaStream_t s);
+constexpr int kTendencyVariants = 4;
 template <typename T> cudaError_t launch_projection(const PoissonArgs<T>& a, cudaStream_t s, int* nlaunch,
                                                     const LaunchHook& hook = LaunchHook());
 template <typename T> cudaError_t launch_diagnostics(const DiagArgs<T>& a, cudaStream_t s);

@@ -1,0 +1,27 @@
+// Fused tendency kernels: float, WENO order 9 (R = 5).
+#include "tendency_kernel.cuh"
+
+namespace ocn {
+
+template <int NTR>
+static cudaError_t launch_f32_r5_n(const TendencyArgs<float>& a, cudaStream_t s) {
+  switch (a.variant) {
+      case 0: return launch_tendency_variant<float, 5, NTR, 32, 8, 1>(a, s);
+      case 1: return launch_tendency_variant<float, 5, NTR, 32, 8, 2>(a, s);
+      case 2: return launch_tendency_variant<float, 5, NTR, 32, 16, 1>(a, s);
+      case 3: return launch_tendency_variant<float, 5, NTR, 32, 4, 3>(a, s);
+      default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_tendency_f32_r5(const TendencyArgs<float>& a, cudaStream_t s) {
+  switch (a.nt) {
+    case 1: return launch_f32_r5_n<1>(a, s);
+    case 2: return launch_f32_r5_n<2>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t upload_tables_f32_r5(const WenoTables<double>& t) { return upload_tables_here(t); }
+
+}  // namespace ocn

@@ -23,7 +23,8 @@ LIB_PATH = os.path.join(HERE, "_lib", "libocn.so")
 OCN_FIELD_U, OCN_FIELD_V, OCN_FIELD_W, OCN_FIELD_TRACER0 = 0, 1, 2, 3
 OCN_FIELD_P, OCN_FIELD_G, OCN_FIELD_NU_E = 10, 20, 30
 OCN_FIELD_TRACER_REF0, OCN_FIELD_RAW = 40, 0x100
-OCN_OPT_GRAPHS, OCN_OPT_SYNC_CHECK, OCN_OPT_KERNEL_TIMING = 1, 2, 3
+OCN_OPT_GRAPHS, OCN_OPT_SYNC_CHECK, OCN_OPT_KERNEL_TIMING, OCN_OPT_TENDENCY_VARIANT = 1, 2, 3, 4
+TENDENCY_VARIANTS = 4
 KERNEL_CLASSES = ["closure", "tendency", "div_fftx", "fft_y", "tridiag", "gauge", "ifftx", "correct"]
 MAX_TRACERS = 4
 CLOSURES = {"none": 0, "scalar": 1, "smagorinsky": 2, "amd": 3}
@@ -35,7 +36,7 @@ STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_NONFIN
 EXPORTS = ["ocn_abi_version", "ocn_last_error", "ocn_grid_create", "ocn_grid_destroy", "ocn_model_create",
            "ocn_model_destroy", "ocn_model_arena_bytes", "ocn_model_bind_arena", "ocn_set_field", "ocn_get_field",
            "ocn_project", "ocn_time_step", "ocn_compute_tendencies", "ocn_diagnostics", "ocn_set_option",
-           "ocn_launches_per_step", "ocn_kernel_times", "ocn_project_noalloc"]
+           "ocn_launches_per_step", "ocn_kernel_times", "ocn_project_noalloc", "ocn_autotune"]
 
 
 class OcnError(RuntimeError):
@@ -91,6 +92,7 @@ def lib(path: str = LIB_PATH):
     L.ocn_set_option.argtypes = [vp, C.c_int, C.c_longlong]
     L.ocn_launches_per_step.argtypes = [vp, C.POINTER(C.c_int)]
     L.ocn_kernel_times.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    L.ocn_autotune.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_double)]
     L.ocn_project_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                       C.POINTER(C.c_double), vp, vp, vp, vp, vp, C.POINTER(C.c_char_p)]
     for name in EXPORTS:
@@ -276,6 +278,14 @@ class Model:
         ms = (C.c_double * n)()
         _check(lib().ocn_kernel_times(self._h, counts, ms), "ocn_kernel_times")
         return {k: (counts[i], ms[i]) for i, k in enumerate(KERNEL_CLASSES)}
+
+    def autotune(self):
+        """Time every tendency tile variant on the current state, keep the fastest.
+        Returns (best index, [ms per launch of each variant])."""
+        best = C.c_int()
+        ms = (C.c_double * TENDENCY_VARIANTS)()
+        _check(lib().ocn_autotune(self._h, C.byref(best), ms), "ocn_autotune")
+        return best.value, list(ms)
 
     def synchronize(self):
         self.stream.synchronize()

@@ -241,6 +241,30 @@ def test_graph_replay_matches_direct_launches(ocn):
     assert a.launches_per_step() == b.launches_per_step() > 0
 
 
+def test_tendency_variants_identical(ocn):
+    """Every tile variant of the FP32 kernel computes exactly the same tendencies and steps
+    (only the assignment of faces to threads changes), on a grid with ragged tiles."""
+    p = inputs.config("les_512", Nx=72, Ny=54, Nz=20)
+    st = inputs.initial_state(p)
+    ref = None
+    for v in range(ocn.TENDENCY_VARIANTS):
+        m = ocn.Model(p)
+        m.set(**st)
+        m.set_option(ocn.OCN_OPT_TENDENCY_VARIANT, v)
+        G = {k: x.cpu().numpy() for k, x in m.compute_tendencies().items()}
+        m.time_step(p["dt"], 2)
+        out = {n: m.get_numpy(n) for n in ("u", "v", "w", "T", "S")}
+        if ref is None:
+            ref = (G, out)
+            continue
+        for k in G:
+            assert np.array_equal(G[k], ref[0][k]), (v, k)
+        for k in out:
+            assert np.array_equal(out[k], ref[1][k]), (v, k)
+    best, ms = m.autotune()
+    assert 0 <= best < ocn.TENDENCY_VARIANTS and all(x > 0 for x in ms)
+
+
 def test_checkpoint_resume_bitwise(ocn):
     """A run split at a step boundary and resumed from the saved state equals the continuous run."""
     p = inputs.config("cbl_256", Nx=64, Ny=32, Nz=16)
