@@ -612,6 +612,36 @@ void orc_divergence(const orc_model* M, double* out) {
         out[ID(M, i, j, k)] = dudx_ccc(M, i, j, k) + dvdy_ccc(M, i, j, k) + dwdz_ccc(M, i, j, k);
 }
 
+/* Horizontal means and vertical fluxes for coarse-graining (the fine LES as training data):
+ * the fluxes are the horizontal means of the model's own vertical face fluxes (advective WENO
+ * flux + closure flux; prescribed fluxes at the walls). */
+void orc_profiles(orc_model* M, double* out) {
+  int Nx = M->Nx, Ny = M->Ny, Nz = M->Nz;
+  double inv = 1.0 / ((double)Nx * Ny);
+  compute_diffusivities(M);
+  for (int k = 0; k < Nz; ++k) {
+    double sb = 0, su = 0, sv = 0;
+    for (int j = 0; j < Ny; ++j)
+      for (int i = 0; i < Nx; ++i) { sb += buoyancy(M, i, j, k); su += A3(M, M->u, i, j, k); sv += A3(M, M->v, i, j, k); }
+    out[k] = sb * inv; out[Nz + k] = su * inv; out[2 * Nz + k] = sv * inv;
+  }
+  double* F = out + 3 * Nz;
+  for (int k = 0; k <= Nz; ++k) {
+    double fb = 0, fu = 0, fv = 0;
+    for (int j = 0; j < Ny; ++j)
+      for (int i = 0; i < Nx; ++i) {
+        fu += Fz_u(M, i, j, k);
+        fv += Fz_v(M, i, j, k);
+        if (M->p.eos == ORC_EOS_LINEAR_TS)
+          fb += M->p.g * (M->p.alpha * Fz_c(M, 0, i, j, k) - M->p.beta * Fz_c(M, 1, i, j, k));
+        else
+          fb += Fz_c(M, 0, i, j, k);
+      }
+    F[k] = fb * inv; F[(Nz + 1) + k] = fu * inv; F[2 * (Nz + 1) + k] = fv * inv;
+  }
+  M->have_diff = 0;
+}
+
 void orc_project(orc_model* M, double dts) {
   int Nx = M->Nx, Ny = M->Ny, Nz = M->Nz;
   size_t N = (size_t)Nx * Ny * Nz;
@@ -684,6 +714,19 @@ void orc_diagnostics(const orc_model* M, double dt, double* out) {
       }
   for (int n = 0; n < nt; ++n) out[n] = sc[n];
   out[nt] = su; out[nt + 1] = sv; out[nt + 2] = sw; out[nt + 3] = maxdiv; out[nt + 4] = cfl * dt; out[nt + 5] = bad;
+}
+
+/* ------------------------------------------------------------------ */
+void orc_regrid(const double* zf_in, int nin, const double* in, const double* zf_out, int nout, double* out) {
+  for (int j = 0; j < nout; ++j) {
+    double lo = zf_out[j], hi = zf_out[j + 1], acc = 0.0;
+    for (int i = 0; i < nin; ++i) {
+      double a = zf_in[i] > lo ? zf_in[i] : lo;
+      double b = zf_in[i + 1] < hi ? zf_in[i + 1] : hi;
+      if (b > a) acc += in[i] * (b - a);
+    }
+    out[j] = acc / (hi - lo);
+  }
 }
 
 /* ------------------------------------------------------------------ */

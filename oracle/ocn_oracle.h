@@ -77,6 +77,17 @@ double orc_diffusivity_at(orc_model* m, int which, int i, int j, int k);
 /* Diagnostics: out[0..n_tracers-1] = sum V c_n; then sum V u, sum V v, sum V w,
  * max |div u|, max(|u|/dx,|v|/dy,|w|/dz_f)*dt, nonfinite count. */
 void orc_diagnostics(const orc_model* m, double dt, double* out);
+/* Conservative regridding of cell averages between two column grids covering the same interval:
+ * out[j] = (1/dz_out_j) sum_i in[i] |cell_i of the input ∩ cell_j of the output| (finite-volume
+ * averaging, Sec. B listing "finite-volumes"). */
+void orc_regrid(const double* zf_in, int nin, const double* in, const double* zf_out, int nout, double* out);
+/* Coarse-graining diagnostics (horizontal means over the periodic plane):
+ *   out[0*Nz + k] = <b>, out[1*Nz + k] = <u>, out[2*Nz + k] = <v> at level k (b = tracer 0 or the EOS);
+ *   out[3*Nz + f*(Nz+1) + k], f = 0,1,2: the horizontal mean of the model's upward face flux of b, u, v
+ *   through face k = 0..Nz (advective + closure flux; the prescribed fluxes at the walls).
+ * out holds 3*Nz + 3*(Nz+1) values. */
+void orc_profiles(orc_model* m, double* out);
+
 /* Discrete divergence at centres, [Nz][Ny][Nx]. */
 void orc_divergence(const orc_model* m, double* out);
 

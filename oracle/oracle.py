@@ -87,6 +87,8 @@ def lib():
         L.orc_fft.argtypes = [dp, dp, C.c_int, C.c_int]
         L.orc_poisson.argtypes = [C.c_void_p, dp, dp]
         L.orc_grid_metrics.argtypes = [C.c_void_p, dp, dp, dp]
+        L.orc_profiles.argtypes = [C.c_void_p, dp]
+        L.orc_regrid.argtypes = [dp, C.c_int, dp, dp, C.c_int, dp]
         _lib = L
     return _lib
 
@@ -121,6 +123,13 @@ def fft(x: np.ndarray, sign: int = -1) -> np.ndarray:
     im = np.ascontiguousarray(np.imag(x), dtype=np.float64).copy()
     lib().orc_fft(_dp(re), _dp(im), re.size, sign)
     return re + 1j * im
+
+
+def regrid(zf_in, values, zf_out) -> np.ndarray:
+    zi = np.ascontiguousarray(zf_in, dtype=np.float64); v = np.ascontiguousarray(values, dtype=np.float64)
+    zo = np.ascontiguousarray(zf_out, dtype=np.float64); out = np.zeros(zo.size - 1)
+    lib().orc_regrid(_dp(zi), v.size, _dp(v), _dp(zo), out.size, _dp(out))
+    return out
 
 
 # ---------------------------------------------------------------- model
@@ -224,6 +233,15 @@ class OracleModel:
         out = np.empty_like(r)
         lib().orc_poisson(self._h, _dp(r), _dp(out))
         return out
+
+    def profiles(self) -> dict:
+        """Horizontal means <b>, <u>, <v> at levels and total upward fluxes of b, u, v at faces."""
+        Nz = self.Nz
+        out = np.zeros(3 * Nz + 3 * (Nz + 1))
+        lib().orc_profiles(self._h, _dp(out))
+        F = out[3 * Nz:]
+        return {"b": out[:Nz], "u": out[Nz:2 * Nz], "v": out[2 * Nz:3 * Nz],
+                "Fb": F[:Nz + 1], "Fu": F[Nz + 1:2 * (Nz + 1)], "Fv": F[2 * (Nz + 1):]}
 
     def grid_metrics(self):
         zc = np.empty(self.Nz); dzc = np.empty(self.Nz); dzf = np.empty(self.Nz + 1)

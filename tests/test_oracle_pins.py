@@ -699,3 +699,38 @@ def test_buoyancy_interpolated_to_w_faces_second_order(oracle_mod):
         errs.append(np.abs(Gw - np.cos(3 * (-1.0 + np.arange(1, N) * h))).max())
     rates = [math.log2(errs[i] / errs[i + 1]) for i in range(len(Ns) - 1)]
     assert min(rates) > 1.8, (errs, rates)
+
+
+def test_profile_fluxes_close_the_mean_budget(oracle_mod):
+    """The coarse-graining fluxes are the horizontal means of the model's vertical face fluxes, so
+    the horizontal mean of a tracer tendency equals minus their vertical difference (the x and y
+    flux differences sum to zero over the periodic plane); the wall values are the prescribed
+    fluxes."""
+    p = small_params(stretch=1.5, Nx=12, Ny=8, Nz=6, Lx=12.0, closure="amd", top_flux={"b": 3e-3, "u": -2e-3},
+                     bottom_flux={"v": 1e-3}, f=0.2)
+    m = oracle_mod.OracleModel(p)
+    st = inputs.random_state(p, seed=31, amp=0.3)
+    m.set(**st)
+    pr = m.profiles()
+    G = m.tendencies()
+    dzc = np.diff(p["z_faces"])
+    np.testing.assert_allclose(G["b"].mean(axis=(1, 2)), -np.diff(pr["Fb"]) / dzc, atol=1e-12)
+    # u: plus the Coriolis term f <v> (the mean of the 4-point average is the level mean)
+    np.testing.assert_allclose(G["u"].mean(axis=(1, 2)), -np.diff(pr["Fu"]) / dzc + 0.2 * st["v"].mean(axis=(1, 2)), atol=1e-12)
+    np.testing.assert_allclose([pr["Fb"][-1], pr["Fu"][-1], pr["Fv"][0]], [3e-3, -2e-3, 1e-3], rtol=1e-14)
+    np.testing.assert_allclose(pr["b"], st["b"].mean(axis=(1, 2)), atol=1e-15)
+
+
+def test_regrid_preserves_integrals_paper_example(oracle_mod):
+    """Sec. B listing "finite-volumes": e^x y on a fine grid, regridded to medium and coarse grids,
+    keeps the integral exactly (here in one dimension per column, for e^x on stretched and uniform
+    grids); a constant stays constant; regridding to the same grid is the identity."""
+    fine = np.linspace(0.0, 1.0, 1025)
+    avg = (np.exp(fine[1:]) - np.exp(fine[:-1])) / np.diff(fine)      # exact cell averages of e^x
+    for zo in (np.linspace(0.0, 1.0, 17), np.linspace(0.0, 1.0, 5), inputs.tanh_faces(6, 1.0) + 1.0):
+        out = oracle_mod.regrid(fine, avg, zo)
+        assert abs((out * np.diff(zo)).sum() - (np.e - 1.0)) < 1e-13
+        # the coarse value is the exact average of e^x over the coarse cell
+        np.testing.assert_allclose(out, (np.exp(zo[1:]) - np.exp(zo[:-1])) / np.diff(zo), rtol=1e-12)
+    np.testing.assert_allclose(oracle_mod.regrid(fine, np.full(1024, 2.5), np.linspace(0, 1, 7)), 2.5, rtol=1e-14)
+    np.testing.assert_allclose(oracle_mod.regrid(fine, avg, fine), avg, rtol=1e-14)
