@@ -730,7 +730,8 @@ def test_regrid_preserves_integrals_paper_example(oracle_mod):
     for zo in (np.linspace(0.0, 1.0, 17), np.linspace(0.0, 1.0, 5), inputs.tanh_faces(6, 1.0) + 1.0):
         out = oracle_mod.regrid(fine, avg, zo)
         assert abs((out * np.diff(zo)).sum() - (np.e - 1.0)) < 1e-13
-        # the coarse value is the exact average of e^x over the coarse cell
-        np.testing.assert_allclose(out, (np.exp(zo[1:]) - np.exp(zo[:-1])) / np.diff(zo), rtol=1e-12)
+        # on nested grids the coarse value is the exact average of e^x over the coarse cell
+        if np.all(np.isin(zo, fine)):
+            np.testing.assert_allclose(out, (np.exp(zo[1:]) - np.exp(zo[:-1])) / np.diff(zo), rtol=1e-12)
     np.testing.assert_allclose(oracle_mod.regrid(fine, np.full(1024, 2.5), np.linspace(0, 1, 7)), 2.5, rtol=1e-14)
     np.testing.assert_allclose(oracle_mod.regrid(fine, avg, fine), avg, rtol=1e-14)
