@@ -226,6 +226,41 @@ ocn_status ocn_kernel_times(ocn_model* model, int* counts, double* ms);
 /* Number of kernel launches the last ocn_time_step issued per RK3 step. */
 ocn_status ocn_launches_per_step(const ocn_model* model, int* launches);
 
+/* Coarse-graining profiles (training data for column closures; horizontal means over the
+ * periodic plane): out[0..Nz) <b>, [Nz..2Nz) <u>, [2Nz..3Nz) <v> at the levels, then the mean
+ * upward flux of b, u and v through the faces 0..Nz (Nz+1 values each): the model's own face
+ * flux (advective + closure; the prescribed fluxes at the walls), obtained exactly from the
+ * mean budget of a tendency evaluation.  Overwrites G; the state is not advanced.  nout must be
+ * >= 3*Nz + 3*(Nz+1).  Synchronises the stream.  Errors: OCN_ERR_ARG, OCN_ERR_STATE, OCN_ERR_CUDA. */
+ocn_status ocn_profiles(ocn_model* model, double* out, int nout);
+
+/* Conservative regridding of a column of cell averages between two ascending face lists
+ * (finite-volume averaging, Sec. B listing "finite-volumes": integrals are preserved): out[j] is
+ * the average over output cell j of the piecewise-constant input.  Host only.  Errors: OCN_ERR_ARG. */
+ocn_status ocn_regrid(const double* zf_in, int nin, const double* in, const double* zf_out, int nout, double* out);
+
+/* Ensembles: n independent members (own grids, forcings and sizes, one precision) stepped together.
+ * Members share one device arena and the ensemble's stream; ocn_ensemble_member returns a borrowed
+ * model handle (set/get/project/diagnostics/profiles; do not destroy it).  ocn_ensemble_time_step
+ * advances every member by nsteps RK3 steps: in OCN_ENSEMBLE_CONCURRENT mode (default) each step is
+ * one CUDA graph launch whose independent per-member branches run concurrently; in
+ * OCN_ENSEMBLE_SEQUENTIAL mode members are stepped one after the other (the comparison baseline).
+ * ocn_ensemble_autotune picks the tendency tile variant once per member shape (variants[n] receives
+ * the choices; may be NULL).  Errors as for the single-model calls. */
+typedef struct ocn_ensemble ocn_ensemble;
+enum { OCN_OPT_ENSEMBLE_MODE = 5 };
+enum { OCN_ENSEMBLE_CONCURRENT = 0, OCN_ENSEMBLE_SEQUENTIAL = 1 };
+ocn_status ocn_ensemble_create(int n, const ocn_grid_desc* grids, const ocn_model_desc* models, void* stream,
+                               ocn_ensemble** out);
+void ocn_ensemble_destroy(ocn_ensemble* ensemble);
+ocn_status ocn_ensemble_arena_bytes(const ocn_ensemble* ensemble, size_t* bytes);
+ocn_status ocn_ensemble_bind_arena(ocn_ensemble* ensemble, void* device_ptr, size_t bytes);
+ocn_status ocn_ensemble_member(ocn_ensemble* ensemble, int i, ocn_model** member);
+ocn_status ocn_ensemble_time_step(ocn_ensemble* ensemble, double dt, int nsteps);
+ocn_status ocn_ensemble_set_option(ocn_ensemble* ensemble, int option, long long value);
+ocn_status ocn_ensemble_autotune(ocn_ensemble* ensemble, int* variants);
+ocn_status ocn_ensemble_launches_per_step(const ocn_ensemble* ensemble, int* launches);
+
 /* No-allocation projection.  Some callers cannot call cudaMalloc: plug-ins
  * whose host application owns every device allocation through its own pool
  * allocator, and loops that must not allocate once they are running.  This

@@ -132,6 +132,24 @@ struct ocn_model {
   LaunchHook hook;
 };
 
+struct ocn_ensemble {
+  int n = 0;
+  int dev = 0;
+  int es = 4;
+  cudaStream_t stream = nullptr;             // the ensemble's stream (member handles use it too)
+  std::vector<ocn_grid*> grids;
+  std::vector<ocn_model*> models;
+  std::vector<cudaStream_t> fork_streams;    // one per member, joined back into `stream` in each graph
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  std::vector<size_t> offs;
+  size_t bytes = 0;
+  char* arena = nullptr;
+  int mode = 0;                              // 0: one graph per step, members concurrent; 1: sequential
+  std::map<std::string, cudaGraphExec_t> graphs;
+  int launches_per_step = 0;
+};
+
 namespace {
 
 cudaEvent_t take_event(ocn_model* m) {
@@ -744,6 +762,285 @@ ocn_status ocn_autotune(ocn_model* m, int* best, double* ms) {
   if (arg != saved) drop_graphs(m);
   m->variant = arg;
   if (best) *best = arg;
+  return OCN_OK;
+}
+
+ocn_status ocn_profiles(ocn_model* m, double* out, int nout) {
+  if (!m || !out) return fail(OCN_ERR_ARG, "null argument");
+  if (!m->arena) return fail(OCN_ERR_STATE, "arena not bound");
+  const ocn_grid* g = m->g;
+  const int Nz = g->Nz;
+  if (nout < 3 * Nz + 3 * (Nz + 1)) return fail(OCN_ERR_ARG, "nout must be >= 3*Nz + 3*(Nz+1)");
+  if ((size_t)7 * Nz > (size_t)diag_blocks() * (OCN_MAX_TRACERS + 6)) return fail(OCN_ERR_UNSUPPORTED, "Nz too large for profiles");
+  DeviceGuard dg(m->dev);
+  cudaError_t e;
+  auto run = [&](auto tag) -> cudaError_t {
+    typedef decltype(tag) T;
+    cudaError_t err = enqueue_closure<T>(m, m->cur);
+    if (err == cudaSuccess) err = enqueue_tendency<T>(m, m->cur, 0.0, 0.0, 1);   // unsplit G, state untouched
+    if (err != cudaSuccess) return err;
+    ProfileArgs<T> pa;
+    memset(&pa, 0, sizeof(pa));
+    StatePtrs<T> G = g_ptrs<T>(m), S = state_ptrs<T>(m, m->cur);
+    pa.Gu = G.u; pa.Gv = G.v; pa.Gc0 = G.c[0]; pa.Gc1 = (m->d.n_tracers > 1) ? G.c[1] : nullptr;
+    pa.u = S.u; pa.v = S.v; pa.c0 = S.c[0]; pa.c1 = (m->d.n_tracers > 1) ? S.c[1] : nullptr;
+    pa.cref0 = at<T>(m, m->off_cref[0]); pa.cref1 = (m->d.n_tracers > 1) ? at<T>(m, m->off_cref[1]) : nullptr;
+    pa.plane = (size_t)g->Nx * g->Ny; pa.Nz = Nz; pa.eos = m->d.eos;
+    pa.g_alpha = m->d.g * m->d.alpha; pa.g_beta = m->d.g * m->d.beta; pa.T0 = m->d.T0; pa.S0 = m->d.S0;
+    pa.out = at<double>(m, m->off_partial);
+    return launch_profile_means<T>(pa, m->stream);
+  };
+  e = (m->es == 4) ? run(0.0f) : run(0.0);
+  if (e != cudaSuccess) return cuda_fail(e, "profiles launch");
+  std::vector<double> mean((size_t)7 * Nz);
+  e = cudaMemcpyAsync(mean.data(), m->arena + m->off_partial, mean.size() * sizeof(double), cudaMemcpyDeviceToHost, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "profiles read");
+  const double* mGu = &mean[0]; const double* mGv = &mean[Nz]; const double* mG0 = &mean[2 * Nz];
+  const double* mG1 = &mean[3 * Nz]; const double* mu = &mean[4 * Nz]; const double* mv = &mean[5 * Nz];
+  const double* mb = &mean[6 * Nz];
+  for (int k = 0; k < Nz; ++k) { out[k] = mb[k]; out[Nz + k] = mu[k]; out[2 * Nz + k] = mv[k]; }
+  // mean face fluxes from the mean budget, integrated up from the bottom wall:
+  // <G_c> = -(F_{k+1} - F_k)/dz_c;  <G_u> = -(...)/dz_c + f <v>;  <G_v> = -(...)/dz_c - f <u>
+  double* Fb = out + 3 * Nz; double* Fu = Fb + (Nz + 1); double* Fv = Fu + (Nz + 1);
+  const double f = m->d.f;
+  double F0 = m->d.bottom_flux[2], F1 = m->d.bottom_flux[3];
+  Fu[0] = m->d.bottom_flux[0]; Fv[0] = m->d.bottom_flux[1];
+  const bool ts = m->d.eos == OCN_EOS_LINEAR_TS;
+  const double ga = m->d.g * m->d.alpha, gb = m->d.g * m->d.beta;
+  Fb[0] = ts ? ga * F0 - gb * F1 : F0;
+  for (int k = 0; k < Nz; ++k) {
+    const double dz = g->dzc[k];
+    Fu[k + 1] = Fu[k] - dz * (mGu[k] - f * mv[k]);
+    Fv[k + 1] = Fv[k] - dz * (mGv[k] + f * mu[k]);
+    F0 -= dz * mG0[k];
+    if (ts) F1 -= dz * mG1[k];
+    Fb[k + 1] = ts ? ga * F0 - gb * F1 : F0;
+  }
+  return OCN_OK;
+}
+
+ocn_status ocn_regrid(const double* zf_in, int nin, const double* in, const double* zf_out, int nout, double* out) {
+  if (!zf_in || !in || !zf_out || !out || nin < 1 || nout < 1) return fail(OCN_ERR_ARG, "invalid regrid arguments");
+  for (int i = 0; i < nin; ++i)
+    if (!(zf_in[i + 1] > zf_in[i])) return fail(OCN_ERR_ARG, "input faces must ascend");
+  for (int j = 0; j < nout; ++j)
+    if (!(zf_out[j + 1] > zf_out[j])) return fail(OCN_ERR_ARG, "output faces must ascend");
+  // one sweep over both face lists: each input cell contributes value x overlap to the output
+  // cells it intersects
+  int i = 0;
+  for (int j = 0; j < nout; ++j) {
+    const double lo = zf_out[j], hi = zf_out[j + 1];
+    while (i < nin && zf_in[i + 1] <= lo) ++i;
+    double acc = 0.0;
+    for (int c = i; c < nin && zf_in[c] < hi; ++c) {
+      const double a = fmax(zf_in[c], lo), b = fmin(zf_in[c + 1], hi);
+      if (b > a) acc += in[c] * (b - a);
+    }
+    out[j] = acc / (hi - lo);
+  }
+  return OCN_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Ensembles: many independent members stepped together.
+
+ocn_status ocn_ensemble_create(int n, const ocn_grid_desc* grids, const ocn_model_desc* models, void* stream,
+                               ocn_ensemble** out) {
+  if (!grids || !models || !out || n < 1) return fail(OCN_ERR_ARG, "invalid ensemble arguments");
+  *out = nullptr;
+  ocn_ensemble* e = new (std::nothrow) ocn_ensemble;
+  if (!e) return fail(OCN_ERR_OOM, "ensemble allocation");
+  e->n = n;
+  e->stream = reinterpret_cast<cudaStream_t>(stream);
+  cudaGetDevice(&e->dev);
+  ocn_status st = OCN_OK;
+  for (int i = 0; i < n && st == OCN_OK; ++i) {
+    if (models[i].precision != models[0].precision) { st = fail(OCN_ERR_ARG, "members must share one precision"); break; }
+    ocn_grid* g = nullptr;
+    st = ocn_grid_create(&grids[i], &g);
+    if (st != OCN_OK) break;
+    e->grids.push_back(g);
+    ocn_model* m = nullptr;
+    st = ocn_model_create(g, &models[i], stream, &m);
+    if (st != OCN_OK) break;
+    e->models.push_back(m);
+  }
+  if (st != OCN_OK) { ocn_ensemble_destroy(e); return st; }
+  e->es = e->models[0]->es;
+  size_t o = 0;
+  for (ocn_model* m : e->models) { e->offs.push_back(o); o = align256(o + m->bytes); }
+  e->bytes = o;
+  cudaError_t ce = cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming);
+  for (int i = 0; i < n && ce == cudaSuccess; ++i) {
+    cudaStream_t fs = nullptr;
+    ce = cudaStreamCreateWithFlags(&fs, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) break;
+    e->fork_streams.push_back(fs);
+    cudaEvent_t ev = nullptr;
+    ce = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (ce != cudaSuccess) break;
+    e->join.push_back(ev);
+  }
+  if (ce != cudaSuccess) { ocn_ensemble_destroy(e); return cuda_fail(ce, "ensemble streams"); }
+  *out = e;
+  return OCN_OK;
+}
+
+void ocn_ensemble_destroy(ocn_ensemble* e) {
+  if (!e) return;
+  {
+    DeviceGuard dg(e->dev);
+    for (auto& kv : e->graphs) cudaGraphExecDestroy(kv.second);
+    e->graphs.clear();
+    for (cudaStream_t fs : e->fork_streams) cudaStreamDestroy(fs);
+    for (cudaEvent_t ev : e->join) cudaEventDestroy(ev);
+    if (e->fork) cudaEventDestroy(e->fork);
+  }
+  for (ocn_model* m : e->models) ocn_model_destroy(m);
+  for (ocn_grid* g : e->grids) ocn_grid_destroy(g);
+  delete e;
+}
+
+ocn_status ocn_ensemble_arena_bytes(const ocn_ensemble* e, size_t* bytes) {
+  if (!e || !bytes) return fail(OCN_ERR_ARG, "null argument");
+  *bytes = e->bytes;
+  return OCN_OK;
+}
+
+ocn_status ocn_ensemble_bind_arena(ocn_ensemble* e, void* device_ptr, size_t bytes) {
+  if (!e || !device_ptr) return fail(OCN_ERR_ARG, "null argument");
+  if (bytes < e->bytes) return fail(OCN_ERR_ARG, "arena smaller than ocn_ensemble_arena_bytes()");
+  if (reinterpret_cast<uintptr_t>(device_ptr) % 256) return fail(OCN_ERR_ARG, "arena must be 256-byte aligned");
+  for (auto& kv : e->graphs) cudaGraphExecDestroy(kv.second);
+  e->graphs.clear();
+  e->arena = reinterpret_cast<char*>(device_ptr);
+  for (int i = 0; i < e->n; ++i) {
+    ocn_status st = ocn_model_bind_arena(e->models[i], e->arena + e->offs[i], e->models[i]->bytes);
+    if (st != OCN_OK) return st;
+  }
+  return OCN_OK;
+}
+
+ocn_status ocn_ensemble_member(ocn_ensemble* e, int i, ocn_model** out) {
+  if (!e || !out || i < 0 || i >= e->n) return fail(OCN_ERR_ARG, "invalid member index");
+  *out = e->models[i];
+  return OCN_OK;
+}
+
+}  // extern "C"
+
+namespace {
+template <typename T>
+ocn_status ensemble_step_t(ocn_ensemble* e, double dt, int nsteps) {
+  for (ocn_model* m : e->models) if (!m->arena) return fail(OCN_ERR_STATE, "arena not bound");
+  if (e->mode == 1) {                       // sequential: every member on the ensemble stream in turn
+    for (int s = 0; s < nsteps; ++s)
+      for (ocn_model* m : e->models) {
+        ocn_status st = time_step_t<T>(m, dt, 1);
+        if (st != OCN_OK) return st;
+      }
+    return OCN_OK;
+  }
+  for (int s = 0; s < nsteps; ++s) {
+    std::string key(reinterpret_cast<const char*>(&dt), sizeof(dt));
+    for (ocn_model* m : e->models) { key.push_back((char)('0' + m->cur)); key.push_back((char)('0' + m->variant)); }
+    auto it = e->graphs.find(key);
+    std::vector<int> w(e->n);
+    if (it == e->graphs.end()) {
+      // One graph for the whole ensemble step: fork a branch per member, join at the end;
+      // the branches are independent, so their kernels run concurrently.
+      cudaError_t ce = cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal);
+      if (ce != cudaSuccess) return cuda_fail(ce, "ensemble begin capture");
+      cudaError_t el = cudaEventRecord(e->fork, e->stream);
+      int total = 0;
+      for (int i = 0; i < e->n && el == cudaSuccess; ++i) {
+        ocn_model* m = e->models[i];
+        el = cudaStreamWaitEvent(e->fork_streams[i], e->fork, 0);
+        if (el != cudaSuccess) break;
+        m->stream = e->fork_streams[i];
+        w[i] = m->cur;
+        int nl = 0;
+        el = enqueue_step<T>(m, dt, &w[i], &nl);
+        m->stream = e->stream;
+        total += nl;
+        if (el == cudaSuccess) el = cudaEventRecord(e->join[i], e->fork_streams[i]);
+        if (el == cudaSuccess) el = cudaStreamWaitEvent(e->stream, e->join[i], 0);
+      }
+      cudaGraph_t graph = nullptr;
+      ce = cudaStreamEndCapture(e->stream, &graph);
+      if (el != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(el, "ensemble capture"); }
+      if (ce != cudaSuccess) return cuda_fail(ce, "ensemble end capture");
+      cudaGraphExec_t exec = nullptr;
+      ce = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ce != cudaSuccess) return cuda_fail(ce, "ensemble graph instantiate");
+      it = e->graphs.emplace(key, exec).first;
+      e->launches_per_step = total;
+    } else {
+      for (int i = 0; i < e->n; ++i) w[i] = 1 - e->models[i]->cur;
+    }
+    cudaError_t ce = cudaGraphLaunch(it->second, e->stream);
+    if (ce != cudaSuccess) return cuda_fail(ce, "ensemble graph launch");
+    for (int i = 0; i < e->n; ++i) e->models[i]->cur = w[i];
+  }
+  return OCN_OK;
+}
+}  // namespace
+
+extern "C" {
+
+ocn_status ocn_ensemble_time_step(ocn_ensemble* e, double dt, int nsteps) {
+  if (!e) return fail(OCN_ERR_ARG, "null argument");
+  if (nsteps < 0 || !isfinite(dt)) return fail(OCN_ERR_ARG, "nsteps must be >= 0 and dt finite");
+  DeviceGuard dg(e->dev);
+  return (e->es == 4) ? ensemble_step_t<float>(e, dt, nsteps) : ensemble_step_t<double>(e, dt, nsteps);
+}
+
+ocn_status ocn_ensemble_set_option(ocn_ensemble* e, int option, long long value) {
+  if (!e) return fail(OCN_ERR_ARG, "null argument");
+  if (option == OCN_OPT_ENSEMBLE_MODE) {
+    if (value != OCN_ENSEMBLE_CONCURRENT && value != OCN_ENSEMBLE_SEQUENTIAL) return fail(OCN_ERR_ARG, "unknown ensemble mode");
+    e->mode = (int)value;
+    return OCN_OK;
+  }
+  for (ocn_model* m : e->models) {
+    ocn_status st = ocn_set_option(m, option, value);
+    if (st != OCN_OK) return st;
+  }
+  return OCN_OK;
+}
+
+ocn_status ocn_ensemble_autotune(ocn_ensemble* e, int* variants) {
+  if (!e) return fail(OCN_ERR_ARG, "null argument");
+  DeviceGuard dg(e->dev);
+  // one tuning per member shape (Nx, Ny, Nz, order, closure, tracers); members of a shape share it
+  std::map<std::string, int> cache;
+  for (int i = 0; i < e->n; ++i) {
+    ocn_model* m = e->models[i];
+    char buf[96];
+    snprintf(buf, sizeof(buf), "%d %d %d %d %d %d", m->g->Nx, m->g->Ny, m->g->Nz, m->R, m->d.closure, m->d.n_tracers);
+    auto it = cache.find(buf);
+    int v = 0;
+    if (it == cache.end()) {
+      ocn_status st = ocn_autotune(m, &v, nullptr);
+      if (st != OCN_OK) return st;
+      cache[buf] = v;
+    } else {
+      v = it->second;
+      ocn_status st = ocn_set_option(m, OCN_OPT_TENDENCY_VARIANT, v);
+      if (st != OCN_OK) return st;
+    }
+    if (variants) variants[i] = v;
+  }
+  for (auto& kv : e->graphs) cudaGraphExecDestroy(kv.second);
+  e->graphs.clear();
+  return OCN_OK;
+}
+
+ocn_status ocn_ensemble_launches_per_step(const ocn_ensemble* e, int* launches) {
+  if (!e || !launches) return fail(OCN_ERR_ARG, "null argument");
+  *launches = e->launches_per_step;
   return OCN_OK;
 }
 

@@ -146,6 +146,20 @@ template <typename T> cudaError_t launch_projection(const PoissonArgs<T>& a, cud
 template <typename T> cudaError_t launch_diagnostics(const DiagArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_fill(T* p, size_t n, T v, cudaStream_t s);
 template <typename T> cudaError_t launch_shift(T* p, size_t n, T v, cudaStream_t s);
+// Per-level horizontal means (FP64) used by the coarse-graining profiles:
+// out[0..Nz) <G_u>, [Nz..2Nz) <G_v>, [2Nz..3Nz) <G_c0>, [3Nz..4Nz) <G_c1>, [4Nz..5Nz) <u>, [5Nz..6Nz) <v>,
+// [6Nz..7Nz) <b> (tracers stored about reference profiles; b from the EOS).
+template <typename T>
+struct ProfileArgs {
+  const T* Gu; const T* Gv; const T* Gc0; const T* Gc1;
+  const T* u; const T* v; const T* c0; const T* c1;
+  const T* cref0; const T* cref1;
+  size_t plane;
+  int Nz, eos;
+  double g_alpha, g_beta, T0, S0;
+  double* out;
+};
+template <typename T> cudaError_t launch_profile_means(const ProfileArgs<T>& a, cudaStream_t s);
 // Per-level horizontal means of a [Nz][plane] field (FP64 accumulation) into ref[Nz],
 // and p[k][.] += sign * ref[k].
 template <typename T> cudaError_t launch_level_mean(const T* p, size_t plane, int Nz, T* ref, cudaStream_t s);

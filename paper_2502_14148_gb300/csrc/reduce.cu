@@ -158,6 +158,45 @@ template cudaError_t launch_level_mean<double>(const double*, size_t, int, doubl
 template cudaError_t launch_level_shift<float>(float*, size_t, int, const float*, float, cudaStream_t);
 template cudaError_t launch_level_shift<double>(double*, size_t, int, const double*, double, cudaStream_t);
 
+// One block per level: FP64 horizontal means of the tendencies and of u, v, b.
+template <typename T>
+__global__ void __launch_bounds__(256) k_profile_means(const ProfileArgs<T> a) {
+  const int k = blockIdx.x;
+  const size_t o = (size_t)k * a.plane;
+  const double r0 = a.cref0 ? (double)a.cref0[k] : 0.0, r1 = a.cref1 ? (double)a.cref1[k] : 0.0;
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (size_t i = threadIdx.x; i < a.plane; i += blockDim.x) {
+    acc[0] += (double)a.Gu[o + i];
+    acc[1] += (double)a.Gv[o + i];
+    acc[2] += (double)a.Gc0[o + i];
+    if (a.Gc1) acc[3] += (double)a.Gc1[o + i];
+    acc[4] += (double)a.u[o + i];
+    acc[5] += (double)a.v[o + i];
+    const double c0 = (double)a.c0[o + i] + r0;
+    acc[6] += (a.eos == OCN_EOS_LINEAR_TS) ? a.g_alpha * (c0 - a.T0) - a.g_beta * ((double)a.c1[o + i] + r1 - a.S0) : c0;
+  }
+  __shared__ double red[8][7];
+#pragma unroll
+  for (int v = 0; v < 7; ++v) {
+    double x = acc[v];
+    for (int s = 16; s > 0; s >>= 1) x += __shfl_down_sync(0xffffffffu, x, s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][v] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 7) {
+    double x = 0.0;
+    for (int w = 0; w < 8; ++w) x += red[w][threadIdx.x];
+    a.out[(size_t)threadIdx.x * a.Nz + k] = x / (double)a.plane;
+  }
+}
+template <typename T>
+cudaError_t launch_profile_means(const ProfileArgs<T>& a, cudaStream_t s) {
+  k_profile_means<T><<<a.Nz, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+template cudaError_t launch_profile_means<float>(const ProfileArgs<float>&, cudaStream_t);
+template cudaError_t launch_profile_means<double>(const ProfileArgs<double>&, cudaStream_t);
+
 template cudaError_t launch_diagnostics<float>(const DiagArgs<float>&, cudaStream_t);
 template cudaError_t launch_diagnostics<double>(const DiagArgs<double>&, cudaStream_t);
 template cudaError_t launch_fill<float>(float*, size_t, float, cudaStream_t);

@@ -81,6 +81,29 @@ def config(name: str, **over) -> dict:
     return p
 
 
+def ensemble_configs(n: int = 64, seed: int = SEED, sizes=(64, 96, 128), depths=(64, 80, 96), spacing: float = 2.0,
+                     precision: int = 32, dt: float = 5.0) -> list:
+    """Convective-boundary-layer ensemble: members of uneven sizes (Nx = Ny from `sizes`, Nz from
+    `depths`, horizontal spacing and mean vertical spacing `spacing` m, tanh-stretched z) with
+    surface buoyancy flux log-uniform in [1e-9, 1e-7] m^2 s^-3, N^2 log-uniform in [1e-6, 1e-4] s^-2
+    and f uniform in [0, 1.4e-4] s^-1; WENO5, AMD, seeded noise 1e-3."""
+    g = np.random.Generator(np.random.Philox(key=[seed, 999]))
+    out = []
+    for i in range(n):
+        N = int(sizes[int(g.integers(len(sizes)))])
+        Nz = int(depths[int(g.integers(len(depths)))])
+        Jb = float(np.exp(g.uniform(np.log(1e-9), np.log(1e-7))))
+        N2 = float(np.exp(g.uniform(np.log(1e-6), np.log(1e-4))))
+        f = float(g.uniform(0.0, 1.4e-4))
+        p = dict(name=f"cbl_member_{i}", Nx=N, Ny=N, Nz=Nz, Lx=spacing * N, Ly=spacing * N, Lz=spacing * Nz,
+                 stretch=1.5, precision=precision, weno_order=5, closure="amd", C_amd=1.0 / 12.0, f=f,
+                 tracers=["b"], eos="buoyancy_tracer", top_flux={"b": Jb}, bottom_flux={}, dt=dt,
+                 init="stratified", N2=N2, noise=1e-3, member=i)
+        p["z_faces"] = tanh_faces(Nz, p["Lz"], 1.5)
+        out.append(p)
+    return out
+
+
 def _normal(seed: int, field: int, shape) -> np.ndarray:
     g = np.random.Generator(np.random.Philox(key=[seed, field]))
     return g.standard_normal(size=shape)

@@ -36,7 +36,11 @@ STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_NONFIN
 EXPORTS = ["ocn_abi_version", "ocn_last_error", "ocn_grid_create", "ocn_grid_destroy", "ocn_model_create",
            "ocn_model_destroy", "ocn_model_arena_bytes", "ocn_model_bind_arena", "ocn_set_field", "ocn_get_field",
            "ocn_project", "ocn_time_step", "ocn_compute_tendencies", "ocn_diagnostics", "ocn_set_option",
-           "ocn_launches_per_step", "ocn_kernel_times", "ocn_project_noalloc", "ocn_autotune"]
+           "ocn_launches_per_step", "ocn_kernel_times", "ocn_project_noalloc", "ocn_autotune", "ocn_profiles",
+           "ocn_regrid", "ocn_ensemble_create", "ocn_ensemble_destroy", "ocn_ensemble_arena_bytes",
+           "ocn_ensemble_bind_arena", "ocn_ensemble_member", "ocn_ensemble_time_step", "ocn_ensemble_set_option",
+           "ocn_ensemble_autotune", "ocn_ensemble_launches_per_step"]
+OCN_OPT_ENSEMBLE_MODE, OCN_ENSEMBLE_CONCURRENT, OCN_ENSEMBLE_SEQUENTIAL = 5, 0, 1
 
 
 class OcnError(RuntimeError):
@@ -93,10 +97,23 @@ def lib(path: str = LIB_PATH):
     L.ocn_launches_per_step.argtypes = [vp, C.POINTER(C.c_int)]
     L.ocn_kernel_times.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_double)]
     L.ocn_autotune.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    dp = C.POINTER(C.c_double)
+    L.ocn_profiles.argtypes = [vp, dp, C.c_int]
+    L.ocn_regrid.argtypes = [dp, C.c_int, dp, dp, C.c_int, dp]
+    L.ocn_ensemble_create.argtypes = [C.c_int, C.POINTER(GridDesc), C.POINTER(ModelDesc), vp, C.POINTER(vp)]
+    L.ocn_ensemble_destroy.argtypes = [vp]
+    L.ocn_ensemble_destroy.restype = None
+    L.ocn_ensemble_arena_bytes.argtypes = [vp, C.POINTER(sz)]
+    L.ocn_ensemble_bind_arena.argtypes = [vp, vp, sz]
+    L.ocn_ensemble_member.argtypes = [vp, C.c_int, C.POINTER(vp)]
+    L.ocn_ensemble_time_step.argtypes = [vp, C.c_double, C.c_int]
+    L.ocn_ensemble_set_option.argtypes = [vp, C.c_int, C.c_longlong]
+    L.ocn_ensemble_autotune.argtypes = [vp, C.POINTER(C.c_int)]
+    L.ocn_ensemble_launches_per_step.argtypes = [vp, C.POINTER(C.c_int)]
     L.ocn_project_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                       C.POINTER(C.c_double), vp, vp, vp, vp, vp, C.POINTER(C.c_char_p)]
     for name in EXPORTS:
-        if name not in ("ocn_abi_version", "ocn_last_error", "ocn_grid_destroy", "ocn_model_destroy"):
+        if name not in ("ocn_abi_version", "ocn_last_error", "ocn_grid_destroy", "ocn_model_destroy", "ocn_ensemble_destroy"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -124,6 +141,35 @@ class Grid:
             self._h = None
 
 
+def model_desc(p: dict) -> ModelDesc:
+    """The C model descriptor of a workload dict."""
+    d = ModelDesc()
+    tracers = list(p.get("tracers", ["b"]))
+    d.precision = int(p.get("precision", 32))
+    d.weno_order = int(p.get("weno_order", 5))
+    d.closure = CLOSURES[p.get("closure", "none")]
+    d.nu, d.kappa = float(p.get("nu", 0.0)), float(p.get("kappa", 0.0))
+    d.Cs, d.Cb, d.Pr = float(p.get("Cs", 0.16)), float(p.get("Cb", 1.0)), float(p.get("Pr", 1.0))
+    d.C_amd = float(p.get("C_amd", 1.0 / 12.0))
+    d.f = float(p.get("f", 0.0))
+    d.n_tracers = len(tracers)
+    d.eos = EOS[p.get("eos", "buoyancy_tracer")]
+    d.g, d.alpha, d.beta = float(p.get("g", 9.81)), float(p.get("alpha", 2e-4)), float(p.get("beta", 8e-4))
+    d.T0, d.S0 = float(p.get("T0", 20.0)), float(p.get("S0", 35.0))
+    for n, name in enumerate(["u", "v"] + tracers):
+        d.top_flux[n] = float(p.get("top_flux", {}).get(name, 0.0))
+        d.bottom_flux[n] = float(p.get("bottom_flux", {}).get(name, 0.0))
+    d.fp64_pivots = int(p.get("fp64_pivots", -1))
+    return d
+
+
+def grid_desc(p: dict):
+    zf = np.ascontiguousarray(p["z_faces"], dtype=np.float64)
+    d = GridDesc(int(p["Nx"]), int(p["Ny"]), int(p["Nz"]), float(p["Lx"]), float(p["Ly"]),
+                 zf.ctypes.data_as(C.POINTER(C.c_double)))
+    return d, zf
+
+
 class Model:
     """NonhydrostaticModel on the GPU.  ``params``: a workload dict (see inputs.config)."""
 
@@ -132,31 +178,12 @@ class Model:
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (the library has no CPU path)")
         p = dict(params)
-        self.params = p
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
-        self.tracers = list(p.get("tracers", ["b"]))
-        self.precision = int(p.get("precision", 32))
-        self.dtype = torch.float32 if self.precision == 32 else torch.float64
-        self.np_dtype = np.float32 if self.precision == 32 else np.float64
+        self._setup(p)
         self.grid = Grid(p["Nx"], p["Ny"], p["Nz"], p["Lx"], p["Ly"], p["z_faces"])
-        self.Nx, self.Ny, self.Nz = self.grid.Nx, self.grid.Ny, self.grid.Nz
-        d = ModelDesc()
-        d.precision = self.precision
-        d.weno_order = int(p.get("weno_order", 5))
-        d.closure = CLOSURES[p.get("closure", "none")]
-        d.nu, d.kappa = float(p.get("nu", 0.0)), float(p.get("kappa", 0.0))
-        d.Cs, d.Cb, d.Pr = float(p.get("Cs", 0.16)), float(p.get("Cb", 1.0)), float(p.get("Pr", 1.0))
-        d.C_amd = float(p.get("C_amd", 1.0 / 12.0))
-        d.f = float(p.get("f", 0.0))
-        d.n_tracers = len(self.tracers)
-        d.eos = EOS[p.get("eos", "buoyancy_tracer")]
-        d.g, d.alpha, d.beta = float(p.get("g", 9.81)), float(p.get("alpha", 2e-4)), float(p.get("beta", 8e-4))
-        d.T0, d.S0 = float(p.get("T0", 20.0)), float(p.get("S0", 35.0))
-        for n, name in enumerate(["u", "v"] + self.tracers):
-            d.top_flux[n] = float(p.get("top_flux", {}).get(name, 0.0))
-            d.bottom_flux[n] = float(p.get("bottom_flux", {}).get(name, 0.0))
-        d.fp64_pivots = int(p.get("fp64_pivots", -1))
+        d = model_desc(p)
         self._desc = d
+        self._owner = True
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
             h = C.c_void_p()
@@ -171,10 +198,27 @@ class Model:
             _check(lib().ocn_model_bind_arena(self._h, C.c_void_p(self.arena.data_ptr()), self.arena_bytes),
                    "ocn_model_bind_arena")
 
+    def _setup(self, p: dict):
+        import torch
+        self.params = p
+        self.tracers = list(p.get("tracers", ["b"]))
+        self.precision = int(p.get("precision", 32))
+        self.dtype = torch.float32 if self.precision == 32 else torch.float64
+        self.np_dtype = np.float32 if self.precision == 32 else np.float64
+        self.Nx, self.Ny, self.Nz = int(p["Nx"]), int(p["Ny"]), int(p["Nz"])
+
+    @classmethod
+    def borrowed(cls, handle, params: dict, device, stream, owner):
+        """A handle owned by someone else (an ensemble member): never destroyed here."""
+        m = cls.__new__(cls)
+        m._setup(dict(params))
+        m.device, m.stream, m._h, m._owner, m._keep = device, stream, handle, False, owner
+        return m
+
     def __del__(self):
-        if getattr(self, "_h", None):
+        if getattr(self, "_h", None) and getattr(self, "_owner", False):
             lib().ocn_model_destroy(self._h)
-            self._h = None
+        self._h = None
 
     # ------------------------------------------------------------------ fields
     def fid(self, name: str) -> int:
@@ -271,6 +315,16 @@ class Model:
         _check(lib().ocn_launches_per_step(self._h, C.byref(n)), "ocn_launches_per_step")
         return n.value
 
+    def profiles(self) -> dict:
+        """Coarse-graining profiles: level means of b, u, v and mean face fluxes of b, u, v."""
+        Nz = self.Nz
+        out = (C.c_double * (3 * Nz + 3 * (Nz + 1)))()
+        _check(lib().ocn_profiles(self._h, out, len(out)), "ocn_profiles")
+        a = np.frombuffer(out, dtype=np.float64).copy()
+        F = a[3 * Nz:]
+        return {"b": a[:Nz], "u": a[Nz:2 * Nz], "v": a[2 * Nz:3 * Nz],
+                "Fb": F[:Nz + 1], "Fu": F[Nz + 1:2 * (Nz + 1)], "Fv": F[2 * (Nz + 1):]}
+
     def kernel_times(self) -> dict:
         """{kernel class: (launches, summed ms)} recorded while OCN_OPT_KERNEL_TIMING is on."""
         n = len(KERNEL_CLASSES)
@@ -286,6 +340,82 @@ class Model:
         ms = (C.c_double * TENDENCY_VARIANTS)()
         _check(lib().ocn_autotune(self._h, C.byref(best), ms), "ocn_autotune")
         return best.value, list(ms)
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+
+def regrid(zf_in, values, zf_out) -> np.ndarray:
+    """Conservative regridding of cell averages between ascending face lists (library host code)."""
+    dp = C.POINTER(C.c_double)
+    zi = np.ascontiguousarray(zf_in, dtype=np.float64); v = np.ascontiguousarray(values, dtype=np.float64)
+    zo = np.ascontiguousarray(zf_out, dtype=np.float64); out = np.zeros(zo.size - 1)
+    _check(lib().ocn_regrid(zi.ctypes.data_as(dp), v.size, v.ctypes.data_as(dp), zo.ctypes.data_as(dp), out.size,
+                            out.ctypes.data_as(dp)), "ocn_regrid")
+    return out
+
+
+class Ensemble:
+    """Many independent members (uneven sizes and forcings) stepped together on one GPU."""
+
+    def __init__(self, params_list, device=None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (the library has no CPU path)")
+        self.params = [dict(p) for p in params_list]
+        n = len(self.params)
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        grids = (GridDesc * n)()
+        models = (ModelDesc * n)()
+        self._zf = []
+        for i, p in enumerate(self.params):
+            gd, zf = grid_desc(p)
+            self._zf.append(zf)
+            grids[i] = gd
+            models[i] = model_desc(p)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+            h = C.c_void_p()
+            _check(lib().ocn_ensemble_create(n, grids, models, C.c_void_p(self.stream.cuda_stream), C.byref(h)),
+                   "ocn_ensemble_create")
+            self._h = h
+            nb = C.c_size_t()
+            _check(lib().ocn_ensemble_arena_bytes(self._h, C.byref(nb)), "ocn_ensemble_arena_bytes")
+            self.arena_bytes = nb.value
+            with torch.cuda.stream(self.stream):
+                self.arena = torch.empty(self.arena_bytes, dtype=torch.uint8, device=self.device)
+            _check(lib().ocn_ensemble_bind_arena(self._h, C.c_void_p(self.arena.data_ptr()), self.arena_bytes),
+                   "ocn_ensemble_bind_arena")
+        self.members = []
+        for i, p in enumerate(self.params):
+            mh = C.c_void_p()
+            _check(lib().ocn_ensemble_member(self._h, i, C.byref(mh)), "ocn_ensemble_member")
+            self.members.append(Model.borrowed(mh, p, self.device, self.stream, self))
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            for m in getattr(self, "members", []):
+                m._h = None
+            lib().ocn_ensemble_destroy(self._h)
+            self._h = None
+
+    def time_step(self, dt: float, nsteps: int = 1):
+        _check(lib().ocn_ensemble_time_step(self._h, float(dt), int(nsteps)), "ocn_ensemble_time_step")
+
+    def set_mode(self, sequential: bool):
+        _check(lib().ocn_ensemble_set_option(self._h, OCN_OPT_ENSEMBLE_MODE,
+                                             OCN_ENSEMBLE_SEQUENTIAL if sequential else OCN_ENSEMBLE_CONCURRENT),
+               "ocn_ensemble_set_option")
+
+    def autotune(self):
+        v = (C.c_int * len(self.members))()
+        _check(lib().ocn_ensemble_autotune(self._h, v), "ocn_ensemble_autotune")
+        return list(v)
+
+    def launches_per_step(self) -> int:
+        n = C.c_int()
+        _check(lib().ocn_ensemble_launches_per_step(self._h, C.byref(n)), "ocn_ensemble_launches_per_step")
+        return n.value
 
     def synchronize(self):
         self.stream.synchronize()
