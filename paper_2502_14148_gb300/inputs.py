@@ -104,6 +104,28 @@ def ensemble_configs(n: int = 64, seed: int = SEED, sizes=(64, 96, 128), depths=
     return out
 
 
+MLP_SIZES = (32, 128, 128, 128, 16)
+
+
+def mlp_init(seed: int = SEED, sizes=MLP_SIZES) -> list:
+    """Seeded initial weights of the column-closure network: W_l ~ N(0, 1/n_in), b_l = 0."""
+    out = []
+    for l in range(len(sizes) - 1):
+        g = np.random.Generator(np.random.Philox(key=[seed, 500 + l]))
+        W = g.standard_normal((sizes[l + 1], sizes[l])) / math.sqrt(sizes[l])
+        out.append((W, np.zeros(sizes[l + 1])))
+    return out
+
+
+def mlp_batch(seed: int, M: int, n_in: int = 32, n_out: int = 16, n_real_in: int = 17, n_real_out: int = 3):
+    """A seeded synthetic batch (features zero-padded to n_in, targets to n_out) for kernel tests."""
+    g = np.random.Generator(np.random.Philox(key=[seed, 600]))
+    X = np.zeros((M, n_in)); X[:, :n_real_in] = g.standard_normal((M, n_real_in))
+    T = np.zeros((M, n_out)); T[:, :n_real_out] = g.standard_normal((M, n_real_out))
+    mask = np.zeros(n_out); mask[:n_real_out] = 1.0
+    return X, T, mask
+
+
 def _normal(seed: int, field: int, shape) -> np.ndarray:
     g = np.random.Generator(np.random.Philox(key=[seed, field]))
     return g.standard_normal(size=shape)
