@@ -293,6 +293,53 @@ ocn_status ocn_ensemble_launches_per_step(const ocn_ensemble* ensemble, int* lau
 ocn_status ocn_project_noalloc(int precision, int Nx, int Ny, int Nz, double Lx, double Ly, const double* z_faces,
                                void* u, void* v, void* w, void* p, void* stream, const char** error);
 
+/* Learned column closure: a multilayer perceptron trained and evaluated on the
+ * 5th-generation tensor cores.  The paper motivates closures calibrated on LES
+ * output (Sec. 3.2.3: CATKE is calibrated against a suite of LES; its outlook:
+ * machine-learned parameterisations) but prints no network; this one is
+ *   z_l = h_{l-1} W_l^T + b_l,  h_l = gelu(z_l) (exact erf form) for hidden layers,
+ *   y = h_{L-1} W_L^T + b_L,
+ * with the masked mean-square loss L = (1/2M) sum_m sum_j mask_j (y_mj - t_mj)^2
+ * and Adam (Kingma & Ba 2015, bias-corrected).  Products run in BF16 with FP32
+ * accumulation; master weights, biases, Adam moments and gradients are FP32.
+ *   sizes      nlayers+1 widths (input, hidden..., output), each 16..256 and a multiple of 16
+ *   max_batch  largest M of any later call (rows are padded to a multiple of 128 internally)
+ *   stream     cudaStream_t for all work (NULL: legacy default stream)
+ * Parameters are one flat FP32 array: for each layer W_l [n_out][n_in] (row-major) then
+ * b_l [n_out]; ocn_mlp_num_params gives its length.  The caller allocates the device
+ * arena (ocn_mlp_arena_bytes, 256-byte aligned) and binds it; binding zeroes it.
+ * X [M][n_in], T and Y [M][n_out], mask [n_out] and grads (flat, the parameter layout)
+ * are FP32 device arrays.  ocn_mlp_forward and ocn_mlp_adam return after enqueueing;
+ * ocn_mlp_gradients, ocn_mlp_set_params/get_params (host side) and ocn_mlp_train_step
+ * with a non-null loss synchronise the stream.  loss (host double) receives L.
+ * ocn_mlp_train_step = gradients then one Adam step (lr; beta1 0.9, beta2 0.999, eps 1e-8);
+ * set_params resets the Adam state.  Errors: OCN_ERR_ARG (sizes, batch, null pointers),
+ * OCN_ERR_STATE (no arena), OCN_ERR_CUDA, OCN_ERR_TIMEOUT (a bounded wait for the tensor
+ * cores gave up; the results are then invalid). */
+#define OCN_MLP_MAX_LAYERS 8
+typedef struct ocn_mlp ocn_mlp;
+ocn_status ocn_mlp_create(int nlayers, const int* sizes, int max_batch, void* stream, ocn_mlp** out);
+void ocn_mlp_destroy(ocn_mlp* mlp);
+ocn_status ocn_mlp_arena_bytes(const ocn_mlp* mlp, size_t* bytes);
+ocn_status ocn_mlp_bind_arena(ocn_mlp* mlp, void* device_ptr, size_t bytes);
+ocn_status ocn_mlp_num_params(const ocn_mlp* mlp, size_t* count);
+ocn_status ocn_mlp_set_params(ocn_mlp* mlp, const float* params, size_t count, int src_is_device);
+ocn_status ocn_mlp_get_params(ocn_mlp* mlp, float* params, size_t count, int dst_is_device);
+ocn_status ocn_mlp_forward(ocn_mlp* mlp, const float* X, int M, float* Y);
+ocn_status ocn_mlp_gradients(ocn_mlp* mlp, const float* X, const float* T, const float* mask, int M, float* grads,
+                             double* loss);
+ocn_status ocn_mlp_adam(ocn_mlp* mlp, const float* grads, double lr, double beta1, double beta2, double eps);
+ocn_status ocn_mlp_train_step(ocn_mlp* mlp, const float* X, const float* T, const float* mask, int M, double lr,
+                              double* loss);
+
+/* The tensor-core product under the network, exposed for testing: D = A B^T with
+ * A [M][K] and B [N][K] BF16 device arrays (K contiguous; lda, ldb >= K and multiples
+ * of 8; 16-byte aligned), D [M][ldd] FP32, 16 <= N <= 256 with N a multiple of 16, K a
+ * positive multiple of 8.  status (device int, may be NULL) is set to 1 if a bounded
+ * wait gave up.  Enqueued on stream.  Errors: OCN_ERR_ARG, OCN_ERR_CUDA. */
+ocn_status ocn_gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, int ldb, float* D, int ldd,
+                         int* status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1066,3 +1066,10 @@ ocn_status ocn_launches_per_step(const ocn_model* m, int* launches) {
 }
 
 }  // extern "C"
+
+namespace ocn {
+ocn_status set_last_error(ocn_status s, const char* msg) {
+  g_err = msg;
+  return s;
+}
+}  // namespace ocn

@@ -165,5 +165,32 @@ template <typename T> cudaError_t launch_profile_means(const ProfileArgs<T>& a, 
 template <typename T> cudaError_t launch_level_mean(const T* p, size_t plane, int Nz, T* ref, cudaStream_t s);
 template <typename T> cudaError_t launch_level_shift(T* p, size_t plane, int Nz, const T* ref, T sign, cudaStream_t s);
 int diag_blocks();
+// Records the text returned by ocn_last_error() on this thread and returns s.
+ocn_status set_last_error(ocn_status s, const char* msg);
+
+// Tensor-core GEMM of the learned column closure (mlp.cu):  D = A . B^T with A [M][K] and
+// B [N][K] BF16 (K contiguous, lda/ldb multiples of 8 elements, 16-byte aligned bases),
+// FP32 accumulation, 16 <= N <= 256 (multiple of 16), K a multiple of 8.  Split-K over
+// gridDim.y: split y covers K range [y*kchunk, (y+1)*kchunk) (kchunk a multiple of 64).
+// Epilogue (row r, column c, x = accumulated value):
+//   mode 0: D[(y*M + r)*ldd + c] = x                        (split-K partials)
+//   mode 1: z = x + bias[c]; D[r*ldd+c] = z (if D); H[r*ldh+c] = bf16(gelu(z));
+//           HT[c*ldht+r] = bf16(gelu(z)) (if HT)
+//   mode 2: D[r*ldd+c] = x + bias[c]
+//   mode 3: g = x * gelu'(Z[r*ldz+c]); D[r*ldd+c] = g (if D); H, HT as mode 1 with g
+// status (if not null) is set to 1 when a bounded wait for the tensor cores gave up.
+struct GemmArgs {
+  const void* A; int lda;
+  const void* B; int ldb;
+  int M, N, K, kchunk;
+  int mode;
+  float* D; int ldd;
+  const float* bias;
+  void* H; int ldh;
+  void* HT; int ldht;
+  const float* Z; int ldz;
+  int* status;
+};
+cudaError_t launch_gemm_tc(const GemmArgs& a, int nsplit, cudaStream_t s);
 
 }  // namespace ocn

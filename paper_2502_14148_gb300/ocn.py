@@ -39,7 +39,10 @@ EXPORTS = ["ocn_abi_version", "ocn_last_error", "ocn_grid_create", "ocn_grid_des
            "ocn_launches_per_step", "ocn_kernel_times", "ocn_project_noalloc", "ocn_autotune", "ocn_profiles",
            "ocn_regrid", "ocn_ensemble_create", "ocn_ensemble_destroy", "ocn_ensemble_arena_bytes",
            "ocn_ensemble_bind_arena", "ocn_ensemble_member", "ocn_ensemble_time_step", "ocn_ensemble_set_option",
-           "ocn_ensemble_autotune", "ocn_ensemble_launches_per_step"]
+           "ocn_ensemble_autotune", "ocn_ensemble_launches_per_step", "ocn_mlp_create", "ocn_mlp_destroy",
+           "ocn_mlp_arena_bytes", "ocn_mlp_bind_arena", "ocn_mlp_num_params", "ocn_mlp_set_params",
+           "ocn_mlp_get_params", "ocn_mlp_forward", "ocn_mlp_gradients", "ocn_mlp_adam", "ocn_mlp_train_step",
+           "ocn_gemm_bf16"]
 OCN_OPT_ENSEMBLE_MODE, OCN_ENSEMBLE_CONCURRENT, OCN_ENSEMBLE_SEQUENTIAL = 5, 0, 1
 
 
@@ -112,8 +115,23 @@ def lib(path: str = LIB_PATH):
     L.ocn_ensemble_launches_per_step.argtypes = [vp, C.POINTER(C.c_int)]
     L.ocn_project_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                       C.POINTER(C.c_double), vp, vp, vp, vp, vp, C.POINTER(C.c_char_p)]
+    ip = C.POINTER(C.c_int)
+    L.ocn_mlp_create.argtypes = [C.c_int, ip, C.c_int, vp, C.POINTER(vp)]
+    L.ocn_mlp_destroy.argtypes = [vp]
+    L.ocn_mlp_destroy.restype = None
+    L.ocn_mlp_arena_bytes.argtypes = [vp, C.POINTER(sz)]
+    L.ocn_mlp_bind_arena.argtypes = [vp, vp, sz]
+    L.ocn_mlp_num_params.argtypes = [vp, C.POINTER(sz)]
+    L.ocn_mlp_set_params.argtypes = [vp, vp, sz, C.c_int]
+    L.ocn_mlp_get_params.argtypes = [vp, vp, sz, C.c_int]
+    L.ocn_mlp_forward.argtypes = [vp, vp, C.c_int, vp]
+    L.ocn_mlp_gradients.argtypes = [vp, vp, vp, vp, C.c_int, vp, dp]
+    L.ocn_mlp_adam.argtypes = [vp, vp, C.c_double, C.c_double, C.c_double, C.c_double]
+    L.ocn_mlp_train_step.argtypes = [vp, vp, vp, vp, C.c_int, C.c_double, dp]
+    L.ocn_gemm_bf16.argtypes = [C.c_int, C.c_int, C.c_int, vp, C.c_int, vp, C.c_int, vp, C.c_int, vp, vp]
     for name in EXPORTS:
-        if name not in ("ocn_abi_version", "ocn_last_error", "ocn_grid_destroy", "ocn_model_destroy", "ocn_ensemble_destroy"):
+        if name not in ("ocn_abi_version", "ocn_last_error", "ocn_grid_destroy", "ocn_model_destroy", "ocn_ensemble_destroy",
+                        "ocn_mlp_destroy"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -419,3 +437,124 @@ class Ensemble:
 
     def synchronize(self):
         self.stream.synchronize()
+
+
+def gemm_bf16(A, B, status=None, stream=None):
+    """D = A B^T on the tensor cores (A [M][K], B [N][K] BF16 CUDA tensors) -> FP32 [M][N]."""
+    import torch
+    assert A.dtype == torch.bfloat16 and B.dtype == torch.bfloat16 and A.is_cuda and B.is_cuda
+    A, B = A.contiguous(), B.contiguous()
+    M, K = A.shape
+    N = B.shape[0]
+    D = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    s = stream if stream is not None else torch.cuda.current_stream(A.device)
+    _check(lib().ocn_gemm_bf16(M, N, K, C.c_void_p(A.data_ptr()), K, C.c_void_p(B.data_ptr()), K,
+                               C.c_void_p(D.data_ptr()), N,
+                               C.c_void_p(status.data_ptr()) if status is not None else None,
+                               C.c_void_p(s.cuda_stream)), "ocn_gemm_bf16")
+    return D
+
+
+class MLP:
+    """The learned column closure's network on the tensor cores (see ocn_mlp_* in include/ocn.h)."""
+
+    def __init__(self, sizes, max_batch: int, device=None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (the library has no CPU path)")
+        self.sizes = tuple(int(x) for x in sizes)
+        self.max_batch = int(max_batch)
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+            arr = (C.c_int * len(self.sizes))(*self.sizes)
+            h = C.c_void_p()
+            _check(lib().ocn_mlp_create(len(self.sizes) - 1, arr, self.max_batch, C.c_void_p(self.stream.cuda_stream),
+                                        C.byref(h)), "ocn_mlp_create")
+            self._h = h
+            nb = C.c_size_t()
+            _check(lib().ocn_mlp_arena_bytes(self._h, C.byref(nb)), "ocn_mlp_arena_bytes")
+            with torch.cuda.stream(self.stream):
+                self.arena = torch.empty(nb.value + 256, dtype=torch.uint8, device=self.device)
+            base = self.arena.data_ptr()
+            aligned = (base + 255) // 256 * 256
+            _check(lib().ocn_mlp_bind_arena(self._h, C.c_void_p(aligned), nb.value), "ocn_mlp_bind_arena")
+            n = C.c_size_t()
+            _check(lib().ocn_mlp_num_params(self._h, C.byref(n)), "ocn_mlp_num_params")
+            self.nparams = n.value
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().ocn_mlp_destroy(self._h)
+            self._h = None
+
+    @staticmethod
+    def flatten(params) -> np.ndarray:
+        """[(W_l [n_out][n_in], b_l)] -> the flat FP32 parameter layout."""
+        return np.concatenate([np.concatenate([np.asarray(W, np.float32).ravel(), np.asarray(b, np.float32)])
+                               for W, b in params]).astype(np.float32)
+
+    def unflatten(self, flat) -> list:
+        out, o = [], 0
+        for l in range(len(self.sizes) - 1):
+            ni, no = self.sizes[l], self.sizes[l + 1]
+            W = np.asarray(flat[o:o + no * ni]).reshape(no, ni); o += no * ni
+            b = np.asarray(flat[o:o + no]); o += no
+            out.append((W, b))
+        return out
+
+    def set_params(self, params):
+        flat = np.ascontiguousarray(self.flatten(params) if isinstance(params, (list, tuple)) else params,
+                                    dtype=np.float32)
+        assert flat.size == self.nparams
+        _check(lib().ocn_mlp_set_params(self._h, C.c_void_p(flat.ctypes.data), flat.size, 0), "ocn_mlp_set_params")
+
+    def get_params(self) -> list:
+        flat = np.zeros(self.nparams, dtype=np.float32)
+        _check(lib().ocn_mlp_get_params(self._h, C.c_void_p(flat.ctypes.data), flat.size, 0), "ocn_mlp_get_params")
+        return self.unflatten(flat)
+
+    def _dev(self, a):
+        import torch
+        return torch.as_tensor(a).to(device=self.device, dtype=torch.float32).contiguous()
+
+    def forward(self, X):
+        import torch
+        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+            X = self._dev(X)
+            Y = torch.empty((X.shape[0], self.sizes[-1]), dtype=torch.float32, device=self.device)
+            _check(lib().ocn_mlp_forward(self._h, C.c_void_p(X.data_ptr()), X.shape[0], C.c_void_p(Y.data_ptr())),
+                   "ocn_mlp_forward")
+        self.stream.synchronize()
+        return Y
+
+    def gradients(self, X, T, mask):
+        """(loss, flat FP32 gradient tensor) of the masked mean-square loss."""
+        import torch
+        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+            X, T, m = self._dev(X), self._dev(T), self._dev(mask)
+            g = torch.empty(self.nparams, dtype=torch.float32, device=self.device)
+            loss = C.c_double()
+            _check(lib().ocn_mlp_gradients(self._h, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()),
+                                           C.c_void_p(m.data_ptr()), X.shape[0], C.c_void_p(g.data_ptr()),
+                                           C.byref(loss)), "ocn_mlp_gradients")
+        return loss.value, g
+
+    def adam(self, grads, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        import torch
+        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+            g = self._dev(grads)
+            _check(lib().ocn_mlp_adam(self._h, C.c_void_p(g.data_ptr()), float(lr), float(beta1), float(beta2),
+                                      float(eps)), "ocn_mlp_adam")
+            self.stream.synchronize()
+
+    def train_step(self, X, T, mask, lr) -> float:
+        """One Adam step on (X, T) (device tensors or arrays); returns the loss before the step."""
+        import torch
+        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+            X, T, m = self._dev(X), self._dev(T), self._dev(mask)
+            loss = C.c_double()
+            _check(lib().ocn_mlp_train_step(self._h, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()),
+                                            C.c_void_p(m.data_ptr()), X.shape[0], float(lr), C.byref(loss)),
+                   "ocn_mlp_train_step")
+        return loss.value
