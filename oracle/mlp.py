@@ -87,3 +87,16 @@ def adam_step(params, grads, state, lr, beta1=0.9, beta2=0.999, eps=1e-8):
             new.append(p - lr * mh / (np.sqrt(vh) + eps))
         out.append((new[0], new[1]))
     return out
+
+
+def closure_fluxes(params, X, mu, sigma, scale, shape):
+    """The learned column closure's face fluxes from raw features X [(Nz+1)*Ny*Nx][NF]:
+    y = forward((X - mu) / sigma), F_q = scale_q * y_q for q = b, ubar, vbar, reshaped to
+    [3][Nz+1][Ny][Nx]; the wall faces carry no flux."""
+    Xn = (np.asarray(X, np.float64) - mu) / sigma
+    y, _ = forward(params, Xn)
+    Nz1, Ny, Nx = shape
+    F = np.stack([scale[q] * y[:, q].reshape(Nz1, Ny, Nx) for q in range(3)])
+    F[:, 0] = 0.0
+    F[:, -1] = 0.0
+    return F

@@ -46,6 +46,9 @@ struct orc_model {
   double *nue, *kape[ORC_MAX_TRACERS];              /* diffusivities at centres */
   double *work;                                     /* Nz*Ny*Nx scratch */
   int have_diff;
+  orc_face_flux_fn flux_fn;                         /* column closure hook (or NULL) */
+  void* flux_ctx;
+  double* Fcol;                                     /* [3][Nz+1][Ny][Nx] face fluxes of b, ubar, vbar */
 };
 
 /* ------------------------------------------------------------------ */
@@ -434,6 +437,8 @@ double orc_tendency_at(orc_model* M, int field, int i, int j, int k) {
   return G_c(M, field - ORC_C0, i, j, k);
 }
 
+static void add_face_flux_divergence(orc_model* M, double* Gu, double* Gv, double* Gb);
+
 static void all_tendencies(orc_model* M, double* Gu, double* Gv, double* Gw, double** Gc) {
   compute_diffusivities(M);
   int Nx = M->Nx, Ny = M->Ny, Nz = M->Nz;
@@ -449,6 +454,7 @@ static void all_tendencies(orc_model* M, double* Gu, double* Gv, double* Gw, dou
       }
   size_t plane = (size_t)Nx * Ny;
   memset(Gw + (size_t)Nz * plane, 0, plane * sizeof(double));
+  if (M->flux_fn) add_face_flux_divergence(M, Gu, Gv, Gc[0]);
 }
 
 void orc_tendencies(orc_model* M, double* Gu, double* Gv, double* Gw, double* Gc) {
@@ -816,7 +822,174 @@ void orc_destroy(orc_model* M) {
   if (!M) return;
   free(M->zf); free(M->zc); free(M->dzc); free(M->dzf);
   free(M->u); free(M->v); free(M->w); free(M->Gu); free(M->Gv); free(M->Gw);
-  free(M->Hu); free(M->Hv); free(M->Hw); free(M->pr); free(M->work); free(M->nue);
+  free(M->Hu); free(M->Hv); free(M->Hw); free(M->pr); free(M->work); free(M->nue); free(M->Fcol);
   for (int n = 0; n < M->nt; ++n) { free(M->c[n]); free(M->Gc[n]); free(M->Hc[n]); free(M->kape[n]); }
   free(M);
+}
+
+/* ================================================================== */
+/* Learned column closure: features, closure fluxes, coarse-graining   */
+/* and the face-flux hook.  Column quantities q = 0: b, 1: ubar (u at   */
+/* the cell centre), 2: vbar; fluxes are upward through the w-faces of  */
+/* the cell-centre columns.                                            */
+static double ubar_c(const orc_model* M, int i, int j, int k) { return 0.5 * (A3(M, M->u, i, j, k) + A3(M, M->u, i + 1, j, k)); }
+static double vbar_c(const orc_model* M, int i, int j, int k) { return 0.5 * (A3(M, M->v, i, j, k) + A3(M, M->v, i, j + 1, k)); }
+static double colq(const orc_model* M, int q, int i, int j, int k) {
+  return q == 0 ? buoyancy(M, i, j, k) : (q == 1 ? ubar_c(M, i, j, k) : vbar_c(M, i, j, k));
+}
+/* d q / dz across face k; zero outside the interior faces 1..Nz-1 */
+static double colgrad(const orc_model* M, int q, int i, int j, int k) {
+  if (k <= 0 || k >= M->Nz) return 0.0;
+  return (colq(M, q, i, j, k) - colq(M, q, i, j, k - 1)) / M->dzf[k];
+}
+
+void orc_closure_features(orc_model* M, double N2_background, double* X) {
+  int Nx = M->Nx, Ny = M->Ny, Nz = M->Nz;
+  size_t plane = (size_t)Nx * Ny;
+  double* h = (double*)calloc(plane, sizeof(double));
+  if (N2_background > 0.0)
+    for (int j = 0; j < Ny; ++j)
+      for (int i = 0; i < Nx; ++i) {
+        double acc = 0.0;
+        for (int k = 1; k < Nz; ++k) {
+          double deficit = 1.0 - colgrad(M, 0, i, j, k) / N2_background;
+          if (deficit > 0.0) acc += deficit * M->dzf[k];
+        }
+        h[(size_t)j * Nx + i] = acc;
+      }
+#pragma omp parallel for collapse(2)
+  for (int k = 0; k <= Nz; ++k)
+    for (int j = 0; j < Ny; ++j)
+      for (int i = 0; i < Nx; ++i) {
+        double* x = X + (((size_t)k * Ny + j) * Nx + i) * ORC_NF;
+        for (int n = 0; n < ORC_NF; ++n) x[n] = 0.0;
+        for (int m = -2; m <= 2; ++m) {
+          x[0 + m + 2] = colgrad(M, 0, i, j, k + m);
+          x[5 + m + 2] = colgrad(M, 1, i, j, k + m);
+          x[10 + m + 2] = colgrad(M, 2, i, j, k + m);
+        }
+        x[15] = M->p.top_flux[2];
+        x[16] = M->p.f;
+        x[17] = N2_background;
+        x[18] = M->zf[Nz] - M->zf[k];
+        x[19] = h[(size_t)j * Nx + i];
+      }
+  free(h);
+}
+
+/* closure (SGS) vertical flux of b, ubar, vbar at face k of column (i,j), 0 at the walls */
+static double col_sgs_flux(const orc_model* M, int q, int i, int j, int k) {
+  if (k <= 0 || k >= M->Nz) return 0.0;
+  if (q == 0) {
+    if (M->p.eos == ORC_EOS_LINEAR_TS) {
+      double fT = -0.5 * (KAP(M, 0, i, j, k - 1) + KAP(M, 0, i, j, k)) * dcdz_ccf(M, M->c[0], i, j, k);
+      double fS = -0.5 * (KAP(M, 1, i, j, k - 1) + KAP(M, 1, i, j, k)) * dcdz_ccf(M, M->c[1], i, j, k);
+      if (M->p.closure == ORC_CLOSURE_SCALAR) { fT = -M->p.kappa * dcdz_ccf(M, M->c[0], i, j, k); fS = -M->p.kappa * dcdz_ccf(M, M->c[1], i, j, k); }
+      if (M->p.closure == ORC_CLOSURE_NONE) return 0.0;
+      return M->p.g * (M->p.alpha * fT - M->p.beta * fS);
+    }
+    if (M->p.closure == ORC_CLOSURE_SCALAR) return -M->p.kappa * colgrad(M, 0, i, j, k);
+    if (M->p.closure == ORC_CLOSURE_NONE) return 0.0;
+    return -0.5 * (KAP(M, 0, i, j, k - 1) + KAP(M, 0, i, j, k)) * colgrad(M, 0, i, j, k);
+  }
+  if (M->p.closure == ORC_CLOSURE_SCALAR) return -M->p.nu * colgrad(M, q, i, j, k);
+  if (M->p.closure == ORC_CLOSURE_NONE) return 0.0;
+  return -0.5 * (NU(M, i, j, k - 1) + NU(M, i, j, k)) * colgrad(M, q, i, j, k);
+}
+
+void orc_column_sgs_flux(orc_model* M, double* F) {
+  int Nx = M->Nx, Ny = M->Ny, Nz = M->Nz;
+  size_t plane = (size_t)Nx * Ny, NW = plane * (Nz + 1);
+  compute_diffusivities(M);
+#pragma omp parallel for collapse(2)
+  for (int k = 0; k <= Nz; ++k)
+    for (int j = 0; j < Ny; ++j)
+      for (int i = 0; i < Nx; ++i)
+        for (int q = 0; q < 3; ++q) F[q * NW + ((size_t)k * Ny + j) * Nx + i] = col_sgs_flux(M, q, i, j, k);
+  M->have_diff = 0;
+}
+
+void orc_coarse_grain(orc_model* M, int cx, int cy, double* out) {
+  int Nx = M->Nx, Ny = M->Ny, Nz = M->Nz;
+  int rx = Nx / cx, ry = Ny / cy;
+  size_t cp = (size_t)cx * cy;
+  double* uc = out;
+  double* vc = uc + (size_t)Nz * cp;
+  double* wc = vc + (size_t)Nz * cp;
+  double* bc = wc + (size_t)(Nz + 1) * cp;
+  double* tau = bc + (size_t)Nz * cp;
+  compute_diffusivities(M);
+  double inv = 1.0 / ((double)rx * ry);
+#pragma omp parallel for collapse(2)
+  for (int k = 0; k <= Nz; ++k)
+    for (int J = 0; J < cy; ++J)
+      for (int I = 0; I < cx; ++I) {
+        size_t cid = ((size_t)k * cy + J) * cx + I;
+        double su = 0, sv = 0, sw = 0, sb = 0;
+        double swq[3] = {0, 0, 0}, sq[3] = {0, 0, 0}, ssgs[3] = {0, 0, 0};
+        for (int jj = 0; jj < ry; ++jj)
+          for (int ii = 0; ii < rx; ++ii) {
+            int i = I * rx + ii, j = J * ry + jj;
+            double w = A3(M, M->w, i, j, k);
+            sw += w;
+            if (k < Nz) {
+              sb += buoyancy(M, i, j, k);
+              if (ii == 0) su += A3(M, M->u, i, j, k);      /* the coarse x-face coincides with fine face I*rx */
+              if (jj == 0) sv += A3(M, M->v, i, j, k);
+            }
+            if (k > 0 && k < Nz)
+              for (int q = 0; q < 3; ++q) {
+                double qf = 0.5 * (colq(M, q, i, j, k - 1) + colq(M, q, i, j, k));
+                swq[q] += w * qf;
+                sq[q] += qf;
+                ssgs[q] += col_sgs_flux(M, q, i, j, k);
+              }
+          }
+        wc[cid] = sw * inv;
+        if (k < Nz) {
+          bc[cid] = sb * inv;
+          uc[cid] = su / ry;
+          vc[cid] = sv / rx;
+        }
+        for (int q = 0; q < 3; ++q) {
+          double t = 0.0;
+          if (k > 0 && k < Nz) t = swq[q] * inv - (sw * inv) * (sq[q] * inv) + ssgs[q] * inv;
+          tau[(size_t)q * (Nz + 1) * cp + cid] = t;
+        }
+      }
+  M->have_diff = 0;
+}
+
+void orc_set_face_flux(orc_model* M, orc_face_flux_fn fn, void* ctx) {
+  M->flux_fn = fn;
+  M->flux_ctx = ctx;
+  if (fn && !M->Fcol) M->Fcol = (double*)calloc((size_t)3 * (M->Nz + 1) * M->Nx * M->Ny, sizeof(double));
+}
+
+/* G_b -= dF_b/dz at centres; G_u, G_v -= dF/dz of the face flux averaged onto the u and v columns.
+ * The flux through the wall faces (k = 0, Nz) is taken as zero whatever the hook wrote. */
+static void add_face_flux_divergence(orc_model* M, double* Gu, double* Gv, double* Gb) {
+  int Nx = M->Nx, Ny = M->Ny, Nz = M->Nz;
+  size_t plane = (size_t)Nx * Ny, NW = plane * (Nz + 1);
+  M->flux_fn(M->flux_ctx, M, M->Fcol);
+  double* F = M->Fcol;
+  for (int q = 0; q < 3; ++q) {
+    memset(F + q * NW, 0, plane * sizeof(double));
+    memset(F + q * NW + (size_t)Nz * plane, 0, plane * sizeof(double));
+  }
+  const double *Fb = F, *Fu = F + NW, *Fv = F + 2 * NW;
+#pragma omp parallel for collapse(2)
+  for (int k = 0; k < Nz; ++k)
+    for (int j = 0; j < Ny; ++j)
+      for (int i = 0; i < Nx; ++i) {
+        size_t id = ID(M, i, j, k);
+        double r = 1.0 / M->dzc[k];
+        Gb[id] -= (A3(M, Fb, i, j, k + 1) - A3(M, Fb, i, j, k)) * r;
+        double fu1 = 0.5 * (A3(M, Fu, i - 1, j, k + 1) + A3(M, Fu, i, j, k + 1));
+        double fu0 = 0.5 * (A3(M, Fu, i - 1, j, k) + A3(M, Fu, i, j, k));
+        Gu[id] -= (fu1 - fu0) * r;
+        double fv1 = 0.5 * (A3(M, Fv, i, j - 1, k + 1) + A3(M, Fv, i, j, k + 1));
+        double fv0 = 0.5 * (A3(M, Fv, i, j - 1, k) + A3(M, Fv, i, j, k));
+        Gv[id] -= (fv1 - fv0) * r;
+      }
 }

@@ -88,6 +88,36 @@ void orc_regrid(const double* zf_in, int nin, const double* in, const double* zf
  * out holds 3*Nz + 3*(Nz+1) values. */
 void orc_profiles(orc_model* m, double* out);
 
+/* --- learned column closure (an extension: the paper motivates closures calibrated on LES,
+ * Sec. 3.2.3, but prints no network).  Column quantities: b, ubar = (u_i + u_{i+1})/2 and
+ * vbar = (v_j + v_{j+1})/2 at cell centres; fluxes are upward through the w-faces of the
+ * cell-centre columns, zero at the walls, arrays [3][Nz+1][Ny][Nx] (b, ubar, vbar). --- */
+enum { ORC_NF = 32, ORC_NF_USED = 20 };
+/* Raw features of every w-face (sample (k, j, i), i fastest; ORC_NF values each, zero padded):
+ *   0-4   db/dz at faces k-2..k+2, 5-9 dubar/dz, 10-14 dvbar/dz (0 for faces outside 1..Nz-1)
+ *   15    surface buoyancy flux (top_flux of tracer 0), 16 f, 17 N2_background,
+ *   18    depth of the face below the top, zf[Nz] - zf[k],
+ *   19    column mixed-layer depth estimate h = sum_{q=1}^{Nz-1} max(0, 1 - (db/dz)_q / N2_background) dzf[q]
+ *         (0 when N2_background <= 0). */
+void orc_closure_features(orc_model* m, double N2_background, double* X);
+/* The closure's own vertical flux of b, ubar, vbar through the interior faces:
+ * -kappa_f dq/dz for b, -nu_f dq/dz for ubar and vbar, face diffusivities the mean of the two
+ * adjacent centres (ScalarDiffusivity: kappa, nu; LINEAR_TS: g (alpha F_T - beta F_S)). */
+void orc_column_sgs_flux(orc_model* m, double* F);
+/* Box filter of the state onto a cx x cy coarse horizontal grid (Nx % cx == 0, Ny % cy == 0; the
+ * vertical grid is kept).  out = [u_c Nz*cy*cx][v_c Nz*cy*cx][w_c (Nz+1)*cy*cx][b_c Nz*cy*cx]
+ * [tau 3*(Nz+1)*cy*cx]: u_c the mean of u over the fine faces on coarse x-face I (rx = Nx/cx fine
+ * columns), v_c likewise, w_c and b_c box means, and the subfilter vertical flux of q in {b, ubar,
+ * vbar} at the interior faces, tau_q = <w q_f> - <w><q_f> + <F_sgs,q> with q_f = (q_{k-1} + q_k)/2
+ * and F_sgs as in orc_column_sgs_flux (0 at the walls). */
+void orc_coarse_grain(orc_model* m, int cx, int cy, double* out);
+/* Hook: when set, every tendency evaluation of the time stepper (and orc_tendencies) calls
+ * fn(ctx, m, F) with the stage state in m, takes F [3][Nz+1][Ny][Nx] (wall faces forced to 0) and
+ * adds -dF_b/dz to the tendency of tracer 0 and -dF/dz of the ubar/vbar fluxes averaged onto the u
+ * and v columns to G_u and G_v (buoyancy-tracer models).  fn = NULL removes it. */
+typedef void (*orc_face_flux_fn)(void* ctx, orc_model* m, double* F);
+void orc_set_face_flux(orc_model* m, orc_face_flux_fn fn, void* ctx);
+
 /* Discrete divergence at centres, [Nz][Ny][Nx]. */
 void orc_divergence(const orc_model* m, double* out);
 

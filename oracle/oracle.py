@@ -89,6 +89,10 @@ def lib():
         L.orc_grid_metrics.argtypes = [C.c_void_p, dp, dp, dp]
         L.orc_profiles.argtypes = [C.c_void_p, dp]
         L.orc_regrid.argtypes = [dp, C.c_int, dp, dp, C.c_int, dp]
+        L.orc_closure_features.argtypes = [C.c_void_p, C.c_double, dp]
+        L.orc_column_sgs_flux.argtypes = [C.c_void_p, dp]
+        L.orc_coarse_grain.argtypes = [C.c_void_p, C.c_int, C.c_int, dp]
+        L.orc_set_face_flux.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         _lib = L
     return _lib
 
@@ -131,6 +135,9 @@ def regrid(zf_in, values, zf_out) -> np.ndarray:
     lib().orc_regrid(_dp(zi), v.size, _dp(v), _dp(zo), out.size, _dp(out))
     return out
 
+
+NF = 32              # feature vector length of the learned column closure (20 used)
+FACE_FLUX_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.POINTER(C.c_double))
 
 # ---------------------------------------------------------------- model
 FIELD_IDS = {"u": 0, "v": 1, "w": 2, "p": 10}
@@ -256,3 +263,46 @@ class OracleModel:
         d.update(sum_u=out[nt], sum_v=out[nt + 1], sum_w=out[nt + 2], max_div=out[nt + 3], cfl=out[nt + 4],
                  nonfinite=int(out[nt + 5]))
         return d
+
+    # ------------------------------------------------------------ learned column closure
+    def closure_features(self, N2_background: float) -> np.ndarray:
+        """Raw column features of every w-face, [(Nz+1)*Ny*Nx][NF] in (k, j, i) order."""
+        X = np.zeros(((self.Nz + 1) * self.Ny * self.Nx, NF))
+        lib().orc_closure_features(self._h, float(N2_background), _dp(X))
+        return X
+
+    def column_sgs_flux(self) -> np.ndarray:
+        """The closure's vertical flux of b, ubar, vbar, [3][Nz+1][Ny][Nx]."""
+        F = np.zeros((3, self.Nz + 1, self.Ny, self.Nx))
+        lib().orc_column_sgs_flux(self._h, _dp(F))
+        return F
+
+    def coarse_grain(self, cx: int, cy: int) -> dict:
+        """Box filter onto cx x cy columns: coarse u, v, w, b and subfilter fluxes tau [3][Nz+1][cy][cx]."""
+        assert self.Nx % cx == 0 and self.Ny % cy == 0
+        Nz = self.Nz
+        n = cx * cy
+        out = np.zeros(3 * Nz * n + (Nz + 1) * n + 3 * (Nz + 1) * n)
+        lib().orc_coarse_grain(self._h, int(cx), int(cy), _dp(out))
+        o = 0
+        res = {}
+        for name, levels in (("u", Nz), ("v", Nz), ("w", Nz + 1), ("b", Nz)):
+            res[name] = out[o:o + levels * n].reshape(levels, cy, cx); o += levels * n
+        res["tau"] = out[o:].reshape(3, Nz + 1, cy, cx)
+        return res
+
+    def set_face_flux(self, fn):
+        """fn(model) -> F [3][Nz+1][Ny][Nx] called at every tendency evaluation (None removes it).
+        Inside fn, ``model`` is this object with the stage state loaded."""
+        if fn is None:
+            lib().orc_set_face_flux(self._h, None, None)
+            self._flux_cb = None
+            return
+        shape = (3, self.Nz + 1, self.Ny, self.Nx)
+
+        def cb(ctx, h, F):
+            out = np.ctypeslib.as_array(F, shape=shape)
+            out[...] = fn(self)
+
+        self._flux_cb = FACE_FLUX_FN(cb)
+        lib().orc_set_face_flux(self._h, C.cast(self._flux_cb, C.c_void_p), None)
