@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define OCN_ABI_VERSION 1
+#define OCN_ABI_VERSION 2
 #define OCN_MAX_TRACERS 4
 
 typedef enum {
@@ -215,7 +215,8 @@ enum {
   OCN_K_GAUGE = 5,       /* pressure gauge */
   OCN_K_IFFTX = 6,       /* inverse real FFT in x */
   OCN_K_CORRECT = 7,     /* velocity correction */
-  OCN_K_COUNT = 8
+  OCN_K_COLUMN_CLOSURE = 8, /* learned column closure (features + network + flux divergence) */
+  OCN_K_COUNT = 9
 };
 
 /* Launch counts and summed device milliseconds per kernel class, accumulated
@@ -313,7 +314,10 @@ ocn_status ocn_project_noalloc(int precision, int Nx, int Ny, int Nz, double Lx,
  * ocn_mlp_gradients, ocn_mlp_set_params/get_params (host side) and ocn_mlp_train_step
  * with a non-null loss synchronise the stream.  loss (host double) receives L.
  * ocn_mlp_train_step = gradients then one Adam step (lr; beta1 0.9, beta2 0.999, eps 1e-8);
- * set_params resets the Adam state.  Errors: OCN_ERR_ARG (sizes, batch, null pointers),
+ * set_params resets the Adam state.  Parameter updates (set_params from device memory,
+ * ocn_mlp_adam, ocn_mlp_train_step without loss) are ordered on the network's stream only:
+ * a model that uses the network on another stream must be ordered after them by the caller
+ * (for example by synchronising the network's stream).  Errors: OCN_ERR_ARG (sizes, batch, null pointers),
  * OCN_ERR_STATE (no arena), OCN_ERR_CUDA, OCN_ERR_TIMEOUT (a bounded wait for the tensor
  * cores gave up; the results are then invalid). */
 #define OCN_MLP_MAX_LAYERS 8
@@ -331,6 +335,47 @@ ocn_status ocn_mlp_gradients(ocn_mlp* mlp, const float* X, const float* T, const
 ocn_status ocn_mlp_adam(ocn_mlp* mlp, const float* grads, double lr, double beta1, double beta2, double eps);
 ocn_status ocn_mlp_train_step(ocn_mlp* mlp, const float* X, const float* T, const float* mask, int M, double lr,
                               double* loss);
+
+/* Learned column closure of a model (FP32 buoyancy-tracer models; others give
+ * OCN_ERR_UNSUPPORTED).  Each w-face k of each cell-centre column (i, j) gets a
+ * vertical flux F_q, q in {b, ubar, vbar} (ubar = (u_i + u_{i+1})/2, vbar likewise),
+ * predicted by a 32-128-128-128-16 network of ocn_mlp_* from 20 raw features:
+ *   0-4   db/dz at faces k-2..k+2, 5-9 dubar/dz, 10-14 dvbar/dz (0 outside faces 1..Nz-1),
+ *   15    surface buoyancy flux (top_flux of tracer 0), 16 f, 17 N2_background,
+ *   18    depth zf[Nz] - zf[k],
+ *   19    mixed-layer depth estimate sum_{q=1}^{Nz-1} max(0, 1 - (db/dz)_q / N2_background) dz_f[q]
+ *         (0 when N2_background <= 0),
+ * normalised x_n = (x - mu) / sigma (features 20..31 are 0), F_q = out_scale[q] y_q, and
+ * zero at the walls.  Each tendency evaluation then adds -dF_b/dz to G_b, and -dF/dz of the
+ * ubar (vbar) flux averaged onto the u (v) columns to G_u (G_v), on top of the model's own
+ * closure (which stays the fallback: ocn_set_column_closure(m, NULL, NULL) removes the learned
+ * part).  The network is borrowed: it must stay alive and bound while the model steps; later
+ * training of it takes effect at once.  The paper motivates closures calibrated on LES
+ * (Sec. 3.2.3) without specifying one; this closure is an extension.
+ * ocn_closure_features writes the raw features of every face of the current state to X
+ * (device FP32 [(Nz+1)*Ny*Nx][32], sample order k, j, i with i fastest).
+ * ocn_column_fluxes writes F (device FP32 [3][Nz+1][Ny][Nx]) of the current state: which 0 =
+ * the model's own closure flux -kappa_f dq/dz (b), -nu_f dq/dz (ubar, vbar) with face
+ * diffusivities the mean of the two adjacent centres; which 1 = the learned flux.
+ * ocn_coarse_grain box-filters the current state onto a cx x cy horizontal grid (cx | Nx,
+ * cy | Ny; vertical grid kept) into out (device FP64, cx*cy*(7*Nz+4) values):
+ *   [u_c Nz*cy*cx][v_c Nz*cy*cx][w_c (Nz+1)*cy*cx][b_c Nz*cy*cx][tau 3*(Nz+1)*cy*cx],
+ * u_c the mean of u over the fine faces on coarse face I, v_c likewise, w_c and b_c box means,
+ * tau_q = <w q_f> - <w><q_f> + <F_q of which 0> at interior faces, q_f = (q_{k-1} + q_k)/2 (the
+ * subfilter vertical flux that a coarse model does not resolve), 0 at the walls.
+ * All three enqueue on the model stream and return.  Errors: OCN_ERR_ARG, OCN_ERR_STATE,
+ * OCN_ERR_UNSUPPORTED, OCN_ERR_CUDA; a bounded wait that gave up inside the network makes
+ * the next ocn_diagnostics return OCN_ERR_TIMEOUT. */
+typedef struct {
+  float mu[32];              /* feature means */
+  float sigma[32];           /* feature scales, > 0 */
+  float out_scale[3];        /* flux scales of b, ubar, vbar */
+  double N2_background;      /* background stratification (feature 17 and the depth estimate) */
+} ocn_column_closure_desc;
+ocn_status ocn_set_column_closure(ocn_model* model, const ocn_mlp* mlp, const ocn_column_closure_desc* desc);
+ocn_status ocn_closure_features(ocn_model* model, double N2_background, float* X);
+ocn_status ocn_column_fluxes(ocn_model* model, int which, float* F);
+ocn_status ocn_coarse_grain(ocn_model* model, int cx, int cy, double* out, size_t nout);
 
 /* The tensor-core product under the network, exposed for testing: D = A B^T with
  * A [M][K] and B [N][K] BF16 device arrays (K contiguous; lda, ldb >= K and multiples

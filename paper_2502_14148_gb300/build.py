@@ -19,7 +19,7 @@ OBJ = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libocn.so")
 SOURCES = ["capi.cu", "coeffs.cpp", "tendency_f32_r5.cu", "tendency_f32_r3.cu", "tendency_f64.cu", "closure.cu",
-           "poisson.cu", "reduce.cu", "noalloc.cu", "mlp.cu"]
+           "poisson.cu", "reduce.cu", "noalloc.cu", "mlp.cu", "column.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -46,6 +46,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OBJ, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     headers = [os.path.join(CSRC, "ocn_internal.cuh"), os.path.join(CSRC, "tendency_kernel.cuh"),
+               os.path.join(CSRC, "column.cuh"),
                os.path.join(ROOT, "include", "ocn.h")]
     flags = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
              "-I" + os.path.join(ROOT, "include")] + ARCH

@@ -18,6 +18,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "ocn_internal.cuh"
@@ -130,6 +131,14 @@ struct ocn_model {
   std::vector<Rec> recs;
   cudaEvent_t ev_open = nullptr;
   LaunchHook hook;
+  // learned column closure (FP32 buoyancy-tracer models): face fluxes, mixed-layer depths,
+  // face depths, the device status word of its bounded waits; the borrowed network and its
+  // normalisation
+  size_t off_colF = 0, off_colh = 0, off_depth = 0, off_status = 0;
+  const ocn_mlp* colc = nullptr;
+  float colc_mu[kColumnFeatures] = {0}, colc_isig[kColumnFeatures] = {0}, colc_scale[3] = {0, 0, 0};
+  double colc_N2 = 0.0;
+  int colc_version = 0;
 };
 
 struct ocn_ensemble {
@@ -199,6 +208,10 @@ StatePtrs<T> g_ptrs(const ocn_model* m) {
   return s;
 }
 
+bool column_closure_capable(const ocn_model* m) {
+  return m->es == 4 && m->d.eos == OCN_EOS_BUOYANCY_TRACER;
+}
+
 void layout(ocn_model* m) {
   const ocn_grid* g = m->g;
   const size_t plane = (size_t)g->Nx * g->Ny;
@@ -228,6 +241,12 @@ void layout(ocn_model* m) {
   for (int t = 0; t < OCN_MAX_TRACERS; ++t) m->off_cref[t] = (t < m->d.n_tracers) ? take(es * g->Nz) : 0;
   m->off_partial = take(sizeof(double) * (size_t)diag_blocks() * (OCN_MAX_TRACERS + 6));
   m->off_diag = take(sizeof(double) * 16);
+  if (column_closure_capable(m)) {
+    m->off_colF = take(sizeof(float) * 3 * Nw);
+    m->off_colh = take(sizeof(float) * plane);
+    m->off_depth = take(sizeof(float) * (g->Nz + 1));
+    m->off_status = take(sizeof(int));
+  }
   m->bytes = o;
 }
 
@@ -331,6 +350,70 @@ cudaError_t enqueue_tendency(ocn_model* m, int which, double dt_gamma, double dt
   return e;
 }
 
+ColumnArgs column_args(const ocn_model* m, int which, double N2bg) {
+  const ocn_grid* g = m->g;
+  ColumnArgs c;
+  memset(&c, 0, sizeof(c));
+  StatePtrs<float> s = state_ptrs<float>(m, which);
+  c.b = s.c[0]; c.cref = at<float>(m, m->off_cref[0]);
+  c.u = s.u; c.v = s.v; c.w = s.w;
+  c.rdzf = at<float>(m, m->off_rdzf); c.rdzc = at<float>(m, m->off_rdzc); c.dzf = at<float>(m, m->off_dzf);
+  c.depth = at<float>(m, m->off_depth);
+  c.nu = m->off_nu ? at<float>(m, m->off_nu) : nullptr;
+  c.kap = m->off_kap[0] ? at<float>(m, m->off_kap[0]) : nullptr;
+  c.closure = m->d.closure; c.nu0 = (float)m->d.nu; c.kappa0 = (float)m->d.kappa; c.inv_Pr = (float)(1.0 / m->d.Pr);
+  c.Nx = g->Nx; c.Ny = g->Ny; c.Nz = g->Nz;
+  c.Jb = (float)m->d.top_flux[2]; c.f = (float)m->d.f; c.N2bg = (float)N2bg;
+  c.h = at<float>(m, m->off_colh);
+  return c;
+}
+
+// The learned closure's face fluxes for state `which` into F ([3][Nz+1][Ny][Nx] FP32).
+cudaError_t enqueue_learned_flux(ocn_model* m, int which, float* F, int* nlaunch) {
+  MlpClosureArgs a;
+  memset(&a, 0, sizeof(a));
+  a.col = column_args(m, which, m->colc_N2);
+  if (!mlp_closure_layers(m->colc, a.W, a.bias)) return cudaErrorInvalidValue;
+  for (int q = 0; q < kColumnFeatures; ++q) { a.mu[q] = m->colc_mu[q]; a.inv_sigma[q] = m->colc_isig[q]; }
+  for (int q = 0; q < 3; ++q) a.scale[q] = m->colc_scale[q];
+  a.F = F;
+  a.status = at<int>(m, m->off_status);
+  m->hook.pre(OCN_K_COLUMN_CLOSURE);
+  cudaError_t e = launch_column_h(a.col, m->stream);
+  if (e == cudaSuccess) e = launch_mlp_closure(a, m->stream);
+  m->hook.post(OCN_K_COLUMN_CLOSURE);
+  if (nlaunch) *nlaunch += 2;
+  return e;
+}
+
+// Learned column closure after the tendency kernel: G += dG, and in mode 0 the new state
+// += dt_gamma dG, with dG = -dF/dz of the learned face fluxes of the stage state.
+template <typename T>
+cudaError_t enqueue_column_closure(ocn_model* m, int which, double dt_gamma, int mode, int* nlaunch) {
+  if constexpr (!std::is_same<T, float>::value) {
+    return cudaSuccess;
+  } else {
+    if (!m->colc) return cudaSuccess;
+    float* F = at<float>(m, m->off_colF);
+    cudaError_t e = enqueue_learned_flux(m, which, F, nlaunch);
+    if (e != cudaSuccess) return e;
+    FaceFluxArgs f;
+    memset(&f, 0, sizeof(f));
+    StatePtrs<float> G = g_ptrs<float>(m), N = state_ptrs<float>(m, 1 - which);
+    f.F = F;
+    f.Gu = G.u; f.Gv = G.v; f.Gb = G.c[0];
+    f.nu_ = N.u; f.nv = N.v; f.nb = N.c[0];
+    f.rdzc = at<float>(m, m->off_rdzc);
+    f.Nx = m->g->Nx; f.Ny = m->g->Ny; f.Nz = m->g->Nz; f.mode = mode;
+    f.dt_gamma = (float)dt_gamma;
+    m->hook.pre(OCN_K_COLUMN_CLOSURE);
+    e = launch_apply_face_flux(f, m->stream);
+    m->hook.post(OCN_K_COLUMN_CLOSURE);
+    if (nlaunch) *nlaunch += 1;
+    return e;
+  }
+}
+
 cudaError_t check_sync(ocn_model* m, cudaError_t e) {
   if (e != cudaSuccess || !m->sync_check) return e;
   return cudaStreamSynchronize(m->stream);
@@ -349,6 +432,8 @@ cudaError_t enqueue_step(ocn_model* m, double dt, int* which, int* nlaunch) {
     e = check_sync(m, enqueue_tendency<T>(m, *which, gam[st] * dt, zet[st] * dt, 0));
     if (e != cudaSuccess) return e;
     ++n;
+    e = check_sync(m, enqueue_column_closure<T>(m, *which, gam[st] * dt, 0, &n));
+    if (e != cudaSuccess) return e;
     int np = 0;
     e = check_sync(m, launch_projection<T>(poisson_args<T>(m, 1 - *which, (gam[st] - zet[st]) * dt), m->stream, &np, m->hook));
     if (e != cudaSuccess) return e;
@@ -540,6 +625,12 @@ ocn_status ocn_model_bind_arena(ocn_model* m, void* device_ptr, size_t bytes) {
   std::vector<char> blob = (m->es == 4) ? metrics_blob<float>(m) : metrics_blob<double>(m);
   e = cudaMemcpyAsync(m->arena + m->off_dzc, blob.data(), blob.size(), cudaMemcpyHostToDevice, m->stream);
   if (e != cudaSuccess) return cuda_fail(e, "upload metrics");
+  std::vector<float> depth;
+  if (m->off_depth) {
+    for (int k = 0; k <= m->g->Nz; ++k) depth.push_back((float)(m->g->zf[m->g->Nz] - m->g->zf[k]));
+    e = cudaMemcpyAsync(m->arena + m->off_depth, depth.data(), depth.size() * sizeof(float), cudaMemcpyHostToDevice, m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "upload depths");
+  }
   e = cudaStreamSynchronize(m->stream);
   if (e != cudaSuccess) return cuda_fail(e, "bind synchronise");
   return OCN_OK;
@@ -654,6 +745,7 @@ ocn_status ocn_compute_tendencies(ocn_model* m) {
   if (m->es == 4) {
     e = check_sync(m, enqueue_closure<float>(m, m->cur));
     if (e == cudaSuccess) e = check_sync(m, enqueue_tendency<float>(m, m->cur, 0.0, 0.0, 1));
+    if (e == cudaSuccess) e = check_sync(m, enqueue_column_closure<float>(m, m->cur, 0.0, 1, nullptr));
   } else {
     e = check_sync(m, enqueue_closure<double>(m, m->cur));
     if (e == cudaSuccess) e = check_sync(m, enqueue_tendency<double>(m, m->cur, 0.0, 0.0, 1));
@@ -693,6 +785,12 @@ ocn_status ocn_diagnostics(ocn_model* m, double dt, double* out, int nout) {
   for (int t = 0; t < nt; ++t)
     for (int k = 0; k < g->Nz; ++k) out[t] += m->cref_host[t][k] * g->Lx * g->Ly * g->dzc[k];
   out[nt + 4] *= dt;
+  if (m->off_status) {
+    int st = 0;
+    e = cudaMemcpy(&st, m->arena + m->off_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (st) return fail(OCN_ERR_TIMEOUT, "a bounded wait of the learned column closure gave up");
+  }
   if (out[nt + 5] > 0 || !isfinite(out[nt + 3])) return fail(OCN_ERR_NONFINITE, "non-finite values in the state");
   if (out[nt + 4] > 1.0) return fail(OCN_ERR_CFL, "advective CFL number above 1");
   return OCN_OK;
@@ -778,6 +876,7 @@ ocn_status ocn_profiles(ocn_model* m, double* out, int nout) {
     typedef decltype(tag) T;
     cudaError_t err = enqueue_closure<T>(m, m->cur);
     if (err == cudaSuccess) err = enqueue_tendency<T>(m, m->cur, 0.0, 0.0, 1);   // unsplit G, state untouched
+    if (err == cudaSuccess) err = enqueue_column_closure<T>(m, m->cur, 0.0, 1, nullptr);
     if (err != cudaSuccess) return err;
     ProfileArgs<T> pa;
     memset(&pa, 0, sizeof(pa));
@@ -817,6 +916,72 @@ ocn_status ocn_profiles(ocn_model* m, double* out, int nout) {
     if (ts) F1 -= dz * mG1[k];
     Fb[k + 1] = ts ? ga * F0 - gb * F1 : F0;
   }
+  return OCN_OK;
+}
+
+ocn_status ocn_set_column_closure(ocn_model* m, const ocn_mlp* mlp, const ocn_column_closure_desc* d) {
+  if (!m) return fail(OCN_ERR_ARG, "null argument");
+  if (!m->arena) return fail(OCN_ERR_STATE, "arena not bound");
+  if (mlp) {
+    if (!m->off_colF) return fail(OCN_ERR_UNSUPPORTED, "the learned column closure needs an FP32 buoyancy-tracer model");
+    if (!d) return fail(OCN_ERR_ARG, "null closure descriptor");
+    const void* W[4];
+    const float* b[4];
+    if (!mlp_closure_layers(mlp, W, b)) return fail(OCN_ERR_UNSUPPORTED, "the network must be 32-128-128-128-16 with a bound arena");
+    for (int q = 0; q < kColumnFeatures; ++q)
+      if (!(d->sigma[q] > 0.0f) || !isfinite(d->mu[q])) return fail(OCN_ERR_ARG, "sigma must be positive, mu finite");
+    for (int q = 0; q < kColumnFeatures; ++q) { m->colc_mu[q] = d->mu[q]; m->colc_isig[q] = 1.0f / d->sigma[q]; }
+    for (int q = 0; q < 3; ++q) m->colc_scale[q] = d->out_scale[q];
+    m->colc_N2 = d->N2_background;
+  }
+  DeviceGuard dg(m->dev);
+  m->colc = mlp;
+  m->colc_version += 1;
+  drop_graphs(m);
+  return OCN_OK;
+}
+
+ocn_status ocn_closure_features(ocn_model* m, double N2_background, float* X) {
+  if (!m || !X) return fail(OCN_ERR_ARG, "null argument");
+  if (!m->arena) return fail(OCN_ERR_STATE, "arena not bound");
+  if (!m->off_colF) return fail(OCN_ERR_UNSUPPORTED, "column features need an FP32 buoyancy-tracer model");
+  DeviceGuard dg(m->dev);
+  cudaError_t e = launch_closure_features(column_args(m, m->cur, N2_background), X, m->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "features");
+  return OCN_OK;
+}
+
+ocn_status ocn_column_fluxes(ocn_model* m, int which, float* F) {
+  if (!m || !F) return fail(OCN_ERR_ARG, "null argument");
+  if (!m->arena) return fail(OCN_ERR_STATE, "arena not bound");
+  if (!m->off_colF) return fail(OCN_ERR_UNSUPPORTED, "column fluxes need an FP32 buoyancy-tracer model");
+  DeviceGuard dg(m->dev);
+  cudaError_t e;
+  if (which == 0) {
+    e = enqueue_closure<float>(m, m->cur);
+    if (e == cudaSuccess) e = launch_column_sgs_flux(column_args(m, m->cur, 0.0), F, m->stream);
+  } else if (which == 1) {
+    if (!m->colc) return fail(OCN_ERR_STATE, "no learned column closure set");
+    e = enqueue_learned_flux(m, m->cur, F, nullptr);
+  } else {
+    return fail(OCN_ERR_ARG, "which must be 0 (closure) or 1 (learned)");
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "column fluxes");
+  return OCN_OK;
+}
+
+ocn_status ocn_coarse_grain(ocn_model* m, int cx, int cy, double* out, size_t nout) {
+  if (!m || !out) return fail(OCN_ERR_ARG, "null argument");
+  if (!m->arena) return fail(OCN_ERR_STATE, "arena not bound");
+  if (!m->off_colF) return fail(OCN_ERR_UNSUPPORTED, "coarse-graining needs an FP32 buoyancy-tracer model");
+  const ocn_grid* g = m->g;
+  if (cx < 1 || cy < 1 || g->Nx % cx || g->Ny % cy) return fail(OCN_ERR_ARG, "cx, cy must divide Nx, Ny");
+  const size_t need = (size_t)cx * cy * (7 * (size_t)g->Nz + 4);
+  if (nout < need) return fail(OCN_ERR_ARG, "out too small: cx*cy*(7*Nz+4) doubles");
+  DeviceGuard dg(m->dev);
+  cudaError_t e = enqueue_closure<float>(m, m->cur);
+  if (e == cudaSuccess) e = launch_coarse_grain(column_args(m, m->cur, 0.0), cx, cy, out, m->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "coarse grain");
   return OCN_OK;
 }
 
@@ -944,7 +1109,10 @@ ocn_status ensemble_step_t(ocn_ensemble* e, double dt, int nsteps) {
   }
   for (int s = 0; s < nsteps; ++s) {
     std::string key(reinterpret_cast<const char*>(&dt), sizeof(dt));
-    for (ocn_model* m : e->models) { key.push_back((char)('0' + m->cur)); key.push_back((char)('0' + m->variant)); }
+    for (ocn_model* m : e->models) {
+      key.push_back((char)('0' + m->cur)); key.push_back((char)('0' + m->variant));
+      key += std::to_string(m->colc_version); key.push_back('/');
+    }
     auto it = e->graphs.find(key);
     std::vector<int> w(e->n);
     if (it == e->graphs.end()) {

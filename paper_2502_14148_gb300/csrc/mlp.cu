@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <new>
 
+#include "column.cuh"
 #include "ocn_internal.cuh"
 
 namespace ocn {
@@ -239,6 +240,177 @@ cudaError_t launch_gemm_tc(const GemmArgs& a, int nsplit, cudaStream_t s) {
 }  // namespace ocn
 
 // ---------------------------------------------------------------------------------------------
+// Fused learned column closure: for 128 w-faces at a time, the raw features are computed from
+// the state, normalised and rounded to BF16 straight into shared memory, the four layers run on
+// the tensor cores with the activations kept on chip (TMEM accumulator -> bias + GELU in
+// registers -> BF16 operand in shared memory), and the three fluxes are written out.  The
+// weights are staged once per CTA; the CTAs are persistent over the tiles.
+namespace ocn {
+namespace {
+
+constexpr int kCF = kColumnFeatures, kCH = 128, kCO = 16;
+constexpr int kSW1 = 0;                             // W1 [128][32]
+constexpr int kSW2 = kSW1 + kCH * kCF * 2;          // W2 [128][128]
+constexpr int kSW3 = kSW2 + kCH * kCH * 2;          // W3 [128][128]
+constexpr int kSW4 = kSW3 + kCH * kCH * 2;          // W4 [16][128]
+constexpr int kSX = kSW4 + kCO * kCH * 2;           // features [128][32]
+constexpr int kSH = kSX + 128 * kCF * 2;            // activations [128][128]
+constexpr int kSB = kSH + 128 * kCH * 2;            // biases (3*128 + 16 floats)
+constexpr int kClosureSmem = kSB + (3 * kCH + kCO) * 4;
+static_assert(kClosureSmem * 2 > 228 * 1024, "one CTA per SM keeps TMEM allocation non-blocking");
+
+// byte offset of element (r, c) of a [rows][K] K-major BF16 matrix in the no-swizzle core-matrix layout
+__device__ __forceinline__ uint32_t cm_off(int r, int c, int K) {
+  return (uint32_t)((r >> 3) * (K / 8) * 128 + (c >> 3) * 128 + (r & 7) * 16 + (c & 7) * 2);
+}
+
+__device__ __forceinline__ void stage_weights(unsigned char* dst, const __nv_bfloat16* W, int no, int ni) {
+  const int cpr = ni / 8;
+  for (int q = threadIdx.x; q < no * cpr; q += blockDim.x) {
+    const int r = q / cpr, kc = q % cpr;
+    *reinterpret_cast<uint4*>(dst + cm_off(r, 8 * kc, ni)) = *reinterpret_cast<const uint4*>(W + (size_t)r * ni + 8 * kc);
+  }
+}
+
+// Issue one layer: D[128 x N] = A[128 x K] . B[N x K]^T (one thread), then commit to the barrier.
+__device__ __forceinline__ void closure_layer_mma(uint32_t tmem, uint32_t a_addr, uint32_t b_addr, int K, int N,
+                                                  uint64_t* bar) {
+  tc_fence_after();
+  const uint32_t sbo = (uint32_t)(K / 8) * 128;
+  const uint32_t idesc = idesc_bf16(128, N);
+  for (int s = 0; s < K / 16; ++s)
+    mma_bf16(tmem, smem_desc(a_addr + s * 256, 128, sbo), smem_desc(b_addr + s * 256, 128, sbo), idesc, s > 0 ? 1u : 0u);
+  mma_commit(bar);
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(256, 1) k_mlp_closure(const MlpClosureArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const ColumnArgs& c = a.col;
+  const size_t plane = (size_t)c.Nx * c.Ny;
+  const size_t nsamp = plane * (c.Nz + 1), NW = nsamp;
+  const long long ntiles = (long long)((nsamp + 127) / 128);
+  if (warp == 0) tmem_alloc(&tmem_base, 128);
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+  }
+  stage_weights(smem + kSW1, static_cast<const __nv_bfloat16*>(a.W[0]), kCH, kCF);
+  stage_weights(smem + kSW2, static_cast<const __nv_bfloat16*>(a.W[1]), kCH, kCH);
+  stage_weights(smem + kSW3, static_cast<const __nv_bfloat16*>(a.W[2]), kCH, kCH);
+  stage_weights(smem + kSW4, static_cast<const __nv_bfloat16*>(a.W[3]), kCO, kCH);
+  float* sbias = reinterpret_cast<float*>(smem + kSB);
+  for (int q = tid; q < 3 * kCH + kCO; q += blockDim.x) sbias[q] = a.bias[q / kCH][q % kCH];
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  const uint32_t s0 = smem_u32(smem);
+  const int quad = warp & 3, half = warp >> 2;
+  const int row = quad * 32 + lane;                 // the TMEM lane / sample row this thread reads back
+  uint32_t phase = 0;
+  bool ok = true;
+  for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    // ---- features of sample row (tid & 127): half 0 the buoyancy part, half 1 the velocity part
+    {
+      const int r = tid & 127;
+      const size_t sidx = (size_t)t * 128 + r;
+      float x[kCF];
+#pragma unroll
+      for (int q = 0; q < kCF; ++q) x[q] = 0.0f;
+      if (sidx < nsamp) {
+        const int k = (int)(sidx / plane), cc = (int)(sidx % plane), i = cc % c.Nx, j = cc / c.Nx;
+        if (tid < 128) column_features_b(c, i, j, k, x);
+        else column_features_uv(c, i, j, k, x);
+      }
+      const bool part_b = tid < 128;
+#pragma unroll
+      for (int q = 0; q < kCF; ++q) {
+        const bool mine = part_b ? (q < 5 || q >= 15) : (q >= 5 && q < 15);
+        if (mine) {
+          const float xn = (sidx < nsamp && q < 20) ? (x[q] - a.mu[q]) * a.inv_sigma[q] : 0.0f;
+          *reinterpret_cast<__nv_bfloat16*>(smem + kSX + cm_off(r, q, kCF)) = __float2bfloat16_rn(xn);
+        }
+      }
+    }
+    // ---- four layers
+    for (int l = 0; l < 4 && ok; ++l) {
+      fence_proxy_async();
+      tc_fence_before();
+      __syncthreads();
+      if (tid == 0) {
+        const int K = (l == 0) ? kCF : kCH, N = (l == 3) ? kCO : kCH;
+        const uint32_t aa = s0 + ((l == 0) ? kSX : kSH);
+        const uint32_t bb = s0 + (l == 0 ? kSW1 : l == 1 ? kSW2 : l == 2 ? kSW3 : kSW4);
+        closure_layer_mma(tmem, aa, bb, K, N, &bar);
+      }
+      const bool done = mbar_wait_bounded(&bar, phase);
+      phase ^= 1u;
+      tc_fence_after();
+      ok = __syncthreads_and(done) != 0;
+      if (!ok) break;
+      if (l < 3) {
+        const float* bl = sbias + l * kCH;
+        for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 16) {
+          float v[16];
+          tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
+          uint32_t pk[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const __nv_bfloat16 lo = __float2bfloat16_rn(gelu_f(v[2 * q] + bl[c0 + 2 * q]));
+            const __nv_bfloat16 hi = __float2bfloat16_rn(gelu_f(v[2 * q + 1] + bl[c0 + 2 * q + 1]));
+            pk[q] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+          }
+          *reinterpret_cast<uint4*>(smem + kSH + cm_off(row, c0, kCH)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          *reinterpret_cast<uint4*>(smem + kSH + cm_off(row, c0 + 8, kCH)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        }
+      } else if (half == 0) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16), v);
+        const size_t sidx = (size_t)t * 128 + row;
+        if (sidx < nsamp) {
+          const int k = (int)(sidx / plane);
+          const bool wall = (k == 0 || k == c.Nz);
+          const float* b4 = sbias + 3 * kCH;
+#pragma unroll
+          for (int q = 0; q < 3; ++q) a.F[(size_t)q * NW + sidx] = wall ? 0.0f : a.scale[q] * (v[q] + b4[q]);
+        }
+      }
+    }
+  }
+  if (!ok) {
+    if (tid == 0 && a.status) atomicExch(a.status, 1);
+    mbar_wait_bounded(&bar, phase ^ 1u);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, 128);
+}
+
+cudaError_t launch_mlp_closure(const MlpClosureArgs& a, cudaStream_t s) {
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 148;
+  }
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_closure, cudaFuncAttributeMaxDynamicSharedMemorySize, kClosureSmem);
+  if (e != cudaSuccess) return e;
+  const size_t nsamp = (size_t)a.col.Nx * a.col.Ny * (a.col.Nz + 1);
+  const long long ntiles = (long long)((nsamp + 127) / 128);
+  const int grid = (int)(ntiles < nsm ? ntiles : nsm);
+  k_mlp_closure<<<grid, 256, kClosureSmem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace ocn
+
+// ---------------------------------------------------------------------------------------------
 // Elementwise and reduction kernels of the training step.
 namespace ocn {
 namespace {
@@ -370,6 +542,20 @@ struct ocn_mlp {
   char* arena = nullptr;
   template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(arena + off); }
 };
+
+namespace ocn {
+bool mlp_closure_layers(const ocn_mlp* n, const void** W, const float** bias) {
+  static const int shape[5] = {32, 128, 128, 128, 16};
+  if (!n || !n->bound || n->L != 4) return false;
+  for (int l = 0; l <= 4; ++l)
+    if (n->sizes[l] != shape[l]) return false;
+  for (int l = 0; l < 4; ++l) {
+    W[l] = n->arena + n->o_W[l];
+    bias[l] = reinterpret_cast<const float*>(n->arena + n->o_p) + n->boff[l];
+  }
+  return true;
+}
+}  // namespace ocn
 
 namespace {
 
@@ -602,10 +788,13 @@ ocn_status ocn_mlp_set_params(ocn_mlp* n, const float* params, size_t count, int
                                   src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, n->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(n->at<float>(n->o_m), 0, 4 * count, n->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(n->at<float>(n->o_v), 0, 4 * count, n->stream);
-  if (e == cudaSuccess && !src_is_device) e = cudaStreamSynchronize(n->stream);
   if (e != cudaSuccess) return mlp_cuda(e, "set params");
   n->t_adam = 0;
-  return mlp_pack(n);
+  ocn_status st = mlp_pack(n);
+  if (st != OCN_OK) return st;
+  // host input: return with the BF16 copies in place, so that models on other streams see them
+  if (!src_is_device && (e = cudaStreamSynchronize(n->stream)) != cudaSuccess) return mlp_cuda(e, "set params");
+  return OCN_OK;
 }
 
 ocn_status ocn_mlp_get_params(ocn_mlp* n, float* params, size_t count, int dst_is_device) {

@@ -193,4 +193,48 @@ struct GemmArgs {
 };
 cudaError_t launch_gemm_tc(const GemmArgs& a, int nsplit, cudaStream_t s);
 
+// ---- learned column closure (column.cu, mlp.cu); FP32 buoyancy-tracer models.
+// Column quantities: b (stored anomaly + reference profile), ubar = (u_i + u_{i+1})/2,
+// vbar = (v_j + v_{j+1})/2 at centres; fluxes live on the w-faces of the centre columns,
+// arrays [3][Nz+1][Ny][Nx] (b, ubar, vbar).
+constexpr int kColumnFeatures = 32;       // padded feature vector (20 used)
+struct ColumnArgs {
+  const float* b; const float* cref;      // tracer 0 anomaly and its reference profile (or null)
+  const float* u; const float* v; const float* w;
+  const float* rdzf;                      // [Nz+1], 0 at the walls
+  const float* rdzc;                      // [Nz]
+  const float* dzf;                       // [Nz+1]
+  const float* depth;                     // [Nz+1]: zf[Nz] - zf[k]
+  const float* nu; const float* kap;      // eddy viscosity / tracer-0 diffusivity at centres (or null)
+  int closure; float nu0, kappa0, inv_Pr;
+  int Nx, Ny, Nz;
+  float Jb, f, N2bg;                      // surface buoyancy flux, Coriolis, background N^2
+  float* h;                               // [Ny][Nx] mixed-layer depth estimate
+};
+cudaError_t launch_column_h(const ColumnArgs& a, cudaStream_t s);
+cudaError_t launch_closure_features(const ColumnArgs& a, float* X, cudaStream_t s);
+cudaError_t launch_column_sgs_flux(const ColumnArgs& a, float* F, cudaStream_t s);
+cudaError_t launch_coarse_grain(const ColumnArgs& a, int cx, int cy, double* out, cudaStream_t s);
+// G += dG and (mode 0) nxt += dt_gamma dG for dG = -dF/dz of the face fluxes (u, v: averaged onto their columns)
+struct FaceFluxArgs {
+  const float* F;
+  float* Gu; float* Gv; float* Gb;
+  float* nu_; float* nv; float* nb;
+  const float* rdzc;
+  int Nx, Ny, Nz, mode;
+  float dt_gamma;
+};
+cudaError_t launch_apply_face_flux(const FaceFluxArgs& a, cudaStream_t s);
+struct MlpClosureArgs {
+  ColumnArgs col;
+  const void* W[4]; const float* bias[4];  // BF16 weights [n_out][n_in], FP32 biases (32-128-128-128-16)
+  float mu[kColumnFeatures], inv_sigma[kColumnFeatures];
+  float scale[3];
+  float* F;                                // [3][Nz+1][Ny][Nx]
+  int* status;                             // set to 1 if a bounded wait gave up
+};
+cudaError_t launch_mlp_closure(const MlpClosureArgs& a, cudaStream_t s);
+// Layer pointers of a network (mlp.cu): returns false unless its shape is 32-128-128-128-16.
+bool mlp_closure_layers(const ocn_mlp* n, const void** W, const float** bias);
+
 }  // namespace ocn

@@ -129,6 +129,28 @@ __device__ __forceinline__ T weno(const T* s, T vel) {
   }
 }
 
+// Closure-flux arithmetic with every operation rounded on its own.  Plain multiplies and adds
+// may be fused into FMAs by the code generator, and it makes that choice separately for every
+// tile variant; spelling the rounding out keeps all variants bit-identical.
+template <typename T> __device__ __forceinline__ T rmul(T a, T b);
+template <> __device__ __forceinline__ float rmul<float>(float a, float b) { return __fmul_rn(a, b); }
+template <> __device__ __forceinline__ double rmul<double>(double a, double b) { return __dmul_rn(a, b); }
+template <typename T> __device__ __forceinline__ T radd(T a, T b);
+template <> __device__ __forceinline__ float radd<float>(float a, float b) { return __fadd_rn(a, b); }
+template <> __device__ __forceinline__ double radd<double>(double a, double b) { return __dadd_rn(a, b); }
+template <typename T> __device__ __forceinline__ T rsub(T a, T b) { return radd<T>(a, -b); }
+// F - c g
+template <typename T> __device__ __forceinline__ T rflux(T F, T c, T g) { return rsub<T>(F, rmul<T>(c, g)); }
+// (a + b + c + d) / 4 and (a + b) / 2
+template <typename T> __device__ __forceinline__ T ravg4(T a, T b, T c, T d) {
+  return rmul<T>(T(0.25), radd<T>(radd<T>(radd<T>(a, b), c), d));
+}
+template <typename T> __device__ __forceinline__ T ravg2(T a, T b) { return rmul<T>(T(0.5), radd<T>(a, b)); }
+// half the sum of a difference quotient and a gradient: ((x - y) r + g) / 2
+template <typename T> __device__ __forceinline__ T rstrain(T x, T y, T r, T g) {
+  return rmul<T>(T(0.5), radd<T>(rmul<T>(rsub<T>(x, y), r), g));
+}
+
 // Centered reconstruction of order 2p at the interface between s[p-1] and s[p].
 template <typename T, int p>
 __device__ __forceinline__ T centered(const T* s) {
@@ -364,8 +386,8 @@ k_tendency(const TendencyArgs<T> a) {
         const T U = centered<T, P>(s + R - P);
         T F = U * weno<T, R>(s, U);
         const T du = (s[R] - s[R - 1]) * rdx;
-        if (scalar) F -= a.nu0 * du;
-        else if (stress) F -= T(2) * pN0[rowc - 1] * du;
+        if (scalar) F = rflux<T>(F, a.nu0, du);
+        else if (stress) F = rflux<T>(F, rmul<T>(T(2), pN0[rowc - 1]), du);
         if (active) FX[0 * FXS + ly * (TX + 1) + lx] = F;
       }
       // v at (face i, face j): advecting centered_y(u), advected WENO_x(v)
@@ -379,11 +401,11 @@ k_tendency(const TendencyArgs<T> a) {
         for (int n = 0; n < 2 * R; ++n) sv[n] = pV[rowc - R + n];
         T F = U * weno<T, R>(sv, U);
         const T dvdx = (sv[R] - sv[R - 1]) * rdx;
-        if (scalar) F -= a.nu0 * dvdx;
+        if (scalar) F = rflux<T>(F, a.nu0, dvdx);
         else if (stress) {
-          const T nuf = T(0.25) * (pN0[rowc - 1 - PW] + pN0[rowc - PW] + pN0[rowc - 1] + pN0[rowc]);
-          const T S12 = T(0.5) * ((pU[rowc] - pU[rowc - PW]) * rdy + dvdx);
-          F -= T(2) * nuf * S12;
+          const T nuf = ravg4<T>(pN0[rowc - 1 - PW], pN0[rowc - PW], pN0[rowc - 1], pN0[rowc]);
+          const T S12 = rstrain<T>(pU[rowc], pU[rowc - PW], rdy, dvdx);
+          F = rflux<T>(F, rmul<T>(T(2), nuf), S12);
         }
         if (active) FX[1 * FXS + ly * (TX + 1) + lx] = F;
       }
@@ -398,11 +420,11 @@ k_tendency(const TendencyArgs<T> a) {
           for (int n = 0; n < 2 * R; ++n) sw[n] = pW0[rowc - R + n];
           F = U * weno<T, R>(sw, U);
           const T dwdx = (sw[R] - sw[R - 1]) * rdx;
-          if (scalar) F -= a.nu0 * dwdx;
+          if (scalar) F = rflux<T>(F, a.nu0, dwdx);
           else if (stress) {
-            const T nuf = T(0.25) * (pNm[rowc - 1] + pNm[rowc] + pN0[rowc - 1] + pN0[rowc]);
-            const T S13 = T(0.5) * ((ru[R - 1] - ru[R - 2]) * rdzf_k + dwdx);
-            F -= T(2) * nuf * S13;
+            const T nuf = ravg4<T>(pNm[rowc - 1], pNm[rowc], pN0[rowc - 1], pN0[rowc]);
+            const T S13 = rstrain<T>(ru[R - 1], ru[R - 2], rdzf_k, dwdx);
+            F = rflux<T>(F, rmul<T>(T(2), nuf), S13);
           }
         }
         if (active) FX[2 * FXS + ly * (TX + 1) + lx] = F;
@@ -417,9 +439,9 @@ k_tendency(const TendencyArgs<T> a) {
         const T U = pU[rowc];
         T F = U * (weno<T, R>(sc, U) + crk[t]);    // reconstruction commutes with the level's constant shift
         const T dc = (sc[R] - sc[R - 1]) * rdx;
-        if (scalar) F -= a.kappa0 * dc;
-        else if (amd) { const T* pK = sK + (3 * t + k % 3) * PLANE; F -= T(0.5) * (pK[rowc - 1] + pK[rowc]) * dc; }
-        else if (stress) F -= T(0.5) * a.inv_Pr * (pN0[rowc - 1] + pN0[rowc]) * dc;
+        if (scalar) F = rflux<T>(F, a.kappa0, dc);
+        else if (amd) { const T* pK = sK + (3 * t + k % 3) * PLANE; F = rflux<T>(F, ravg2<T>(pK[rowc - 1], pK[rowc]), dc); }
+        else if (stress) F = rflux<T>(F, rmul<T>(a.inv_Pr, ravg2<T>(pN0[rowc - 1], pN0[rowc])), dc);
         if (active) FX[(3 + t) * FXS + ly * (TX + 1) + lx] = F;
       }
     }
@@ -437,11 +459,11 @@ k_tendency(const TendencyArgs<T> a) {
         for (int n = 0; n < 2 * R; ++n) su[n] = pU[rowc + (n - R) * PW];
         T F = V * weno<T, R>(su, V);
         const T dudy = (su[R] - su[R - 1]) * rdy;
-        if (scalar) F -= a.nu0 * dudy;
+        if (scalar) F = rflux<T>(F, a.nu0, dudy);
         else if (stress) {
-          const T nuf = T(0.25) * (pN0[rowc - 1 - PW] + pN0[rowc - PW] + pN0[rowc - 1] + pN0[rowc]);
-          const T S12 = T(0.5) * (dudy + (pV[rowc] - pV[rowc - 1]) * rdx);
-          F -= T(2) * nuf * S12;
+          const T nuf = ravg4<T>(pN0[rowc - 1 - PW], pN0[rowc - PW], pN0[rowc - 1], pN0[rowc]);
+          const T S12 = rstrain<T>(pV[rowc], pV[rowc - 1], rdx, dudy);
+          F = rflux<T>(F, rmul<T>(T(2), nuf), S12);
         }
         if (active) FY[0 * FYS + ly * TX + lx] = F;
       }
@@ -453,8 +475,8 @@ k_tendency(const TendencyArgs<T> a) {
         const T V = centered<T, P>(sv + R - P);
         T F = V * weno<T, R>(sv, V);
         const T dv = (sv[R] - sv[R - 1]) * rdy;
-        if (scalar) F -= a.nu0 * dv;
-        else if (stress) F -= T(2) * pN0[rowc - PW] * dv;
+        if (scalar) F = rflux<T>(F, a.nu0, dv);
+        else if (stress) F = rflux<T>(F, rmul<T>(T(2), pN0[rowc - PW]), dv);
         if (active) FY[1 * FYS + ly * TX + lx] = F;
       }
       // w at (face j, face k): advecting centered_z(v) (own column), advected WENO_y(w)
@@ -468,11 +490,11 @@ k_tendency(const TendencyArgs<T> a) {
           for (int n = 0; n < 2 * R; ++n) sw[n] = pW0[rowc + (n - R) * PW];
           F = V * weno<T, R>(sw, V);
           const T dwdy = (sw[R] - sw[R - 1]) * rdy;
-          if (scalar) F -= a.nu0 * dwdy;
+          if (scalar) F = rflux<T>(F, a.nu0, dwdy);
           else if (stress) {
-            const T nuf = T(0.25) * (pNm[rowc - PW] + pNm[rowc] + pN0[rowc - PW] + pN0[rowc]);
-            const T S23 = T(0.5) * ((rv[R - 1] - rv[R - 2]) * rdzf_k + dwdy);
-            F -= T(2) * nuf * S23;
+            const T nuf = ravg4<T>(pNm[rowc - PW], pNm[rowc], pN0[rowc - PW], pN0[rowc]);
+            const T S23 = rstrain<T>(rv[R - 1], rv[R - 2], rdzf_k, dwdy);
+            F = rflux<T>(F, rmul<T>(T(2), nuf), S23);
           }
         }
         if (active) FY[2 * FYS + ly * TX + lx] = F;
@@ -486,9 +508,9 @@ k_tendency(const TendencyArgs<T> a) {
         const T V = pV[rowc];
         T F = V * (weno<T, R>(sc, V) + crk[t]);
         const T dc = (sc[R] - sc[R - 1]) * rdy;
-        if (scalar) F -= a.kappa0 * dc;
-        else if (amd) { const T* pK = sK + (3 * t + k % 3) * PLANE; F -= T(0.5) * (pK[rowc - PW] + pK[rowc]) * dc; }
-        else if (stress) F -= T(0.5) * a.inv_Pr * (pN0[rowc - PW] + pN0[rowc]) * dc;
+        if (scalar) F = rflux<T>(F, a.kappa0, dc);
+        else if (amd) { const T* pK = sK + (3 * t + k % 3) * PLANE; F = rflux<T>(F, ravg2<T>(pK[rowc - PW], pK[rowc]), dc); }
+        else if (stress) F = rflux<T>(F, rmul<T>(a.inv_Pr, ravg2<T>(pN0[rowc - PW], pN0[rowc])), dc);
         if (active) FY[(3 + t) * FYS + ly * TX + lx] = F;
       }
     }
@@ -510,11 +532,11 @@ k_tendency(const TendencyArgs<T> a) {
         const T Wv = centered<T, P>(cw);
         T F = Wv * weno_reduced<T, R>(ru, r, Wv);
         const T dudz = (ru[R] - ru[R - 1]) * rdzf_k1;
-        if (scalar) F -= a.nu0 * dudz;
+        if (scalar) F = rflux<T>(F, a.nu0, dudz);
         else if (stress) {
-          const T nuf = T(0.25) * (pN0[rowc - 1] + pN0[rowc] + pN1[rowc - 1] + pN1[rowc]);
-          const T S13 = T(0.5) * (dudz + (pW1[rowc] - pW1[rowc - 1]) * rdx);
-          F -= T(2) * nuf * S13;
+          const T nuf = ravg4<T>(pN0[rowc - 1], pN0[rowc], pN1[rowc - 1], pN1[rowc]);
+          const T S13 = rstrain<T>(pW1[rowc], pW1[rowc - 1], rdx, dudz);
+          F = rflux<T>(F, rmul<T>(T(2), nuf), S13);
         }
         nz_u = F;
       }
@@ -526,11 +548,11 @@ k_tendency(const TendencyArgs<T> a) {
         const T Wv = centered<T, P>(cw);
         T F = Wv * weno_reduced<T, R>(rv, r, Wv);
         const T dvdz = (rv[R] - rv[R - 1]) * rdzf_k1;
-        if (scalar) F -= a.nu0 * dvdz;
+        if (scalar) F = rflux<T>(F, a.nu0, dvdz);
         else if (stress) {
-          const T nuf = T(0.25) * (pN0[rowc - PW] + pN0[rowc] + pN1[rowc - PW] + pN1[rowc]);
-          const T S23 = T(0.5) * (dvdz + (pW1[rowc] - pW1[rowc - PW]) * rdy);
-          F -= T(2) * nuf * S23;
+          const T nuf = ravg4<T>(pN0[rowc - PW], pN0[rowc], pN1[rowc - PW], pN1[rowc]);
+          const T S23 = rstrain<T>(pW1[rowc], pW1[rowc - PW], rdy, dvdz);
+          F = rflux<T>(F, rmul<T>(T(2), nuf), S23);
         }
         nz_v = F;
       }
@@ -540,12 +562,12 @@ k_tendency(const TendencyArgs<T> a) {
         const T Wv = rw[R];
         T F = Wv * weno_reduced<T, R>(rc[t], r, Wv);
         const T dc = (rc[t][R] - rc[t][R - 1]) * rdzf_k1;
-        if (scalar) F -= a.kappa0 * dc;
+        if (scalar) F = rflux<T>(F, a.kappa0, dc);
         else if (amd) {
           const T* pK0 = sK + (3 * t + k % 3) * PLANE;
           const T* pK1 = sK + (3 * t + (k + 1) % 3) * PLANE;
-          F -= T(0.5) * (pK0[rowc] + pK1[rowc]) * dc;
-        } else if (stress) F -= T(0.5) * a.inv_Pr * (pN0[rowc] + pN1[rowc]) * dc;
+          F = rflux<T>(F, ravg2<T>(pK0[rowc], pK1[rowc]), dc);
+        } else if (stress) F = rflux<T>(F, rmul<T>(a.inv_Pr, ravg2<T>(pN0[rowc], pN1[rowc])), dc);
         nz_c[t] = F;
       }
       // w through centre k (w interface k+1; valid faces 0..Nz)
@@ -555,8 +577,8 @@ k_tendency(const TendencyArgs<T> a) {
         const T Wv = centered_reduced<T, R, 0>(rw, pw_);
         T F = Wv * weno_reduced<T, R>(rw, rw_, Wv);
         const T dw = (rw[R] - rw[R - 1]) * rdzc_k;
-        if (scalar) F -= a.nu0 * dw;
-        else if (stress) F -= T(2) * pN0[rowc] * dw;
+        if (scalar) F = rflux<T>(F, a.nu0, dw);
+        else if (stress) F = rflux<T>(F, rmul<T>(T(2), pN0[rowc]), dw);
         nz_w = F;
       }
     }

@@ -25,7 +25,8 @@ OCN_FIELD_P, OCN_FIELD_G, OCN_FIELD_NU_E = 10, 20, 30
 OCN_FIELD_TRACER_REF0, OCN_FIELD_RAW = 40, 0x100
 OCN_OPT_GRAPHS, OCN_OPT_SYNC_CHECK, OCN_OPT_KERNEL_TIMING, OCN_OPT_TENDENCY_VARIANT = 1, 2, 3, 4
 TENDENCY_VARIANTS = 4
-KERNEL_CLASSES = ["closure", "tendency", "div_fftx", "fft_y", "tridiag", "gauge", "ifftx", "correct"]
+KERNEL_CLASSES = ["closure", "tendency", "div_fftx", "fft_y", "tridiag", "gauge", "ifftx", "correct", "column_closure"]
+COLUMN_FEATURES = 32
 MAX_TRACERS = 4
 CLOSURES = {"none": 0, "scalar": 1, "smagorinsky": 2, "amd": 3}
 EOS = {"buoyancy_tracer": 0, "linear_ts": 1}
@@ -42,7 +43,8 @@ EXPORTS = ["ocn_abi_version", "ocn_last_error", "ocn_grid_create", "ocn_grid_des
            "ocn_ensemble_autotune", "ocn_ensemble_launches_per_step", "ocn_mlp_create", "ocn_mlp_destroy",
            "ocn_mlp_arena_bytes", "ocn_mlp_bind_arena", "ocn_mlp_num_params", "ocn_mlp_set_params",
            "ocn_mlp_get_params", "ocn_mlp_forward", "ocn_mlp_gradients", "ocn_mlp_adam", "ocn_mlp_train_step",
-           "ocn_gemm_bf16"]
+           "ocn_gemm_bf16", "ocn_set_column_closure", "ocn_closure_features", "ocn_column_fluxes",
+           "ocn_coarse_grain"]
 OCN_OPT_ENSEMBLE_MODE, OCN_ENSEMBLE_CONCURRENT, OCN_ENSEMBLE_SEQUENTIAL = 5, 0, 1
 
 
@@ -68,6 +70,11 @@ class ModelDesc(C.Structure):
         ("top_flux", C.c_double * (2 + MAX_TRACERS)), ("bottom_flux", C.c_double * (2 + MAX_TRACERS)),
         ("fp64_pivots", C.c_int),
     ]
+
+
+class ColumnClosureDesc(C.Structure):
+    _fields_ = [("mu", C.c_float * COLUMN_FEATURES), ("sigma", C.c_float * COLUMN_FEATURES),
+                ("out_scale", C.c_float * 3), ("N2_background", C.c_double)]
 
 
 _lib = None
@@ -128,6 +135,10 @@ def lib(path: str = LIB_PATH):
     L.ocn_mlp_gradients.argtypes = [vp, vp, vp, vp, C.c_int, vp, dp]
     L.ocn_mlp_adam.argtypes = [vp, vp, C.c_double, C.c_double, C.c_double, C.c_double]
     L.ocn_mlp_train_step.argtypes = [vp, vp, vp, vp, C.c_int, C.c_double, dp]
+    L.ocn_set_column_closure.argtypes = [vp, vp, C.POINTER(ColumnClosureDesc)]
+    L.ocn_closure_features.argtypes = [vp, C.c_double, vp]
+    L.ocn_column_fluxes.argtypes = [vp, C.c_int, vp]
+    L.ocn_coarse_grain.argtypes = [vp, C.c_int, C.c_int, vp, sz]
     L.ocn_gemm_bf16.argtypes = [C.c_int, C.c_int, C.c_int, vp, C.c_int, vp, C.c_int, vp, C.c_int, vp, vp]
     for name in EXPORTS:
         if name not in ("ocn_abi_version", "ocn_last_error", "ocn_grid_destroy", "ocn_model_destroy", "ocn_ensemble_destroy",
@@ -342,6 +353,63 @@ class Model:
         F = a[3 * Nz:]
         return {"b": a[:Nz], "u": a[Nz:2 * Nz], "v": a[2 * Nz:3 * Nz],
                 "Fb": F[:Nz + 1], "Fu": F[Nz + 1:2 * (Nz + 1)], "Fv": F[2 * (Nz + 1):]}
+
+    # ------------------------------------------------------------ learned column closure
+    def set_column_closure(self, mlp, mu=None, sigma=None, out_scale=(1.0, 1.0, 1.0), N2_background=0.0):
+        """Attach a trained network (an MLP of shape 32-128-128-128-16) as the learned column closure;
+        mlp=None removes it (the model's own closure remains)."""
+        if mlp is None:
+            _check(lib().ocn_set_column_closure(self._h, None, None), "ocn_set_column_closure")
+            self._colc = None
+            return
+        d = ColumnClosureDesc()
+        mu = np.zeros(COLUMN_FEATURES) if mu is None else np.asarray(mu, np.float64)
+        sigma = np.ones(COLUMN_FEATURES) if sigma is None else np.asarray(sigma, np.float64)
+        for q in range(COLUMN_FEATURES):
+            d.mu[q] = float(mu[q]); d.sigma[q] = float(sigma[q])
+        for q in range(3):
+            d.out_scale[q] = float(out_scale[q])
+        d.N2_background = float(N2_background)
+        _check(lib().ocn_set_column_closure(self._h, mlp._h, C.byref(d)), "ocn_set_column_closure")
+        self._colc = mlp          # keep the network alive while attached
+
+    def closure_features(self, N2_background: float):
+        """Raw column features of every w-face, a device tensor [(Nz+1)*Ny*Nx][32]."""
+        import torch
+        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+            X = torch.empty(((self.Nz + 1) * self.Ny * self.Nx, COLUMN_FEATURES), dtype=torch.float32,
+                            device=self.device)
+            _check(lib().ocn_closure_features(self._h, float(N2_background), C.c_void_p(X.data_ptr())),
+                   "ocn_closure_features")
+        self.stream.synchronize()
+        return X
+
+    def column_fluxes(self, learned: bool = False):
+        """Face fluxes of b, ubar, vbar [3][Nz+1][Ny][Nx]: the model's closure (default) or the learned one."""
+        import torch
+        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+            F = torch.empty((3, self.Nz + 1, self.Ny, self.Nx), dtype=torch.float32, device=self.device)
+            _check(lib().ocn_column_fluxes(self._h, 1 if learned else 0, C.c_void_p(F.data_ptr())),
+                   "ocn_column_fluxes")
+        self.stream.synchronize()
+        return F
+
+    def coarse_grain(self, cx: int, cy: int) -> dict:
+        """Box filter onto cx x cy columns: coarse u, v, w, b and subfilter fluxes tau [3][Nz+1][cy][cx]
+        (device FP64 tensors)."""
+        import torch
+        Nz = self.Nz
+        n = cx * cy
+        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+            out = torch.empty(n * (7 * Nz + 4), dtype=torch.float64, device=self.device)
+            _check(lib().ocn_coarse_grain(self._h, int(cx), int(cy), C.c_void_p(out.data_ptr()), out.numel()),
+                   "ocn_coarse_grain")
+        self.stream.synchronize()
+        res, o = {}, 0
+        for name, levels in (("u", Nz), ("v", Nz), ("w", Nz + 1), ("b", Nz)):
+            res[name] = out[o:o + levels * n].view(levels, cy, cx); o += levels * n
+        res["tau"] = out[o:].view(3, Nz + 1, cy, cx)
+        return res
 
     def kernel_times(self) -> dict:
         """{kernel class: (launches, summed ms)} recorded while OCN_OPT_KERNEL_TIMING is on."""

@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported(libocn):
 
 def test_abi_version_and_grid_validation(libocn):
     from paper_2502_14148_gb300 import ocn
-    assert libocn.ocn_abi_version() == 1
+    assert libocn.ocn_abi_version() == 2
     zf = np.linspace(-1, 0, 9)
     g = ocn.Grid(16, 12, 8, 1.0, 1.0, zf)          # host-only call
     assert g._h
