@@ -76,28 +76,48 @@ def substep_bytes_per_cell(p: dict) -> int:
     return (4 * n + 9) * w
 
 
+FALLBACK_BF16_TFLOPS = 1900.0
+
+
 def measured_peaks() -> dict:
     try:
         with open(MEASURED_PEAKS) as f:
             d = json.load(f)
-        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured", "sm_max_mhz": float(d.get("sm_max_mhz", SM_MAX_MHZ))}
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured", "sm_max_mhz": float(d.get("sm_max_mhz", SM_MAX_MHZ)),
+                "bf16_tflops": float(d.get("bf16_tflops", FALLBACK_BF16_TFLOPS)),
+                "bf16_tflops_sustained": float(d.get("bf16_tflops_sustained", FALLBACK_BF16_TFLOPS))}
     except Exception:
-        return {"hbm_gbs": FALLBACK_HBM_GBS, "source": "fallback", "sm_max_mhz": SM_MAX_MHZ}
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "source": "fallback", "sm_max_mhz": SM_MAX_MHZ,
+                "bf16_tflops": FALLBACK_BF16_TFLOPS, "bf16_tflops_sustained": FALLBACK_BF16_TFLOPS}
+
+
+# the closure network: 32 -> 128 -> 128 -> 128 -> 16, two flops per multiply-add
+MLP_FLOPS_PER_SAMPLE = 2 * (32 * 128 + 128 * 128 + 128 * 128 + 128 * 16)
+
+
+PROFILED_SOURCES = {"tendency": ["tendency_kernel.cuh", "tendency_f32_r5.cu", "tendency_f32_r3.cu"],
+                    "mlp_closure": ["mlp.cu", "column.cuh"]}
+
+
+def source_hash(kernel: str) -> str:
+    """sha256 (first 16 hex digits) of the sources a profiled kernel is compiled from."""
+    h = hashlib.sha256()
+    for name in PROFILED_SOURCES[kernel]:
+        h.update(open(os.path.join(ROOT, "paper_2502_14148_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def profiled_traffic(kernel: str, workload: str):
     """DRAM bytes per launch from the committed ncu summary, valid only while the kernel
-    source hash recorded there matches the current source (else None)."""
+    source hash recorded there matches the current sources (else None)."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
-    src = os.path.join(ROOT, "paper_2502_14148_gb300", "csrc", "tendency.cu" if kernel == "tendency" else "poisson.cu")
     try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         fields = {}
         for line in open(path):
             if ":" in line:
                 k, v = line.split(":", 1)
                 fields[k.strip()] = v.strip()
-        if fields.get("source_sha256_16") != h:
+        if fields.get("source_sha256_16") != source_hash(kernel):
             return None
         return float(fields["dram_bytes_per_full_launch"])
     except Exception:
@@ -405,14 +425,170 @@ def run_ensemble(args, world, rank, local):
     return 0
 
 
+def run_closure(args, world, rank, local):
+    """Coarse runs with the learned column closure: args.members coarse CBL instances of 16 x 16
+    columns (each on its forcing's vertical grid), AMD + the trained closure against plain AMD,
+    both one graph per ensemble step.  The closure is first trained by the library (a 32-forcing,
+    3 h experiment whose held-out errors are reported); the fused tensor-core closure kernel is
+    then timed alone on the same number of faces for its roofline."""
+    import torch
+    from paper_2502_14148_gb300 import build, closure, inputs, ocn
+    if rank == 0 or world == 1:
+        build.build()
+    barrier(world)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    t0 = time.time()
+    res = closure.experiment(n_members=32, n_train=24, t_end=3 * 3600.0, dt=10.0, every=180, train_steps=2000,
+                             log=lambda *a: None)
+    t_exp = time.time() - t0
+    net, mu, sigma, scale, ysc = res["nets"]["mlp"]
+    cl = closure.closure_for(net, mu, sigma, scale, ysc)
+    fine = inputs.ensemble_configs(n=args.members, seed=inputs.SEED + 7, dt=10.0)
+    ps = [closure.coarse_config(p) for p in fine]
+    cells = sum(p["Nx"] * p["Ny"] * p["Nz"] for p in ps)
+    faces = sum(p["Nx"] * p["Ny"] * (p["Nz"] + 1) for p in ps)
+    dt = 10.0
+    timings = {}
+    for mode in ("plain", "learned"):
+        E = ocn.Ensemble(ps, device=dev)
+        for i, p in enumerate(ps):
+            E.members[i].set(**inputs.initial_state(p, seed=inputs.SEED + i + 1000 * rank))
+            if mode == "learned":
+                E.members[i].set_column_closure(*cl(p), p["N2"])
+        E.time_step(dt, args.warmup)
+        E.synchronize()
+        ck = ClockSampler(local) if mode == "learned" else None
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(E.stream)
+        E.time_step(dt, args.steps)
+        e1.record(E.stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        d = E.members[0].diagnostics(dt)
+        timings[mode] = (max_over_ranks(e0.elapsed_time(e1), world), ck.stop() if ck else None, E.launches_per_step(), d)
+        del E
+    # the fused closure kernel alone, on one model with as many faces (same kernel, one launch)
+    side = 256
+    nz = max(8, int(round(faces / (side * side))) - 1)
+    q = closure.coarse_config(dict(fine[0], Nz=nz, z_faces=inputs.tanh_faces(nz, fine[0]["Lz"])), side, side)
+    big = ocn.Model(q, device=dev)
+    big.set(**inputs.initial_state(q, seed=inputs.SEED))
+    big.set_column_closure(*cl(q), q["N2"])
+    nsamp = side * side * (nz + 1)
+    F = torch.empty((3, nz + 1, side, side), dtype=torch.float32, device=dev)
+    reps = 20
+    for _ in range(3):
+        big.column_fluxes(learned=True)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(big.stream):
+        e0.record(big.stream)
+        for _ in range(reps):
+            ocn.lib().ocn_column_fluxes(big._h, 1, ocn.C.c_void_p(F.data_ptr()))
+        e1.record(big.stream)
+    torch.cuda.synchronize(dev)
+    t_kernel = e0.elapsed_time(e1) / reps * 1e-3
+    if rank != 0:
+        return 0
+    peaks = measured_peaks()
+    ms_p, _, _, _ = timings["plain"]
+    ms_l, clocks, launches, d = timings["learned"]
+    val = cells * 3 * args.steps * world / (ms_l * 1e-3)
+    achieved = MLP_FLOPS_PER_SAMPLE * nsamp / t_kernel / 1e12
+    s = res["summary"]
+    line = {"metric": "cell-RK3-substeps/sec", "value": val, "unit": "cell-substeps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_l / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 state, bf16 network", "data": "synthetic",
+            "config": {"workload": f"{len(ps)} coarse CBL instances of 16x16 columns ({cells/1e6:.2f} M cells, "
+                                   f"{faces/1e6:.2f} M closure faces per substage; Nz in {{64,80,96}}, WENO5, "
+                                   f"AMD + learned column closure, FP32, dt={dt} s)",
+                       "mode": "one CUDA graph per ensemble step, members on concurrent branches"},
+            "gpu_launches": launches * args.steps,
+            "plain_amd": {"value": cells * 3 * args.steps * world / (ms_p * 1e-3), "ms_per_step": ms_p / args.steps},
+            "closure_overhead": ms_l / ms_p,
+            "roofline": {"bound": "tensor", "kernel": "k_mlp_closure", "achieved": achieved,
+                         "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": achieved / peaks["bf16_tflops"],
+                         "traffic": None,
+                         "algorithmic": f"{MLP_FLOPS_PER_SAMPLE} flops per face x {nsamp} faces per launch",
+                         "peak_source": f"{peaks['source']} bf16 burst", "ms_per_launch": t_kernel * 1e3},
+            "flux_error": {"held_out_forcings": s["n_members"] - s["n_train"],
+                           "b_profile": {"plain_amd": s["amd_b"], "learned": s["mlp_b"]},
+                           "buoyancy_flux": {"plain_amd": s["amd_Fb"], "learned": s["mlp_Fb"]},
+                           "training_samples": s["mlp_samples"], "experiment_seconds": t_exp,
+                           "definition": "normalised RMS vs coarse-grained fine LES over 30-min snapshots to 3 h"},
+            "clocks": clocks,
+            "checks": {"member0_max_div": d["max_div"], "member0_nonfinite": d["nonfinite"]}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_closure_kernel(args, world, rank, local):
+    """The fused tensor-core closure kernel alone (features -> 4-layer BF16 network -> fluxes) on
+    one FP32 CBL model of --size (default 256x256x80 = 5.3 M faces, the face count of 256 coarse
+    16 x 16 instances), with the seeded initial network: its cost does not depend on training."""
+    import torch
+    from paper_2502_14148_gb300 import build, closure, inputs, ocn
+    if rank == 0 or world == 1:
+        build.build()
+    barrier(world)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    nx, ny, nz = (int(x) for x in (args.size or "256x256x80").split("x"))
+    base = inputs.ensemble_configs(n=1, dt=10.0)[0]
+    q = closure.coarse_config(dict(base, Nz=nz, z_faces=inputs.tanh_faces(nz, base["Lz"])), nx, ny)
+    m = ocn.Model(q, device=dev)
+    m.set(**inputs.initial_state(q, seed=inputs.SEED + rank))
+    net = ocn.MLP(inputs.MLP_SIZES, max_batch=1024, device=dev)
+    net.set_params(inputs.mlp_init())
+    X = m.closure_features(q["N2"])
+    mu, sigma = closure.normalisation(X)
+    m.set_column_closure(net, mu, sigma, (q["top_flux"]["b"], 0.0, 0.0), q["N2"])
+    nsamp = nx * ny * (nz + 1)
+    F = torch.empty((3, nz + 1, ny, nx), dtype=torch.float32, device=dev)
+    for _ in range(max(args.warmup, 1)):
+        ocn._check(ocn.lib().ocn_column_fluxes(m._h, 1, ocn.C.c_void_p(F.data_ptr())), "ocn_column_fluxes")
+    torch.cuda.synchronize(dev)
+    ck = ClockSampler(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(m.stream)
+    for _ in range(args.steps):
+        ocn._check(ocn.lib().ocn_column_fluxes(m._h, 1, ocn.C.c_void_p(F.data_ptr())), "ocn_column_fluxes")
+    e1.record(m.stream)
+    torch.cuda.synchronize(dev)
+    clocks = ck.stop()
+    t = max_over_ranks(e0.elapsed_time(e1) / args.steps, world) * 1e-3
+    if rank != 0:
+        return 0
+    peaks = measured_peaks()
+    achieved = MLP_FLOPS_PER_SAMPLE * nsamp / t / 1e12
+    line = {"metric": "closure faces/sec", "value": nsamp * world / t, "unit": "faces/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)", "data": "synthetic",
+            "config": {"workload": f"learned column closure kernel, {nx}x{ny}x{nz} FP32 CBL state, {nsamp} faces",
+                       "launches_per_step": 2},
+            "roofline": {"bound": "tensor", "kernel": "k_mlp_closure", "achieved": achieved, "peak": peaks["bf16_tflops"],
+                         "unit": "TFLOP/s", "frac": achieved / peaks["bf16_tflops"],
+                         "traffic": profiled_traffic("mlp_closure", f"{nx}x{ny}x{nz}"),
+                         "algorithmic": f"{MLP_FLOPS_PER_SAMPLE} flops per face x {nsamp} faces per launch",
+                         "peak_source": f"{peaks['source']} bf16 burst"},
+            "gpu_launches": 2 * args.steps, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="les_512", help="les_512 (default), cbl_256, taylor_green_32 or ensemble")
-    ap.add_argument("--members", type=int, default=64, help="ensemble members (--workload ensemble)")
+    ap.add_argument("--workload", default="les_512", help="les_512 (default), cbl_256, taylor_green_32, ensemble, closure or closure_kernel")
+    ap.add_argument("--members", type=int, default=None,
+                    help="instances: ensemble members (--workload ensemble, default 64) or coarse instances "
+                         "(--workload closure, default 256)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--size", default=None, help="NxxNyxNz: the workload's physics and spacing on another grid (profiling)")
     args = ap.parse_args()
@@ -421,7 +597,13 @@ def main():
         if args.impl == "reference":
             return run_reference(args, world, rank)
         if args.workload == "ensemble":
+            args.members = args.members or 64
             return run_ensemble(args, world, rank, local)
+        if args.workload == "closure":
+            args.members = args.members or 256
+            return run_closure(args, world, rank, local)
+        if args.workload == "closure_kernel":
+            return run_closure_kernel(args, world, rank, local)
         return run_ours(args, world, rank, local)
     finally:
         if world > 1:

@@ -44,5 +44,4 @@ __device__ __forceinline__ void column_features_uv(const ColumnArgs& a, int i, i
     x[10 + m + 2] = col_grad(a, 2, i, j, k + m);
   }
 }
-
 }  // namespace ocn

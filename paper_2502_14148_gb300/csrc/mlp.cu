@@ -112,9 +112,28 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// GELU evaluated in the tanh form of Hendrycks & Gimpel (2016),
+//   gelu(z) ~ z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))),
+// with the hardware tanh approximation.  Its largest deviation from the erf definition
+// z Phi(z) is 4.7e-4 (at z = 2.7, where gelu = 2.69), well inside the BF16 rounding that the
+// activation receives next; gelu_prime_f is the derivative of the same form.
+__device__ __forceinline__ float tanh_fast(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+constexpr float kGeluK = 0.7978845608028654f;    // sqrt(2/pi)
+constexpr float kGeluC = 0.044715f;
+constexpr float kGeluKC = kGeluK * kGeluC;
+__device__ __forceinline__ float gelu_f(float z) {
+  const float t = tanh_fast(z * fmaf(kGeluKC, z * z, kGeluK));
+  const float hz = 0.5f * z;
+  return fmaf(hz, t, hz);
+}
 __device__ __forceinline__ float gelu_prime_f(float z) {
-  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+  const float z2 = z * z;
+  const float t = tanh_fast(kGeluK * fmaf(kGeluC * z, z2, z));
+  return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * kGeluK * fmaf(3.0f * kGeluC, z2, 1.0f);
 }
 
 // Copy a rows x kChunkK BF16 tile (row r, columns k0..k0+63 of a [rows][ld] array) into the
@@ -253,11 +272,13 @@ constexpr int kSW1 = 0;                             // W1 [128][32]
 constexpr int kSW2 = kSW1 + kCH * kCF * 2;          // W2 [128][128]
 constexpr int kSW3 = kSW2 + kCH * kCH * 2;          // W3 [128][128]
 constexpr int kSW4 = kSW3 + kCH * kCH * 2;          // W4 [16][128]
-constexpr int kSX = kSW4 + kCO * kCH * 2;           // features [128][32]
-constexpr int kSH = kSX + 128 * kCF * 2;            // activations [128][128]
+constexpr int kSH = kSW4 + kCO * kCH * 2;           // activations [128][128]
+constexpr int kSX = kSH;                            // features [128][32]: only live until layer 1's MMA
+                                                    // has read them, before its epilogue writes kSH
 constexpr int kSB = kSH + 128 * kCH * 2;            // biases (3*128 + 16 floats)
 constexpr int kClosureSmem = kSB + (3 * kCH + kCO) * 4;
-static_assert(kClosureSmem * 2 > 228 * 1024, "one CTA per SM keeps TMEM allocation non-blocking");
+// two CTAs per SM (2 x 128 TMEM columns); a third cannot fit, so allocation never blocks
+static_assert(kClosureSmem * 2 + 2048 <= 228 * 1024 && kClosureSmem * 3 > 228 * 1024, "two CTAs per SM");
 
 // byte offset of element (r, c) of a [rows][K] K-major BF16 matrix in the no-swizzle core-matrix layout
 __device__ __forceinline__ uint32_t cm_off(int r, int c, int K) {
@@ -285,7 +306,9 @@ __device__ __forceinline__ void closure_layer_mma(uint32_t tmem, uint32_t a_addr
 
 }  // namespace
 
-__global__ void __launch_bounds__(256, 1) k_mlp_closure(const MlpClosureArgs a) {
+constexpr int kClosureThreads = 256;   // two warps per TMEM lane quadrant, 64 columns each
+
+__global__ void __launch_bounds__(kClosureThreads, 2) k_mlp_closure(const MlpClosureArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint64_t bar;
   __shared__ uint32_t tmem_base;
@@ -310,32 +333,46 @@ __global__ void __launch_bounds__(256, 1) k_mlp_closure(const MlpClosureArgs a) 
   tc_fence_after();
   const uint32_t tmem = tmem_base;
   const uint32_t s0 = smem_u32(smem);
-  const int quad = warp & 3, half = warp >> 2;
+  const int quad = warp & 3, half = warp >> 2;      // TMEM lanes 32*quad.., columns 64*half..
   const int row = quad * 32 + lane;                 // the TMEM lane / sample row this thread reads back
   uint32_t phase = 0;
   bool ok = true;
   for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-    // ---- features of sample row (tid & 127): half 0 the buoyancy part, half 1 the velocity part
+    // ---- features of sample row (tid & 127), half of them per thread: part 0 the db/dz stencil
+    //      (features 0-4) and the non-local features 15-19 plus the zero padding, part 1 the
+    //      dubar/dz and dvbar/dz stencils (features 5-14)
     {
-      const int r = tid & 127;
+      const int r = tid & 127, fp = tid >> 7;
       const size_t sidx = (size_t)t * 128 + r;
-      float x[kCF];
+      const bool valid = sidx < nsamp;
+      float g[10];
 #pragma unroll
-      for (int q = 0; q < kCF; ++q) x[q] = 0.0f;
-      if (sidx < nsamp) {
-        const int k = (int)(sidx / plane), cc = (int)(sidx % plane), i = cc % c.Nx, j = cc / c.Nx;
-        if (tid < 128) column_features_b(c, i, j, k, x);
-        else column_features_uv(c, i, j, k, x);
-      }
-      const bool part_b = tid < 128;
+      for (int m = 0; m < 10; ++m) g[m] = 0.0f;
+      if (valid) {
+        const uint32_t s32 = (uint32_t)sidx, p32 = (uint32_t)plane;      // < 2^31 (checked at launch)
+        const int k = (int)(s32 / p32), cc = (int)(s32 - (uint32_t)k * p32);
+        const int j = cc / c.Nx, i = cc - j * c.Nx;
+        if (fp == 0) {
 #pragma unroll
-      for (int q = 0; q < kCF; ++q) {
-        const bool mine = part_b ? (q < 5 || q >= 15) : (q >= 5 && q < 15);
-        if (mine) {
-          const float xn = (sidx < nsamp && q < 20) ? (x[q] - a.mu[q]) * a.inv_sigma[q] : 0.0f;
-          *reinterpret_cast<__nv_bfloat16*>(smem + kSX + cm_off(r, q, kCF)) = __float2bfloat16_rn(xn);
+          for (int m = 0; m < 5; ++m) g[m] = col_grad(c, 0, i, j, k + m - 2);
+          g[5] = c.Jb; g[6] = c.f; g[7] = c.N2bg; g[8] = c.depth[k]; g[9] = c.h[(size_t)j * c.Nx + i];
+        } else {
+#pragma unroll
+          for (int m = 0; m < 5; ++m) {
+            g[m] = col_grad(c, 1, i, j, k + m - 2);
+            g[5 + m] = col_grad(c, 2, i, j, k + m - 2);
+          }
         }
       }
+#pragma unroll
+      for (int m = 0; m < 10; ++m) {
+        const int q = (fp == 0) ? (m < 5 ? m : 10 + m) : 5 + m;
+        const float xn = valid ? (g[m] - a.mu[q]) * a.inv_sigma[q] : 0.0f;
+        *reinterpret_cast<__nv_bfloat16*>(smem + kSX + cm_off(r, q, kCF)) = __float2bfloat16_rn(xn);
+      }
+      if (fp == 0)
+        for (int q = 20; q < kCF; ++q)
+          *reinterpret_cast<__nv_bfloat16*>(smem + kSX + cm_off(r, q, kCF)) = __float2bfloat16_rn(0.0f);
     }
     // ---- four layers
     for (int l = 0; l < 4 && ok; ++l) {
@@ -355,25 +392,27 @@ __global__ void __launch_bounds__(256, 1) k_mlp_closure(const MlpClosureArgs a) 
       if (!ok) break;
       if (l < 3) {
         const float* bl = sbias + l * kCH;
-        for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 16) {
+#pragma unroll
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+          const int cb = half * 64 + c0;
           float v[16];
-          tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
+          tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)cb, v);
           uint32_t pk[8];
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
-            const __nv_bfloat16 lo = __float2bfloat16_rn(gelu_f(v[2 * q] + bl[c0 + 2 * q]));
-            const __nv_bfloat16 hi = __float2bfloat16_rn(gelu_f(v[2 * q + 1] + bl[c0 + 2 * q + 1]));
-            pk[q] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(gelu_f(v[2 * q] + bl[cb + 2 * q]),
+                                                            gelu_f(v[2 * q + 1] + bl[cb + 2 * q + 1]));
+            pk[q] = *reinterpret_cast<const uint32_t*>(&h2);
           }
-          *reinterpret_cast<uint4*>(smem + kSH + cm_off(row, c0, kCH)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-          *reinterpret_cast<uint4*>(smem + kSH + cm_off(row, c0 + 8, kCH)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+          *reinterpret_cast<uint4*>(smem + kSH + cm_off(row, cb, kCH)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          *reinterpret_cast<uint4*>(smem + kSH + cm_off(row, cb + 8, kCH)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
         }
       } else if (half == 0) {
         float v[16];
         tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16), v);
         const size_t sidx = (size_t)t * 128 + row;
         if (sidx < nsamp) {
-          const int k = (int)(sidx / plane);
+          const int k = (int)((uint32_t)sidx / (uint32_t)plane);
           const bool wall = (k == 0 || k == c.Nz);
           const float* b4 = sbias + 3 * kCH;
 #pragma unroll
@@ -402,9 +441,10 @@ cudaError_t launch_mlp_closure(const MlpClosureArgs& a, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(k_mlp_closure, cudaFuncAttributeMaxDynamicSharedMemorySize, kClosureSmem);
   if (e != cudaSuccess) return e;
   const size_t nsamp = (size_t)a.col.Nx * a.col.Ny * (a.col.Nz + 1);
+  if (nsamp + 128 >= ((size_t)1 << 31)) return cudaErrorInvalidValue;    // 32-bit face indices
   const long long ntiles = (long long)((nsamp + 127) / 128);
-  const int grid = (int)(ntiles < nsm ? ntiles : nsm);
-  k_mlp_closure<<<grid, 256, kClosureSmem, s>>>(a);
+  const int grid = (int)(ntiles < 2 * nsm ? ntiles : 2 * nsm);
+  k_mlp_closure<<<grid, kClosureThreads, kClosureSmem, s>>>(a);
   return cudaGetLastError();
 }
 
