@@ -46,6 +46,8 @@ struct orc_model {
   double *nue, *kape[ORC_MAX_TRACERS];              /* diffusivities at centres */
   double *work;                                     /* Nz*Ny*Nx scratch */
   int have_diff;
+  double *nuz, *kapz;                               /* vertical diffusivity profiles at faces (or NULL) */
+  int ab_started;                                   /* QAB2: a previous tendency exists */
   orc_face_flux_fn flux_fn;                         /* column closure hook (or NULL) */
   void* flux_ctx;
   double* Fcol;                                     /* [3][Nz+1][Ny][Nx] face fluxes of b, ubar, vbar */
@@ -438,6 +440,8 @@ double orc_tendency_at(orc_model* M, int field, int i, int j, int k) {
 }
 
 static void add_face_flux_divergence(orc_model* M, double* Gu, double* Gv, double* Gb);
+static void add_vertical_diffusion(orc_model* M, double* Gu, double* Gv, double* Gw, double** Gc);
+static void implicit_vertical_step(orc_model* M, double dtau);
 
 static void all_tendencies(orc_model* M, double* Gu, double* Gv, double* Gw, double** Gc) {
   compute_diffusivities(M);
@@ -455,6 +459,7 @@ static void all_tendencies(orc_model* M, double* Gu, double* Gv, double* Gw, dou
   size_t plane = (size_t)Nx * Ny;
   memset(Gw + (size_t)Nz * plane, 0, plane * sizeof(double));
   if (M->flux_fn) add_face_flux_divergence(M, Gu, Gv, Gc[0]);
+  if (!M->p.vertical_implicit && (M->nuz || M->kapz)) add_vertical_diffusion(M, Gu, Gv, Gw, Gc);
 }
 
 void orc_tendencies(orc_model* M, double* Gu, double* Gv, double* Gw, double* Gc) {
@@ -671,24 +676,37 @@ void orc_project(orc_model* M, double dts) {
 static const double RK_GAMMA[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
 static const double RK_ZETA[3] = {0.0, 17.0 / 60.0, 5.0 / 12.0};
 
-void orc_time_step(orc_model* M, double dt, int nsteps) {
+/* One stage: c <- c + dt (g H - z G), G <- H, the semi-implicit vertical diffusion over dtau, the projection
+ * over dtau (Eq. rk3 or Eq. qab2 with Eqs. tracer-time-discretization, predictor-velocity). */
+static void stage(orc_model* M, double dt, double g, double z, double dtau) {
   size_t plane = (size_t)M->Nx * M->Ny, N = plane * M->Nz;
+  all_tendencies(M, M->Hu, M->Hv, M->Hw, M->Hc);
+#pragma omp parallel for schedule(static)
+  for (size_t n = 0; n < N; ++n) {
+    M->u[n] += dt * (g * M->Hu[n] - z * M->Gu[n]);
+    M->v[n] += dt * (g * M->Hv[n] - z * M->Gv[n]);
+    if (n >= plane) M->w[n] += dt * (g * M->Hw[n] - z * M->Gw[n]);
+    for (int t = 0; t < M->nt; ++t) M->c[t][n] += dt * (g * M->Hc[t][n] - z * M->Gc[t][n]);
+    M->Gu[n] = M->Hu[n]; M->Gv[n] = M->Hv[n]; M->Gw[n] = M->Hw[n];
+    for (int t = 0; t < M->nt; ++t) M->Gc[t][n] = M->Hc[t][n];
+  }
+  M->have_diff = 0;
+  if (M->p.vertical_implicit && (M->nuz || M->kapz)) implicit_vertical_step(M, dtau);
+  orc_project(M, dtau);
+}
+
+void orc_time_step(orc_model* M, double dt, int nsteps) {
   for (int step = 0; step < nsteps; ++step) {
+    if (M->p.timestepper == ORC_QAB2) {
+      /* Eq. qab2: (3/2 + chi) G^m - (1/2 + chi) G^{m-1}; the first step is forward Euler (chi = -1/2) */
+      const double chi = M->ab_started ? M->p.chi : -0.5;
+      stage(M, dt, 1.5 + chi, 0.5 + chi, dt);
+      M->ab_started = 1;
+      continue;
+    }
     for (int st = 0; st < 3; ++st) {
       double g = RK_GAMMA[st], z = RK_ZETA[st];
-      all_tendencies(M, M->Hu, M->Hv, M->Hw, M->Hc);
-      /* predictor / tracer update (Eq. rk3, Eq. predictor-velocity without implicit part) */
-#pragma omp parallel for schedule(static)
-      for (size_t n = 0; n < N; ++n) {
-        M->u[n] += dt * (g * M->Hu[n] - z * M->Gu[n]);
-        M->v[n] += dt * (g * M->Hv[n] - z * M->Gv[n]);
-        if (n >= plane) M->w[n] += dt * (g * M->Hw[n] - z * M->Gw[n]);
-        for (int t = 0; t < M->nt; ++t) M->c[t][n] += dt * (g * M->Hc[t][n] - z * M->Gc[t][n]);
-        M->Gu[n] = M->Hu[n]; M->Gv[n] = M->Hv[n]; M->Gw[n] = M->Hw[n];
-        for (int t = 0; t < M->nt; ++t) M->Gc[t][n] = M->Hc[t][n];
-      }
-      M->have_diff = 0;
-      orc_project(M, (g - z) * dt);
+      stage(M, dt, g, z, (g - z) * dt);
     }
   }
 }
@@ -764,6 +782,7 @@ static double* field_ptr(const orc_model* M, int field) {
 void orc_set(orc_model* M, int field, const double* src) {
   double* d = field_ptr(M, field);
   if (!d) return;
+  M->ab_started = 0;
   memcpy(d, src, sizeof(double) * orc_field_len(M, field));
   if (field == ORC_W) {   /* impenetrable walls */
     size_t plane = (size_t)M->Nx * M->Ny;
@@ -780,6 +799,7 @@ void orc_get(const orc_model* M, int field, double* dst) {
 
 orc_model* orc_create(const orc_params* p) {
   if (p->Nx < 1 || p->Ny < 1 || p->Nz < 1) return NULL;
+  if ((p->nu_z || p->kappa_z) && p->Nz > 512) return NULL;       /* column buffers of the vertical solver */
   if (p->weno_order < 1 || p->weno_order > 2 * ORC_RMAX - 1 || (p->weno_order % 2) == 0) return NULL;
   if (p->n_tracers < 0 || p->n_tracers > ORC_MAX_TRACERS) return NULL;
   if (p->eos == ORC_EOS_LINEAR_TS && p->n_tracers < 2) return NULL;
@@ -812,6 +832,9 @@ orc_model* orc_create(const orc_params* p) {
     M->Hc[n] = (double*)calloc(N, sizeof(double));
     M->kape[n] = (double*)calloc(N, sizeof(double));
   }
+  if (p->nu_z) { M->nuz = (double*)malloc(sizeof(double) * (Nz + 1)); memcpy(M->nuz, p->nu_z, sizeof(double) * (Nz + 1)); }
+  if (p->kappa_z) { M->kapz = (double*)malloc(sizeof(double) * (Nz + 1)); memcpy(M->kapz, p->kappa_z, sizeof(double) * (Nz + 1)); }
+  M->p.nu_z = M->nuz; M->p.kappa_z = M->kapz;
 #ifdef _OPENMP
   if (p->nthreads > 0) omp_set_num_threads(p->nthreads);
 #endif
@@ -822,7 +845,7 @@ void orc_destroy(orc_model* M) {
   if (!M) return;
   free(M->zf); free(M->zc); free(M->dzc); free(M->dzf);
   free(M->u); free(M->v); free(M->w); free(M->Gu); free(M->Gv); free(M->Gw);
-  free(M->Hu); free(M->Hv); free(M->Hw); free(M->pr); free(M->work); free(M->nue); free(M->Fcol);
+  free(M->Hu); free(M->Hv); free(M->Hw); free(M->pr); free(M->work); free(M->nue); free(M->Fcol); free(M->nuz); free(M->kapz);
   for (int n = 0; n < M->nt; ++n) { free(M->c[n]); free(M->Gc[n]); free(M->Hc[n]); free(M->kape[n]); }
   free(M);
 }
@@ -992,4 +1015,116 @@ static void add_face_flux_divergence(orc_model* M, double* Gu, double* Gv, doubl
         double fv0 = 0.5 * (A3(M, Fv, i, j - 1, k) + A3(M, Fv, i, j, k));
         Gv[id] -= (fv1 - fv0) * r;
       }
+}
+
+/* ================================================================== */
+/* Vertical diffusion with a z-profile of diffusivity (explicit term   */
+/* or the semi-implicit step), Eqs. tracer-with-tendency,               */
+/* tracer-time-discretization, predictor-velocity.                      */
+void orc_vertical_diffusion(const orc_model* M, int stag, const double* kf, const double* q, double* out) {
+  int Nz = M->Nz;
+  if (stag == 0) {
+    for (int k = 0; k < Nz; ++k) {
+      double Fb = (k == 0) ? 0.0 : -kf[k] * (q[k] - q[k - 1]) / M->dzf[k];
+      double Ft = (k == Nz - 1) ? 0.0 : -kf[k + 1] * (q[k + 1] - q[k]) / M->dzf[k + 1];
+      out[k] = -(Ft - Fb) / M->dzc[k];
+    }
+  } else {
+    out[0] = 0.0; out[Nz] = 0.0;
+    for (int k = 1; k < Nz; ++k) {
+      double kb = 0.5 * (kf[k - 1] + kf[k]), kt = 0.5 * (kf[k] + kf[k + 1]);
+      double Fb = -kb * (q[k] - q[k - 1]) / M->dzc[k - 1];
+      double Ft = -kt * (q[k + 1] - q[k]) / M->dzc[k];
+      out[k] = -(Ft - Fb) / M->dzf[k];
+    }
+  }
+}
+
+/* (I - dtau D) q = rhs by the Thomas algorithm; for face-staggered q the walls stay 0. */
+void orc_vertical_implicit_solve(const orc_model* M, int stag, const double* kf, double dtau, const double* rhs, double* q) {
+  int Nz = M->Nz;
+  int n0 = (stag == 0) ? 0 : 1, n1 = (stag == 0) ? Nz - 1 : Nz - 1;   /* unknowns n0..n1 */
+  int n = n1 - n0 + 1;
+  double* a = (double*)calloc(n, sizeof(double));
+  double* b = (double*)calloc(n, sizeof(double));
+  double* c = (double*)calloc(n, sizeof(double));
+  double* d = (double*)calloc(n, sizeof(double));
+  for (int r = 0; r < n; ++r) {
+    int k = n0 + r;
+    double lo = 0.0, hi = 0.0, h;
+    if (stag == 0) {
+      h = M->dzc[k];
+      if (k > 0) lo = kf[k] / M->dzf[k];
+      if (k < Nz - 1) hi = kf[k + 1] / M->dzf[k + 1];
+    } else {
+      h = M->dzf[k];
+      lo = 0.5 * (kf[k - 1] + kf[k]) / M->dzc[k - 1];
+      hi = 0.5 * (kf[k] + kf[k + 1]) / M->dzc[k];
+    }
+    /* row: -dtau lo/h q_{k-1} + (1 + dtau (lo + hi)/h) q_k - dtau hi/h q_{k+1} = rhs_k */
+    a[r] = (r > 0) ? -dtau * lo / h : 0.0;
+    c[r] = (r < n - 1) ? -dtau * hi / h : 0.0;
+    b[r] = 1.0 + dtau * (lo + hi) / h;
+    d[r] = rhs[k];
+  }
+  for (int r = 1; r < n; ++r) {
+    double w = a[r] / b[r - 1];
+    b[r] -= w * c[r - 1];
+    d[r] -= w * d[r - 1];
+  }
+  double* x = (double*)calloc(n, sizeof(double));
+  x[n - 1] = d[n - 1] / b[n - 1];
+  for (int r = n - 2; r >= 0; --r) x[r] = (d[r] - c[r] * x[r + 1]) / b[r];
+  if (stag == 1) { q[0] = 0.0; q[Nz] = 0.0; }
+  for (int r = 0; r < n; ++r) q[n0 + r] = x[r];
+  free(a); free(b); free(c); free(d); free(x);
+}
+
+/* Gather a column (stride plane), apply f, scatter back. */
+static void column_apply_explicit(const orc_model* M, int stag, const double* kf, double* f, double* G) {
+  int Nx = M->Nx, Ny = M->Ny, Nz = M->Nz, L = Nz + stag;
+  size_t plane = (size_t)Nx * Ny;
+#pragma omp parallel for collapse(2)
+  for (int j = 0; j < Ny; ++j)
+    for (int i = 0; i < Nx; ++i) {
+      double q[512 + 2], o[512 + 2];
+      size_t c0 = (size_t)j * Nx + i;
+      for (int k = 0; k < L; ++k) q[k] = f[c0 + k * plane];
+      orc_vertical_diffusion(M, stag, kf, q, o);
+      for (int k = 0; k < L; ++k) G[c0 + k * plane] += o[k];
+    }
+}
+
+static void add_vertical_diffusion(orc_model* M, double* Gu, double* Gv, double* Gw, double** Gc) {
+  if (M->nuz) {
+    column_apply_explicit(M, 0, M->nuz, M->u, Gu);
+    column_apply_explicit(M, 0, M->nuz, M->v, Gv);
+    column_apply_explicit(M, 1, M->nuz, M->w, Gw);
+  }
+  if (M->kapz)
+    for (int t = 0; t < M->nt; ++t) column_apply_explicit(M, 0, M->kapz, M->c[t], Gc[t]);
+}
+
+static void column_solve(const orc_model* M, int stag, const double* kf, double dtau, double* f) {
+  int Nx = M->Nx, Ny = M->Ny, Nz = M->Nz, L = Nz + stag;
+  size_t plane = (size_t)Nx * Ny;
+#pragma omp parallel for collapse(2)
+  for (int j = 0; j < Ny; ++j)
+    for (int i = 0; i < Nx; ++i) {
+      double r[512 + 2], q[512 + 2];
+      size_t c0 = (size_t)j * Nx + i;
+      for (int k = 0; k < L; ++k) r[k] = f[c0 + k * plane];
+      orc_vertical_implicit_solve(M, stag, kf, dtau, r, q);
+      for (int k = 0; k < L; ++k) f[c0 + k * plane] = q[k];
+    }
+}
+
+static void implicit_vertical_step(orc_model* M, double dtau) {
+  if (M->nuz) {
+    column_solve(M, 0, M->nuz, dtau, M->u);
+    column_solve(M, 0, M->nuz, dtau, M->v);
+    column_solve(M, 1, M->nuz, dtau, M->w);
+  }
+  if (M->kapz)
+    for (int t = 0; t < M->nt; ++t) column_solve(M, 0, M->kapz, dtau, M->c[t]);
 }

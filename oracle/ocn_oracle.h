@@ -45,7 +45,19 @@ typedef struct {
   double top_flux[2 + ORC_MAX_TRACERS];     /* u, v, tracers: upward flux through the top face */
   double bottom_flux[2 + ORC_MAX_TRACERS];  /* u, v, tracers: upward flux through the bottom face */
   int nthreads;              /* OpenMP threads (<=0: default) */
+  /* time stepper: ORC_RK3 (Eq. rk3) or ORC_QAB2 (Eq. qab2 with chi; the first step after orc_set of any
+   * field is forward Euler, chi = -1/2) */
+  int timestepper;
+  double chi;
+  /* vertical diffusivity profiles at the w-faces (Nz+1 values each, copied; NULL = none): nu_z for
+   * u, v, w and kappa_z for every tracer (Eqs. tracer-with-tendency, momentum-tendency-definition);
+   * vertical_implicit = 1 treats them with the semi-implicit step of Eq. tracer-time-discretization /
+   * predictor-velocity, 0 adds them to the explicit tendency */
+  const double* nu_z;
+  const double* kappa_z;
+  int vertical_implicit;
 } orc_params;
+enum { ORC_RK3 = 0, ORC_QAB2 = 1 };
 
 typedef struct orc_model orc_model;
 
@@ -117,6 +129,15 @@ void orc_coarse_grain(orc_model* m, int cx, int cy, double* out);
  * and v columns to G_u and G_v (buoyancy-tracer models).  fn = NULL removes it. */
 typedef void (*orc_face_flux_fn)(void* ctx, orc_model* m, double* F);
 void orc_set_face_flux(orc_model* m, orc_face_flux_fn fn, void* ctx);
+
+/* Vertical diffusion operator D(q) = d/dz (kappa dq/dz) of one column with no flux through the walls,
+ * second order (fluxes -kappa_f (q_k - q_{k-1})/dz_f at the interior faces, divergence over dz_c):
+ * staggering 0 = q at centres (Nz values, kappa at the Nz+1 faces), 1 = q at the faces (Nz+1 values,
+ * walls held at 0, diffusivity at the centres = mean of the two faces).  The implicit solve returns
+ * q with (I - dtau D) q = rhs (Thomas algorithm in FP64). */
+void orc_vertical_diffusion(const orc_model* m, int staggering, const double* kappa_faces, const double* q, double* out);
+void orc_vertical_implicit_solve(const orc_model* m, int staggering, const double* kappa_faces, double dtau,
+                                 const double* rhs, double* q);
 
 /* Discrete divergence at centres, [Nz][Ny][Nx]. */
 void orc_divergence(const orc_model* m, double* out);

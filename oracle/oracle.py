@@ -52,6 +52,8 @@ class _Params(C.Structure):
         ("top_flux", C.c_double * (2 + MAX_TRACERS)),
         ("bottom_flux", C.c_double * (2 + MAX_TRACERS)),
         ("nthreads", C.c_int),
+        ("timestepper", C.c_int), ("chi", C.c_double),
+        ("nu_z", C.POINTER(C.c_double)), ("kappa_z", C.POINTER(C.c_double)), ("vertical_implicit", C.c_int),
     ]
 
 
@@ -93,6 +95,8 @@ def lib():
         L.orc_column_sgs_flux.argtypes = [C.c_void_p, dp]
         L.orc_coarse_grain.argtypes = [C.c_void_p, C.c_int, C.c_int, dp]
         L.orc_set_face_flux.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        L.orc_vertical_diffusion.argtypes = [C.c_void_p, C.c_int, dp, dp, dp]
+        L.orc_vertical_implicit_solve.argtypes = [C.c_void_p, C.c_int, dp, C.c_double, dp, dp]
         _lib = L
     return _lib
 
@@ -175,6 +179,16 @@ class OracleModel:
             P.top_flux[n] = float(p.get("top_flux", {}).get(name, 0.0))
             P.bottom_flux[n] = float(p.get("bottom_flux", {}).get(name, 0.0))
         P.nthreads = int(p.get("nthreads", 0))
+        P.timestepper = {"rk3": 0, "qab2": 1}[p.get("timestepper", "rk3")]
+        P.chi = float(p.get("chi", 0.1))
+        self._nuz = self._kapz = None
+        if p.get("nu_z") is not None:
+            self._nuz = np.ascontiguousarray(np.broadcast_to(np.asarray(p["nu_z"], np.float64), (self.Nz + 1,)))
+            P.nu_z = _dp(self._nuz)
+        if p.get("kappa_z") is not None:
+            self._kapz = np.ascontiguousarray(np.broadcast_to(np.asarray(p["kappa_z"], np.float64), (self.Nz + 1,)))
+            P.kappa_z = _dp(self._kapz)
+        P.vertical_implicit = int(bool(p.get("vertical_implicit", False)))
         self._P = P
         self._h = lib().orc_create(C.byref(P))
         if not self._h:
@@ -306,3 +320,17 @@ class OracleModel:
 
         self._flux_cb = FACE_FLUX_FN(cb)
         lib().orc_set_face_flux(self._h, C.cast(self._flux_cb, C.c_void_p), None)
+
+    def vertical_diffusion(self, q, kappa_faces, staggering: int = 0) -> np.ndarray:
+        """D(q) = d/dz(kappa dq/dz) of one column (staggering 0: centres, 1: faces)."""
+        q = np.ascontiguousarray(q, np.float64); kf = np.ascontiguousarray(kappa_faces, np.float64)
+        out = np.zeros_like(q)
+        lib().orc_vertical_diffusion(self._h, int(staggering), _dp(kf), _dp(q), _dp(out))
+        return out
+
+    def vertical_implicit_solve(self, rhs, kappa_faces, dtau: float, staggering: int = 0) -> np.ndarray:
+        """q with (I - dtau D) q = rhs for one column."""
+        r = np.ascontiguousarray(rhs, np.float64); kf = np.ascontiguousarray(kappa_faces, np.float64)
+        out = np.zeros_like(r)
+        lib().orc_vertical_implicit_solve(self._h, int(staggering), _dp(kf), float(dtau), _dp(r), _dp(out))
+        return out
