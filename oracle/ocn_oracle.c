@@ -678,9 +678,36 @@ static const double RK_ZETA[3] = {0.0, 17.0 / 60.0, 5.0 / 12.0};
 
 /* One stage: c <- c + dt (g H - z G), G <- H, the semi-implicit vertical diffusion over dtau, the projection
  * over dtau (Eq. rk3 or Eq. qab2 with Eqs. tracer-time-discretization, predictor-velocity). */
+/* The stepper's tendencies follow Eq. pressure-decomposition: b leaves the w equation and the
+ * hydrostatic pressure anomaly p_hy (d p_hy/dz = b, discretely (p_hy(k) - p_hy(k-1))/dz_f(k) =
+ * (b(k-1) + b(k))/2 with p_hy = 0 in the bottom cell of each column) enters u and v as -grad_h p_hy.
+ * With explicit terms only this differs from keeping b in G_w by a discrete gradient, which the
+ * projection removes; the semi-implicit vertical step acts on the split form, as Eq.
+ * predictor-velocity states. */
+static void hydrostatic_split(orc_model* M, double* Hu, double* Hv, double* Hw) {
+  int Nx = M->Nx, Ny = M->Ny, Nz = M->Nz;
+  double* ph = M->work;
+  for (int j = 0; j < Ny; ++j)
+    for (int i = 0; i < Nx; ++i) {
+      ph[ID(M, i, j, 0)] = 0.0;
+      for (int k = 1; k < Nz; ++k)
+        ph[ID(M, i, j, k)] = ph[ID(M, i, j, k - 1)] + M->dzf[k] * 0.5 * (buoyancy(M, i, j, k - 1) + buoyancy(M, i, j, k));
+    }
+#pragma omp parallel for collapse(2)
+  for (int k = 0; k < Nz; ++k)
+    for (int j = 0; j < Ny; ++j)
+      for (int i = 0; i < Nx; ++i) {
+        size_t id = ID(M, i, j, k);
+        Hu[id] -= (A3(M, ph, i, j, k) - A3(M, ph, i - 1, j, k)) / M->dx;
+        Hv[id] -= (A3(M, ph, i, j, k) - A3(M, ph, i, j - 1, k)) / M->dy;
+        if (k > 0) Hw[id] -= 0.5 * (buoyancy(M, i, j, k - 1) + buoyancy(M, i, j, k));
+      }
+}
+
 static void stage(orc_model* M, double dt, double g, double z, double dtau) {
   size_t plane = (size_t)M->Nx * M->Ny, N = plane * M->Nz;
   all_tendencies(M, M->Hu, M->Hv, M->Hw, M->Hc);
+  hydrostatic_split(M, M->Hu, M->Hv, M->Hw);
 #pragma omp parallel for schedule(static)
   for (size_t n = 0; n < N; ++n) {
     M->u[n] += dt * (g * M->Hu[n] - z * M->Gu[n]);
@@ -782,7 +809,7 @@ static double* field_ptr(const orc_model* M, int field) {
 void orc_set(orc_model* M, int field, const double* src) {
   double* d = field_ptr(M, field);
   if (!d) return;
-  M->ab_started = 0;
+  M->ab_started = (field >= ORC_G) ? 1 : 0;   /* QAB2: a restored G^{m-1} continues the run */
   memcpy(d, src, sizeof(double) * orc_field_len(M, field));
   if (field == ORC_W) {   /* impenetrable walls */
     size_t plane = (size_t)M->Nx * M->Ny;

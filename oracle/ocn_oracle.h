@@ -45,8 +45,8 @@ typedef struct {
   double top_flux[2 + ORC_MAX_TRACERS];     /* u, v, tracers: upward flux through the top face */
   double bottom_flux[2 + ORC_MAX_TRACERS];  /* u, v, tracers: upward flux through the bottom face */
   int nthreads;              /* OpenMP threads (<=0: default) */
-  /* time stepper: ORC_RK3 (Eq. rk3) or ORC_QAB2 (Eq. qab2 with chi; the first step after orc_set of any
-   * field is forward Euler, chi = -1/2) */
+  /* time stepper: ORC_RK3 (Eq. rk3) or ORC_QAB2 (Eq. qab2 with chi; the first step after orc_set of a
+   * state field is forward Euler, chi = -1/2; orc_set of a G field marks the run as continuing) */
   int timestepper;
   double chi;
   /* vertical diffusivity profiles at the w-faces (Nz+1 values each, copied; NULL = none): nu_z for
