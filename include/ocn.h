@@ -216,7 +216,8 @@ enum {
   OCN_K_IFFTX = 6,       /* inverse real FFT in x */
   OCN_K_CORRECT = 7,     /* velocity correction */
   OCN_K_COLUMN_CLOSURE = 8, /* learned column closure (features + network + flux divergence) */
-  OCN_K_COUNT = 9
+  OCN_K_VERTICAL = 9,    /* vertical diffusion with diffusivity profiles (explicit or implicit) */
+  OCN_K_COUNT = 10
 };
 
 /* Launch counts and summed device milliseconds per kernel class, accumulated
@@ -335,6 +336,27 @@ ocn_status ocn_mlp_gradients(ocn_mlp* mlp, const float* X, const float* T, const
 ocn_status ocn_mlp_adam(ocn_mlp* mlp, const float* grads, double lr, double beta1, double beta2, double eps);
 ocn_status ocn_mlp_train_step(ocn_mlp* mlp, const float* X, const float* T, const float* mask, int M, double lr,
                               double* loss);
+
+/* Time stepper (Appendix A.1).  OCN_STEPPER_RK3 (default): the low-storage RK3 of Eq. rk3, three
+ * substages per step.  OCN_STEPPER_QAB2: Eq. qab2, one tendency evaluation and one projection per
+ * step, G^{m+1} weights (3/2 + chi, -(1/2 + chi)); the first step after any state field is set is
+ * forward Euler (chi = -1/2), and restoring an OCN_FIELD_G field marks the run as continuing (set
+ * the state first, then G, to restart a QAB2 run bitwise).  Errors: OCN_ERR_ARG. */
+enum { OCN_STEPPER_RK3 = 0, OCN_STEPPER_QAB2 = 1 };
+ocn_status ocn_set_time_stepper(ocn_model* model, int scheme, double chi);
+
+/* Vertical diffusion with diffusivity profiles (Eq. tracer-with-tendency and Eq.
+ * momentum-tendency-definition): nu_faces applies to u, v, w and kappa_faces to every tracer,
+ * both given at the Nz+1 w-faces in host memory (copied; NULL = none; values finite and >= 0).
+ * Second-order finite volumes with no flux through the walls; w uses the mean of the two faces
+ * at each centre.  implicit = 0 adds d/dz(kappa dq/dz) to the explicit tendency; implicit = 1
+ * solves (1 - dtau d/dz kappa d/dz) q = q~ down every column after each stage update (Eq.
+ * tracer-time-discretization, Eq. predictor-velocity), dtau the stage step ((gamma - zeta) dt,
+ * dt for QAB2), before the projection.  The implicit solver keeps 3 Nz pivot values in shared
+ * memory: Nz <= 4096 in FP32 and 2048 in FP64, else OCN_ERR_UNSUPPORTED.  ocn_compute_tendencies
+ * and ocn_profiles include only the explicit form.  Errors: OCN_ERR_ARG, OCN_ERR_STATE, OCN_ERR_UNSUPPORTED, OCN_ERR_CUDA. */
+ocn_status ocn_set_vertical_diffusivity(ocn_model* model, const double* nu_faces, const double* kappa_faces,
+                                        int implicit);
 
 /* Learned column closure of a model (FP32 buoyancy-tracer models; others give
  * OCN_ERR_UNSUPPORTED).  Each w-face k of each cell-centre column (i, j) gets a

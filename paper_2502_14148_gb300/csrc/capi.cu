@@ -139,6 +139,12 @@ struct ocn_model {
   float colc_mu[kColumnFeatures] = {0}, colc_isig[kColumnFeatures] = {0}, colc_scale[3] = {0, 0, 0};
   double colc_N2 = 0.0;
   int colc_version = 0;
+  // time stepper (Eq. rk3 or Eq. qab2) and vertical diffusivity profiles (explicit or semi-implicit)
+  int stepper = OCN_STEPPER_RK3;
+  double chi = 0.1;
+  bool ab_started = false;         // QAB2: G^{m-1} holds a previous tendency
+  size_t off_nuz = 0, off_kapz = 0;
+  bool vnu = false, vkap = false, vimplicit = false;
 };
 
 struct ocn_ensemble {
@@ -241,6 +247,8 @@ void layout(ocn_model* m) {
   for (int t = 0; t < OCN_MAX_TRACERS; ++t) m->off_cref[t] = (t < m->d.n_tracers) ? take(es * g->Nz) : 0;
   m->off_partial = take(sizeof(double) * (size_t)diag_blocks() * (OCN_MAX_TRACERS + 6));
   m->off_diag = take(sizeof(double) * 16);
+  m->off_nuz = take(es * (g->Nz + 1));
+  m->off_kapz = take(es * (g->Nz + 1));
   if (column_closure_capable(m)) {
     m->off_colF = take(sizeof(float) * 3 * Nw);
     m->off_colh = take(sizeof(float) * plane);
@@ -414,28 +422,66 @@ cudaError_t enqueue_column_closure(ocn_model* m, int which, double dt_gamma, int
   }
 }
 
+// Vertical diffusion of the substage: explicit (G += D(stage state), new state += dt_gamma D) or
+// semi-implicit (new state <- (I - dtau D)^{-1} new state); mode 1 (tendencies only) adds the
+// explicit term to G and skips the implicit step.
+template <typename T>
+cudaError_t enqueue_vertical(ocn_model* m, int which, double dt_gamma, double dtau, int mode, int* nlaunch) {
+  if (!m->vnu && !m->vkap) return cudaSuccess;
+  if (m->vimplicit && mode == 1) return cudaSuccess;
+  VDiffArgs<T> a;
+  memset(&a, 0, sizeof(a));
+  StatePtrs<T> cur = state_ptrs<T>(m, which), nxt = state_ptrs<T>(m, 1 - which), G = g_ptrs<T>(m);
+  a.qin[0] = cur.u; a.qin[1] = cur.v; a.qin[2] = cur.w;
+  a.qout[0] = nxt.u; a.qout[1] = nxt.v; a.qout[2] = nxt.w;
+  a.G[0] = G.u; a.G[1] = G.v; a.G[2] = G.w;
+  for (int t = 0; t < m->d.n_tracers; ++t) {
+    a.qin[3 + t] = cur.c[t]; a.qout[3 + t] = nxt.c[t]; a.G[3 + t] = G.c[t];
+    a.cref[t] = at<T>(m, m->off_cref[t]);
+  }
+  a.nuz = at<T>(m, m->off_nuz); a.kapz = at<T>(m, m->off_kapz);
+  a.dzc = at<T>(m, m->off_dzc); a.dzf = at<T>(m, m->off_dzf);
+  a.Nx = m->g->Nx; a.Ny = m->g->Ny; a.Nz = m->g->Nz; a.nt = m->d.n_tracers;
+  a.fields = (m->vnu ? 7 : 0) | (m->vkap ? (((1 << m->d.n_tracers) - 1) << 3) : 0);
+  a.mode = mode;
+  a.dt_gamma = (T)dt_gamma; a.dtau = (T)dtau;
+  m->hook.pre(OCN_K_VERTICAL);
+  cudaError_t e = launch_vertical_diffusion<T>(a, m->vimplicit, m->stream);
+  m->hook.post(OCN_K_VERTICAL);
+  if (nlaunch) *nlaunch += 1;
+  return e;
+}
+
 cudaError_t check_sync(ocn_model* m, cudaError_t e) {
   if (e != cudaSuccess || !m->sync_check) return e;
   return cudaStreamSynchronize(m->stream);
 }
 
-// Enqueue one full RK3 step starting from buffer `which`; returns the final buffer.
+// Enqueue one full time step starting from buffer `which` (three RK3 substages, or one QAB2 stage
+// whose chi is -1/2 on the first step after the state was set); returns the final buffer.
 template <typename T>
 cudaError_t enqueue_step(ocn_model* m, double dt, int* which, int* nlaunch) {
   static const double gam[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
   static const double zet[3] = {0.0, 17.0 / 60.0, 5.0 / 12.0};
+  const bool qab2 = m->stepper == OCN_STEPPER_QAB2;
+  const double chi = m->ab_started ? m->chi : -0.5;
+  const int nst = qab2 ? 1 : 3;
   int n = 0;
-  for (int st = 0; st < 3; ++st) {
+  for (int st = 0; st < nst; ++st) {
+    const double g = qab2 ? 1.5 + chi : gam[st], z = qab2 ? 0.5 + chi : zet[st];
+    const double dtau = (g - z) * dt;
     cudaError_t e = check_sync(m, enqueue_closure<T>(m, *which));
     if (e != cudaSuccess) return e;
     if (m->off_nu) ++n;
-    e = check_sync(m, enqueue_tendency<T>(m, *which, gam[st] * dt, zet[st] * dt, 0));
+    e = check_sync(m, enqueue_tendency<T>(m, *which, g * dt, z * dt, 0));
     if (e != cudaSuccess) return e;
     ++n;
-    e = check_sync(m, enqueue_column_closure<T>(m, *which, gam[st] * dt, 0, &n));
+    e = check_sync(m, enqueue_column_closure<T>(m, *which, g * dt, 0, &n));
+    if (e != cudaSuccess) return e;
+    e = check_sync(m, enqueue_vertical<T>(m, *which, g * dt, dtau, 0, &n));
     if (e != cudaSuccess) return e;
     int np = 0;
-    e = check_sync(m, launch_projection<T>(poisson_args<T>(m, 1 - *which, (gam[st] - zet[st]) * dt), m->stream, &np, m->hook));
+    e = check_sync(m, launch_projection<T>(poisson_args<T>(m, 1 - *which, dtau), m->stream, &np, m->hook));
     if (e != cudaSuccess) return e;
     n += np;
     *which = 1 - *which;
@@ -454,11 +500,13 @@ ocn_status time_step_t(ocn_model* m, double dt, int nsteps) {
       if (e != cudaSuccess) return cuda_fail(e, "time step launch");
       m->cur = w;
       m->launches_per_step = nl;
+      if (m->stepper == OCN_STEPPER_QAB2) m->ab_started = true;
       continue;
     }
     uint64_t key;
     memcpy(&key, &dt, sizeof(key));
-    auto it = m->graph_cache.find({key, m->cur});
+    const int gk = m->cur + 2 * (m->ab_started ? 1 : 0) + 4 * m->stepper;
+    auto it = m->graph_cache.find({key, gk});
     cudaGraphExec_t exec = nullptr;
     int w = m->cur;
     if (it == m->graph_cache.end()) {
@@ -473,7 +521,7 @@ ocn_status time_step_t(ocn_model* m, double dt, int nsteps) {
       e = cudaGraphInstantiate(&exec, graph, 0);
       cudaGraphDestroy(graph);
       if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
-      m->graph_cache[{key, m->cur}] = exec;
+      m->graph_cache[{key, gk}] = exec;
       m->launches_per_step = nl;
     } else {
       exec = it->second;
@@ -482,6 +530,7 @@ ocn_status time_step_t(ocn_model* m, double dt, int nsteps) {
     cudaError_t e = cudaGraphLaunch(exec, m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "graph launch");
     m->cur = w;
+    if (m->stepper == OCN_STEPPER_QAB2) m->ab_started = true;
   }
   return OCN_OK;
 }
@@ -646,6 +695,8 @@ ocn_status ocn_set_field(ocn_model* m, int field, const void* src, size_t nbytes
   if (nbytes != elems * (size_t)m->es) return fail(OCN_ERR_ARG, "byte count does not match the field size");
   cudaError_t e = cudaMemcpyAsync(dst, src, nbytes, src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, m->stream);
   if (e != cudaSuccess) return cuda_fail(e, "set field copy");
+  // QAB2 restarts with an Euler step after the state is set, and continues when G^{m-1} is restored
+  m->ab_started = (field >= OCN_FIELD_G && field < OCN_FIELD_G + 3 + OCN_MAX_TRACERS);
   const int tr = (field & OCN_FIELD_RAW) ? -1 : field - OCN_FIELD_TRACER0;
   const int rf = field - OCN_FIELD_TRACER_REF0;
   if (rf >= 0 && rf < m->d.n_tracers) {   // a reference profile set as is: refresh the host mirror
@@ -746,9 +797,11 @@ ocn_status ocn_compute_tendencies(ocn_model* m) {
     e = check_sync(m, enqueue_closure<float>(m, m->cur));
     if (e == cudaSuccess) e = check_sync(m, enqueue_tendency<float>(m, m->cur, 0.0, 0.0, 1));
     if (e == cudaSuccess) e = check_sync(m, enqueue_column_closure<float>(m, m->cur, 0.0, 1, nullptr));
+    if (e == cudaSuccess) e = check_sync(m, enqueue_vertical<float>(m, m->cur, 0.0, 0.0, 1, nullptr));
   } else {
     e = check_sync(m, enqueue_closure<double>(m, m->cur));
     if (e == cudaSuccess) e = check_sync(m, enqueue_tendency<double>(m, m->cur, 0.0, 0.0, 1));
+    if (e == cudaSuccess) e = check_sync(m, enqueue_vertical<double>(m, m->cur, 0.0, 0.0, 1, nullptr));
   }
   if (e != cudaSuccess) return cuda_fail(e, "tendencies");
   return OCN_OK;
@@ -877,6 +930,7 @@ ocn_status ocn_profiles(ocn_model* m, double* out, int nout) {
     cudaError_t err = enqueue_closure<T>(m, m->cur);
     if (err == cudaSuccess) err = enqueue_tendency<T>(m, m->cur, 0.0, 0.0, 1);   // unsplit G, state untouched
     if (err == cudaSuccess) err = enqueue_column_closure<T>(m, m->cur, 0.0, 1, nullptr);
+    if (err == cudaSuccess) err = enqueue_vertical<T>(m, m->cur, 0.0, 0.0, 1, nullptr);
     if (err != cudaSuccess) return err;
     ProfileArgs<T> pa;
     memset(&pa, 0, sizeof(pa));
@@ -916,6 +970,48 @@ ocn_status ocn_profiles(ocn_model* m, double* out, int nout) {
     if (ts) F1 -= dz * mG1[k];
     Fb[k + 1] = ts ? ga * F0 - gb * F1 : F0;
   }
+  return OCN_OK;
+}
+
+ocn_status ocn_set_time_stepper(ocn_model* m, int scheme, double chi) {
+  if (!m) return fail(OCN_ERR_ARG, "null argument");
+  if (scheme != OCN_STEPPER_RK3 && scheme != OCN_STEPPER_QAB2) return fail(OCN_ERR_ARG, "unknown time stepper");
+  if (!isfinite(chi)) return fail(OCN_ERR_ARG, "chi must be finite");
+  DeviceGuard dg(m->dev);
+  m->stepper = scheme;
+  m->chi = chi;
+  m->ab_started = false;
+  drop_graphs(m);
+  return OCN_OK;
+}
+
+ocn_status ocn_set_vertical_diffusivity(ocn_model* m, const double* nu_faces, const double* kappa_faces, int implicit) {
+  if (!m) return fail(OCN_ERR_ARG, "null argument");
+  if (!m->arena) return fail(OCN_ERR_STATE, "arena not bound");
+  const int n = m->g->Nz + 1;
+  for (const double* p : {nu_faces, kappa_faces})
+    if (p)
+      for (int k = 0; k < n; ++k)
+        if (!(p[k] >= 0.0) || !isfinite(p[k])) return fail(OCN_ERR_ARG, "diffusivities must be finite and >= 0");
+  if (implicit && 3 * (size_t)m->es * m->g->Nz > 48 * 1024) return fail(OCN_ERR_UNSUPPORTED, "Nz too large for the implicit solver");
+  DeviceGuard dg(m->dev);
+  std::vector<char> buf((size_t)n * m->es);
+  auto upload = [&](const double* p, size_t off) -> cudaError_t {
+    for (int k = 0; k < n; ++k) {
+      if (m->es == 4) reinterpret_cast<float*>(buf.data())[k] = (float)p[k];
+      else reinterpret_cast<double*>(buf.data())[k] = p[k];
+    }
+    cudaError_t e = cudaMemcpyAsync(m->arena + off, buf.data(), buf.size(), cudaMemcpyHostToDevice, m->stream);
+    return e == cudaSuccess ? cudaStreamSynchronize(m->stream) : e;
+  };
+  cudaError_t e = cudaSuccess;
+  if (nu_faces) e = upload(nu_faces, m->off_nuz);
+  if (e == cudaSuccess && kappa_faces) e = upload(kappa_faces, m->off_kapz);
+  if (e != cudaSuccess) return cuda_fail(e, "vertical diffusivity upload");
+  m->vnu = nu_faces != nullptr;
+  m->vkap = kappa_faces != nullptr;
+  m->vimplicit = implicit != 0;
+  drop_graphs(m);
   return OCN_OK;
 }
 
@@ -1112,6 +1208,7 @@ ocn_status ensemble_step_t(ocn_ensemble* e, double dt, int nsteps) {
     for (ocn_model* m : e->models) {
       key.push_back((char)('0' + m->cur)); key.push_back((char)('0' + m->variant));
       key += std::to_string(m->colc_version); key.push_back('/');
+      key.push_back((char)('0' + m->stepper)); key.push_back(m->ab_started ? 'a' : 'e');
     }
     auto it = e->graphs.find(key);
     std::vector<int> w(e->n);
@@ -1150,7 +1247,10 @@ ocn_status ensemble_step_t(ocn_ensemble* e, double dt, int nsteps) {
     }
     cudaError_t ce = cudaGraphLaunch(it->second, e->stream);
     if (ce != cudaSuccess) return cuda_fail(ce, "ensemble graph launch");
-    for (int i = 0; i < e->n; ++i) e->models[i]->cur = w[i];
+    for (int i = 0; i < e->n; ++i) {
+      e->models[i]->cur = w[i];
+      if (e->models[i]->stepper == OCN_STEPPER_QAB2) e->models[i]->ab_started = true;
+    }
   }
   return OCN_OK;
 }

@@ -168,6 +168,24 @@ int diag_blocks();
 // Records the text returned by ocn_last_error() on this thread and returns s.
 ocn_status set_last_error(ocn_status s, const char* msg);
 
+// Vertical diffusion with diffusivity profiles at the w-faces (vertical.cu): fields f = 0 u, 1 v,
+// 2 w, 3 + n tracer n; bit f of `fields` selects them.  Explicit: G += D(qin), mode 0 also
+// qout += dt_gamma D(qin).  Implicit: qout <- (I - dtau D)^{-1} qout in place.
+template <typename T>
+struct VDiffArgs {
+  const T* qin[3 + kMaxTracers];
+  T* qout[3 + kMaxTracers];
+  T* G[3 + kMaxTracers];
+  const T* cref[kMaxTracers];
+  const T* nuz; const T* kapz;             // [Nz+1]
+  const T* dzc; const T* dzf;              // dz_c [Nz], dz_f [Nz+1] (interior faces 1..Nz-1)
+  int Nx, Ny, Nz, nt;
+  int fields;
+  int mode;
+  T dt_gamma, dtau;
+};
+template <typename T> cudaError_t launch_vertical_diffusion(const VDiffArgs<T>& a, bool implicit, cudaStream_t s);
+
 // Tensor-core GEMM of the learned column closure (mlp.cu):  D = A . B^T with A [M][K] and
 // B [N][K] BF16 (K contiguous, lda/ldb multiples of 8 elements, 16-byte aligned bases),
 // FP32 accumulation, 16 <= N <= 256 (multiple of 16), K a multiple of 8.  Split-K over

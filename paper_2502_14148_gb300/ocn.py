@@ -25,7 +25,9 @@ OCN_FIELD_P, OCN_FIELD_G, OCN_FIELD_NU_E = 10, 20, 30
 OCN_FIELD_TRACER_REF0, OCN_FIELD_RAW = 40, 0x100
 OCN_OPT_GRAPHS, OCN_OPT_SYNC_CHECK, OCN_OPT_KERNEL_TIMING, OCN_OPT_TENDENCY_VARIANT = 1, 2, 3, 4
 TENDENCY_VARIANTS = 4
-KERNEL_CLASSES = ["closure", "tendency", "div_fftx", "fft_y", "tridiag", "gauge", "ifftx", "correct", "column_closure"]
+KERNEL_CLASSES = ["closure", "tendency", "div_fftx", "fft_y", "tridiag", "gauge", "ifftx", "correct", "column_closure",
+                  "vertical"]
+STEPPERS = {"rk3": 0, "qab2": 1}
 COLUMN_FEATURES = 32
 MAX_TRACERS = 4
 CLOSURES = {"none": 0, "scalar": 1, "smagorinsky": 2, "amd": 3}
@@ -44,7 +46,7 @@ EXPORTS = ["ocn_abi_version", "ocn_last_error", "ocn_grid_create", "ocn_grid_des
            "ocn_mlp_arena_bytes", "ocn_mlp_bind_arena", "ocn_mlp_num_params", "ocn_mlp_set_params",
            "ocn_mlp_get_params", "ocn_mlp_forward", "ocn_mlp_gradients", "ocn_mlp_adam", "ocn_mlp_train_step",
            "ocn_gemm_bf16", "ocn_set_column_closure", "ocn_closure_features", "ocn_column_fluxes",
-           "ocn_coarse_grain"]
+           "ocn_coarse_grain", "ocn_set_time_stepper", "ocn_set_vertical_diffusivity"]
 OCN_OPT_ENSEMBLE_MODE, OCN_ENSEMBLE_CONCURRENT, OCN_ENSEMBLE_SEQUENTIAL = 5, 0, 1
 
 
@@ -136,6 +138,8 @@ def lib(path: str = LIB_PATH):
     L.ocn_mlp_adam.argtypes = [vp, vp, C.c_double, C.c_double, C.c_double, C.c_double]
     L.ocn_mlp_train_step.argtypes = [vp, vp, vp, vp, C.c_int, C.c_double, dp]
     L.ocn_set_column_closure.argtypes = [vp, vp, C.POINTER(ColumnClosureDesc)]
+    L.ocn_set_time_stepper.argtypes = [vp, C.c_int, C.c_double]
+    L.ocn_set_vertical_diffusivity.argtypes = [vp, dp, dp, C.c_int]
     L.ocn_closure_features.argtypes = [vp, C.c_double, vp]
     L.ocn_column_fluxes.argtypes = [vp, C.c_int, vp]
     L.ocn_coarse_grain.argtypes = [vp, C.c_int, C.c_int, vp, sz]
@@ -226,6 +230,30 @@ class Model:
                 self.arena = torch.empty(self.arena_bytes, dtype=torch.uint8, device=self.device)
             _check(lib().ocn_model_bind_arena(self._h, C.c_void_p(self.arena.data_ptr()), self.arena_bytes),
                    "ocn_model_bind_arena")
+        self._apply_schemes(p)
+
+    def _apply_schemes(self, p: dict):
+        """The workload keys for the time stepper and vertical diffusivities (as the oracle reads them)."""
+        if p.get("timestepper", "rk3") != "rk3" or "chi" in p:
+            self.set_time_stepper(p.get("timestepper", "rk3"), p.get("chi", 0.1))
+        if p.get("nu_z") is not None or p.get("kappa_z") is not None:
+            self.set_vertical_diffusivity(p.get("nu_z"), p.get("kappa_z"), bool(p.get("vertical_implicit", False)))
+
+    def set_time_stepper(self, scheme: str = "rk3", chi: float = 0.1):
+        _check(lib().ocn_set_time_stepper(self._h, STEPPERS[scheme], float(chi)), "ocn_set_time_stepper")
+        self.params["timestepper"], self.params["chi"] = scheme, float(chi)
+
+    def set_vertical_diffusivity(self, nu=None, kappa=None, implicit: bool = False):
+        """Diffusivity profiles at the Nz+1 w-faces (scalars broadcast) for u, v, w (nu) and tracers (kappa)."""
+        def arr(x):
+            if x is None:
+                return None, None
+            a = np.ascontiguousarray(np.broadcast_to(np.asarray(x, np.float64), (self.Nz + 1,)))
+            return a, a.ctypes.data_as(C.POINTER(C.c_double))
+        a_nu, p_nu = arr(nu)
+        a_ka, p_ka = arr(kappa)
+        _check(lib().ocn_set_vertical_diffusivity(self._h, p_nu, p_ka, int(bool(implicit))),
+               "ocn_set_vertical_diffusivity")
 
     def _setup(self, p: dict):
         import torch
@@ -306,8 +334,11 @@ class Model:
                                    host_tensor.numel() * host_tensor.element_size(), 0), "ocn_get_field")
 
     def checkpoint(self) -> dict:
-        """Device copies of everything a bitwise restart needs (state, raw tracer anomalies, profiles)."""
+        """Device copies of everything a bitwise restart needs (state, raw tracer anomalies, profiles,
+        and for QAB2 the previous tendencies, restored last)."""
         names = ["u", "v", "w"] + [f"raw_{t}" for t in self.tracers] + [f"ref_{t}" for t in self.tracers]
+        if self.params.get("timestepper", "rk3") == "qab2":
+            names += ["G_u", "G_v", "G_w"] + [f"G_{t}" for t in self.tracers]
         return {n: self.get(n).clone() for n in names}
 
     def restore(self, ckpt: dict):
@@ -476,7 +507,9 @@ class Ensemble:
         for i, p in enumerate(self.params):
             mh = C.c_void_p()
             _check(lib().ocn_ensemble_member(self._h, i, C.byref(mh)), "ocn_ensemble_member")
-            self.members.append(Model.borrowed(mh, p, self.device, self.stream, self))
+            member = Model.borrowed(mh, p, self.device, self.stream, self)
+            member._apply_schemes(p)
+            self.members.append(member)
 
     def __del__(self):
         if getattr(self, "_h", None):
