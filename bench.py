@@ -269,6 +269,15 @@ def run_ours(args, world, rank, local):
     model = ocn.Model(p, device=dev)
     model.set(**st)
     dt = p["dt"]
+    qab2 = args.stepper == "qab2"
+    if qab2:
+        model.set_time_stepper("qab2", 0.1)
+    if args.vertical != "none":
+        # a surface-intensified vertical diffusivity profile (boundary-layer-like), same for momentum and tracers
+        zf = np.asarray(p["z_faces"])
+        prof = 1e-2 * np.exp((zf - zf[-1]) / 32.0)
+        model.set_vertical_diffusivity(prof, prof, implicit=(args.vertical == "implicit"))
+    substeps = 1 if qab2 else 3
     variant, variant_ms = model.autotune()        # tile variant of the tendency kernel
 
     model.time_step(dt, args.warmup)              # warm-up (graph capture, clocks)
@@ -292,7 +301,7 @@ def run_ours(args, world, rank, local):
     model.set_option(ocn.OCN_OPT_KERNEL_TIMING, 0)
     launches = sum(c for c, _ in ktimes.values())
     ms = max_over_ranks(ms_local, world)
-    value = cells * 3 * args.steps * world / (ms * 1e-3)
+    value = cells * substeps * args.steps * world / (ms * 1e-3)
     d = model.diagnostics(dt)
 
     # ---- e2e: through the C ABI with pinned host buffers, copies inside the timed region
@@ -317,7 +326,7 @@ def run_ours(args, world, rank, local):
         for n in names:
             model.get_host(n, host_out[n])
     t_e2e = max_over_ranks(time.perf_counter() - t0, world)
-    e2e_value = cells * 3 * k_e2e * world / t_e2e
+    e2e_value = cells * substeps * k_e2e * world / t_e2e
 
     if rank != 0:
         return 0
@@ -335,18 +344,32 @@ def run_ours(args, world, rank, local):
         traffic = profiled_traffic("tendency", p["name"])
         roof = {"bound": "alu", "kernel": "k_tendency", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
+                "traffic_source": "profiles/tendency_les_512.txt: an RK3 first-substage launch (no G_prev read), "
+                                  "scaled from 256x256x128 by the cell count",
                 "algorithmic": f"{flops_cell} FP32 flops per cell (FMA = 2) x {cells} cells per launch",
                 "peak_source": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 x {clock_mhz:.0f} MHz"}
     else:
         roof = None
     sub_bytes = substep_bytes_per_cell(p) * cells
-    t_sub = ms / args.steps / 3 * 1e-3
+    t_sub = ms / args.steps / substeps * 1e-3
+    metric, unit = ("cell-QAB2-steps/sec", "cell-steps/s") if qab2 else ("cell-RK3-substeps/sec", "cell-substeps/s")
+    vroof = None
+    if "vertical" in per_class:
+        nfield = 3 + len(model.tracers)
+        vbytes = cells * nfield * 2 * (4 if p["precision"] == 32 else 8)
+        vt = per_class["vertical"]["ms_per_launch"] * 1e-3
+        vroof = {"bound": "hbm", "kernel": "k_vdiff_" + args.vertical, "achieved": vbytes / vt / 1e9,
+                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": vbytes / vt / 1e9 / peaks["hbm_gbs"],
+                 "algorithmic": f"{nfield} fields x (read + write) x {4 if p['precision'] == 32 else 8} B per cell",
+                 "ms_per_launch": vt * 1e3}
     line = {
-        "metric": "cell-RK3-substeps/sec", "value": value, "unit": "cell-substeps/s", "n_gpus": world,
+        "metric": metric, "value": value, "unit": unit, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if p["precision"] == 32 else "f64",
         "data": "synthetic",
-        "config": {"workload": workload_desc(p), "parallelism": "replicas" if world > 1 else "single",
+        "config": {"workload": workload_desc(p) + ("" if not qab2 else ", QAB2 (chi 0.1)") +
+                               ("" if args.vertical == "none" else f", {args.vertical} vertical diffusion profile"),
+                   "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (model state 1.3 GB)", "graphs": False,
                    "kernel_events": True, "tendency_variant": variant,
                    "autotune_ms": [round(x, 3) for x in variant_ms]},
@@ -355,6 +378,7 @@ def run_ours(args, world, rank, local):
                         "frac": sub_bytes / t_sub / 1e9 / peaks["hbm_gbs"], "peak_source": peaks["source"],
                         "algorithmic": f"{substep_bytes_per_cell(p)} B per cell per substage"},
         "kernels": per_class,
+        "vertical_roofline": vroof,
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": "cell-substeps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": k_e2e, "path": "ocn_set_field/ocn_time_step/ocn_get_field with pinned host buffers"},
@@ -363,7 +387,7 @@ def run_ours(args, world, rank, local):
     }
     if args.size:
         line["config"]["workload"] += " (resized for profiling, not a bench line)"
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and not qab2 and args.vertical == "none":
         rate, sps, cores, sample = oracle_rate(args.workload, 1)
         line["cpu_baseline"] = {"value": rate, "unit": "cell-substeps/s", "cores": cores, "kind": "oracle",
                                 "sample": sample}
@@ -590,6 +614,9 @@ def main():
                     help="instances: ensemble members (--workload ensemble, default 64) or coarse instances "
                          "(--workload closure, default 256)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--stepper", default="rk3", choices=["rk3", "qab2"], help="time stepper (default RK3)")
+    ap.add_argument("--vertical", default="none", choices=["none", "explicit", "implicit"],
+                    help="add a vertical diffusivity profile, explicit or semi-implicit")
     ap.add_argument("--size", default=None, help="NxxNyxNz: the workload's physics and spacing on another grid (profiling)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
