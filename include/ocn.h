@@ -352,8 +352,8 @@ ocn_status ocn_set_time_stepper(ocn_model* model, int scheme, double chi);
  * at each centre.  implicit = 0 adds d/dz(kappa dq/dz) to the explicit tendency; implicit = 1
  * solves (1 - dtau d/dz kappa d/dz) q = q~ down every column after each stage update (Eq.
  * tracer-time-discretization, Eq. predictor-velocity), dtau the stage step ((gamma - zeta) dt,
- * dt for QAB2), before the projection.  The implicit solver keeps 3 Nz pivot values in shared
- * memory: Nz <= 4096 in FP32 and 2048 in FP64, else OCN_ERR_UNSUPPORTED.  ocn_compute_tendencies
+ * dt for QAB2), before the projection.  The implicit solver keeps 4 Nz factor values in shared
+ * memory: Nz <= 3072 in FP32 and 1536 in FP64, else OCN_ERR_UNSUPPORTED.  ocn_compute_tendencies
  * and ocn_profiles include only the explicit form.  Errors: OCN_ERR_ARG, OCN_ERR_STATE, OCN_ERR_UNSUPPORTED, OCN_ERR_CUDA. */
 ocn_status ocn_set_vertical_diffusivity(ocn_model* model, const double* nu_faces, const double* kappa_faces,
                                         int implicit);

@@ -993,7 +993,7 @@ ocn_status ocn_set_vertical_diffusivity(ocn_model* m, const double* nu_faces, co
     if (p)
       for (int k = 0; k < n; ++k)
         if (!(p[k] >= 0.0) || !isfinite(p[k])) return fail(OCN_ERR_ARG, "diffusivities must be finite and >= 0");
-  if (implicit && 3 * (size_t)m->es * m->g->Nz > 48 * 1024) return fail(OCN_ERR_UNSUPPORTED, "Nz too large for the implicit solver");
+  if (implicit && 4 * (size_t)m->es * m->g->Nz > 48 * 1024) return fail(OCN_ERR_UNSUPPORTED, "Nz too large for the implicit solver");
   DeviceGuard dg(m->dev);
   std::vector<char> buf((size_t)n * m->es);
   auto upload = [&](const double* p, size_t off) -> cudaError_t {

@@ -32,10 +32,10 @@ __global__ void __launch_bounds__(kColsPerBlock) k_vdiff_explicit(const VDiffArg
   const size_t plane = (size_t)a.Nx * a.Ny;
   const size_t col = (size_t)blockIdx.x * kColsPerBlock + threadIdx.x;
   if (col >= plane) return;
-  const T* kf = (f < 3) ? a.nuz : a.kapz;
-  const T* qi = a.qin[f];
-  T* qo = a.qout[f];
-  T* G = a.G[f];
+  const T* __restrict__ kf = (f < 3) ? a.nuz : a.kapz;
+  const T* __restrict__ qi = a.qin[f];
+  T* __restrict__ qo = a.qout[f];
+  T* __restrict__ G = a.G[f];
   const int Nz = a.Nz;
   if (f != 2) {                                    // centres
     T qc = qval(a, f, qi, col, 0);
@@ -69,7 +69,11 @@ __global__ void __launch_bounds__(kColsPerBlock) k_vdiff_explicit(const VDiffArg
 }
 
 // Implicit: the tridiagonal of field f is the same for every column, so each block factors it
-// once into shared memory (sub-diagonal a, 1/pivot, c') and every thread sweeps its column.
+// once into shared memory (sub-diagonal a, 1/pivot, c', and for tracers dtau D(ref)) and every
+// thread sweeps its column.  Levels move in chunks of kChunk: a chunk's loads are issued together,
+// swept in registers, then stored, so the loads of a column are not serialised behind its stores.
+constexpr int kChunk = 8;
+
 template <typename T>
 __global__ void __launch_bounds__(kColsPerBlock) k_vdiff_implicit(const VDiffArgs<T> a) {
   extern __shared__ __align__(16) unsigned char vsm[];
@@ -82,7 +86,9 @@ __global__ void __launch_bounds__(kColsPerBlock) k_vdiff_implicit(const VDiffArg
   T* sa = reinterpret_cast<T*>(vsm);
   T* sinv = sa + Nz;
   T* scp = sinv + Nz;
+  T* sref = scp + Nz;
   const T* kf = (f < 3) ? a.nuz : a.kapz;
+  const T* ref = (f >= 3) ? a.cref[f - 3] : nullptr;
   const T dtau = a.dtau;
   if (threadIdx.x == 0) {
     T cprev = T(0);
@@ -106,33 +112,55 @@ __global__ void __launch_bounds__(kColsPerBlock) k_vdiff_implicit(const VDiffArg
       sinv[r] = inv;
       scp[r] = sup * inv;
       cprev = scp[r];
+      T dr = T(0);
+      if (ref) {                                   // dtau D(ref) at centre k
+        const T Fb = (k > 0) ? -kf[k] * (ref[k] - ref[k - 1]) / a.dzf[k] : T(0);
+        const T Ft = (k < Nz - 1) ? -kf[k + 1] * (ref[k + 1] - ref[k]) / a.dzf[k + 1] : T(0);
+        dr = dtau * (-(Ft - Fb) / a.dzc[k]);
+      }
+      sref[r] = dr;
     }
   }
   __syncthreads();
   const size_t plane = (size_t)a.Nx * a.Ny;
   const size_t col = (size_t)blockIdx.x * kColsPerBlock + threadIdx.x;
   if (col >= plane) return;
-  T* q = a.qout[f];
-  const T* ref = (f >= 3) ? a.cref[f - 3] : nullptr;
-  // forward sweep (d' overwrites the column), then back substitution
+  T* q = a.qout[f] + col + (size_t)n0 * plane;      // unknown r at q[r * plane]
+  // forward sweep: d' overwrites the column
   T dprev = T(0);
-  for (int r = 0; r < n; ++r) {
-    const int k = n0 + r;
-    const size_t id = (size_t)k * plane + col;
-    T d = q[id];
-    if (ref) {                                     // + dtau D(ref) at centre k
-      const T Fb = (k > 0) ? -kf[k] * (ref[k] - ref[k - 1]) / a.dzf[k] : T(0);
-      const T Ft = (k < Nz - 1) ? -kf[k + 1] * (ref[k + 1] - ref[k]) / a.dzf[k + 1] : T(0);
-      d += dtau * (-(Ft - Fb) / a.dzc[k]);
+  for (int r0 = 0; r0 < n; r0 += kChunk) {
+    T d[kChunk];
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u) d[u] = (r0 + u < n) ? q[(size_t)(r0 + u) * plane] : T(0);
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u) {
+      const int r = r0 + u;
+      if (r < n) {
+        dprev = (d[u] + sref[r] - sa[r] * dprev) * sinv[r];
+        d[u] = dprev;
+      }
     }
-    dprev = (d - sa[r] * dprev) * sinv[r];
-    q[id] = dprev;
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u)
+      if (r0 + u < n) q[(size_t)(r0 + u) * plane] = d[u];
   }
+  // back substitution, top down, chunk by chunk
   T x = dprev;
-  for (int r = n - 2; r >= 0; --r) {
-    const size_t id = (size_t)(n0 + r) * plane + col;
-    x = q[id] - scp[r] * x;
-    q[id] = x;
+  for (int r1 = n - 2; r1 >= 0; r1 -= kChunk) {
+    T d[kChunk];
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u) d[u] = (r1 - u >= 0) ? q[(size_t)(r1 - u) * plane] : T(0);
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u) {
+      const int r = r1 - u;
+      if (r >= 0) {
+        x = d[u] - scp[r] * x;
+        d[u] = x;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u)
+      if (r1 - u >= 0) q[(size_t)(r1 - u) * plane] = d[u];
   }
 }
 
@@ -143,7 +171,7 @@ cudaError_t launch_vertical_diffusion(const VDiffArgs<T>& a, bool implicit, cuda
   const size_t plane = (size_t)a.Nx * a.Ny;
   dim3 grid((unsigned)((plane + kColsPerBlock - 1) / kColsPerBlock), 3 + a.nt);
   if (implicit) {
-    const size_t smem = 3 * sizeof(T) * (size_t)a.Nz;
+    const size_t smem = 4 * sizeof(T) * (size_t)a.Nz;
     if (smem > 48 * 1024) return cudaErrorInvalidValue;
     k_vdiff_implicit<T><<<grid, kColsPerBlock, smem, s>>>(a);
   } else {
