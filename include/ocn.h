@@ -407,6 +407,13 @@ ocn_status ocn_coarse_grain(ocn_model* model, int cx, int cy, double* out, size_
 ocn_status ocn_gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, int ldb, float* D, int ldd,
                          int* status, void* stream);
 
+/* Failure-detection test of the tensor-core kernels' bounded waits: launches the GEMM kernel with its
+ * MMA and commit left out, so the bounded mbarrier wait runs out after about 0.5 s; the kernel sets
+ * *status (device int) to 1, waits once more (bounded), frees its tensor memory and returns, leaving
+ * the context usable.  Enqueued on stream.  This entry allocates 20 KB of device memory on first use
+ * (kept until exit) -- the one exception to the no-allocation rule, for tests only. */
+ocn_status ocn_gemm_timeout_test(int* status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -98,6 +98,9 @@ def normalisation(X):
     const = sd <= 1e-6 * np.abs(m)
     mu[:FEATURES_USED] = m
     sigma[:FEATURES_USED] = np.where(const, np.maximum(np.abs(m), 1e-30), np.where(sd > 0, sd, 1.0))
+    # the mixed-layer depth is a length like the face depth: never scale it below a thousandth of the
+    # depths' spread, so that a column without a mixed layer (h at rounding level) stays near zero
+    sigma[19] = max(sigma[19], 1e-3 * sigma[18])
     return mu, sigma
 
 

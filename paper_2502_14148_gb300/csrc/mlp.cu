@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const GemmArgs a) {
     stage_tile(sB, static_cast<const __nv_bfloat16*>(a.B), a.ldb, 0, N, N, k0, ke);
     fence_proxy_async();
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && !a.no_issue) {
       tc_fence_after();
       const int steps = (min(kChunkK, ke - k0) + 15) / 16;
       for (int s = 0; s < steps; ++s) {
@@ -905,6 +905,30 @@ ocn_status ocn_mlp_train_step(ocn_mlp* n, const float* X, const float* T, const 
     return mlp_read_status(n);
   }
   return OCN_OK;
+}
+
+// The timeout path of the tensor-core kernels, for failure-detection tests: the GEMM kernel runs with
+// its MMA and commit left out, so its bounded mbarrier wait runs out (about 0.5 s), the kernel records
+// the failure in *status, waits once more (bounded) and frees its tensor memory.
+ocn_status ocn_gemm_timeout_test(int* status, void* stream) {
+  if (!status) return mlp_fail(OCN_ERR_ARG, "null pointer");
+  static __nv_bfloat16* zeros = nullptr;
+  static float* sink = nullptr;
+  if (!zeros) {
+    // a 128 x 64 BF16 operand and a 128 x 16 result, allocated once for this test entry only
+    cudaError_t e = cudaMalloc(&zeros, 128 * 64 * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMalloc(&sink, 128 * 16 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(zeros, 0, 128 * 64 * sizeof(__nv_bfloat16));
+    if (e != cudaSuccess) return mlp_cuda(e, "timeout test buffers");
+  }
+  ocn::GemmArgs g;
+  memset(&g, 0, sizeof(g));
+  g.A = zeros; g.lda = 64;
+  g.B = zeros; g.ldb = 64;
+  g.M = 128; g.N = 16; g.K = 64; g.kchunk = 64;
+  g.mode = 0; g.D = sink; g.ldd = 16; g.status = status;
+  g.no_issue = 1;
+  return mlp_cuda(ocn::launch_gemm_tc(g, 1, reinterpret_cast<cudaStream_t>(stream)), "timeout test");
 }
 
 // C entry point for the bare GEMM (used by the tests of the tensor-core path).

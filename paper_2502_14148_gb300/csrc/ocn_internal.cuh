@@ -208,6 +208,7 @@ struct GemmArgs {
   void* HT; int ldht;
   const float* Z; int ldz;
   int* status;
+  int no_issue;                    // test of the timeout path: stage, but issue no MMA and no commit
 };
 cudaError_t launch_gemm_tc(const GemmArgs& a, int nsplit, cudaStream_t s);
 

@@ -46,7 +46,7 @@ EXPORTS = ["ocn_abi_version", "ocn_last_error", "ocn_grid_create", "ocn_grid_des
            "ocn_mlp_arena_bytes", "ocn_mlp_bind_arena", "ocn_mlp_num_params", "ocn_mlp_set_params",
            "ocn_mlp_get_params", "ocn_mlp_forward", "ocn_mlp_gradients", "ocn_mlp_adam", "ocn_mlp_train_step",
            "ocn_gemm_bf16", "ocn_set_column_closure", "ocn_closure_features", "ocn_column_fluxes",
-           "ocn_coarse_grain", "ocn_set_time_stepper", "ocn_set_vertical_diffusivity"]
+           "ocn_coarse_grain", "ocn_set_time_stepper", "ocn_set_vertical_diffusivity", "ocn_gemm_timeout_test"]
 OCN_OPT_ENSEMBLE_MODE, OCN_ENSEMBLE_CONCURRENT, OCN_ENSEMBLE_SEQUENTIAL = 5, 0, 1
 
 
@@ -143,6 +143,7 @@ def lib(path: str = LIB_PATH):
     L.ocn_closure_features.argtypes = [vp, C.c_double, vp]
     L.ocn_column_fluxes.argtypes = [vp, C.c_int, vp]
     L.ocn_coarse_grain.argtypes = [vp, C.c_int, C.c_int, vp, sz]
+    L.ocn_gemm_timeout_test.argtypes = [vp, vp]
     L.ocn_gemm_bf16.argtypes = [C.c_int, C.c_int, C.c_int, vp, C.c_int, vp, C.c_int, vp, C.c_int, vp, vp]
     for name in EXPORTS:
         if name not in ("ocn_abi_version", "ocn_last_error", "ocn_grid_destroy", "ocn_model_destroy", "ocn_ensemble_destroy",

@@ -160,3 +160,24 @@ def test_bad_batch_sizes_are_rejected():
         net.forward(np.zeros((257, 32), np.float32))
     with pytest.raises(ocn.OcnError):
         ocn.MLP((32, 60, 16), max_batch=256)
+
+
+def test_bounded_wait_times_out_and_reports():
+    """Failure detection without a fault: a tensor-core kernel whose MMA is never issued gives up its
+    bounded wait, reports through its status word and leaves the context usable (a normal GEMM after
+    it is still exact)."""
+    torch = _torch()
+    import time
+    from paper_2502_14148_gb300 import ocn
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    t0 = time.perf_counter()
+    ocn._check(ocn.lib().ocn_gemm_timeout_test(ocn.C.c_void_p(status.data_ptr()),
+                                               ocn.C.c_void_p(torch.cuda.current_stream().cuda_stream)), "timeout")
+    torch.cuda.synchronize()
+    waited = time.perf_counter() - t0
+    assert int(status.item()) == 1
+    assert 0.2 < waited < 10.0
+    A = _bf16_round(np.eye(128, 32)).cuda()
+    D = ocn.gemm_bf16(A, A[:16].contiguous())
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(D.cpu().numpy(), np.eye(128, 32) @ np.eye(128, 32)[:16].T)
