@@ -8,9 +8,11 @@ namespace ocn {
 // Eddy diffusivities at cell centres (Sec. 3.1.1): Smagorinsky-Lilly and AMD.
 // One thread per (i, j) column marching up in z: the values on face / level
 // k+1 loaded for one level are reused as the k values of the next, so each cell
-// costs about twenty loads (horizontal neighbours come through L1).
+// costs about twenty loads (horizontal neighbours come through L1).  The march is
+// latency-bound, so residency matters most: in FP32, four 256-thread CTAs per SM
+// (registers capped at 64) measured 1.5x faster than three; more CTAs spill.
 template <typename T>
-__global__ void __launch_bounds__(256) k_closure(const ClosureArgs<T> a) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_closure(const ClosureArgs<T> a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int Nx = a.Nx, Ny = a.Ny, Nz = a.Nz;
