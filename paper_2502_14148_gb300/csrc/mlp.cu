@@ -337,10 +337,45 @@ __global__ void __launch_bounds__(kClosureThreads, 2) k_mlp_closure(const MlpClo
   const int row = quad * 32 + lane;                 // the TMEM lane / sample row this thread reads back
   uint32_t phase = 0;
   bool ok = true;
+  // raw column values of this thread's face for the features: part 0 b at levels k-3..k+2 (0-5),
+  // the face depth (6) and the column's mixed-layer depth (7); part 1 u at faces i and i+1 (0-5,
+  // 6-11) and v at faces j and j+1 (12-17, 18-23) at levels k-3..k+2; 0 outside the column
+  float raw[24];
+  auto load_raw = [&](long long tt) {
+#pragma unroll
+    for (int m = 0; m < 24; ++m) raw[m] = 0.0f;
+    const size_t sidx = (size_t)tt * 128 + (tid & 127);
+    if (tt >= ntiles || sidx >= nsamp) return;
+    const uint32_t s32 = (uint32_t)sidx, p32 = (uint32_t)plane;
+    const int k = (int)(s32 / p32), cc = (int)(s32 - (uint32_t)k * p32);
+    const int j = cc / c.Nx, i = cc - j * c.Nx;
+    const int ip = (i + 1 == c.Nx) ? 0 : i + 1, jp = (j + 1 == c.Ny) ? 0 : j + 1;
+    if ((tid >> 7) == 0) {
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        const int lev = k - 3 + m;
+        if (lev >= 0 && lev < c.Nz) raw[m] = __ldg(c.b + col_id(c, i, j, lev));
+      }
+      raw[6] = __ldg(c.depth + k);
+      raw[7] = __ldg(c.h + (size_t)j * c.Nx + i);
+    } else {
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        const int lev = k - 3 + m;
+        if (lev >= 0 && lev < c.Nz) {
+          raw[m] = __ldg(c.u + col_id(c, i, j, lev));
+          raw[6 + m] = __ldg(c.u + col_id(c, ip, j, lev));
+          raw[12 + m] = __ldg(c.v + col_id(c, i, j, lev));
+          raw[18 + m] = __ldg(c.v + col_id(c, i, jp, lev));
+        }
+      }
+    }
+  };
+  load_raw(blockIdx.x);
   for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-    // ---- features of sample row (tid & 127), half of them per thread: part 0 the db/dz stencil
-    //      (features 0-4) and the non-local features 15-19 plus the zero padding, part 1 the
-    //      dubar/dz and dvbar/dz stencils (features 5-14)
+    // ---- features of sample row (tid & 127) from the raw values prefetched for this tile, half of
+    //      them per thread: part 0 the db/dz stencil (features 0-4) and the non-local features
+    //      15-19 plus the zero padding, part 1 the dubar/dz and dvbar/dz stencils (features 5-14)
     {
       const int r = tid & 127, fp = tid >> 7;
       const size_t sidx = (size_t)t * 128 + r;
@@ -349,20 +384,24 @@ __global__ void __launch_bounds__(kClosureThreads, 2) k_mlp_closure(const MlpClo
 #pragma unroll
       for (int m = 0; m < 10; ++m) g[m] = 0.0f;
       if (valid) {
-        const uint32_t s32 = (uint32_t)sidx, p32 = (uint32_t)plane;      // < 2^31 (checked at launch)
-        const int k = (int)(s32 / p32), cc = (int)(s32 - (uint32_t)k * p32);
-        const int j = cc / c.Nx, i = cc - j * c.Nx;
-        if (fp == 0) {
+        const int k = (int)((uint32_t)sidx / (uint32_t)plane);
+        // face q = k - 2 + m lies between levels q - 1 (raw index m) and q (raw index m + 1)
 #pragma unroll
-          for (int m = 0; m < 5; ++m) g[m] = col_grad(c, 0, i, j, k + m - 2);
-          g[5] = c.Jb; g[6] = c.f; g[7] = c.N2bg; g[8] = c.depth[k]; g[9] = c.h[(size_t)j * c.Nx + i];
-        } else {
-#pragma unroll
-          for (int m = 0; m < 5; ++m) {
-            g[m] = col_grad(c, 1, i, j, k + m - 2);
-            g[5 + m] = col_grad(c, 2, i, j, k + m - 2);
+        for (int m = 0; m < 5; ++m) {
+          const int q = k - 2 + m;
+          if (q >= 1 && q < c.Nz) {
+            const float rz = __ldg(c.rdzf + q);
+            if (fp == 0) {
+              float d = raw[m + 1] - raw[m];
+              if (c.cref) d += __ldg(c.cref + q) - __ldg(c.cref + q - 1);
+              g[m] = d * rz;
+            } else {
+              g[m] = 0.5f * ((raw[m + 1] + raw[6 + m + 1]) - (raw[m] + raw[6 + m])) * rz;
+              g[5 + m] = 0.5f * ((raw[12 + m + 1] + raw[18 + m + 1]) - (raw[12 + m] + raw[18 + m])) * rz;
+            }
           }
         }
+        if (fp == 0) { g[5] = c.Jb; g[6] = c.f; g[7] = c.N2bg; g[8] = raw[6]; g[9] = raw[7]; }
       }
 #pragma unroll
       for (int m = 0; m < 10; ++m) {
@@ -374,6 +413,8 @@ __global__ void __launch_bounds__(kClosureThreads, 2) k_mlp_closure(const MlpClo
         for (int q = 20; q < kCF; ++q)
           *reinterpret_cast<__nv_bfloat16*>(smem + kSX + cm_off(r, q, kCF)) = __float2bfloat16_rn(0.0f);
     }
+    // ---- prefetch the next tile's raw values: they arrive while this tile's four MMA rounds run
+    load_raw(t + gridDim.x);
     // ---- four layers
     for (int l = 0; l < 4 && ok; ++l) {
       fence_proxy_async();
@@ -397,11 +438,17 @@ __global__ void __launch_bounds__(kClosureThreads, 2) k_mlp_closure(const MlpClo
           const int cb = half * 64 + c0;
           float v[16];
           tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)cb, v);
+          float bv[16];                              // the 16 biases, four 16-byte shared loads
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float4 b4 = reinterpret_cast<const float4*>(bl + cb)[q];
+            bv[4 * q] = b4.x; bv[4 * q + 1] = b4.y; bv[4 * q + 2] = b4.z; bv[4 * q + 3] = b4.w;
+          }
           uint32_t pk[8];
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
-            const __nv_bfloat162 h2 = __floats2bfloat162_rn(gelu_f(v[2 * q] + bl[cb + 2 * q]),
-                                                            gelu_f(v[2 * q + 1] + bl[cb + 2 * q + 1]));
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(gelu_f(v[2 * q] + bv[2 * q]),
+                                                            gelu_f(v[2 * q + 1] + bv[2 * q + 1]));
             pk[q] = *reinterpret_cast<const uint32_t*>(&h2);
           }
           *reinterpret_cast<uint4*>(smem + kSH + cm_off(row, cb, kCH)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
