@@ -194,9 +194,9 @@ enum { OCN_OPT_GRAPHS = 1, OCN_OPT_SYNC_CHECK = 2, OCN_OPT_KERNEL_TIMING = 3, OC
 ocn_status ocn_set_option(ocn_model* model, int option, long long value);
 
 /* Tile variants of the FP32 tendency kernel (OCN_OPT_TENDENCY_VARIANT): 0 = 32x8
- * columns per CTA, one CTA per SM (default); 1 = 32x8, two CTAs per SM; 2 = 32x16;
- * 3 = 32x4, three CTAs per SM.  All compute the same values. */
-#define OCN_TENDENCY_VARIANTS 4
+ * columns per CTA, one CTA per SM; 1 = 32x8, two CTAs per SM; 2 = 32x16; 3 = 32x4,
+ * three CTAs per SM; 4 = 32x14 (default); 5 = 32x12.  All compute the same values. */
+#define OCN_TENDENCY_VARIANTS 6
 
 /* Autotuner: times every tendency variant on the model's current state (tendency
  * only: the state is not advanced; G is overwritten), selects the fastest and

@@ -112,7 +112,7 @@ struct ocn_model {
   char* arena = nullptr;
   int cur = 0;
   bool graphs = true, sync_check = false;
-  int variant = 0;                  // FP32 tendency tile variant
+  int variant = 4;                  // FP32 tendency tile variant (32x14: 128 registers, 16 warps, no spills)
   std::map<std::pair<uint64_t, int>, cudaGraphExec_t> graph_cache;
   int launches_per_step = 0;
   FftPlan px, py;

@@ -65,7 +65,8 @@ struct TendencyArgs {
   T top[2 + kMaxTracers], bot[2 + kMaxTracers];
   T dt_gamma, dt_zeta;    // RK coefficients times dt
   int mode;               // 0: RK update + G;  1: G only
-  int variant;            // tile variant of the FP32 kernel (0: 32x8 one CTA/SM, 1: 32x8 two, 2: 32x16, 3: 32x4 three)
+  int variant;            // tile variant of the FP32 kernel (0: 32x8 one CTA/SM, 1: 32x8 two, 2: 32x16, 3: 32x4 three,
+                          // 4: 32x14, 5: 32x12)
 };
 
 template <typename T>
@@ -140,7 +141,7 @@ template <> cudaError_t launch_tendency<float>(const TendencyArgs<float>& a, int
 template <> cudaError_t launch_tendency<double>(const TendencyArgs<double>& a, int weno_r, cudaStream_t s);
 cudaError_t launch_tendency_f32_r5(const TendencyArgs<float>& a, cudaStream_t s);
 cudaError_t launch_tendency_f32_r3(const TendencyArgs<float>& a, cudaStream_t s);
-constexpr int kTendencyVariants = 4;
+constexpr int kTendencyVariants = 6;
 template <typename T> cudaError_t launch_projection(const PoissonArgs<T>& a, cudaStream_t s, int* nlaunch,
                                                     const LaunchHook& hook = LaunchHook());
 template <typename T> cudaError_t launch_diagnostics(const DiagArgs<T>& a, cudaStream_t s);

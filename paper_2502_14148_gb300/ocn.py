@@ -24,7 +24,7 @@ OCN_FIELD_U, OCN_FIELD_V, OCN_FIELD_W, OCN_FIELD_TRACER0 = 0, 1, 2, 3
 OCN_FIELD_P, OCN_FIELD_G, OCN_FIELD_NU_E = 10, 20, 30
 OCN_FIELD_TRACER_REF0, OCN_FIELD_RAW = 40, 0x100
 OCN_OPT_GRAPHS, OCN_OPT_SYNC_CHECK, OCN_OPT_KERNEL_TIMING, OCN_OPT_TENDENCY_VARIANT = 1, 2, 3, 4
-TENDENCY_VARIANTS = 4
+TENDENCY_VARIANTS = 6
 KERNEL_CLASSES = ["closure", "tendency", "div_fftx", "fft_y", "tridiag", "gauge", "ifftx", "correct", "column_closure",
                   "vertical"]
 STEPPERS = {"rk3": 0, "qab2": 1}
