@@ -407,6 +407,11 @@ ocn_status ocn_coarse_grain(ocn_model* model, int cx, int cy, double* out, size_
 ocn_status ocn_gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, int ldb, float* D, int ldd,
                          int* status, void* stream);
 
+/* Measured FP32 FMA throughput of the current device in TFLOP/s (an FMA counts 2): independent
+ * fused multiply-add chains on every SM for about 10 ms; the measured denominator of ALU-bound
+ * rooflines.  Synchronises the stream.  Errors: OCN_ERR_ARG, OCN_ERR_CUDA. */
+ocn_status ocn_fp32_fma_peak(double* tflops, void* stream);
+
 /* Failure-detection test of the tensor-core kernels' bounded waits: launches the GEMM kernel with its
  * MMA and commit left out, so the bounded mbarrier wait runs out after about 0.5 s; the kernel sets
  * *status (device int) to 1, waits once more (bounded), frees its tensor memory and returns, leaving

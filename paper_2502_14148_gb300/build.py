@@ -19,7 +19,7 @@ OBJ = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libocn.so")
 SOURCES = ["capi.cu", "coeffs.cpp", "tendency_f32_r5.cu", "tendency_f32_r3.cu", "tendency_f64.cu", "closure.cu",
-           "poisson.cu", "reduce.cu", "noalloc.cu", "mlp.cu", "column.cu", "vertical.cu"]
+           "poisson.cu", "reduce.cu", "noalloc.cu", "mlp.cu", "column.cu", "vertical.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -46,7 +46,8 @@ EXPORTS = ["ocn_abi_version", "ocn_last_error", "ocn_grid_create", "ocn_grid_des
            "ocn_mlp_arena_bytes", "ocn_mlp_bind_arena", "ocn_mlp_num_params", "ocn_mlp_set_params",
            "ocn_mlp_get_params", "ocn_mlp_forward", "ocn_mlp_gradients", "ocn_mlp_adam", "ocn_mlp_train_step",
            "ocn_gemm_bf16", "ocn_set_column_closure", "ocn_closure_features", "ocn_column_fluxes",
-           "ocn_coarse_grain", "ocn_set_time_stepper", "ocn_set_vertical_diffusivity", "ocn_gemm_timeout_test"]
+           "ocn_coarse_grain", "ocn_set_time_stepper", "ocn_set_vertical_diffusivity", "ocn_gemm_timeout_test",
+           "ocn_fp32_fma_peak"]
 OCN_OPT_ENSEMBLE_MODE, OCN_ENSEMBLE_CONCURRENT, OCN_ENSEMBLE_SEQUENTIAL = 5, 0, 1
 
 
@@ -144,6 +145,7 @@ def lib(path: str = LIB_PATH):
     L.ocn_column_fluxes.argtypes = [vp, C.c_int, vp]
     L.ocn_coarse_grain.argtypes = [vp, C.c_int, C.c_int, vp, sz]
     L.ocn_gemm_timeout_test.argtypes = [vp, vp]
+    L.ocn_fp32_fma_peak.argtypes = [dp, vp]
     L.ocn_gemm_bf16.argtypes = [C.c_int, C.c_int, C.c_int, vp, C.c_int, vp, C.c_int, vp, C.c_int, vp, vp]
     for name in EXPORTS:
         if name not in ("ocn_abi_version", "ocn_last_error", "ocn_grid_destroy", "ocn_model_destroy", "ocn_ensemble_destroy",
@@ -660,3 +662,12 @@ class MLP:
                                             C.c_void_p(m.data_ptr()), X.shape[0], float(lr), C.byref(loss)),
                    "ocn_mlp_train_step")
         return loss.value
+
+
+def fp32_fma_peak(stream=None) -> float:
+    """Measured FP32 FMA throughput of the current device (TFLOP/s, FMA = 2 flops)."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    out = C.c_double()
+    _check(lib().ocn_fp32_fma_peak(C.byref(out), C.c_void_p(s.cuda_stream)), "ocn_fp32_fma_peak")
+    return out.value
