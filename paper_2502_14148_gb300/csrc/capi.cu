@@ -106,7 +106,7 @@ struct ocn_model {
   size_t bytes = 0;
   size_t off_state[2][3 + OCN_MAX_TRACERS];
   size_t off_G[3 + OCN_MAX_TRACERS];
-  size_t off_p = 0, off_nu = 0, off_kap[OCN_MAX_TRACERS], off_spec = 0, off_cpiv = 0;
+  size_t off_p = 0, off_nu = 0, off_kap[OCN_MAX_TRACERS], off_spec = 0, off_cpiv = 0, off_pinv = 0;
   size_t off_dzc = 0, off_rdzc = 0, off_dzf = 0, off_rdzf = 0, off_lamx = 0, off_lamy = 0, off_twx = 0, off_twy = 0;
   size_t off_partial = 0, off_diag = 0;
   char* arena = nullptr;
@@ -236,6 +236,7 @@ void layout(ocn_model* m) {
   const size_t S = (size_t)(g->Nx / 2 + 1) * g->Ny * g->Nz;
   m->off_spec = take(2 * es * S);
   m->off_cpiv = take(es * S);
+  m->off_pinv = take(es * S);
   m->off_dzc = take(es * g->Nz);
   m->off_rdzc = take(es * g->Nz);
   m->off_dzf = take(es * (g->Nz + 1));
@@ -293,6 +294,7 @@ PoissonArgs<T> poisson_args(const ocn_model* m, int which, double dts) {
   a.p = at<T>(m, m->off_p);
   a.spec = at<T>(m, m->off_spec);
   a.cpiv = at<T>(m, m->off_cpiv);
+  a.pinv = at<T>(m, m->off_pinv);
   a.rdzc = at<T>(m, m->off_rdzc); a.rdzf = at<T>(m, m->off_rdzf); a.dzc = at<T>(m, m->off_dzc);
   a.lamx = at<T>(m, m->off_lamx); a.lamy = at<T>(m, m->off_lamy);
   a.twx = at<T>(m, m->off_twx); a.twy = at<T>(m, m->off_twy);
@@ -674,6 +676,10 @@ ocn_status ocn_model_bind_arena(ocn_model* m, void* device_ptr, size_t bytes) {
   std::vector<char> blob = (m->es == 4) ? metrics_blob<float>(m) : metrics_blob<double>(m);
   e = cudaMemcpyAsync(m->arena + m->off_dzc, blob.data(), blob.size(), cudaMemcpyHostToDevice, m->stream);
   if (e != cudaSuccess) return cuda_fail(e, "upload metrics");
+  // the projection's tridiagonal systems depend only on the grid: factor them once
+  e = (m->es == 4) ? launch_tridiag_factor<float>(poisson_args<float>(m, 0, 1.0), m->stream)
+                   : launch_tridiag_factor<double>(poisson_args<double>(m, 0, 1.0), m->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "tridiagonal factorisation");
   std::vector<float> depth;
   if (m->off_depth) {
     for (int k = 0; k <= m->g->Nz; ++k) depth.push_back((float)(m->g->zf[m->g->Nz] - m->g->zf[k]));

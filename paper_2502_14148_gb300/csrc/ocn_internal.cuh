@@ -98,7 +98,8 @@ struct PoissonArgs {
   T* u; T* v; T* w;            // velocity to project (in place)
   T* p;                        // pressure out
   T* spec;                     // complex [Nz][Ny][Nx/2+1] interleaved (re, im)
-  T* cpiv;                     // Thomas pivots [Nz][Ny][Nx/2+1] (when fp64 pivots: double storage)
+  T* cpiv;                     // Thomas pivots c' [Nz][Ny][Nx/2+1]
+  T* pinv;                     // 1 / Thomas diagonal [Nz][Ny][Nx/2+1] when stored (else null: computed per solve)
   const T* rdzc; const T* rdzf; const T* dzc;
   const T* lamx;               // [Nx/2+1]
   const T* lamy;               // [Ny]
@@ -145,6 +146,9 @@ constexpr int kTendencyVariants = 6;
 template <typename T> cudaError_t launch_projection(const PoissonArgs<T>& a, cudaStream_t s, int* nlaunch,
                                                     const LaunchHook& hook = LaunchHook());
 template <typename T> cudaError_t launch_diagnostics(const DiagArgs<T>& a, cudaStream_t s);
+// Factor the projection's tridiagonal systems once (they depend only on the grid): fills a.cpiv
+// and a.pinv, the pivots computed in FP64 when a.fp64_pivots.
+template <typename T> cudaError_t launch_tridiag_factor(const PoissonArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_fill(T* p, size_t n, T v, cudaStream_t s);
 template <typename T> cudaError_t launch_shift(T* p, size_t n, T v, cudaStream_t s);
 // Per-level horizontal means (FP64) used by the coarse-graining profiles:

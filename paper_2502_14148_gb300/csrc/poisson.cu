@@ -229,7 +229,22 @@ __global__ void __launch_bounds__(256) k_fft_y(const PoissonArgs<T> a, int CW, i
 
 // Thomas algorithm per horizontal wavenumber.  a_k p_{k-1} + b_k p_k + c_k p_{k+1} = r_k,
 // a_k = 1/(dzc_k dzf_k), c_k = 1/(dzc_k dzf_{k+1}) (zero at the walls: Neumann),
-// b_k = -(a_k + c_k) + lambda_x + lambda_y.
+// b_k = -(a_k + c_k) + lambda_x + lambda_y; the (0,0) column's first row is p_0 = 0 (gauge).
+// The coefficients depend only on the grid, so the elimination is factored once
+// (k_tridiag_factor: c'_k and 1/(b_k - a_k c'_{k-1}) in precision P, stored in T) and each solve
+// is two sweeps of multiply-adds (k_tridiag_solve), levels moved in batches of kTriChunk so that
+// their loads are issued together.  k_tridiag factors and solves in one pass (for callers
+// without the factor arrays).
+template <typename T, typename P>
+__device__ __forceinline__ void tri_coeffs(const PoissonArgs<T>& a, int k, int Nz, P lam, bool gauge, P& ak, P& bk,
+                                           P& ck) {
+  const P rz = (P)__ldg(a.rdzc + k);
+  ak = (k > 0) ? rz * (P)__ldg(a.rdzf + k) : P(0);
+  ck = (k < Nz - 1) ? rz * (P)__ldg(a.rdzf + k + 1) : P(0);
+  bk = -(ak + ck) + lam;
+  if (gauge && k == 0) { ak = P(0); bk = P(1); ck = P(0); }
+}
+
 template <typename T, typename P>
 __global__ void __launch_bounds__(256) k_tridiag(const PoissonArgs<T> a) {
   typedef typename CT<T>::type C;
@@ -245,12 +260,10 @@ __global__ void __launch_bounds__(256) k_tridiag(const PoissonArgs<T> a) {
   P cprev = P(0);
   C dprev = {T(0), T(0)};
   for (int k = 0; k < Nz; ++k) {
-    const P rz = (P)__ldg(a.rdzc + k);
-    P ak = (k > 0) ? rz * (P)__ldg(a.rdzf + k) : P(0);
-    P ck = (k < Nz - 1) ? rz * (P)__ldg(a.rdzf + k + 1) : P(0);
-    P bk = -(ak + ck) + lam;
+    P ak, bk, ck;
+    tri_coeffs<T, P>(a, k, Nz, lam, gauge, ak, bk, ck);
     C r = x[(size_t)k * pl];
-    if (gauge && k == 0) { ak = P(0); bk = P(1); ck = P(0); r = C{T(0), T(0)}; }
+    if (gauge && k == 0) r = C{T(0), T(0)};
     const P inv = P(1) / (bk - ak * cprev);
     cprev = ck * inv;
     const T ti = (T)inv, ta = (T)ak;
@@ -267,6 +280,89 @@ __global__ void __launch_bounds__(256) k_tridiag(const PoissonArgs<T> a) {
     d.y -= c * pn.y;
     x[(size_t)k * pl] = d;
     pn = d;
+  }
+}
+
+template <typename T, typename P>
+__global__ void __launch_bounds__(256) k_tridiag_factor(const PoissonArgs<T> a) {
+  const int S = a.Mx + 1, Ny = a.Ny, Nz = a.Nz;
+  const int kx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ky = blockIdx.y;
+  if (kx >= S) return;
+  const size_t pl = (size_t)Ny * S, o = (size_t)ky * S + kx;
+  const P lam = (P)__ldg(a.lamx + kx) + (P)__ldg(a.lamy + ky);
+  const bool gauge = (kx == 0 && ky == 0);
+  P cprev = P(0);
+  for (int k = 0; k < Nz; ++k) {
+    P ak, bk, ck;
+    tri_coeffs<T, P>(a, k, Nz, lam, gauge, ak, bk, ck);
+    const P inv = P(1) / (bk - ak * cprev);
+    cprev = ck * inv;
+    a.pinv[(size_t)k * pl + o] = (T)inv;
+    a.cpiv[(size_t)k * pl + o] = (T)cprev;
+  }
+}
+
+constexpr int kTriChunk = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_tridiag_solve(const PoissonArgs<T> a) {
+  typedef typename CT<T>::type C;
+  const int S = a.Mx + 1, Ny = a.Ny, Nz = a.Nz;
+  const int kx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ky = blockIdx.y;
+  if (kx >= S) return;
+  const size_t pl = (size_t)Ny * S, o = (size_t)ky * S + kx;
+  C* x = reinterpret_cast<C*>(a.spec) + o;
+  const T* cp = a.cpiv + o;
+  const T* pinv = a.pinv + o;
+  const bool gauge = (kx == 0 && ky == 0);
+  C dprev = {T(0), T(0)};
+  for (int k0 = 0; k0 < Nz; k0 += kTriChunk) {
+    C r[kTriChunk];
+    T iv[kTriChunk];
+#pragma unroll
+    for (int u = 0; u < kTriChunk; ++u) {
+      const int k = k0 + u;
+      r[u] = (k < Nz) ? x[(size_t)k * pl] : C{T(0), T(0)};
+      iv[u] = (k < Nz) ? __ldg(pinv + (size_t)k * pl) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kTriChunk; ++u) {
+      const int k = k0 + u;
+      if (k < Nz) {
+        const T ta = (k > 0) ? __ldg(a.rdzc + k) * __ldg(a.rdzf + k) : T(0);
+        C rr = r[u];
+        if (gauge && k == 0) rr = C{T(0), T(0)};
+        dprev = C{(rr.x - ta * dprev.x) * iv[u], (rr.y - ta * dprev.y) * iv[u]};
+        r[u] = dprev;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kTriChunk; ++u)
+      if (k0 + u < Nz) x[(size_t)(k0 + u) * pl] = r[u];
+  }
+  C pn = dprev;
+  for (int k1 = Nz - 2; k1 >= 0; k1 -= kTriChunk) {
+    C d[kTriChunk];
+    T c[kTriChunk];
+#pragma unroll
+    for (int u = 0; u < kTriChunk; ++u) {
+      const int k = k1 - u;
+      d[u] = (k >= 0) ? x[(size_t)k * pl] : C{T(0), T(0)};
+      c[u] = (k >= 0) ? __ldg(cp + (size_t)k * pl) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kTriChunk; ++u) {
+      if (k1 - u >= 0) {
+        d[u].x -= c[u] * pn.x;
+        d[u].y -= c[u] * pn.y;
+        pn = d[u];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kTriChunk; ++u)
+      if (k1 - u >= 0) x[(size_t)(k1 - u) * pl] = d[u];
   }
 }
 
@@ -343,7 +439,8 @@ cudaError_t launch_projection(const PoissonArgs<T>& a, cudaStream_t s, int* nlau
   ++n;
   dim3 gt((a.Mx + 1 + 127) / 128, a.Ny);
   hook.pre(OCN_K_TRIDIAG);
-  if (a.fp64_pivots) k_tridiag<T, double><<<gt, 128, 0, s>>>(a);
+  if (a.pinv) k_tridiag_solve<T><<<gt, 128, 0, s>>>(a);
+  else if (a.fp64_pivots) k_tridiag<T, double><<<gt, 128, 0, s>>>(a);
   else k_tridiag<T, T><<<gt, 128, 0, s>>>(a);
   hook.post(OCN_K_TRIDIAG);
   ++n;
@@ -367,6 +464,17 @@ cudaError_t launch_projection(const PoissonArgs<T>& a, cudaStream_t s, int* nlau
   if (nlaunch) *nlaunch = n;
   return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_tridiag_factor(const PoissonArgs<T>& a, cudaStream_t s) {
+  if (!a.pinv || !a.cpiv) return cudaErrorInvalidValue;
+  dim3 gt((a.Mx + 1 + 127) / 128, a.Ny);
+  if (a.fp64_pivots) k_tridiag_factor<T, double><<<gt, 128, 0, s>>>(a);
+  else k_tridiag_factor<T, T><<<gt, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+template cudaError_t launch_tridiag_factor<float>(const PoissonArgs<float>&, cudaStream_t);
+template cudaError_t launch_tridiag_factor<double>(const PoissonArgs<double>&, cudaStream_t);
 
 template cudaError_t launch_projection<float>(const PoissonArgs<float>&, cudaStream_t, int*, const LaunchHook&);
 template cudaError_t launch_projection<double>(const PoissonArgs<double>&, cudaStream_t, int*, const LaunchHook&);
