@@ -1,6 +1,8 @@
 // Eddy diffusivities (Smagorinsky-Lilly, AMD) at cell centres.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "ocn_internal.cuh"
 
 namespace ocn {
@@ -35,14 +37,30 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_closure(const C
       return a.g_alpha * (__ldg(a.cur.c[0] + o) + cref(0, kk) - a.T0) - a.g_beta * (__ldg(a.cur.c[1] + o) + cref(1, kk) - a.S0);
     return __ldg(a.cur.c[0] + o) + cref(0, kk);
   };
+  // this CTA's chunk of levels [kb, ke) (blockIdx.z); the march state is set up at kb from the level
+  // below, so chunks are independent
+  const int nch = gridDim.z, per = (Nz + nch - 1) / nch;
+  const int kb = blockIdx.z * per, ke = min(Nz, kb + per);
+  if (kb >= ke) return;
+  const size_t Lb = (size_t)kb * plane;
   // carried from level to level: u at (i|ip, j) and v at (i, j|jp) on the current level, w on face k,
   // the two lower-face z-derivatives, b below
-  T u0 = __ldg(U + c00), u1 = __ldg(U + cp0);
-  T v0 = __ldg(V + c00), v1 = __ldg(V + c0p);
-  T w00 = __ldg(W + c00), wm0 = __ldg(W + cm0), wp0 = __ldg(W + cp0), w0m = __ldg(W + c0m), w0p = __ldg(W + c0p);
+  T u0 = __ldg(U + Lb + c00), u1 = __ldg(U + Lb + cp0);
+  T v0 = __ldg(V + Lb + c00), v1 = __ldg(V + Lb + c0p);
+  T w00 = __ldg(W + Lb + c00), wm0 = __ldg(W + Lb + cm0), wp0 = __ldg(W + Lb + cp0), w0m = __ldg(W + Lb + c0m),
+    w0p = __ldg(W + Lb + c0p);
   T dudz_lo0 = T(0), dudz_lo1 = T(0), dvdz_lo0 = T(0), dvdz_lo1 = T(0);   // faces at k (walls: 0)
-  T b_prev = T(0), b_cur = (a.closure == OCN_CLOSURE_SMAGORINSKY) ? buoy(0) : T(0);
-  for (int k = 0; k < Nz; ++k) {
+  if (kb > 0) {
+    const size_t Lm = Lb - plane;
+    const T r = __ldg(a.rdzf + kb);
+    dudz_lo0 = (u0 - __ldg(U + Lm + c00)) * r;
+    dudz_lo1 = (u1 - __ldg(U + Lm + cp0)) * r;
+    dvdz_lo0 = (v0 - __ldg(V + Lm + c00)) * r;
+    dvdz_lo1 = (v1 - __ldg(V + Lm + c0p)) * r;
+  }
+  const bool smag = (a.closure == OCN_CLOSURE_SMAGORINSKY);
+  T b_prev = (smag && kb > 0) ? buoy(kb - 1) : T(0), b_cur = smag ? buoy(kb) : T(0);
+  for (int k = kb; k < ke; ++k) {
     const size_t L = (size_t)k * plane, L1 = L + plane;
     const T rdzc = __ldg(a.rdzc + k);
     const T rdzf1 = (k + 1 < Nz) ? __ldg(a.rdzf + k + 1) : T(0);
@@ -134,7 +152,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_closure(const C
 template <typename T>
 cudaError_t launch_closure(const ClosureArgs<T>& a, cudaStream_t s) {
   dim3 blk(32, 8);
-  dim3 grid((a.Nx + 31) / 32, (a.Ny + 7) / 8);
+  // z chunks so that small horizontal grids still fill the GPU (about a million threads), each
+  // chunk at least 16 levels deep
+  const long long cols = (long long)a.Nx * a.Ny;
+  int nch = (int)((1000000 + cols - 1) / cols);
+  nch = std::max(1, std::min(nch, a.Nz / 16));
+  dim3 grid((a.Nx + 31) / 32, (a.Ny + 7) / 8, nch);
   k_closure<T><<<grid, blk, 0, s>>>(a);
   return cudaGetLastError();
 }
