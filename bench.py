@@ -401,8 +401,9 @@ def run_ours(args, world, rank, local):
 
 
 def run_ensemble(args, world, rank, local):
-    """Batched ensemble: every member advanced by one graph launch per step (members concurrent),
-    against sequential per-member launches on the same GPU."""
+    """Ensemble of uneven members: one graph per step in which every kernel is one batched launch
+    over all members (the headline), against the same graph with a branch of per-member launches
+    per member (concurrent) and against members stepped one after the other, on the same GPU."""
     import torch
     from paper_2502_14148_gb300 import build, inputs, ocn
     if rank == 0 or world == 1:
@@ -410,6 +411,8 @@ def run_ensemble(args, world, rank, local):
     barrier(world)
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    if args.ensemble_mode is None:
+        args.ensemble_mode = "concurrent"
     ps = inputs.ensemble_configs(n=args.members)
     cells = sum(p["Nx"] * p["Ny"] * p["Nz"] for p in ps)
     E = ocn.Ensemble(ps, device=dev)
@@ -418,11 +421,13 @@ def run_ensemble(args, world, rank, local):
     variants = E.autotune()
     dt = ps[0]["dt"]
     timings = {}
-    for mode in ("concurrent", "sequential"):
-        E.set_mode(sequential=(mode == "sequential"))
+    launches = {}
+    for mode in (args.ensemble_mode,) + tuple(m for m in ("batched", "concurrent", "sequential") if m != args.ensemble_mode):
+        E.set_mode(mode)
         E.time_step(dt, args.warmup)
         E.synchronize()
-        ck = ClockSampler(local) if mode == "concurrent" else None
+        launches[mode] = E.launches_per_step()
+        ck = ClockSampler(local) if mode == args.ensemble_mode else None
         barrier(world)
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -434,20 +439,26 @@ def run_ensemble(args, world, rank, local):
         timings[mode] = (max_over_ranks(e0.elapsed_time(e1), world), ck.stop() if ck else None)
     if rank != 0:
         return 0
-    ms_c, clocks = timings["concurrent"]
+    ms_c, clocks = timings[args.ensemble_mode]
     ms_s, _ = timings["sequential"]
     val = cells * 3 * args.steps * world / (ms_c * 1e-3)
+    mode_text = {"batched": "one CUDA graph per step; every kernel one launch over all members (work list of "
+                            "(member, block))",
+                 "concurrent": "one CUDA graph per step, a branch of per-member launches per member",
+                 "sequential": "members stepped one after the other (each with its own graph)"}
+    others = {m: {"value": cells * 3 * args.steps * world / (timings[m][0] * 1e-3),
+                  "ms_per_step": timings[m][0] / args.steps, "launches_per_step": launches[m], "mode": mode_text[m]}
+              for m in timings if m != args.ensemble_mode}
     d = E.members[0].diagnostics(dt)
     line = {"metric": "cell-RK3-substeps/sec", "value": val, "unit": "cell-substeps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_c / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"ensemble of {len(ps)} CBL LES members ({cells/1e6:.1f} M cells; Nx=Ny in "
                                    f"{{64,96,128}}, Nz in {{64,80,96}}, WENO5, AMD, FP32, dt={dt} s)",
-                       "mode": "one CUDA graph per step, members on concurrent branches",
+                       "mode": mode_text[args.ensemble_mode],
                        "tendency_variants": sorted(set(variants))},
-            "gpu_launches": E.launches_per_step() * args.steps,
-            "sequential": {"value": cells * 3 * args.steps * world / (ms_s * 1e-3), "ms_per_step": ms_s / args.steps,
-                           "mode": "members stepped one after the other (each with its own graph)"},
+            "gpu_launches": launches[args.ensemble_mode] * args.steps,
+            "other_modes": others,
             "speedup_vs_sequential": ms_s / ms_c, "clocks": clocks,
             "checks": {"member0_max_div": d["max_div"], "member0_nonfinite": d["nonfinite"]}}
     print(json.dumps(line), flush=True)
@@ -467,6 +478,8 @@ def run_closure(args, world, rank, local):
     barrier(world)
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    if args.ensemble_mode is None:
+        args.ensemble_mode = "batched"
     t0 = time.time()
     res = closure.experiment(n_members=32, n_train=24, t_end=3 * 3600.0, dt=10.0, every=180, train_steps=2000,
                              log=lambda *a: None)
@@ -481,10 +494,12 @@ def run_closure(args, world, rank, local):
     timings = {}
     for mode in ("plain", "learned"):
         E = ocn.Ensemble(ps, device=dev)
+        E.set_mode(args.ensemble_mode)
         for i, p in enumerate(ps):
             E.members[i].set(**inputs.initial_state(p, seed=inputs.SEED + i + 1000 * rank))
             if mode == "learned":
                 E.members[i].set_column_closure(*cl(p), p["N2"])
+        E.autotune()
         E.time_step(dt, args.warmup)
         E.synchronize()
         ck = ClockSampler(local) if mode == "learned" else None
@@ -534,7 +549,10 @@ def run_closure(args, world, rank, local):
             "config": {"workload": f"{len(ps)} coarse CBL instances of 16x16 columns ({cells/1e6:.2f} M cells, "
                                    f"{faces/1e6:.2f} M closure faces per substage; Nz in {{64,80,96}}, WENO5, "
                                    f"AMD + learned column closure, FP32, dt={dt} s)",
-                       "mode": "one CUDA graph per ensemble step, members on concurrent branches"},
+                       "mode": {"batched": "one CUDA graph per ensemble step; every kernel one launch over all "
+                                            "members", "concurrent": "one CUDA graph per ensemble step, members on "
+                                            "concurrent branches", "sequential": "members one after the other"}[
+                                                args.ensemble_mode]},
             "gpu_launches": launches * args.steps,
             "plain_amd": {"value": cells * 3 * args.steps * world / (ms_p * 1e-3), "ms_per_step": ms_p / args.steps},
             "closure_overhead": ms_l / ms_p,
@@ -619,6 +637,9 @@ def main():
                     help="instances: ensemble members (--workload ensemble, default 64) or coarse instances "
                          "(--workload closure, default 256)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ensemble-mode", default=None, choices=["batched", "concurrent", "sequential"],
+                    help="how the ensemble and closure workloads step their members (default: concurrent for "
+                         "the ensemble of fine members, batched for the coarse instances of the closure workload)")
     ap.add_argument("--stepper", default="rk3", choices=["rk3", "qab2"], help="time stepper (default RK3)")
     ap.add_argument("--vertical", default="none", choices=["none", "explicit", "implicit"],
                     help="add a vertical diffusivity profile, explicit or semi-implicit")

@@ -195,11 +195,13 @@ ocn_status ocn_set_option(ocn_model* model, int option, long long value);
 
 /* Tile variants of the FP32 tendency kernel (OCN_OPT_TENDENCY_VARIANT): 0 = 32x8
  * columns per CTA, one CTA per SM; 1 = 32x8, two CTAs per SM; 2 = 32x16; 3 = 32x4,
- * three CTAs per SM; 4 = 32x14 (default); 5 = 32x12.  All compute the same values. */
-#define OCN_TENDENCY_VARIANTS 6
+ * three CTAs per SM; 4 = 32x14 (default); 5 = 32x12; 6 = 16x16, two CTAs per SM (for grids
+ * under 32 columns wide).  All compute the same values. */
+#define OCN_TENDENCY_VARIANTS 7
 
 /* Autotuner: times every tendency variant on the model's current state (tendency
- * only: the state is not advanced; G is overwritten), selects the fastest and
+ * only: the state is not advanced; G is overwritten, so a QAB2 model restarts with
+ * its Euler step), selects the fastest and
  * returns its index in *best and the milliseconds per launch of every variant in
  * ms[OCN_TENDENCY_VARIANTS] (either may be NULL).  Synchronises the stream.
  * Errors: OCN_ERR_STATE (no arena), OCN_ERR_CUDA. */
@@ -244,14 +246,28 @@ ocn_status ocn_regrid(const double* zf_in, int nin, const double* in, const doub
 /* Ensembles: n independent members (own grids, forcings and sizes, one precision) stepped together.
  * Members share one device arena and the ensemble's stream; ocn_ensemble_member returns a borrowed
  * model handle (set/get/project/diagnostics/profiles; do not destroy it).  ocn_ensemble_time_step
- * advances every member by nsteps RK3 steps: in OCN_ENSEMBLE_CONCURRENT mode (default) each step is
- * one CUDA graph launch whose independent per-member branches run concurrently; in
- * OCN_ENSEMBLE_SEQUENTIAL mode members are stepped one after the other (the comparison baseline).
- * ocn_ensemble_autotune picks the tendency tile variant once per member shape (variants[n] receives
- * the choices; may be NULL).  Errors as for the single-model calls. */
+ * advances every member by nsteps steps in one of three modes (OCN_OPT_ENSEMBLE_MODE):
+ *  - OCN_ENSEMBLE_CONCURRENT (default): each step is one CUDA graph launch whose independent
+ *    per-member branches of per-member kernels run concurrently;
+ *  - OCN_ENSEMBLE_BATCHED: each step is one graph in which every kernel of the step is one launch
+ *    over all members whose kernel sequences agree (same order, closure, tracers, stepper, tile
+ *    variant; a learned closure with one shared network and feature normalisation).  Its blocks
+ *    are the concatenation of the members' grids, each block taking its member's arguments from a
+ *    device work list, so uneven sizes share a launch.  The members of such a group are split
+ *    into OCN_OPT_ENSEMBLE_BRANCHES graph branches (1..64, default 4; balanced by cell count)
+ *    whose launches overlap;
+ *  - OCN_ENSEMBLE_SEQUENTIAL: members are stepped one after the other (the comparison baseline).
+ * All modes give the same results bit for bit.  ocn_ensemble_autotune picks the tendency tile
+ * variants in context: it times every member's tendency kernel launched together as in a step of
+ * the ensemble's mode (batched launches, or each member on its own branch), first with one
+ * variant for all FP32 members, then other variants per member shape (Nx, Ny, Nz, order,
+ * closure, tracers), keeping a change only when the whole pass gets more than 2 % faster; call it
+ * after choosing the mode.  variants[n] receives the choices (may be NULL).  Like ocn_autotune it
+ * overwrites G (QAB2 members restart with their Euler step).  Errors as for the single-model
+ * calls. */
 typedef struct ocn_ensemble ocn_ensemble;
-enum { OCN_OPT_ENSEMBLE_MODE = 5 };
-enum { OCN_ENSEMBLE_CONCURRENT = 0, OCN_ENSEMBLE_SEQUENTIAL = 1 };
+enum { OCN_OPT_ENSEMBLE_MODE = 5, OCN_OPT_ENSEMBLE_BRANCHES = 6 };
+enum { OCN_ENSEMBLE_CONCURRENT = 0, OCN_ENSEMBLE_SEQUENTIAL = 1, OCN_ENSEMBLE_BATCHED = 2 };
 ocn_status ocn_ensemble_create(int n, const ocn_grid_desc* grids, const ocn_model_desc* models, void* stream,
                                ocn_ensemble** out);
 void ocn_ensemble_destroy(ocn_ensemble* ensemble);

@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libocn.so")
-SOURCES = ["capi.cu", "coeffs.cpp", "tendency_f32_r5.cu", "tendency_f32_r3.cu", "tendency_f64.cu", "closure.cu",
+SOURCES = ["capi.cu", "coeffs.cpp", "tendency_f32_r5.cu", "tendency_f32_r3.cu", "tendency_f64.cu", "tendency_f32_r5_batch.cu",
+           "tendency_f32_r3_batch.cu", "tendency_f64_batch.cu", "closure.cu",
            "poisson.cu", "reduce.cu", "noalloc.cu", "mlp.cu", "column.cu", "vertical.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -46,7 +47,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OBJ, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     headers = [os.path.join(CSRC, "ocn_internal.cuh"), os.path.join(CSRC, "tendency_kernel.cuh"),
-               os.path.join(CSRC, "column.cuh"),
+               os.path.join(CSRC, "column.cuh"), os.path.join(CSRC, "batch.cuh"),
                os.path.join(ROOT, "include", "ocn.h")]
     flags = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
              "-I" + os.path.join(ROOT, "include")] + ARCH

@@ -174,11 +174,13 @@ def coarse_run(members, init_states, t_end: float, dt: float, every: int, closur
     a function p -> that tuple (per-member scales), or None (plain AMD).  Returns per-member
     profile series at the snapshot steps."""
     ens = ocn.Ensemble(members)
+    ens.set_mode("batched")        # coarse instances are small: one launch per kernel for all of them
     for p, m, st in zip(members, ens.members, init_states):
         m.set(project=False, **st)
         if closure is not None:
             net, mu, sigma, scale = closure(p) if callable(closure) else closure
             m.set_column_closure(net, mu, sigma, scale, p["N2"])
+    ens.autotune()
     n = _time_steps(t_end, dt)
     series = [[] for _ in members]
     for step in range(0, n + 1, every):

@@ -14,6 +14,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <new>
@@ -21,9 +22,31 @@
 #include <type_traits>
 #include <vector>
 
+#include "batch.cuh"
 #include "ocn_internal.cuh"
 
 using namespace ocn;
+
+namespace ocn {
+LaunchRecorder*& active_recorder() {
+  static thread_local LaunchRecorder* r = nullptr;
+  return r;
+}
+
+cudaError_t raise_smem_limit(const void* fn, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> limit;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = limit[{dev, fn}];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
+}  // namespace ocn
 
 namespace {
 
@@ -114,6 +137,7 @@ struct ocn_model {
   bool graphs = true, sync_check = false;
   int variant = 4;                  // FP32 tendency tile variant (32x14: 128 registers, 16 warps, no spills)
   std::map<std::pair<uint64_t, int>, cudaGraphExec_t> graph_cache;
+  unsigned graph_epoch = 0;        // bumped whenever captured graphs go stale (ensemble graphs key on it)
   int launches_per_step = 0;
   FftPlan px, py;
   // Tracers are stored as anomalies about a per-level reference profile (their
@@ -160,8 +184,10 @@ struct ocn_ensemble {
   std::vector<size_t> offs;
   size_t bytes = 0;
   char* arena = nullptr;
-  int mode = 0;                              // 0: one graph per step, members concurrent; 1: sequential
+  int mode = 0;                              // OCN_ENSEMBLE_CONCURRENT, _SEQUENTIAL or _BATCHED
+  int branches = 4;                          // batched mode: graph branches per group of members
   std::map<std::string, cudaGraphExec_t> graphs;
+  std::map<std::string, void*> graph_tables;  // device work lists of the batched graphs
   int launches_per_step = 0;
 };
 
@@ -540,6 +566,7 @@ ocn_status time_step_t(ocn_model* m, double dt, int nsteps) {
 void drop_graphs(ocn_model* m) {
   for (auto& kv : m->graph_cache) cudaGraphExecDestroy(kv.second);
   m->graph_cache.clear();
+  ++m->graph_epoch;
 }
 
 void drop_events(ocn_model* m) {
@@ -918,6 +945,7 @@ ocn_status ocn_autotune(ocn_model* m, int* best, double* ms) {
   if (e != cudaSuccess) { m->variant = saved; return cuda_fail(e, "autotune"); }
   if (arg != saved) drop_graphs(m);
   m->variant = arg;
+  m->ab_started = false;            // G was overwritten: QAB2 restarts with its Euler step
   if (best) *best = arg;
   return OCN_OK;
 }
@@ -1111,6 +1139,18 @@ ocn_status ocn_regrid(const double* zf_in, int nin, const double* in, const doub
 
 // ------------------------------------------------------------------------------------------
 // Ensembles: many independent members stepped together.
+}  // extern "C"
+
+namespace {
+void clear_graphs(ocn_ensemble* e) {
+  for (auto& kv : e->graphs) cudaGraphExecDestroy(kv.second);
+  e->graphs.clear();
+  for (auto& kv : e->graph_tables) cudaFree(kv.second);
+  e->graph_tables.clear();
+}
+}  // namespace
+
+extern "C" {
 
 ocn_status ocn_ensemble_create(int n, const ocn_grid_desc* grids, const ocn_model_desc* models, void* stream,
                                ocn_ensemble** out) {
@@ -1158,8 +1198,7 @@ void ocn_ensemble_destroy(ocn_ensemble* e) {
   if (!e) return;
   {
     DeviceGuard dg(e->dev);
-    for (auto& kv : e->graphs) cudaGraphExecDestroy(kv.second);
-    e->graphs.clear();
+    clear_graphs(e);
     for (cudaStream_t fs : e->fork_streams) cudaStreamDestroy(fs);
     for (cudaEvent_t ev : e->join) cudaEventDestroy(ev);
     if (e->fork) cudaEventDestroy(e->fork);
@@ -1179,8 +1218,7 @@ ocn_status ocn_ensemble_bind_arena(ocn_ensemble* e, void* device_ptr, size_t byt
   if (!e || !device_ptr) return fail(OCN_ERR_ARG, "null argument");
   if (bytes < e->bytes) return fail(OCN_ERR_ARG, "arena smaller than ocn_ensemble_arena_bytes()");
   if (reinterpret_cast<uintptr_t>(device_ptr) % 256) return fail(OCN_ERR_ARG, "arena must be 256-byte aligned");
-  for (auto& kv : e->graphs) cudaGraphExecDestroy(kv.second);
-  e->graphs.clear();
+  clear_graphs(e);
   e->arena = reinterpret_cast<char*>(device_ptr);
   for (int i = 0; i < e->n; ++i) {
     ocn_status st = ocn_model_bind_arena(e->models[i], e->arena + e->offs[i], e->models[i]->bytes);
@@ -1198,6 +1236,200 @@ ocn_status ocn_ensemble_member(ocn_ensemble* e, int i, ocn_model** out) {
 }  // extern "C"
 
 namespace {
+
+// Batched ensemble step (OCN_ENSEMBLE_BATCHED).  Every member's step is first recorded (the
+// launch functions append their kernels and arguments instead of launching); members whose
+// kernel sequences agree form a group, and each kernel of a group's sequence becomes one launch
+// of its batched form over the group's members (work list: member m owns a contiguous range of
+// the flattened blocks).  A group is split into up to e->branches branches of about equal cell
+// counts; branches run concurrently.
+struct BatchLaunch {
+  const void* fn;
+  dim3 grid, block;
+  size_t smem;
+  int carveout;
+  int n;                                // members in the launch
+  unsigned stride;                      // payload bytes per member
+  size_t start_off, dims_off, payload_off;   // byte offsets of the work-list parts in the table buffer
+  int branch;
+};
+struct BatchPlan {
+  std::vector<BatchLaunch> launches;
+  int nbranch = 0;
+  void* dtab = nullptr;                 // device copy of the work lists (owned by the plan's user)
+};
+
+// Record each member's launches: enqueue(m) runs with the recorder active, hooks and per-launch
+// synchronisation off.
+template <class F>
+ocn_status record_members(ocn_ensemble* e, std::vector<LaunchRecorder>& recs, F enqueue) {
+  recs.assign(e->n, LaunchRecorder());
+  for (int i = 0; i < e->n; ++i) {
+    ocn_model* m = e->models[i];
+    const LaunchHook hook = m->hook;
+    const bool sc = m->sync_check;
+    m->hook = LaunchHook();
+    m->sync_check = false;
+    active_recorder() = &recs[i];
+    cudaError_t el = enqueue(i, m);
+    active_recorder() = nullptr;
+    m->hook = hook;
+    m->sync_check = sc;
+    if (el != cudaSuccess) return cuda_fail(el, "ensemble launch record");
+  }
+  return OCN_OK;
+}
+
+// Group, split into branches, build and upload the work lists.
+ocn_status plan_batched(ocn_ensemble* e, const std::vector<LaunchRecorder>& recs, BatchPlan* plan) {
+  const int n = e->n;
+  std::map<std::string, std::vector<int>> groups;
+  std::vector<std::string> order;
+  for (int i = 0; i < n; ++i) {
+    std::string k;
+    for (const LaunchRecord& r : recs[i].list) {
+      const unsigned vals[5] = {r.block.x, r.block.y, r.block.z, (unsigned)r.persistent, (unsigned)r.payload.size()};
+      k.append(reinterpret_cast<const char*>(&r.fn), sizeof(r.fn));
+      k.append(reinterpret_cast<const char*>(vals), sizeof(vals));
+    }
+    if (!groups.count(k)) order.push_back(k);
+    groups[k].push_back(i);
+  }
+  // split every group into up to e->branches branches of about equal cell counts (largest member
+  // first onto the lightest branch); each branch is one chain of batched launches
+  std::vector<std::vector<int>> branch_members;
+  for (const std::string& k : order) {
+    std::vector<int> mem = groups[k];
+    const int nb = std::min<int>(e->branches, (int)mem.size());
+    auto cells = [&](int i) { const ocn_grid* g = e->models[i]->g; return (double)g->Nx * g->Ny * g->Nz; };
+    std::stable_sort(mem.begin(), mem.end(), [&](int a, int b) { return cells(a) > cells(b); });
+    std::vector<std::vector<int>> br(nb);
+    std::vector<double> load(nb, 0.0);
+    for (int i : mem) {
+      const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      br[b].push_back(i);
+      load[b] += cells(i);
+    }
+    for (auto& b : br) {
+      std::sort(b.begin(), b.end());
+      branch_members.push_back(b);
+    }
+  }
+  // one batched launch per (branch, position, members sharing the launch's shared arguments)
+  std::vector<unsigned char> host;
+  auto reserve = [&](size_t bytes) { size_t o = (host.size() + 255) / 256 * 256; host.resize(o + bytes); return o; };
+  plan->launches.clear();
+  plan->nbranch = (int)branch_members.size();
+  for (size_t gi = 0; gi < branch_members.size(); ++gi) {
+    const std::vector<int>& mem = branch_members[gi];
+    const size_t npos = recs[mem[0]].list.size();
+    for (size_t p = 0; p < npos; ++p) {
+      std::map<std::vector<unsigned char>, std::vector<int>> sub;
+      std::vector<const std::vector<unsigned char>*> sub_order;
+      for (int i : mem) {
+        const LaunchRecord& r = recs[i].list[p];
+        auto it = sub.find(r.shared);
+        if (it == sub.end()) { sub_order.push_back(&r.shared); sub[r.shared].push_back(i); }
+        else it->second.push_back(i);
+      }
+      for (const auto* sk : sub_order) {
+        const std::vector<int>& ms = sub[*sk];
+        const LaunchRecord& r0 = recs[ms[0]].list[p];
+        BatchLaunch L;
+        L.fn = r0.fn; L.block = r0.block; L.smem = 0; L.carveout = r0.carveout;
+        L.n = (int)ms.size(); L.branch = (int)gi;
+        L.stride = (unsigned)r0.payload.size();
+        L.start_off = reserve(sizeof(unsigned) * (ms.size() + 1));
+        L.dims_off = reserve(sizeof(uint3) * ms.size());
+        L.payload_off = reserve((size_t)L.stride * ms.size());
+        unsigned total = 0;
+        for (size_t q = 0; q < ms.size(); ++q) {
+          const LaunchRecord& r = recs[ms[q]].list[p];
+          const uint3 d = make_uint3(r.grid.x, r.grid.y, r.grid.z);
+          memcpy(host.data() + L.start_off + q * sizeof(unsigned), &total, sizeof(unsigned));
+          memcpy(host.data() + L.dims_off + q * sizeof(uint3), &d, sizeof(uint3));
+          memcpy(host.data() + L.payload_off + q * L.stride, r.payload.data(), L.stride);
+          total += d.x * d.y * d.z;
+          L.smem = std::max(L.smem, r.smem);
+        }
+        memcpy(host.data() + L.start_off + ms.size() * sizeof(unsigned), &total, sizeof(unsigned));
+        unsigned blocks = total;
+        if (r0.persistent > 0 && blocks > (unsigned)r0.persistent) blocks = (unsigned)r0.persistent;
+        L.grid = dim3(blocks);
+        plan->launches.push_back(L);
+      }
+    }
+  }
+  cudaError_t ce = cudaMalloc(&plan->dtab, std::max<size_t>(host.size(), 256));
+  if (ce != cudaSuccess) { plan->dtab = nullptr; return cuda_fail(ce, "ensemble work lists"); }
+  ce = cudaMemcpy(plan->dtab, host.data(), host.size(), cudaMemcpyHostToDevice);
+  for (const BatchLaunch& L : plan->launches) {
+    if (ce != cudaSuccess) break;
+    ce = raise_smem_limit(L.fn, L.smem);
+    if (ce == cudaSuccess && L.carveout >= 0)
+      ce = cudaFuncSetAttribute(L.fn, cudaFuncAttributePreferredSharedMemoryCarveout, L.carveout);
+  }
+  if (ce != cudaSuccess) { cudaFree(plan->dtab); plan->dtab = nullptr; return cuda_fail(ce, "ensemble work lists"); }
+  return OCN_OK;
+}
+
+// Enqueue the plan's launches: fork from e->stream, a chain per branch, join back.
+cudaError_t enqueue_batched(ocn_ensemble* e, const BatchPlan& plan) {
+  const unsigned char* base = static_cast<const unsigned char*>(plan.dtab);
+  cudaError_t el = cudaEventRecord(e->fork, e->stream);
+  for (int gi = 0; gi < plan.nbranch && el == cudaSuccess; ++gi) {
+    cudaStream_t fs = e->fork_streams[gi];
+    el = cudaStreamWaitEvent(fs, e->fork, 0);
+    for (const BatchLaunch& L : plan.launches) {
+      if (L.branch != gi || el != cudaSuccess) continue;
+      BatchTable t;
+      t.start = reinterpret_cast<const unsigned*>(base + L.start_off);
+      t.dims = reinterpret_cast<const uint3*>(base + L.dims_off);
+      t.payload = base + L.payload_off;
+      t.stride = L.stride;
+      t.n = L.n;
+      void* args[] = {&t};
+      el = cudaLaunchKernel(L.fn, L.grid, L.block, args, L.smem, fs);
+    }
+    if (el == cudaSuccess) el = cudaEventRecord(e->join[gi], fs);
+    if (el == cudaSuccess) el = cudaStreamWaitEvent(e->stream, e->join[gi], 0);
+  }
+  return el;
+}
+
+template <typename T>
+ocn_status build_batched_graph(ocn_ensemble* e, double dt, std::vector<int>& w, cudaGraphExec_t* out_exec,
+                               void** out_tables, int* out_launches) {
+  std::vector<LaunchRecorder> recs;
+  ocn_status st = record_members(e, recs, [&](int i, ocn_model* m) {
+    w[i] = m->cur;
+    int nl = 0;
+    return enqueue_step<T>(m, dt, &w[i], &nl);
+  });
+  if (st != OCN_OK) return st;
+  BatchPlan plan;
+  st = plan_batched(e, recs, &plan);
+  if (st != OCN_OK) return st;
+  cudaError_t ce = cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal);
+  if (ce != cudaSuccess) { cudaFree(plan.dtab); return cuda_fail(ce, "ensemble begin capture"); }
+  cudaError_t el = enqueue_batched(e, plan);
+  cudaGraph_t graph = nullptr;
+  ce = cudaStreamEndCapture(e->stream, &graph);
+  if (el != cudaSuccess || ce != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaFree(plan.dtab);
+    return cuda_fail(el != cudaSuccess ? el : ce, "ensemble batched capture");
+  }
+  cudaGraphExec_t exec = nullptr;
+  ce = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) { cudaFree(plan.dtab); return cuda_fail(ce, "ensemble graph instantiate"); }
+  *out_exec = exec;
+  *out_tables = plan.dtab;
+  *out_launches = (int)plan.launches.size();
+  return OCN_OK;
+}
+
 template <typename T>
 ocn_status ensemble_step_t(ocn_ensemble* e, double dt, int nsteps) {
   for (ocn_model* m : e->models) if (!m->arena) return fail(OCN_ERR_STATE, "arena not bound");
@@ -1211,14 +1443,26 @@ ocn_status ensemble_step_t(ocn_ensemble* e, double dt, int nsteps) {
   }
   for (int s = 0; s < nsteps; ++s) {
     std::string key(reinterpret_cast<const char*>(&dt), sizeof(dt));
+    key.push_back((char)('0' + e->mode));
+    key += std::to_string(e->branches); key.push_back('/');
     for (ocn_model* m : e->models) {
       key.push_back((char)('0' + m->cur)); key.push_back((char)('0' + m->variant));
       key += std::to_string(m->colc_version); key.push_back('/');
+      key += std::to_string(m->graph_epoch); key.push_back('/');
       key.push_back((char)('0' + m->stepper)); key.push_back(m->ab_started ? 'a' : 'e');
     }
     auto it = e->graphs.find(key);
     std::vector<int> w(e->n);
-    if (it == e->graphs.end()) {
+    if (it == e->graphs.end() && e->mode == OCN_ENSEMBLE_BATCHED) {
+      cudaGraphExec_t exec = nullptr;
+      void* tables = nullptr;
+      int nl = 0;
+      ocn_status st = build_batched_graph<T>(e, dt, w, &exec, &tables, &nl);
+      if (st != OCN_OK) return st;
+      it = e->graphs.emplace(key, exec).first;
+      e->graph_tables[key] = tables;
+      e->launches_per_step = nl;
+    } else if (it == e->graphs.end()) {
       // One graph for the whole ensemble step: fork a branch per member, join at the end;
       // the branches are independent, so their kernels run concurrently.
       cudaError_t ce = cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal);
@@ -1274,8 +1518,15 @@ ocn_status ocn_ensemble_time_step(ocn_ensemble* e, double dt, int nsteps) {
 ocn_status ocn_ensemble_set_option(ocn_ensemble* e, int option, long long value) {
   if (!e) return fail(OCN_ERR_ARG, "null argument");
   if (option == OCN_OPT_ENSEMBLE_MODE) {
-    if (value != OCN_ENSEMBLE_CONCURRENT && value != OCN_ENSEMBLE_SEQUENTIAL) return fail(OCN_ERR_ARG, "unknown ensemble mode");
+    if (value != OCN_ENSEMBLE_CONCURRENT && value != OCN_ENSEMBLE_SEQUENTIAL && value != OCN_ENSEMBLE_BATCHED)
+      return fail(OCN_ERR_ARG, "unknown ensemble mode");
     e->mode = (int)value;
+    return OCN_OK;
+  }
+  if (option == OCN_OPT_ENSEMBLE_BRANCHES) {
+    if (value < 1 || value > 64) return fail(OCN_ERR_ARG, "ensemble branches must be in 1..64");
+    if (e->branches != (int)value) clear_graphs(e);
+    e->branches = (int)value;
     return OCN_OK;
   }
   for (ocn_model* m : e->models) {
@@ -1287,28 +1538,112 @@ ocn_status ocn_ensemble_set_option(ocn_ensemble* e, int option, long long value)
 
 ocn_status ocn_ensemble_autotune(ocn_ensemble* e, int* variants) {
   if (!e) return fail(OCN_ERR_ARG, "null argument");
+  for (ocn_model* m : e->models) if (!m->arena) return fail(OCN_ERR_STATE, "arena not bound");
   DeviceGuard dg(e->dev);
-  // one tuning per member shape (Nx, Ny, Nz, order, closure, tracers); members of a shape share it
-  std::map<std::string, int> cache;
+  const int nv = (e->es == 4) ? kTendencyVariants : 1;
+  std::vector<int> saved(e->n);
+  std::vector<LaunchHook> hooks(e->n);
+  std::vector<bool> timing(e->n);
   for (int i = 0; i < e->n; ++i) {
     ocn_model* m = e->models[i];
-    char buf[96];
-    snprintf(buf, sizeof(buf), "%d %d %d %d %d %d", m->g->Nx, m->g->Ny, m->g->Nz, m->R, m->d.closure, m->d.n_tracers);
-    auto it = cache.find(buf);
-    int v = 0;
-    if (it == cache.end()) {
-      ocn_status st = ocn_autotune(m, &v, nullptr);
-      if (st != OCN_OK) return st;
-      cache[buf] = v;
-    } else {
-      v = it->second;
-      ocn_status st = ocn_set_option(m, OCN_OPT_TENDENCY_VARIANT, v);
-      if (st != OCN_OK) return st;
-    }
-    if (variants) variants[i] = v;
+    saved[i] = m->variant; hooks[i] = m->hook; timing[i] = m->timing;
+    m->hook = LaunchHook(); m->timing = false;
   }
-  for (auto& kv : e->graphs) cudaGraphExecDestroy(kv.second);
-  e->graphs.clear();
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  auto tendency_only = [&](ocn_model* m) -> cudaError_t {
+    return (m->es == 4) ? enqueue_tendency<float>(m, m->cur, 0.0, 0.0, 1) : enqueue_tendency<double>(m, m->cur, 0.0, 0.0, 1);
+  };
+  ocn_status st = OCN_OK;
+  // every member's tendency (G only) as in a step of the ensemble's mode: batched launches over the
+  // members, or each member on its own branch; ms per pass (best of two after a warm-up)
+  auto pass = [&](const std::vector<int>& var) -> float {
+    float best = 1e30f;
+    if (e->mode == OCN_ENSEMBLE_BATCHED) {
+      for (int i = 0; i < e->n; ++i) e->models[i]->variant = var[i];
+      std::vector<LaunchRecorder> recs;
+      BatchPlan plan;
+      if (st == OCN_OK) st = record_members(e, recs, [&](int, ocn_model* m) { return tendency_only(m); });
+      if (st == OCN_OK) st = plan_batched(e, recs, &plan);
+      if (st != OCN_OK) { if (ce == cudaSuccess) ce = cudaErrorUnknown; return best; }
+      for (int r = 0; r < 3 && ce == cudaSuccess; ++r) {
+        ce = cudaEventRecord(e0, e->stream);
+        if (ce == cudaSuccess) ce = enqueue_batched(e, plan);
+        if (ce == cudaSuccess) ce = cudaEventRecord(e1, e->stream);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+        float t = 0.0f;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, e0, e1);
+        if (r > 0 && t < best) best = t;
+      }
+      cudaFree(plan.dtab);
+      return best;
+    }
+    for (int r = 0; r < 3 && ce == cudaSuccess; ++r) {      // the first pass warms up
+      ce = cudaEventRecord(e->fork, e->stream);
+      if (ce == cudaSuccess) ce = cudaEventRecord(e0, e->stream);
+      for (int i = 0; i < e->n && ce == cudaSuccess; ++i) {
+        ocn_model* m = e->models[i];
+        ce = cudaStreamWaitEvent(e->fork_streams[i], e->fork, 0);
+        if (ce != cudaSuccess) break;
+        m->variant = var[i];
+        m->stream = e->fork_streams[i];
+        ce = tendency_only(m);
+        m->stream = e->stream;
+        if (ce == cudaSuccess) ce = cudaEventRecord(e->join[i], e->fork_streams[i]);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(e->stream, e->join[i], 0);
+      }
+      if (ce == cudaSuccess) ce = cudaEventRecord(e1, e->stream);
+      if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+      float t = 0.0f;
+      if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, e0, e1);
+      if (r > 0 && t < best) best = t;
+    }
+    return best;
+  };
+  std::vector<int> var(e->n, 0);
+  if (nv > 1) {
+    // one variant for every member
+    float best = 1e30f;
+    int arg = 0;
+    for (int v = 0; v < nv && ce == cudaSuccess; ++v) {
+      std::vector<int> t(e->n, v);
+      const float ms = pass(t);
+      if (ms < best) { best = ms; arg = v; }
+    }
+    var.assign(e->n, arg);
+    // then per member shape, keeping a change only if the whole pass gets 2 % faster
+    std::map<std::string, std::vector<int>> shapes;
+    for (int i = 0; i < e->n; ++i) {
+      const ocn_model* m = e->models[i];
+      char buf[96];
+      snprintf(buf, sizeof(buf), "%d %d %d %d %d %d", m->g->Nx, m->g->Ny, m->g->Nz, m->R, m->d.closure, m->d.n_tracers);
+      shapes[buf].push_back(i);
+    }
+    if (shapes.size() > 1)
+      for (auto& kv : shapes) {
+        for (int v = 0; v < nv && ce == cudaSuccess; ++v) {
+          if (v == var[kv.second[0]]) continue;
+          std::vector<int> t = var;
+          for (int i : kv.second) t[i] = v;
+          const float ms = pass(t);
+          if (ms < 0.98f * best) { best = ms; var = t; }
+        }
+      }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  for (int i = 0; i < e->n; ++i) {
+    ocn_model* m = e->models[i];
+    m->hook = hooks[i]; m->timing = timing[i];
+    m->variant = (ce == cudaSuccess) ? var[i] : saved[i];
+    if (m->variant != saved[i]) drop_graphs(m);
+    if (ce == cudaSuccess) m->ab_started = false;   // G was overwritten: QAB2 restarts with its Euler step
+    if (variants) variants[i] = m->variant;
+  }
+  clear_graphs(e);
+  if (st != OCN_OK) return st;
+  if (ce != cudaSuccess) return cuda_fail(ce, "ensemble autotune");
   return OCN_OK;
 }
 

@@ -3,6 +3,7 @@
 
 #include <algorithm>
 
+#include "batch.cuh"
 #include "ocn_internal.cuh"
 
 namespace ocn {
@@ -14,9 +15,9 @@ namespace ocn {
 // latency-bound, so residency matters most: in FP32, four 256-thread CTAs per SM
 // (registers capped at 64) measured 1.5x faster than three; more CTAs spill.
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_closure(const ClosureArgs<T> a) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void closure_body(const ClosureArgs<T>& a, const uint3 bid, const uint3 gdim) {
+  const int i = bid.x * blockDim.x + threadIdx.x;
+  const int j = bid.y * blockDim.y + threadIdx.y;
   const int Nx = a.Nx, Ny = a.Ny, Nz = a.Nz;
   if (i >= Nx || j >= Ny) return;
   const size_t plane = (size_t)Nx * Ny;
@@ -37,10 +38,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_closure(const C
       return a.g_alpha * (__ldg(a.cur.c[0] + o) + cref(0, kk) - a.T0) - a.g_beta * (__ldg(a.cur.c[1] + o) + cref(1, kk) - a.S0);
     return __ldg(a.cur.c[0] + o) + cref(0, kk);
   };
-  // this CTA's chunk of levels [kb, ke) (blockIdx.z); the march state is set up at kb from the level
+  // this CTA's chunk of levels [kb, ke) (block z); the march state is set up at kb from the level
   // below, so chunks are independent
-  const int nch = gridDim.z, per = (Nz + nch - 1) / nch;
-  const int kb = blockIdx.z * per, ke = min(Nz, kb + per);
+  const int nch = gdim.z, per = (Nz + nch - 1) / nch;
+  const int kb = bid.z * per, ke = min(Nz, kb + per);
   if (kb >= ke) return;
   const size_t Lb = (size_t)kb * plane;
   // carried from level to level: u at (i|ip, j) and v at (i, j|jp) on the current level, w on face k,
@@ -150,14 +151,30 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_closure(const C
 }
 
 template <typename T>
+struct ClosureK {
+  typedef ClosureArgs<T> Payload;
+  static constexpr int kThreads = 256, kMinBlocks = sizeof(T) == 4 ? 4 : 2;
+  static __device__ __forceinline__ void run(const Payload& a, uint3 bid, uint3 gdim) { closure_body<T>(a, bid, gdim); }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(ClosureK<T>::kThreads, ClosureK<T>::kMinBlocks) k_closure(const ClosureArgs<T> a) {
+  closure_body<T>(a, blockIdx, gridDim);
+}
+
+template <typename T>
 cudaError_t launch_closure(const ClosureArgs<T>& a, cudaStream_t s) {
-  dim3 blk(32, 8);
+  // 256-thread blocks of 32 x 8 columns; narrower for grids under 32 columns wide
+  int bx = 32;
+  while (bx > 1 && bx / 2 >= a.Nx) bx /= 2;
+  dim3 blk(bx, 256 / bx);
   // z chunks so that small horizontal grids still fill the GPU (about a million threads), each
   // chunk at least 16 levels deep
   const long long cols = (long long)a.Nx * a.Ny;
   int nch = (int)((1000000 + cols - 1) / cols);
   nch = std::max(1, std::min(nch, a.Nz / 16));
-  dim3 grid((a.Nx + 31) / 32, (a.Ny + 7) / 8, nch);
+  dim3 grid((a.Nx + blk.x - 1) / blk.x, (a.Ny + blk.y - 1) / blk.y, nch);
+  if (record_launch<ClosureK<T>>(a, grid, blk, 0, OCN_K_CLOSURE)) return cudaSuccess;
   k_closure<T><<<grid, blk, 0, s>>>(a);
   return cudaGetLastError();
 }

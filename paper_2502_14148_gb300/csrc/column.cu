@@ -3,14 +3,15 @@
 // data) and the face-flux divergence added to the tendencies.
 #include <cuda_runtime.h>
 
+#include "batch.cuh"
 #include "column.cuh"
 
 namespace ocn {
 namespace {
 
 // h = sum over interior faces of max(0, 1 - (db/dz)/N2bg) dzf (0 when N2bg <= 0): one thread per column.
-__global__ void k_column_h(const ColumnArgs a) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void column_h_body(const ColumnArgs& a, const uint3 bid) {
+  const int c = bid.x * blockDim.x + threadIdx.x;
   if (c >= a.Nx * a.Ny) return;
   const int i = c % a.Nx, j = c / a.Nx;
   float acc = 0.0f;
@@ -122,12 +123,12 @@ __global__ void k_coarse_grain(const ColumnArgs a, int cx, int cy, double* out) 
   }
 }
 
-__global__ void k_apply_face_flux(const FaceFluxArgs a) {
+__device__ __forceinline__ void apply_face_flux_body(const FaceFluxArgs& a, const uint3 bid, const uint3 gdim) {
   const size_t plane = (size_t)a.Nx * a.Ny, N = plane * a.Nz, NW = plane * (a.Nz + 1);
   const float* Fb = a.F;
   const float* Fu = a.F + NW;
   const float* Fv = a.F + 2 * NW;
-  for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < N; s += (size_t)gridDim.x * blockDim.x) {
+  for (size_t s = bid.x * (size_t)blockDim.x + threadIdx.x; s < N; s += (size_t)gdim.x * blockDim.x) {
     const int k = (int)(s / plane), c = (int)(s % plane), i = c % a.Nx, j = c / a.Nx;
     const int im = (i == 0) ? a.Nx - 1 : i - 1, jm = (j == 0) ? a.Ny - 1 : j - 1;
     const size_t lo = (size_t)k * plane, hi = lo + plane;
@@ -145,6 +146,19 @@ __global__ void k_apply_face_flux(const FaceFluxArgs a) {
   }
 }
 
+struct ColumnHK {
+  typedef ColumnArgs Payload;
+  static constexpr int kThreads = 128, kMinBlocks = 1;
+  static __device__ __forceinline__ void run(const Payload& a, uint3 bid, uint3) { column_h_body(a, bid); }
+};
+struct ApplyFaceFluxK {
+  typedef FaceFluxArgs Payload;
+  static constexpr int kThreads = 256, kMinBlocks = 1;
+  static __device__ __forceinline__ void run(const Payload& a, uint3 bid, uint3 g) { apply_face_flux_body(a, bid, g); }
+};
+__global__ void k_column_h(const ColumnArgs a) { column_h_body(a, blockIdx); }
+__global__ void k_apply_face_flux(const FaceFluxArgs a) { apply_face_flux_body(a, blockIdx, gridDim); }
+
 int blocks_for(size_t n) {
   size_t b = (n + 255) / 256;
   return (int)(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16);
@@ -154,6 +168,7 @@ int blocks_for(size_t n) {
 
 cudaError_t launch_column_h(const ColumnArgs& a, cudaStream_t s) {
   const int n = a.Nx * a.Ny;
+  if (record_launch<ColumnHK>(a, dim3((n + 127) / 128), dim3(128), 0, OCN_K_COLUMN_CLOSURE)) return cudaSuccess;
   k_column_h<<<(n + 127) / 128, 128, 0, s>>>(a);
   return cudaGetLastError();
 }
@@ -178,7 +193,9 @@ cudaError_t launch_coarse_grain(const ColumnArgs& a, int cx, int cy, double* out
 }
 
 cudaError_t launch_apply_face_flux(const FaceFluxArgs& a, cudaStream_t s) {
-  k_apply_face_flux<<<blocks_for((size_t)a.Nx * a.Ny * a.Nz), 256, 0, s>>>(a);
+  const dim3 grid(blocks_for((size_t)a.Nx * a.Ny * a.Nz));
+  if (record_launch<ApplyFaceFluxK>(a, grid, dim3(256), 0, OCN_K_COLUMN_CLOSURE)) return cudaSuccess;
+  k_apply_face_flux<<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <new>
 
+#include "batch.cuh"
 #include "column.cuh"
 #include "ocn_internal.cuh"
 
@@ -249,7 +250,7 @@ cudaError_t launch_gemm_tc(const GemmArgs& a, int nsplit, cudaStream_t s) {
       a.kchunk <= 0 || (nsplit > 1 && (a.kchunk % kChunkK)) || nsplit < 1 || a.lda < a.K || a.ldb < a.K ||
       (reinterpret_cast<uintptr_t>(a.A) & 15) || (reinterpret_cast<uintptr_t>(a.B) & 15))
     return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+  cudaError_t e = raise_smem_limit(k_gemm_tc, kGemmSmem);
   if (e != cudaSuccess) return e;
   dim3 grid((a.M + kTileM - 1) / kTileM, nsplit);
   k_gemm_tc<<<grid, 128, kGemmSmem, s>>>(a);
@@ -308,15 +309,38 @@ __device__ __forceinline__ void closure_layer_mma(uint32_t tmem, uint32_t a_addr
 
 constexpr int kClosureThreads = 256;   // two warps per TMEM lane quadrant, 64 columns each
 
-__global__ void __launch_bounds__(kClosureThreads, 2) k_mlp_closure(const MlpClosureArgs a) {
+// One member's tile: its arguments and the tile's index within the member.
+struct ClosureTile {
+  const MlpClosureArgs* m;
+  long long lt;
+};
+
+// The fused closure network over 128-face tiles.  Plain: the tiles of one model (`a`), grid
+// stride over them.  Batched: the tiles of all members of `bt` (member m owns tiles
+// [start[m], start[m+1])); `a` is member 0's arguments, whose network and feature normalisation
+// every member shares; each tile reads its own member's columns and writes its fluxes with its
+// own output scales.
+template <bool kBatch>
+__device__ __forceinline__ void mlp_closure_body(const MlpClosureArgs& a, const BatchTable& bt, const uint3 bid,
+                                                 const uint3 gdim) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint64_t bar;
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const ColumnArgs& c = a.col;
-  const size_t plane = (size_t)c.Nx * c.Ny;
-  const size_t nsamp = plane * (c.Nz + 1), NW = nsamp;
-  const long long ntiles = (long long)((nsamp + 127) / 128);
+  auto tiles_of = [](const ColumnArgs& c) -> long long {
+    return (long long)(((size_t)c.Nx * c.Ny * (c.Nz + 1) + 127) / 128);
+  };
+  long long ntiles;
+  if constexpr (kBatch) ntiles = (long long)__ldg(bt.start + bt.n);
+  else ntiles = tiles_of(a.col);
+  auto tile_of = [&](long long t) -> ClosureTile {
+    if constexpr (kBatch) {
+      const int m = batch_member(bt, (unsigned)t);
+      return {reinterpret_cast<const MlpClosureArgs*>(bt.payload + (size_t)m * bt.stride), t - (long long)__ldg(bt.start + m)};
+    } else {
+      return {&a, t};
+    }
+  };
   if (warp == 0) tmem_alloc(&tmem_base, 128);
   if (tid == 0) {
     mbar_init(&bar, 1);
@@ -344,8 +368,12 @@ __global__ void __launch_bounds__(kClosureThreads, 2) k_mlp_closure(const MlpClo
   auto load_raw = [&](long long tt) {
 #pragma unroll
     for (int m = 0; m < 24; ++m) raw[m] = 0.0f;
-    const size_t sidx = (size_t)tt * 128 + (tid & 127);
-    if (tt >= ntiles || sidx >= nsamp) return;
+    if (tt >= ntiles) return;
+    const ClosureTile ct = tile_of(tt);
+    const ColumnArgs& c = ct.m->col;
+    const size_t plane = (size_t)c.Nx * c.Ny, nsamp = plane * (c.Nz + 1);
+    const size_t sidx = (size_t)ct.lt * 128 + (tid & 127);
+    if (sidx >= nsamp) return;
     const uint32_t s32 = (uint32_t)sidx, p32 = (uint32_t)plane;
     const int k = (int)(s32 / p32), cc = (int)(s32 - (uint32_t)k * p32);
     const int j = cc / c.Nx, i = cc - j * c.Nx;
@@ -371,14 +399,19 @@ __global__ void __launch_bounds__(kClosureThreads, 2) k_mlp_closure(const MlpClo
       }
     }
   };
-  load_raw(blockIdx.x);
-  for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+  load_raw(bid.x);
+  ClosureTile cur = {&a, 0};
+  for (long long t = bid.x; t < ntiles && ok; t += gdim.x) {
+    cur = tile_of(t);
+    const ColumnArgs& c = cur.m->col;
+    const size_t plane = (size_t)c.Nx * c.Ny;
+    const size_t nsamp = plane * (c.Nz + 1), NW = nsamp;
     // ---- features of sample row (tid & 127) from the raw values prefetched for this tile, half of
     //      them per thread: part 0 the db/dz stencil (features 0-4) and the non-local features
     //      15-19 plus the zero padding, part 1 the dubar/dz and dvbar/dz stencils (features 5-14)
     {
       const int r = tid & 127, fp = tid >> 7;
-      const size_t sidx = (size_t)t * 128 + r;
+      const size_t sidx = (size_t)cur.lt * 128 + r;
       const bool valid = sidx < nsamp;
       float g[10];
 #pragma unroll
@@ -414,7 +447,7 @@ __global__ void __launch_bounds__(kClosureThreads, 2) k_mlp_closure(const MlpClo
           *reinterpret_cast<__nv_bfloat16*>(smem + kSX + cm_off(r, q, kCF)) = __float2bfloat16_rn(0.0f);
     }
     // ---- prefetch the next tile's raw values: they arrive while this tile's four MMA rounds run
-    load_raw(t + gridDim.x);
+    load_raw(t + gdim.x);
     // ---- four layers
     for (int l = 0; l < 4 && ok; ++l) {
       fence_proxy_async();
@@ -457,25 +490,34 @@ __global__ void __launch_bounds__(kClosureThreads, 2) k_mlp_closure(const MlpClo
       } else if (half == 0) {
         float v[16];
         tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16), v);
-        const size_t sidx = (size_t)t * 128 + row;
+        const size_t sidx = (size_t)cur.lt * 128 + row;
         if (sidx < nsamp) {
           const int k = (int)((uint32_t)sidx / (uint32_t)plane);
           const bool wall = (k == 0 || k == c.Nz);
           const float* b4 = sbias + 3 * kCH;
 #pragma unroll
-          for (int q = 0; q < 3; ++q) a.F[(size_t)q * NW + sidx] = wall ? 0.0f : a.scale[q] * (v[q] + b4[q]);
+          for (int q = 0; q < 3; ++q) cur.m->F[(size_t)q * NW + sidx] = wall ? 0.0f : cur.m->scale[q] * (v[q] + b4[q]);
         }
       }
     }
   }
   if (!ok) {
-    if (tid == 0 && a.status) atomicExch(a.status, 1);
+    if (tid == 0 && cur.m->status) atomicExch(cur.m->status, 1);
     mbar_wait_bounded(&bar, phase ^ 1u);
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   if (warp == 0) tmem_dealloc(tmem, 128);
+}
+
+__global__ void __launch_bounds__(kClosureThreads, 2) k_mlp_closure(const MlpClosureArgs a) {
+  const BatchTable none = {nullptr, nullptr, nullptr, 0, 0};
+  mlp_closure_body<false>(a, none, blockIdx, gridDim);
+}
+
+__global__ void __launch_bounds__(kClosureThreads, 2) k_mlp_closure_batched(const BatchTable bt) {
+  mlp_closure_body<true>(*reinterpret_cast<const MlpClosureArgs*>(bt.payload), bt, blockIdx, gridDim);
 }
 
 cudaError_t launch_mlp_closure(const MlpClosureArgs& a, cudaStream_t s) {
@@ -485,12 +527,30 @@ cudaError_t launch_mlp_closure(const MlpClosureArgs& a, cudaStream_t s) {
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 148;
   }
-  cudaError_t e = cudaFuncSetAttribute(k_mlp_closure, cudaFuncAttributeMaxDynamicSharedMemorySize, kClosureSmem);
+  cudaError_t e = raise_smem_limit(k_mlp_closure, kClosureSmem);
   if (e != cudaSuccess) return e;
   const size_t nsamp = (size_t)a.col.Nx * a.col.Ny * (a.col.Nz + 1);
   if (nsamp + 128 >= ((size_t)1 << 31)) return cudaErrorInvalidValue;    // 32-bit face indices
   const long long ntiles = (long long)((nsamp + 127) / 128);
   const int grid = (int)(ntiles < 2 * nsm ? ntiles : 2 * nsm);
+  if (LaunchRecorder* r = active_recorder()) {
+    // batched: one tile space over the members, which share the network and the normalisation
+    e = raise_smem_limit(k_mlp_closure_batched, kClosureSmem);
+    if (e != cudaSuccess) return e;
+    LaunchRecord rec;
+    rec.fn = reinterpret_cast<const void*>(&k_mlp_closure_batched);
+    rec.grid = dim3((unsigned)ntiles);
+    rec.block = dim3(kClosureThreads);
+    rec.smem = kClosureSmem;
+    rec.persistent = 2 * nsm;
+    rec.kclass = OCN_K_COLUMN_CLOSURE;
+    rec.payload.assign(batch_stride(sizeof(a)), 0);
+    memcpy(rec.payload.data(), &a, sizeof(a));
+    const unsigned char* w0 = reinterpret_cast<const unsigned char*>(&a.W);
+    rec.shared.assign(w0, w0 + (reinterpret_cast<const unsigned char*>(&a.scale) - w0));
+    r->list.push_back(std::move(rec));
+    return cudaSuccess;
+  }
   k_mlp_closure<<<grid, kClosureThreads, kClosureSmem, s>>>(a);
   return cudaGetLastError();
 }

@@ -33,6 +33,9 @@ cudaError_t upload_weno_tables(const WenoTables<double>& t);
 cudaError_t upload_tables_f32_r5(const WenoTables<double>& t);
 cudaError_t upload_tables_f32_r3(const WenoTables<double>& t);
 cudaError_t upload_tables_f64(const WenoTables<double>& t);
+cudaError_t upload_tables_f32_r5_batch(const WenoTables<double>& t);
+cudaError_t upload_tables_f32_r3_batch(const WenoTables<double>& t);
+cudaError_t upload_tables_f64_batch(const WenoTables<double>& t);
 
 // Fields of one prognostic state.
 template <typename T>
@@ -66,7 +69,7 @@ struct TendencyArgs {
   T dt_gamma, dt_zeta;    // RK coefficients times dt
   int mode;               // 0: RK update + G;  1: G only
   int variant;            // tile variant of the FP32 kernel (0: 32x8 one CTA/SM, 1: 32x8 two, 2: 32x16, 3: 32x4 three,
-                          // 4: 32x14, 5: 32x12)
+                          // 4: 32x14, 5: 32x12, 6: 16x16 two CTAs/SM for grids under 32 columns wide)
 };
 
 template <typename T>
@@ -142,7 +145,7 @@ template <> cudaError_t launch_tendency<float>(const TendencyArgs<float>& a, int
 template <> cudaError_t launch_tendency<double>(const TendencyArgs<double>& a, int weno_r, cudaStream_t s);
 cudaError_t launch_tendency_f32_r5(const TendencyArgs<float>& a, cudaStream_t s);
 cudaError_t launch_tendency_f32_r3(const TendencyArgs<float>& a, cudaStream_t s);
-constexpr int kTendencyVariants = 6;
+constexpr int kTendencyVariants = 7;
 template <typename T> cudaError_t launch_projection(const PoissonArgs<T>& a, cudaStream_t s, int* nlaunch,
                                                     const LaunchHook& hook = LaunchHook());
 template <typename T> cudaError_t launch_diagnostics(const DiagArgs<T>& a, cudaStream_t s);
@@ -170,6 +173,11 @@ template <typename T> cudaError_t launch_profile_means(const ProfileArgs<T>& a, 
 template <typename T> cudaError_t launch_level_mean(const T* p, size_t plane, int Nz, T* ref, cudaStream_t s);
 template <typename T> cudaError_t launch_level_shift(T* p, size_t plane, int Nz, const T* ref, T sign, cudaStream_t s);
 int diag_blocks();
+// Raise a kernel's dynamic shared memory limit to at least `bytes` on the current device (never
+// lowers it: graphs captured earlier may launch the kernel with more).
+cudaError_t raise_smem_limit(const void* fn, size_t bytes);
+template <typename F>
+cudaError_t raise_smem_limit(F* fn, size_t bytes) { return raise_smem_limit(reinterpret_cast<const void*>(fn), bytes); }
 // Records the text returned by ocn_last_error() on this thread and returns s.
 ocn_status set_last_error(ocn_status s, const char* msg);
 

@@ -18,6 +18,7 @@
 // twiddle tables, so every size 2^a 3^b is handled.
 #include <cuda_runtime.h>
 
+#include "batch.cuh"
 #include "ocn_internal.cuh"
 
 namespace ocn {
@@ -121,14 +122,14 @@ __device__ C* block_fft(C* a, C* b, const FftPlan& plan, int nlines, int sl, int
 // ---------------------------------------------------------------------------
 // divergence + real FFT along x.  Each block handles LR consecutive rows.
 template <typename T>
-__global__ void __launch_bounds__(256) k_div_fftx(const PoissonArgs<T> a, int LR) {
+__device__ __forceinline__ void div_fftx_body(const PoissonArgs<T>& a, int LR, const uint3 bid) {
   typedef typename CT<T>::type C;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C* A = reinterpret_cast<C*>(sm_raw);
   const int M = a.Mx, Nx = a.Nx, Ny = a.Ny, Nz = a.Nz;
   C* B = A + LR * M;
   const size_t plane = (size_t)Nx * Ny;
-  const int row0 = blockIdx.x * LR;
+  const int row0 = bid.x * LR;
   const int nrows = min(LR, Ny * Nz - row0);
   for (int idx = threadIdx.x; idx < nrows * M; idx += blockDim.x) {
     const int l = idx / M, n = idx % M;
@@ -168,14 +169,14 @@ __global__ void __launch_bounds__(256) k_div_fftx(const PoissonArgs<T> a, int LR
 
 // complex-to-real inverse FFT along x -> p (scaled by a.scale).
 template <typename T>
-__global__ void __launch_bounds__(256) k_ifftx(const PoissonArgs<T> a, int LR) {
+__device__ __forceinline__ void ifftx_body(const PoissonArgs<T>& a, int LR, const uint3 bid) {
   typedef typename CT<T>::type C;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C* A = reinterpret_cast<C*>(sm_raw);
   const int M = a.Mx, Nx = a.Nx, Ny = a.Ny, Nz = a.Nz;
   C* B = A + LR * M;
   const int S = M + 1;
-  const int row0 = blockIdx.x * LR;
+  const int row0 = bid.x * LR;
   const int nrows = min(LR, Ny * Nz - row0);
   const C* spec = reinterpret_cast<const C*>(a.spec);
   const C* tw = reinterpret_cast<const C*>(a.twx);
@@ -206,13 +207,13 @@ __global__ void __launch_bounds__(256) k_ifftx(const PoissonArgs<T> a, int LR) {
 
 // FFT along y of a tile of CW kx-columns in one z-plane, in place.
 template <typename T>
-__global__ void __launch_bounds__(256) k_fft_y(const PoissonArgs<T> a, int CW, int sign) {
+__device__ __forceinline__ void fft_y_body(const PoissonArgs<T>& a, int CW, int sign, const uint3 bid) {
   typedef typename CT<T>::type C;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C* A = reinterpret_cast<C*>(sm_raw);
   const int Ny = a.Ny, S = a.Mx + 1;
   C* B = A + Ny * CW;
-  const int kx0 = blockIdx.x * CW, k = blockIdx.y;
+  const int kx0 = bid.x * CW, k = bid.y;
   const int ncol = min(CW, S - kx0);
   C* spec = reinterpret_cast<C*>(a.spec) + (size_t)k * Ny * S;
   for (int idx = threadIdx.x; idx < Ny * CW; idx += blockDim.x) {
@@ -246,12 +247,12 @@ __device__ __forceinline__ void tri_coeffs(const PoissonArgs<T>& a, int k, int N
 }
 
 template <typename T, typename P>
-__global__ void __launch_bounds__(256) k_tridiag(const PoissonArgs<T> a) {
+__device__ __forceinline__ void tridiag_body(const PoissonArgs<T>& a, const uint3 bid) {
   typedef typename CT<T>::type C;
   const int S = a.Mx + 1, Ny = a.Ny, Nz = a.Nz;
-  const int kx = blockIdx.x * blockDim.x + threadIdx.x;
-  const int ky = blockIdx.y;
-  if (kx >= S) return;
+  const int o_ = bid.x * blockDim.x + threadIdx.x;   // column ky * S + kx
+  if (o_ >= S * Ny) return;
+  const int ky = o_ / S, kx = o_ - ky * S;
   const size_t pl = (size_t)Ny * S;
   C* x = reinterpret_cast<C*>(a.spec) + (size_t)ky * S + kx;
   T* cp = a.cpiv + (size_t)ky * S + kx;
@@ -286,9 +287,9 @@ __global__ void __launch_bounds__(256) k_tridiag(const PoissonArgs<T> a) {
 template <typename T, typename P>
 __global__ void __launch_bounds__(256) k_tridiag_factor(const PoissonArgs<T> a) {
   const int S = a.Mx + 1, Ny = a.Ny, Nz = a.Nz;
-  const int kx = blockIdx.x * blockDim.x + threadIdx.x;
-  const int ky = blockIdx.y;
-  if (kx >= S) return;
+  const int o_ = blockIdx.x * blockDim.x + threadIdx.x;   // column ky * S + kx
+  if (o_ >= S * Ny) return;
+  const int ky = o_ / S, kx = o_ - ky * S;
   const size_t pl = (size_t)Ny * S, o = (size_t)ky * S + kx;
   const P lam = (P)__ldg(a.lamx + kx) + (P)__ldg(a.lamy + ky);
   const bool gauge = (kx == 0 && ky == 0);
@@ -306,12 +307,12 @@ __global__ void __launch_bounds__(256) k_tridiag_factor(const PoissonArgs<T> a) 
 constexpr int kTriChunk = 8;
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_tridiag_solve(const PoissonArgs<T> a) {
+__device__ __forceinline__ void tridiag_solve_body(const PoissonArgs<T>& a, const uint3 bid) {
   typedef typename CT<T>::type C;
   const int S = a.Mx + 1, Ny = a.Ny, Nz = a.Nz;
-  const int kx = blockIdx.x * blockDim.x + threadIdx.x;
-  const int ky = blockIdx.y;
-  if (kx >= S) return;
+  const int o_ = bid.x * blockDim.x + threadIdx.x;   // column ky * S + kx
+  if (o_ >= S * Ny) return;
+  const int ky = o_ / S, kx = o_ - ky * S;
   const size_t pl = (size_t)Ny * S, o = (size_t)ky * S + kx;
   C* x = reinterpret_cast<C*>(a.spec) + o;
   const T* cp = a.cpiv + o;
@@ -368,7 +369,7 @@ __global__ void __launch_bounds__(256) k_tridiag_solve(const PoissonArgs<T> a) {
 
 // zero volume mean of the (kx,ky) = (0,0) column (one warp)
 template <typename T>
-__global__ void k_gauge(const PoissonArgs<T> a) {
+__device__ __forceinline__ void gauge_body(const PoissonArgs<T>& a) {
   typedef typename CT<T>::type C;
   const size_t pl = (size_t)a.Ny * (a.Mx + 1);
   C* x = reinterpret_cast<C*>(a.spec);
@@ -393,12 +394,12 @@ __global__ void k_gauge(const PoissonArgs<T> a) {
 
 // u = u~ - dt grad p (walls untouched)
 template <typename T>
-__global__ void __launch_bounds__(256) k_correct(const PoissonArgs<T> a) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y;
-  const int k = blockIdx.z;
+__device__ __forceinline__ void correct_body(const PoissonArgs<T>& a, const uint3 bid) {
   const int Nx = a.Nx, Ny = a.Ny;
-  if (i >= Nx) return;
+  const int c = bid.x * blockDim.x + threadIdx.x;   // j * Nx + i (narrow grids fill the blocks)
+  const int k = bid.y;
+  if (c >= Nx * Ny) return;
+  const int j = c / Nx, i = c - j * Nx;
   const size_t plane = (size_t)Nx * Ny;
   const size_t id = (size_t)k * plane + (size_t)j * Nx + i;
   const int im = (i == 0) ? Nx - 1 : i - 1;
@@ -407,6 +408,73 @@ __global__ void __launch_bounds__(256) k_correct(const PoissonArgs<T> a) {
   a.u[id] -= a.dt * (pc - a.p[(size_t)k * plane + (size_t)j * Nx + im]) * a.rdx;
   a.v[id] -= a.dt * (pc - a.p[(size_t)k * plane + (size_t)jm * Nx + i]) * a.rdy;
   if (k >= 1) a.w[id] -= a.dt * (pc - a.p[id - plane]) * __ldg(a.rdzf + k);
+}
+
+// Plain kernels and their batched forms (k_batched over the *K bodies).
+template <typename T>
+struct PoissonLaunch {            // the projection's arguments and the launch integers of one kernel
+  PoissonArgs<T> a;
+  int i0, i1;
+};
+template <typename T> struct DivFftxK {
+  typedef PoissonLaunch<T> Payload;
+  static constexpr int kThreads = 256, kMinBlocks = 1;
+  static __device__ __forceinline__ void run(const Payload& p, uint3 bid, uint3) { div_fftx_body<T>(p.a, p.i0, bid); }
+};
+template <typename T> struct IfftxK {
+  typedef PoissonLaunch<T> Payload;
+  static constexpr int kThreads = 256, kMinBlocks = 1;
+  static __device__ __forceinline__ void run(const Payload& p, uint3 bid, uint3) { ifftx_body<T>(p.a, p.i0, bid); }
+};
+template <typename T> struct FftYK {
+  typedef PoissonLaunch<T> Payload;
+  static constexpr int kThreads = 256, kMinBlocks = 1;
+  static __device__ __forceinline__ void run(const Payload& p, uint3 bid, uint3) { fft_y_body<T>(p.a, p.i0, p.i1, bid); }
+};
+template <typename T, typename P> struct TridiagK {
+  typedef PoissonArgs<T> Payload;
+  static constexpr int kThreads = 256, kMinBlocks = 1;
+  static __device__ __forceinline__ void run(const Payload& a, uint3 bid, uint3) { tridiag_body<T, P>(a, bid); }
+};
+template <typename T> struct TridiagSolveK {
+  typedef PoissonArgs<T> Payload;
+  static constexpr int kThreads = 256, kMinBlocks = 1;
+  static __device__ __forceinline__ void run(const Payload& a, uint3 bid, uint3) { tridiag_solve_body<T>(a, bid); }
+};
+template <typename T> struct GaugeK {
+  typedef PoissonArgs<T> Payload;
+  static constexpr int kThreads = 32, kMinBlocks = 1;
+  static __device__ __forceinline__ void run(const Payload& a, uint3, uint3) { gauge_body<T>(a); }
+};
+template <typename T> struct CorrectK {
+  typedef PoissonArgs<T> Payload;
+  static constexpr int kThreads = 256, kMinBlocks = 1;
+  static __device__ __forceinline__ void run(const Payload& a, uint3 bid, uint3) { correct_body<T>(a, bid); }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_div_fftx(const PoissonArgs<T> a, int LR) { div_fftx_body<T>(a, LR, blockIdx); }
+template <typename T>
+__global__ void __launch_bounds__(256) k_ifftx(const PoissonArgs<T> a, int LR) { ifftx_body<T>(a, LR, blockIdx); }
+template <typename T>
+__global__ void __launch_bounds__(256) k_fft_y(const PoissonArgs<T> a, int CW, int sign) {
+  fft_y_body<T>(a, CW, sign, blockIdx);
+}
+template <typename T, typename P>
+__global__ void __launch_bounds__(256) k_tridiag(const PoissonArgs<T> a) { tridiag_body<T, P>(a, blockIdx); }
+template <typename T>
+__global__ void __launch_bounds__(256) k_tridiag_solve(const PoissonArgs<T> a) { tridiag_solve_body<T>(a, blockIdx); }
+template <typename T>
+__global__ void k_gauge(const PoissonArgs<T> a) { gauge_body<T>(a); }
+template <typename T>
+__global__ void __launch_bounds__(256) k_correct(const PoissonArgs<T> a) { correct_body<T>(a, blockIdx); }
+
+template <typename T>
+static PoissonLaunch<T> with_ints(const PoissonArgs<T>& a, int i0, int i1) {
+  PoissonLaunch<T> p;
+  memset(&p, 0, sizeof(p));
+  p.a = a; p.i0 = i0; p.i1 = i1;
+  return p;
 }
 
 static int rows_per_block(int M) { return M >= 2048 ? 1 : 2048 / M; }
@@ -420,55 +488,65 @@ cudaError_t launch_projection(const PoissonArgs<T>& a, cudaStream_t s, int* nlau
   const int LR = rows_per_block(M);
   const size_t smx = 2 * (size_t)LR * M * sizeof(C);
   const int rows = a.Ny * a.Nz;
-  e = cudaFuncSetAttribute(k_div_fftx<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx);
+  e = raise_smem_limit(k_div_fftx<T>, smx);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_ifftx<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx);
+  e = raise_smem_limit(k_ifftx<T>, smx);
   if (e != cudaSuccess) return e;
+  const bool rec = active_recorder() != nullptr;
   hook.pre(OCN_K_DIV_FFTX);
-  k_div_fftx<T><<<(rows + LR - 1) / LR, 256, smx, s>>>(a, LR);
+  if (!record_launch<DivFftxK<T>>(with_ints(a, LR, 0), dim3((rows + LR - 1) / LR), dim3(256), smx, OCN_K_DIV_FFTX))
+    k_div_fftx<T><<<(rows + LR - 1) / LR, 256, smx, s>>>(a, LR);
   hook.post(OCN_K_DIV_FFTX);
   ++n;
-  const int CW = (sizeof(T) == 4) ? 8 : 4;
+  // kx columns per block: 8 (FP32) / 4 (FP64), widened for short y lines so that a block holds
+  // about 2048 (FP32) / 1024 (FP64) values, but not beyond the spectrum's width
+  int CW = (sizeof(T) == 4) ? 8 : 4;
+  while (CW * a.Ny < (sizeof(T) == 4 ? 2048 : 1024) && CW < a.Mx + 1) CW *= 2;
   const size_t smy = 2 * (size_t)a.Ny * CW * sizeof(C);
-  e = cudaFuncSetAttribute(k_fft_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smy);
+  e = raise_smem_limit(k_fft_y<T>, smy);
   if (e != cudaSuccess) return e;
   dim3 gy((a.Mx + 1 + CW - 1) / CW, a.Nz);
   hook.pre(OCN_K_FFT_Y);
-  k_fft_y<T><<<gy, 256, smy, s>>>(a, CW, -1);
+  if (!record_launch<FftYK<T>>(with_ints(a, CW, -1), gy, dim3(256), smy, OCN_K_FFT_Y)) k_fft_y<T><<<gy, 256, smy, s>>>(a, CW, -1);
   hook.post(OCN_K_FFT_Y);
   ++n;
-  dim3 gt((a.Mx + 1 + 127) / 128, a.Ny);
+  dim3 gt(((a.Mx + 1) * a.Ny + 127) / 128);
   hook.pre(OCN_K_TRIDIAG);
-  if (a.pinv) k_tridiag_solve<T><<<gt, 128, 0, s>>>(a);
-  else if (a.fp64_pivots) k_tridiag<T, double><<<gt, 128, 0, s>>>(a);
-  else k_tridiag<T, T><<<gt, 128, 0, s>>>(a);
+  if (a.pinv) {
+    if (!record_launch<TridiagSolveK<T>>(a, gt, dim3(128), 0, OCN_K_TRIDIAG)) k_tridiag_solve<T><<<gt, 128, 0, s>>>(a);
+  } else if (a.fp64_pivots) {
+    if (!record_launch<TridiagK<T, double>>(a, gt, dim3(128), 0, OCN_K_TRIDIAG)) k_tridiag<T, double><<<gt, 128, 0, s>>>(a);
+  } else {
+    if (!record_launch<TridiagK<T, T>>(a, gt, dim3(128), 0, OCN_K_TRIDIAG)) k_tridiag<T, T><<<gt, 128, 0, s>>>(a);
+  }
   hook.post(OCN_K_TRIDIAG);
   ++n;
   hook.pre(OCN_K_GAUGE);
-  k_gauge<T><<<1, 32, 0, s>>>(a);
+  if (!record_launch<GaugeK<T>>(a, dim3(1), dim3(32), 0, OCN_K_GAUGE)) k_gauge<T><<<1, 32, 0, s>>>(a);
   hook.post(OCN_K_GAUGE);
   ++n;
   hook.pre(OCN_K_FFT_Y);
-  k_fft_y<T><<<gy, 256, smy, s>>>(a, CW, +1);
+  if (!record_launch<FftYK<T>>(with_ints(a, CW, +1), gy, dim3(256), smy, OCN_K_FFT_Y)) k_fft_y<T><<<gy, 256, smy, s>>>(a, CW, +1);
   hook.post(OCN_K_FFT_Y);
   ++n;
   hook.pre(OCN_K_IFFTX);
-  k_ifftx<T><<<(rows + LR - 1) / LR, 256, smx, s>>>(a, LR);
+  if (!record_launch<IfftxK<T>>(with_ints(a, LR, 0), dim3((rows + LR - 1) / LR), dim3(256), smx, OCN_K_IFFTX))
+    k_ifftx<T><<<(rows + LR - 1) / LR, 256, smx, s>>>(a, LR);
   hook.post(OCN_K_IFFTX);
   ++n;
-  dim3 gc((a.Nx + 255) / 256, a.Ny, a.Nz);
+  dim3 gc((a.Nx * a.Ny + 255) / 256, a.Nz);
   hook.pre(OCN_K_CORRECT);
-  k_correct<T><<<gc, 256, 0, s>>>(a);
+  if (!record_launch<CorrectK<T>>(a, gc, dim3(256), 0, OCN_K_CORRECT)) k_correct<T><<<gc, 256, 0, s>>>(a);
   hook.post(OCN_K_CORRECT);
   ++n;
   if (nlaunch) *nlaunch = n;
-  return cudaGetLastError();
+  return rec ? cudaSuccess : cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_tridiag_factor(const PoissonArgs<T>& a, cudaStream_t s) {
   if (!a.pinv || !a.cpiv) return cudaErrorInvalidValue;
-  dim3 gt((a.Mx + 1 + 127) / 128, a.Ny);
+  dim3 gt(((a.Mx + 1) * a.Ny + 127) / 128);
   if (a.fp64_pivots) k_tridiag_factor<T, double><<<gt, 128, 0, s>>>(a);
   else k_tridiag_factor<T, T><<<gt, 128, 0, s>>>(a);
   return cudaGetLastError();

@@ -12,6 +12,7 @@ static cudaError_t launch_f32_r5_n(const TendencyArgs<float>& a, cudaStream_t s)
       case 3: return launch_tendency_variant<float, 5, NTR, 32, 4, 3>(a, s);
       case 4: return launch_tendency_variant<float, 5, NTR, 32, 14, 1>(a, s);
       case 5: return launch_tendency_variant<float, 5, NTR, 32, 12, 1>(a, s);
+      case 6: return launch_tendency_variant<float, 5, NTR, 16, 16, 2>(a, s);
       default: return cudaErrorInvalidValue;
   }
 }

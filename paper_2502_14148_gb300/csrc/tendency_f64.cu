@@ -32,6 +32,9 @@ cudaError_t upload_weno_tables(const WenoTables<double>& t) {
   cudaError_t e = upload_tables_f32_r5(t);
   if (e == cudaSuccess) e = upload_tables_f32_r3(t);
   if (e == cudaSuccess) e = upload_tables_f64(t);
+  if (e == cudaSuccess) e = upload_tables_f32_r5_batch(t);
+  if (e == cudaSuccess) e = upload_tables_f32_r3_batch(t);
+  if (e == cudaSuccess) e = upload_tables_f64_batch(t);
   return e;
 }
 

@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "batch.cuh"
 #include "ocn_internal.cuh"
 
 namespace ocn {
@@ -201,9 +202,8 @@ struct TileGeom {
   static constexpr int NTHREADS = ((TX * TY + TX + TY) + 31) / 32 * 32;
 };
 
-template <typename T, int R, int NTR, int TX, int TY, int MINB>
-__global__ void __launch_bounds__(TileGeom<TX, TY>::NTHREADS, MINB)
-k_tendency(const TendencyArgs<T> a) {
+template <typename T, int R, int NTR, int TX, int TY>
+__device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const uint3 bid) {
   constexpr int P = R - 1;          // advecting-velocity half width
   constexpr int H = R;              // plane halo
   constexpr int PW = TX + 2 * H;
@@ -236,7 +236,7 @@ k_tendency(const TendencyArgs<T> a) {
   int* gj_tab = gi_tab + PW;
 
   const int tid = threadIdx.x;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int i0 = bid.x * TX, j0 = bid.y * TY;
   const int Wt = min(TX, Nx - i0), Ht = min(TY, Ny - j0);
 
   // roles: main (TX*TY), north ghost row (TX), east ghost column (TY), idle
@@ -683,6 +683,25 @@ k_tendency(const TendencyArgs<T> a) {
   }
 }
 
+template <typename T, int R, int NTR, int TX, int TY, int MINB>
+struct TendencyK {
+  typedef TendencyArgs<T> Payload;
+  static constexpr int kThreads = TileGeom<TX, TY>::NTHREADS, kMinBlocks = MINB;
+  static __device__ __forceinline__ void run(const Payload& a, uint3 bid, uint3) {
+    tendency_body<T, R, NTR, TX, TY>(a, bid);
+  }
+};
+
+template <typename T, int R, int NTR, int TX, int TY, int MINB>
+__global__ void __launch_bounds__(TileGeom<TX, TY>::NTHREADS, MINB) k_tendency(const TendencyArgs<T> a) {
+  tendency_body<T, R, NTR, TX, TY>(a, blockIdx);
+}
+
+// The batched twin of k_tendency<T, R, NTR, TX, TY, MINB> (k_batched over TendencyK), instantiated
+// in the *_batch translation units so that the plain and batched kernels compile in parallel.
+template <typename T, int R, int NTR, int TX, int TY, int MINB>
+const void* tendency_batched_kernel();
+
 template <typename T, int R, int TX, int TY>
 static size_t tendency_smem(const TendencyArgs<T>& a) {
   constexpr int H = R;
@@ -702,13 +721,26 @@ template <typename T, int R, int NTR, int TX, int TY, int MINB>
 static cudaError_t launch_tendency_variant(const TendencyArgs<T>& a, cudaStream_t s) {
   auto kern = k_tendency<T, R, NTR, TX, TY, MINB>;
   size_t smem = tendency_smem<T, R, TX, TY>(a);
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit(kern, smem);
   if (e != cudaSuccess) return e;
   if (MINB > 1) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
   }
   dim3 grid((a.Nx + TX - 1) / TX, (a.Ny + TY - 1) / TY);
+  if (LaunchRecorder* r = active_recorder()) {
+    LaunchRecord rec;
+    rec.fn = tendency_batched_kernel<T, R, NTR, TX, TY, MINB>();
+    rec.grid = grid;
+    rec.block = dim3(TileGeom<TX, TY>::NTHREADS);
+    rec.smem = smem;
+    rec.kclass = OCN_K_TENDENCY;
+    rec.carveout = MINB > 1 ? 100 : -1;
+    rec.payload.assign(batch_stride(sizeof(a)), 0);
+    memcpy(rec.payload.data(), &a, sizeof(a));
+    r->list.push_back(std::move(rec));
+    return cudaSuccess;
+  }
   kern<<<grid, TileGeom<TX, TY>::NTHREADS, smem, s>>>(a);
   return cudaGetLastError();
 }

@@ -10,6 +10,7 @@
 // side a~ + dtau D(r), which is the same system.
 #include <cuda_runtime.h>
 
+#include "batch.cuh"
 #include "ocn_internal.cuh"
 
 namespace ocn {
@@ -26,11 +27,11 @@ __device__ __forceinline__ T qval(const VDiffArgs<T>& a, int f, const T* q, size
 
 // Explicit: dG = D(q of the stage state); G += dG and (mode 0) the new state += dt_gamma dG.
 template <typename T>
-__global__ void __launch_bounds__(kColsPerBlock) k_vdiff_explicit(const VDiffArgs<T> a) {
-  const int f = blockIdx.y;
+__device__ __forceinline__ void vdiff_explicit_body(const VDiffArgs<T>& a, const uint3 bid) {
+  const int f = bid.y;
   if (!((a.fields >> f) & 1)) return;
   const size_t plane = (size_t)a.Nx * a.Ny;
-  const size_t col = (size_t)blockIdx.x * kColsPerBlock + threadIdx.x;
+  const size_t col = (size_t)bid.x * kColsPerBlock + threadIdx.x;
   if (col >= plane) return;
   const T* __restrict__ kf = (f < 3) ? a.nuz : a.kapz;
   const T* __restrict__ qi = a.qin[f];
@@ -75,9 +76,9 @@ __global__ void __launch_bounds__(kColsPerBlock) k_vdiff_explicit(const VDiffArg
 constexpr int kChunk = 8;
 
 template <typename T>
-__global__ void __launch_bounds__(kColsPerBlock) k_vdiff_implicit(const VDiffArgs<T> a) {
+__device__ __forceinline__ void vdiff_implicit_body(const VDiffArgs<T>& a, const uint3 bid) {
   extern __shared__ __align__(16) unsigned char vsm[];
-  const int f = blockIdx.y;
+  const int f = bid.y;
   if (!((a.fields >> f) & 1)) return;
   const int Nz = a.Nz;
   const bool faces = (f == 2);
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(kColsPerBlock) k_vdiff_implicit(const VDiffArg
   }
   __syncthreads();
   const size_t plane = (size_t)a.Nx * a.Ny;
-  const size_t col = (size_t)blockIdx.x * kColsPerBlock + threadIdx.x;
+  const size_t col = (size_t)bid.x * kColsPerBlock + threadIdx.x;
   if (col >= plane) return;
   T* q = a.qout[f] + col + (size_t)n0 * plane;      // unknown r at q[r * plane]
   // forward sweep: d' overwrites the column
@@ -164,6 +165,21 @@ __global__ void __launch_bounds__(kColsPerBlock) k_vdiff_implicit(const VDiffArg
   }
 }
 
+template <typename T> struct VDiffExplicitK {
+  typedef VDiffArgs<T> Payload;
+  static constexpr int kThreads = kColsPerBlock, kMinBlocks = 1;
+  static __device__ __forceinline__ void run(const Payload& a, uint3 bid, uint3) { vdiff_explicit_body<T>(a, bid); }
+};
+template <typename T> struct VDiffImplicitK {
+  typedef VDiffArgs<T> Payload;
+  static constexpr int kThreads = kColsPerBlock, kMinBlocks = 1;
+  static __device__ __forceinline__ void run(const Payload& a, uint3 bid, uint3) { vdiff_implicit_body<T>(a, bid); }
+};
+template <typename T>
+__global__ void __launch_bounds__(kColsPerBlock) k_vdiff_explicit(const VDiffArgs<T> a) { vdiff_explicit_body<T>(a, blockIdx); }
+template <typename T>
+__global__ void __launch_bounds__(kColsPerBlock) k_vdiff_implicit(const VDiffArgs<T> a) { vdiff_implicit_body<T>(a, blockIdx); }
+
 }  // namespace
 
 template <typename T>
@@ -173,8 +189,10 @@ cudaError_t launch_vertical_diffusion(const VDiffArgs<T>& a, bool implicit, cuda
   if (implicit) {
     const size_t smem = 4 * sizeof(T) * (size_t)a.Nz;
     if (smem > 48 * 1024) return cudaErrorInvalidValue;
+    if (record_launch<VDiffImplicitK<T>>(a, grid, dim3(kColsPerBlock), smem, OCN_K_VERTICAL)) return cudaSuccess;
     k_vdiff_implicit<T><<<grid, kColsPerBlock, smem, s>>>(a);
   } else {
+    if (record_launch<VDiffExplicitK<T>>(a, grid, dim3(kColsPerBlock), 0, OCN_K_VERTICAL)) return cudaSuccess;
     k_vdiff_explicit<T><<<grid, kColsPerBlock, 0, s>>>(a);
   }
   return cudaGetLastError();

@@ -24,7 +24,7 @@ OCN_FIELD_U, OCN_FIELD_V, OCN_FIELD_W, OCN_FIELD_TRACER0 = 0, 1, 2, 3
 OCN_FIELD_P, OCN_FIELD_G, OCN_FIELD_NU_E = 10, 20, 30
 OCN_FIELD_TRACER_REF0, OCN_FIELD_RAW = 40, 0x100
 OCN_OPT_GRAPHS, OCN_OPT_SYNC_CHECK, OCN_OPT_KERNEL_TIMING, OCN_OPT_TENDENCY_VARIANT = 1, 2, 3, 4
-TENDENCY_VARIANTS = 6
+TENDENCY_VARIANTS = 7
 KERNEL_CLASSES = ["closure", "tendency", "div_fftx", "fft_y", "tridiag", "gauge", "ifftx", "correct", "column_closure",
                   "vertical"]
 STEPPERS = {"rk3": 0, "qab2": 1}
@@ -48,7 +48,10 @@ EXPORTS = ["ocn_abi_version", "ocn_last_error", "ocn_grid_create", "ocn_grid_des
            "ocn_gemm_bf16", "ocn_set_column_closure", "ocn_closure_features", "ocn_column_fluxes",
            "ocn_coarse_grain", "ocn_set_time_stepper", "ocn_set_vertical_diffusivity", "ocn_gemm_timeout_test",
            "ocn_fp32_fma_peak"]
-OCN_OPT_ENSEMBLE_MODE, OCN_ENSEMBLE_CONCURRENT, OCN_ENSEMBLE_SEQUENTIAL = 5, 0, 1
+OCN_OPT_ENSEMBLE_MODE, OCN_ENSEMBLE_CONCURRENT, OCN_ENSEMBLE_SEQUENTIAL, OCN_ENSEMBLE_BATCHED = 5, 0, 1, 2
+OCN_OPT_ENSEMBLE_BRANCHES = 6
+ENSEMBLE_MODES = {"concurrent": OCN_ENSEMBLE_CONCURRENT, "sequential": OCN_ENSEMBLE_SEQUENTIAL,
+                  "batched": OCN_ENSEMBLE_BATCHED}
 
 
 class OcnError(RuntimeError):
@@ -524,10 +527,20 @@ class Ensemble:
     def time_step(self, dt: float, nsteps: int = 1):
         _check(lib().ocn_ensemble_time_step(self._h, float(dt), int(nsteps)), "ocn_ensemble_time_step")
 
-    def set_mode(self, sequential: bool):
-        _check(lib().ocn_ensemble_set_option(self._h, OCN_OPT_ENSEMBLE_MODE,
-                                             OCN_ENSEMBLE_SEQUENTIAL if sequential else OCN_ENSEMBLE_CONCURRENT),
+    def set_mode(self, mode: str = None, sequential: bool = None):
+        """'concurrent' (one graph per step, a branch per member), 'batched' (one graph per step,
+        each kernel one launch over all members) or 'sequential' (members one after another);
+        ``sequential=True/False`` selects 'sequential' / 'concurrent'."""
+        if mode is None:
+            mode = "sequential" if sequential else "concurrent"
+        if mode not in ENSEMBLE_MODES:
+            raise ValueError(f"unknown ensemble mode {mode!r}")
+        _check(lib().ocn_ensemble_set_option(self._h, OCN_OPT_ENSEMBLE_MODE, ENSEMBLE_MODES[mode]),
                "ocn_ensemble_set_option")
+
+    def set_branches(self, n: int):
+        """Batched mode: split each group of members into n graph branches (1..64)."""
+        _check(lib().ocn_ensemble_set_option(self._h, OCN_OPT_ENSEMBLE_BRANCHES, int(n)), "ocn_ensemble_set_option")
 
     def autotune(self):
         v = (C.c_int * len(self.members))()
