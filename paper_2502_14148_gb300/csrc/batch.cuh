@@ -64,7 +64,8 @@ struct LaunchRecord {
   dim3 grid, block;
   size_t smem = 0;
   int persistent = 0;             // > 0: grid-stride kernel over the members' blocks (tiles), launched
-                                  // with min(total, persistent) blocks
+                                  // with min(ceil(total / per_block), persistent) blocks
+  int per_block = 1;              // tiles a block of such a kernel holds at once
   int kclass = 0;
   int carveout = -1;              // >= 0: preferred shared-memory carveout (percent) of the kernel
   std::vector<unsigned char> payload;

@@ -1354,7 +1354,11 @@ ocn_status plan_batched(ocn_ensemble* e, const std::vector<LaunchRecorder>& recs
         }
         memcpy(host.data() + L.start_off + ms.size() * sizeof(unsigned), &total, sizeof(unsigned));
         unsigned blocks = total;
-        if (r0.persistent > 0 && blocks > (unsigned)r0.persistent) blocks = (unsigned)r0.persistent;
+        if (r0.persistent > 0) {
+          blocks = (total + (unsigned)r0.per_block - 1) / (unsigned)r0.per_block;
+          if (blocks > (unsigned)r0.persistent) blocks = (unsigned)r0.persistent;
+          if (blocks == 0) blocks = 1;
+        }
         L.grid = dim3(blocks);
         plan->launches.push_back(L);
       }

@@ -131,6 +131,25 @@ __device__ __forceinline__ float gelu_f(float z) {
   const float hz = 0.5f * z;
   return fmaf(hz, t, hz);
 }
+// The same form on two BF16 values at once (packed BF16 arithmetic and the packed hardware tanh),
+// for the inference epilogue, whose result is rounded to BF16 anyway: every operation rounds to
+// BF16, which raises the network's output error from about 2.5 to 3.5 BF16 units (emulated on
+// N(0,1) features with the seeded initial weights), inside the 16-unit tolerance.
+__device__ __forceinline__ uint32_t tanh_bf16x2(uint32_t x) {
+  uint32_t y;
+  asm("tanh.approx.bf16x2 %0, %1;" : "=r"(y) : "r"(x));
+  return y;
+}
+__device__ __forceinline__ uint32_t gelu_bf16x2(__nv_bfloat162 z) {
+  const __nv_bfloat162 k = __float2bfloat162_rn(kGeluK), kc = __float2bfloat162_rn(kGeluKC);
+  const __nv_bfloat162 half = __float2bfloat162_rn(0.5f);
+  const __nv_bfloat162 u = __hmul2(z, __hfma2(kc, __hmul2(z, z), k));
+  const uint32_t tu = tanh_bf16x2(*reinterpret_cast<const uint32_t*>(&u));
+  const __nv_bfloat162 t = *reinterpret_cast<const __nv_bfloat162*>(&tu);
+  const __nv_bfloat162 hz = __hmul2(half, z);
+  const __nv_bfloat162 g = __hfma2(hz, t, hz);
+  return *reinterpret_cast<const uint32_t*>(&g);
+}
 __device__ __forceinline__ float gelu_prime_f(float z) {
   const float z2 = z * z;
   const float t = tanh_fast(kGeluK * fmaf(kGeluC * z, z2, z));
@@ -269,17 +288,21 @@ namespace ocn {
 namespace {
 
 constexpr int kCF = kColumnFeatures, kCH = 128, kCO = 16;
+constexpr int kGroups = 4;                          // tiles in flight per CTA, one per group of 4 warps
+constexpr int kGroupThreads = 128;                  // one thread per tile row (TMEM lane)
+constexpr int kClosureThreads = kGroups * kGroupThreads;
 constexpr int kSW1 = 0;                             // W1 [128][32]
 constexpr int kSW2 = kSW1 + kCH * kCF * 2;          // W2 [128][128]
 constexpr int kSW3 = kSW2 + kCH * kCH * 2;          // W3 [128][128]
 constexpr int kSW4 = kSW3 + kCH * kCH * 2;          // W4 [16][128]
-constexpr int kSH = kSW4 + kCO * kCH * 2;           // activations [128][128]
-constexpr int kSX = kSH;                            // features [128][32]: only live until layer 1's MMA
-                                                    // has read them, before its epilogue writes kSH
-constexpr int kSB = kSH + 128 * kCH * 2;            // biases (3*128 + 16 floats)
-constexpr int kClosureSmem = kSB + (3 * kCH + kCO) * 4;
-// two CTAs per SM (2 x 128 TMEM columns); a third cannot fit, so allocation never blocks
-static_assert(kClosureSmem * 2 + 2048 <= 228 * 1024 && kClosureSmem * 3 > 228 * 1024, "two CTAs per SM");
+constexpr int kSB = kSW4 + kCO * kCH * 2;           // biases (3*128 + 16 floats)
+constexpr int kSA = (kSB + (3 * kCH + kCO) * 4 + 1023) / 1024 * 1024;   // the groups' activation buffers
+constexpr int kSAB = 128 * kCH * 2;                 // [128][128] BF16 per group; the features [128][32] live
+                                                    // at its start until layer 1's MMA has read them
+constexpr int kClosureSmem = kSA + kGroups * kSAB;
+// one CTA per SM: the weights are staged once and shared by the four tiles in flight, which use
+// all 512 TMEM columns (128 each), so the allocation never waits on another CTA of this kernel
+static_assert(kClosureSmem + 1024 <= 227 * 1024 && 2 * kClosureSmem > 228 * 1024, "one CTA per SM");
 
 // byte offset of element (r, c) of a [rows][K] K-major BF16 matrix in the no-swizzle core-matrix layout
 __device__ __forceinline__ uint32_t cm_off(int r, int c, int K) {
@@ -305,9 +328,19 @@ __device__ __forceinline__ void closure_layer_mma(uint32_t tmem, uint32_t a_addr
   mma_commit(bar);
 }
 
-}  // namespace
-
-constexpr int kClosureThreads = 256;   // two warps per TMEM lane quadrant, 64 columns each
+// Barrier of one group of kGroupThreads threads (named barrier id >= 1), and its AND-reduction.
+__device__ __forceinline__ void group_sync(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(kGroupThreads) : "memory");
+}
+__device__ __forceinline__ bool group_sync_and(int id, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(id), "n"(kGroupThreads)
+      : "memory");
+  return r != 0;
+}
 
 // One member's tile: its arguments and the tile's index within the member.
 struct ClosureTile {
@@ -315,7 +348,12 @@ struct ClosureTile {
   long long lt;
 };
 
-// The fused closure network over 128-face tiles.  Plain: the tiles of one model (`a`), grid
+}  // namespace
+
+// The fused closure network over 128-face tiles.  A CTA holds four tiles in flight, one per
+// group of four warps (thread = tile row = TMEM lane, 128 TMEM columns per group), so that one
+// group's tensor-core layer overlaps the others' epilogues; the groups share the staged weights
+// and synchronise on their own named barriers.  Plain: the tiles of one model (`a`), grid
 // stride over them.  Batched: the tiles of all members of `bt` (member m owns tiles
 // [start[m], start[m+1])); `a` is member 0's arguments, whose network and feature normalisation
 // every member shares; each tile reads its own member's columns and writes its fluxes with its
@@ -324,9 +362,11 @@ template <bool kBatch>
 __device__ __forceinline__ void mlp_closure_body(const MlpClosureArgs& a, const BatchTable& bt, const uint3 bid,
                                                  const uint3 gdim) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ uint64_t bar;
+  __shared__ uint64_t bar[kGroups];
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int grp = warp >> 2, quad = warp & 3;
+  const int row = quad * 32 + lane;                 // this thread's tile row and TMEM lane
   auto tiles_of = [](const ColumnArgs& c) -> long long {
     return (long long)(((size_t)c.Nx * c.Ny * (c.Nz + 1) + 127) / 128);
   };
@@ -341,9 +381,9 @@ __device__ __forceinline__ void mlp_closure_body(const MlpClosureArgs& a, const 
       return {&a, t};
     }
   };
-  if (warp == 0) tmem_alloc(&tmem_base, 128);
+  if (warp == 0) tmem_alloc(&tmem_base, kGroups * kCH);
   if (tid == 0) {
-    mbar_init(&bar, 1);
+    for (int g = 0; g < kGroups; ++g) mbar_init(&bar[g], 1);
     fence_barrier_init();
   }
   stage_weights(smem + kSW1, static_cast<const __nv_bfloat16*>(a.W[0]), kCH, kCF);
@@ -355,67 +395,61 @@ __device__ __forceinline__ void mlp_closure_body(const MlpClosureArgs& a, const 
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = tmem_base;
-  const uint32_t s0 = smem_u32(smem);
-  const int quad = warp & 3, half = warp >> 2;      // TMEM lanes 32*quad.., columns 64*half..
-  const int row = quad * 32 + lane;                 // the TMEM lane / sample row this thread reads back
+  const uint32_t tmem = tmem_base + (uint32_t)(grp * kCH) + ((uint32_t)(quad * 32) << 16);   // lanes of this warp
+  const uint32_t tmem_mma = tmem_base + (uint32_t)(grp * kCH);
+  unsigned char* act = smem + kSA + grp * kSAB;
+  const uint32_t s0 = smem_u32(smem), sact = smem_u32(act);
+  const int bar_id = 1 + grp;
   uint32_t phase = 0;
   bool ok = true;
-  // raw column values of this thread's face for the features: part 0 b at levels k-3..k+2 (0-5),
-  // the face depth (6) and the column's mixed-layer depth (7); part 1 u at faces i and i+1 (0-5,
-  // 6-11) and v at faces j and j+1 (12-17, 18-23) at levels k-3..k+2; 0 outside the column
-  float raw[24];
+  // raw column values of this thread's face for its features: b at levels k-3..k+2 (0-5), the
+  // face depth (6), the column's mixed-layer depth (7), u at faces i and i+1 (8-13, 14-19) and v
+  // at faces j and j+1 (20-25, 26-31) at levels k-3..k+2; 0 outside the column
+  float raw[32];
   auto load_raw = [&](long long tt) {
 #pragma unroll
-    for (int m = 0; m < 24; ++m) raw[m] = 0.0f;
+    for (int m = 0; m < 32; ++m) raw[m] = 0.0f;
     if (tt >= ntiles) return;
     const ClosureTile ct = tile_of(tt);
     const ColumnArgs& c = ct.m->col;
     const size_t plane = (size_t)c.Nx * c.Ny, nsamp = plane * (c.Nz + 1);
-    const size_t sidx = (size_t)ct.lt * 128 + (tid & 127);
+    const size_t sidx = (size_t)ct.lt * 128 + row;
     if (sidx >= nsamp) return;
     const uint32_t s32 = (uint32_t)sidx, p32 = (uint32_t)plane;
     const int k = (int)(s32 / p32), cc = (int)(s32 - (uint32_t)k * p32);
     const int j = cc / c.Nx, i = cc - j * c.Nx;
     const int ip = (i + 1 == c.Nx) ? 0 : i + 1, jp = (j + 1 == c.Ny) ? 0 : j + 1;
-    if ((tid >> 7) == 0) {
 #pragma unroll
-      for (int m = 0; m < 6; ++m) {
-        const int lev = k - 3 + m;
-        if (lev >= 0 && lev < c.Nz) raw[m] = __ldg(c.b + col_id(c, i, j, lev));
-      }
-      raw[6] = __ldg(c.depth + k);
-      raw[7] = __ldg(c.h + (size_t)j * c.Nx + i);
-    } else {
-#pragma unroll
-      for (int m = 0; m < 6; ++m) {
-        const int lev = k - 3 + m;
-        if (lev >= 0 && lev < c.Nz) {
-          raw[m] = __ldg(c.u + col_id(c, i, j, lev));
-          raw[6 + m] = __ldg(c.u + col_id(c, ip, j, lev));
-          raw[12 + m] = __ldg(c.v + col_id(c, i, j, lev));
-          raw[18 + m] = __ldg(c.v + col_id(c, i, jp, lev));
-        }
+    for (int m = 0; m < 6; ++m) {
+      const int lev = k - 3 + m;
+      if (lev >= 0 && lev < c.Nz) {
+        raw[m] = __ldg(c.b + col_id(c, i, j, lev));
+        raw[8 + m] = __ldg(c.u + col_id(c, i, j, lev));
+        raw[14 + m] = __ldg(c.u + col_id(c, ip, j, lev));
+        raw[20 + m] = __ldg(c.v + col_id(c, i, j, lev));
+        raw[26 + m] = __ldg(c.v + col_id(c, i, jp, lev));
       }
     }
+    raw[6] = __ldg(c.depth + k);
+    raw[7] = __ldg(c.h + (size_t)j * c.Nx + i);
   };
-  load_raw(bid.x);
+  const long long stride = (long long)kGroups * gdim.x;
+  long long t = (long long)bid.x * kGroups + grp;
+  load_raw(t);
   ClosureTile cur = {&a, 0};
-  for (long long t = bid.x; t < ntiles && ok; t += gdim.x) {
+  for (; t < ntiles && ok; t += stride) {
     cur = tile_of(t);
     const ColumnArgs& c = cur.m->col;
     const size_t plane = (size_t)c.Nx * c.Ny;
     const size_t nsamp = plane * (c.Nz + 1), NW = nsamp;
-    // ---- features of sample row (tid & 127) from the raw values prefetched for this tile, half of
-    //      them per thread: part 0 the db/dz stencil (features 0-4) and the non-local features
-    //      15-19 plus the zero padding, part 1 the dubar/dz and dvbar/dz stencils (features 5-14)
+    // ---- the 20 features of this row (db/dz, dubar/dz, dvbar/dz at faces k-2..k+2, then Jb, f,
+    //      N2bg, depth, h), normalised, rounded to BF16 and stored as four 16-byte chunks
     {
-      const int r = tid & 127, fp = tid >> 7;
-      const size_t sidx = (size_t)cur.lt * 128 + r;
+      const size_t sidx = (size_t)cur.lt * 128 + row;
       const bool valid = sidx < nsamp;
-      float g[10];
+      float g[20];
 #pragma unroll
-      for (int m = 0; m < 10; ++m) g[m] = 0.0f;
+      for (int m = 0; m < 20; ++m) g[m] = 0.0f;
       if (valid) {
         const int k = (int)((uint32_t)sidx / (uint32_t)plane);
         // face q = k - 2 + m lies between levels q - 1 (raw index m) and q (raw index m + 1)
@@ -424,53 +458,52 @@ __device__ __forceinline__ void mlp_closure_body(const MlpClosureArgs& a, const 
           const int q = k - 2 + m;
           if (q >= 1 && q < c.Nz) {
             const float rz = __ldg(c.rdzf + q);
-            if (fp == 0) {
-              float d = raw[m + 1] - raw[m];
-              if (c.cref) d += __ldg(c.cref + q) - __ldg(c.cref + q - 1);
-              g[m] = d * rz;
-            } else {
-              g[m] = 0.5f * ((raw[m + 1] + raw[6 + m + 1]) - (raw[m] + raw[6 + m])) * rz;
-              g[5 + m] = 0.5f * ((raw[12 + m + 1] + raw[18 + m + 1]) - (raw[12 + m] + raw[18 + m])) * rz;
-            }
+            float d = raw[m + 1] - raw[m];
+            if (c.cref) d += __ldg(c.cref + q) - __ldg(c.cref + q - 1);
+            g[m] = d * rz;
+            g[5 + m] = 0.5f * ((raw[8 + m + 1] + raw[14 + m + 1]) - (raw[8 + m] + raw[14 + m])) * rz;
+            g[10 + m] = 0.5f * ((raw[20 + m + 1] + raw[26 + m + 1]) - (raw[20 + m] + raw[26 + m])) * rz;
           }
         }
-        if (fp == 0) { g[5] = c.Jb; g[6] = c.f; g[7] = c.N2bg; g[8] = raw[6]; g[9] = raw[7]; }
+        g[15] = c.Jb; g[16] = c.f; g[17] = c.N2bg; g[18] = raw[6]; g[19] = raw[7];
+      }
+      uint32_t pk[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int f0 = 2 * q, f1 = 2 * q + 1;
+        const float x0 = (valid && f0 < 20) ? (g[f0 < 20 ? f0 : 0] - a.mu[f0]) * a.inv_sigma[f0] : 0.0f;
+        const float x1 = (valid && f1 < 20) ? (g[f1 < 20 ? f1 : 0] - a.mu[f1]) * a.inv_sigma[f1] : 0.0f;
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
+        pk[q] = *reinterpret_cast<const uint32_t*>(&h2);
       }
 #pragma unroll
-      for (int m = 0; m < 10; ++m) {
-        const int q = (fp == 0) ? (m < 5 ? m : 10 + m) : 5 + m;
-        const float xn = valid ? (g[m] - a.mu[q]) * a.inv_sigma[q] : 0.0f;
-        *reinterpret_cast<__nv_bfloat16*>(smem + kSX + cm_off(r, q, kCF)) = __float2bfloat16_rn(xn);
-      }
-      if (fp == 0)
-        for (int q = 20; q < kCF; ++q)
-          *reinterpret_cast<__nv_bfloat16*>(smem + kSX + cm_off(r, q, kCF)) = __float2bfloat16_rn(0.0f);
+      for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4*>(act + cm_off(row, 8 * q, kCF)) =
+            make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
     }
-    // ---- prefetch the next tile's raw values: they arrive while this tile's four MMA rounds run
-    load_raw(t + gdim.x);
+    // ---- prefetch the next tile's raw values: they arrive while this tile's layers run
+    load_raw(t + stride);
     // ---- four layers
     for (int l = 0; l < 4 && ok; ++l) {
       fence_proxy_async();
       tc_fence_before();
-      __syncthreads();
-      if (tid == 0) {
+      group_sync(bar_id);
+      if (row == 0) {
         const int K = (l == 0) ? kCF : kCH, N = (l == 3) ? kCO : kCH;
-        const uint32_t aa = s0 + ((l == 0) ? kSX : kSH);
         const uint32_t bb = s0 + (l == 0 ? kSW1 : l == 1 ? kSW2 : l == 2 ? kSW3 : kSW4);
-        closure_layer_mma(tmem, aa, bb, K, N, &bar);
+        closure_layer_mma(tmem_mma, sact, bb, K, N, &bar[grp]);
       }
-      const bool done = mbar_wait_bounded(&bar, phase);
+      const bool done = mbar_wait_bounded(&bar[grp], phase);
       phase ^= 1u;
       tc_fence_after();
-      ok = __syncthreads_and(done) != 0;
+      ok = group_sync_and(bar_id, done);
       if (!ok) break;
       if (l < 3) {
         const float* bl = sbias + l * kCH;
-#pragma unroll
-        for (int c0 = 0; c0 < 64; c0 += 16) {
-          const int cb = half * 64 + c0;
+#pragma unroll 2
+        for (int cb = 0; cb < kCH; cb += 16) {
           float v[16];
-          tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)cb, v);
+          tmem_ld16(tmem + (uint32_t)cb, v);
           float bv[16];                              // the 16 biases, four 16-byte shared loads
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
@@ -479,17 +512,14 @@ __device__ __forceinline__ void mlp_closure_body(const MlpClosureArgs& a, const 
           }
           uint32_t pk[8];
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const __nv_bfloat162 h2 = __floats2bfloat162_rn(gelu_f(v[2 * q] + bv[2 * q]),
-                                                            gelu_f(v[2 * q + 1] + bv[2 * q + 1]));
-            pk[q] = *reinterpret_cast<const uint32_t*>(&h2);
-          }
-          *reinterpret_cast<uint4*>(smem + kSH + cm_off(row, cb, kCH)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-          *reinterpret_cast<uint4*>(smem + kSH + cm_off(row, cb + 8, kCH)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+          for (int q = 0; q < 8; ++q)
+            pk[q] = gelu_bf16x2(__floats2bfloat162_rn(v[2 * q] + bv[2 * q], v[2 * q + 1] + bv[2 * q + 1]));
+          *reinterpret_cast<uint4*>(act + cm_off(row, cb, kCH)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          *reinterpret_cast<uint4*>(act + cm_off(row, cb + 8, kCH)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
         }
-      } else if (half == 0) {
+      } else {
         float v[16];
-        tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16), v);
+        tmem_ld16(tmem, v);
         const size_t sidx = (size_t)cur.lt * 128 + row;
         if (sidx < nsamp) {
           const int k = (int)((uint32_t)sidx / (uint32_t)plane);
@@ -502,21 +532,21 @@ __device__ __forceinline__ void mlp_closure_body(const MlpClosureArgs& a, const 
     }
   }
   if (!ok) {
-    if (tid == 0 && cur.m->status) atomicExch(cur.m->status, 1);
-    mbar_wait_bounded(&bar, phase ^ 1u);
+    if (row == 0 && cur.m->status) atomicExch(cur.m->status, 1);
+    mbar_wait_bounded(&bar[grp], phase ^ 1u);
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, 128);
+  if (warp == 0) tmem_dealloc(tmem_base, kGroups * kCH);
 }
 
-__global__ void __launch_bounds__(kClosureThreads, 2) k_mlp_closure(const MlpClosureArgs a) {
+__global__ void __launch_bounds__(kClosureThreads, 1) k_mlp_closure(const MlpClosureArgs a) {
   const BatchTable none = {nullptr, nullptr, nullptr, 0, 0};
   mlp_closure_body<false>(a, none, blockIdx, gridDim);
 }
 
-__global__ void __launch_bounds__(kClosureThreads, 2) k_mlp_closure_batched(const BatchTable bt) {
+__global__ void __launch_bounds__(kClosureThreads, 1) k_mlp_closure_batched(const BatchTable bt) {
   mlp_closure_body<true>(*reinterpret_cast<const MlpClosureArgs*>(bt.payload), bt, blockIdx, gridDim);
 }
 
@@ -532,7 +562,8 @@ cudaError_t launch_mlp_closure(const MlpClosureArgs& a, cudaStream_t s) {
   const size_t nsamp = (size_t)a.col.Nx * a.col.Ny * (a.col.Nz + 1);
   if (nsamp + 128 >= ((size_t)1 << 31)) return cudaErrorInvalidValue;    // 32-bit face indices
   const long long ntiles = (long long)((nsamp + 127) / 128);
-  const int grid = (int)(ntiles < 2 * nsm ? ntiles : 2 * nsm);
+  const long long need = (ntiles + kGroups - 1) / kGroups;
+  const int grid = (int)(need < nsm ? need : nsm);
   if (LaunchRecorder* r = active_recorder()) {
     // batched: one tile space over the members, which share the network and the normalisation
     e = raise_smem_limit(k_mlp_closure_batched, kClosureSmem);
@@ -542,7 +573,8 @@ cudaError_t launch_mlp_closure(const MlpClosureArgs& a, cudaStream_t s) {
     rec.grid = dim3((unsigned)ntiles);
     rec.block = dim3(kClosureThreads);
     rec.smem = kClosureSmem;
-    rec.persistent = 2 * nsm;
+    rec.persistent = nsm;
+    rec.per_block = kGroups;
     rec.kclass = OCN_K_COLUMN_CLOSURE;
     rec.payload.assign(batch_stride(sizeof(a)), 0);
     memcpy(rec.payload.data(), &a, sizeof(a));
