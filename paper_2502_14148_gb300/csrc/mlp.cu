@@ -113,6 +113,23 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 lanes x 32 bits, 32 consecutive columns per thread (one load, one wait).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // GELU evaluated in the tanh form of Hendrycks & Gimpel (2016),
 //   gelu(z) ~ z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))),
 // with the hardware tanh approximation.  Its largest deviation from the erf definition
@@ -404,11 +421,13 @@ __device__ __forceinline__ void mlp_closure_body(const MlpClosureArgs& a, const 
   bool ok = true;
   // raw column values of this thread's face for its features: b at levels k-3..k+2 (0-5), the
   // face depth (6), the column's mixed-layer depth (7), u at faces i and i+1 (8-13, 14-19) and v
-  // at faces j and j+1 (20-25, 26-31) at levels k-3..k+2; 0 outside the column
-  float raw[32];
+  // at faces j and j+1 (20-25, 26-31) at levels k-3..k+2; then for the faces q = k-2..k+2 the
+  // inverse spacing 1/dz_f (32-36) and the reference-profile step cref[q] - cref[q-1] (37-41);
+  // 0 outside the column
+  float raw[42];
   auto load_raw = [&](long long tt) {
 #pragma unroll
-    for (int m = 0; m < 32; ++m) raw[m] = 0.0f;
+    for (int m = 0; m < 42; ++m) raw[m] = 0.0f;
     if (tt >= ntiles) return;
     const ClosureTile ct = tile_of(tt);
     const ColumnArgs& c = ct.m->col;
@@ -432,6 +451,14 @@ __device__ __forceinline__ void mlp_closure_body(const MlpClosureArgs& a, const 
     }
     raw[6] = __ldg(c.depth + k);
     raw[7] = __ldg(c.h + (size_t)j * c.Nx + i);
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      const int q = k - 2 + m;
+      if (q >= 1 && q < c.Nz) {
+        raw[32 + m] = __ldg(c.rdzf + q);
+        if (c.cref) raw[37 + m] = __ldg(c.cref + q) - __ldg(c.cref + q - 1);
+      }
+    }
   };
   const long long stride = (long long)kGroups * gdim.x;
   long long t = (long long)bid.x * kGroups + grp;
@@ -457,9 +484,9 @@ __device__ __forceinline__ void mlp_closure_body(const MlpClosureArgs& a, const 
         for (int m = 0; m < 5; ++m) {
           const int q = k - 2 + m;
           if (q >= 1 && q < c.Nz) {
-            const float rz = __ldg(c.rdzf + q);
+            const float rz = raw[32 + m];
             float d = raw[m + 1] - raw[m];
-            if (c.cref) d += __ldg(c.cref + q) - __ldg(c.cref + q - 1);
+            if (c.cref) d += raw[37 + m];
             g[m] = d * rz;
             g[5 + m] = 0.5f * ((raw[8 + m + 1] + raw[14 + m + 1]) - (raw[8 + m] + raw[14 + m])) * rz;
             g[10 + m] = 0.5f * ((raw[20 + m + 1] + raw[26 + m + 1]) - (raw[20 + m] + raw[26 + m])) * rz;
@@ -500,22 +527,24 @@ __device__ __forceinline__ void mlp_closure_body(const MlpClosureArgs& a, const 
       if (!ok) break;
       if (l < 3) {
         const float* bl = sbias + l * kCH;
-#pragma unroll 2
-        for (int cb = 0; cb < kCH; cb += 16) {
-          float v[16];
-          tmem_ld16(tmem + (uint32_t)cb, v);
-          float bv[16];                              // the 16 biases, four 16-byte shared loads
+        for (int cb = 0; cb < kCH; cb += 32) {
+          float v[32];
+          tmem_ld32(tmem + (uint32_t)cb, v);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float4 b4 = reinterpret_cast<const float4*>(bl + cb)[q];
-            bv[4 * q] = b4.x; bv[4 * q + 1] = b4.y; bv[4 * q + 2] = b4.z; bv[4 * q + 3] = b4.w;
+          for (int h = 0; h < 2; ++h) {
+            float bv[16];                            // 16 biases, four 16-byte shared loads
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float4 b4 = reinterpret_cast<const float4*>(bl + cb + 16 * h)[q];
+              bv[4 * q] = b4.x; bv[4 * q + 1] = b4.y; bv[4 * q + 2] = b4.z; bv[4 * q + 3] = b4.w;
+            }
+            uint32_t pk[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              pk[q] = gelu_bf16x2(__floats2bfloat162_rn(v[16 * h + 2 * q] + bv[2 * q], v[16 * h + 2 * q + 1] + bv[2 * q + 1]));
+            *reinterpret_cast<uint4*>(act + cm_off(row, cb + 16 * h, kCH)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            *reinterpret_cast<uint4*>(act + cm_off(row, cb + 16 * h + 8, kCH)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
           }
-          uint32_t pk[8];
-#pragma unroll
-          for (int q = 0; q < 8; ++q)
-            pk[q] = gelu_bf16x2(__floats2bfloat162_rn(v[2 * q] + bv[2 * q], v[2 * q + 1] + bv[2 * q + 1]));
-          *reinterpret_cast<uint4*>(act + cm_off(row, cb, kCH)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-          *reinterpret_cast<uint4*>(act + cm_off(row, cb + 8, kCH)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
         }
       } else {
         float v[16];
