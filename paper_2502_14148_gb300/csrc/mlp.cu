@@ -130,6 +130,24 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Split form for software pipelining: the load's registers are not valid until tmem_wait16
+// (which names them as operands, so that no use is scheduled before it).
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait16(uint32_t (&r)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
+}
+
 // GELU evaluated in the tanh form of Hendrycks & Gimpel (2016),
 //   gelu(z) ~ z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))),
 // with the hardware tanh approximation.  Its largest deviation from the erf definition
@@ -527,23 +545,30 @@ __device__ __forceinline__ void mlp_closure_body(const MlpClosureArgs& a, const 
       if (!ok) break;
       if (l < 3) {
         const float* bl = sbias + l * kCH;
-        for (int cb = 0; cb < kCH; cb += 32) {
-          float v[32];
-          tmem_ld32(tmem + (uint32_t)cb, v);
+        // 16-column chunks, the next chunk's TMEM load in flight while this one is processed
+        uint32_t ra[16], rb[16];
+        tmem_ld16_async(tmem, ra);
+        tmem_wait16(ra);
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            float bv[16];                            // 16 biases, four 16-byte shared loads
+        for (int cb = 0; cb < kCH; cb += 16) {
+          if (cb + 16 < kCH) tmem_ld16_async(tmem + (uint32_t)(cb + 16), rb);
+          float bv[16];                              // 16 biases, four 16-byte shared loads
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const float4 b4 = reinterpret_cast<const float4*>(bl + cb + 16 * h)[q];
-              bv[4 * q] = b4.x; bv[4 * q + 1] = b4.y; bv[4 * q + 2] = b4.z; bv[4 * q + 3] = b4.w;
-            }
-            uint32_t pk[8];
+          for (int q = 0; q < 4; ++q) {
+            const float4 b4 = reinterpret_cast<const float4*>(bl + cb)[q];
+            bv[4 * q] = b4.x; bv[4 * q + 1] = b4.y; bv[4 * q + 2] = b4.z; bv[4 * q + 3] = b4.w;
+          }
+          uint32_t pk[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-              pk[q] = gelu_bf16x2(__floats2bfloat162_rn(v[16 * h + 2 * q] + bv[2 * q], v[16 * h + 2 * q + 1] + bv[2 * q + 1]));
-            *reinterpret_cast<uint4*>(act + cm_off(row, cb + 16 * h, kCH)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-            *reinterpret_cast<uint4*>(act + cm_off(row, cb + 16 * h + 8, kCH)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+          for (int q = 0; q < 8; ++q)
+            pk[q] = gelu_bf16x2(__floats2bfloat162_rn(__uint_as_float(ra[2 * q]) + bv[2 * q],
+                                                      __uint_as_float(ra[2 * q + 1]) + bv[2 * q + 1]));
+          *reinterpret_cast<uint4*>(act + cm_off(row, cb, kCH)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          *reinterpret_cast<uint4*>(act + cm_off(row, cb + 8, kCH)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+          if (cb + 16 < kCH) {
+            tmem_wait16(rb);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) ra[q] = rb[q];
           }
         }
       } else {
