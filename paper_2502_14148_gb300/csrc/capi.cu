@@ -1437,12 +1437,16 @@ ocn_status build_batched_graph(ocn_ensemble* e, double dt, std::vector<int>& w, 
 template <typename T>
 ocn_status ensemble_step_t(ocn_ensemble* e, double dt, int nsteps) {
   for (ocn_model* m : e->models) if (!m->arena) return fail(OCN_ERR_STATE, "arena not bound");
-  if (e->mode == 1) {                       // sequential: every member on the ensemble stream in turn
-    for (int s = 0; s < nsteps; ++s)
+  if (e->mode == OCN_ENSEMBLE_SEQUENTIAL) {   // every member on the ensemble stream in turn
+    for (int s = 0; s < nsteps; ++s) {
+      int total = 0;
       for (ocn_model* m : e->models) {
         ocn_status st = time_step_t<T>(m, dt, 1);
         if (st != OCN_OK) return st;
+        total += m->launches_per_step;
       }
+      e->launches_per_step = total;
+    }
     return OCN_OK;
   }
   for (int s = 0; s < nsteps; ++s) {
