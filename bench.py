@@ -34,6 +34,7 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 CPU_SAMPLE = dict(Nx=128, Ny=128, Nz=64)     # bounded oracle sample, same spacing and physics
+CPU_SAMPLE_1CORE = dict(Nx=64, Ny=64, Nz=64)  # the single-core oracle sample
 
 
 # ------------------------------------------------------------------ algorithmic counts
@@ -205,12 +206,13 @@ def max_over_ranks(x: float, world: int) -> float:
 
 
 # ------------------------------------------------------------------ oracle legs
-def oracle_rate(workload: str, steps: int, warmup: int = 0):
-    """Time the FP64 oracle (as it stands) on the bounded sample; returns (cell-substeps/s, s/step, cores)."""
+def oracle_rate(workload: str, steps: int, warmup: int = 0, cores: int = None, sample=CPU_SAMPLE):
+    """Time the FP64 oracle (as it stands) on the bounded sample with `cores` threads (default:
+    all host cores); returns (cell-substeps/s, s/step, cores, sample description)."""
     from oracle import oracle
     from paper_2502_14148_gb300 import inputs
-    cores = os.cpu_count() or 1
-    p = inputs.config(workload, **CPU_SAMPLE)
+    cores = cores or os.cpu_count() or 1
+    p = inputs.config(workload, **sample)
     p["nthreads"] = cores
     m = oracle.OracleModel(p)
     m.set(**inputs.initial_state(p))
@@ -270,13 +272,17 @@ def run_ours(args, world, rank, local):
     model.set(**st)
     dt = p["dt"]
     qab2 = args.stepper == "qab2"
-    if qab2:
-        model.set_time_stepper("qab2", 0.1)
-    if args.vertical != "none":
-        # a surface-intensified vertical diffusivity profile (boundary-layer-like), same for momentum and tracers
-        zf = np.asarray(p["z_faces"])
-        prof = 1e-2 * np.exp((zf - zf[-1]) / 32.0)
-        model.set_vertical_diffusivity(prof, prof, implicit=(args.vertical == "implicit"))
+
+    def configure(m):
+        if qab2:
+            m.set_time_stepper("qab2", 0.1)
+        if args.vertical != "none":
+            # a surface-intensified vertical diffusivity profile (boundary-layer-like), same for momentum and tracers
+            zf = np.asarray(p["z_faces"])
+            prof = 1e-2 * np.exp((zf - zf[-1]) / 32.0)
+            m.set_vertical_diffusivity(prof, prof, implicit=(args.vertical == "implicit"))
+
+    configure(model)
     substeps = 1 if qab2 else 3
     variant, variant_ms = model.autotune()        # tile variant of the tendency kernel
 
@@ -310,24 +316,43 @@ def run_ours(args, world, rank, local):
     host_out = {n: torch.empty(model.shape(n), dtype=torch.float32).pin_memory() for n in names}
     h2d = sum(t.numel() * t.element_size() for t in host_in.values())
     d2h = sum(t.numel() * t.element_size() for t in host_out.values())
-    k_e2e = max(1, min(args.steps, 5))
+    k_e2e = max(2, min(args.steps, 6))
     model.set_option(ocn.OCN_OPT_GRAPHS, 1)
-    for _ in range(2):                             # warm the e2e path: both buffer parities' step graphs
+    # a second instance, so that one instance's host transfers overlap the other's step
+    model2 = ocn.Model(p, device=dev)
+    configure(model2)
+    model2.set_option(ocn.OCN_OPT_TENDENCY_VARIANT, variant)
+    pair = (model, model2)
+    outs = (host_out, {n: torch.empty(model.shape(n), dtype=torch.float32).pin_memory() for n in names})
+
+    def put(m):
         for n in names:
-            model.set_host(n, host_in[n])
-        model.time_step(dt, 1)
+            m.set_host(n, host_in[n])
+
+    def take(m, out):
         for n in names:
-            model.get_host(n, host_out[n])
+            m.get_host(n, out[n])
+
+    for m, out in zip(pair, outs):
+        for _ in range(2):                         # warm the e2e path: both buffer parities' step graphs
+            put(m); m.time_step(dt, 1); take(m, out)
     barrier(world)
-    t0 = time.perf_counter()
+    t0 = time.perf_counter()                       # serial: copy in, step, copy out, one step at a time
     for _ in range(k_e2e):
-        for n in names:
-            model.set_host(n, host_in[n])
-        model.time_step(dt, 1)
-        for n in names:
-            model.get_host(n, host_out[n])
+        put(model); model.time_step(dt, 1); take(model, host_out)
+    t_serial = max_over_ranks(time.perf_counter() - t0, world)
+    barrier(world)
+    t0 = time.perf_counter()                       # pipelined over the two instances
+    put(pair[0]); pair[0].time_step(dt, 1)
+    for i in range(1, k_e2e):
+        x, y = pair[i % 2], pair[(i - 1) % 2]
+        put(x); x.time_step(dt, 1)                 # step i's copies in and launch ...
+        take(y, outs[(i - 1) % 2])                 # ... while step i-1 finishes and is copied out
+    take(pair[(k_e2e - 1) % 2], outs[(k_e2e - 1) % 2])
     t_e2e = max_over_ranks(time.perf_counter() - t0, world)
     e2e_value = cells * substeps * k_e2e * world / t_e2e
+    e2e_serial = cells * substeps * k_e2e * world / t_serial
+    del model2
     fma_peak = max(ocn.fp32_fma_peak() for _ in range(3))     # measured ALU denominator
 
     if rank != 0:
@@ -386,7 +411,10 @@ def run_ours(args, world, rank, local):
         "vertical_roofline": vroof,
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": "cell-substeps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "steps": k_e2e, "path": "ocn_set_field/ocn_time_step/ocn_get_field with pinned host buffers"},
+                "steps": k_e2e, "path": "ocn_set_field/ocn_time_step/ocn_get_field with pinned host buffers; two "
+                                        "model instances alternate, so step i's copy-in and launch precede the "
+                                        "copy-out of step i-1",
+                "serial": {"value": e2e_serial, "path": "copy in, step, copy out, one step at a time"}},
         "clocks": ck,
         "checks": {"max_div": d["max_div"], "cfl": d["cfl"], "nonfinite": d["nonfinite"]},
     }
@@ -394,8 +422,10 @@ def run_ours(args, world, rank, local):
         line["config"]["workload"] += " (resized for profiling, not a bench line)"
     if world == 1 and not args.no_cpu_baseline and not qab2 and args.vertical == "none":
         rate, sps, cores, sample = oracle_rate(args.workload, 1)
+        r1, _, _, sample1 = oracle_rate(args.workload, 1, cores=1, sample=CPU_SAMPLE_1CORE)
         line["cpu_baseline"] = {"value": rate, "unit": "cell-substeps/s", "cores": cores, "kind": "oracle",
-                                "sample": sample}
+                                "sample": sample,
+                                "single_core": {"value": r1, "unit": "cell-substeps/s", "cores": 1, "sample": sample1}}
     print(json.dumps(line), flush=True)
     return 0
 

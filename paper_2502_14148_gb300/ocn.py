@@ -13,6 +13,7 @@ boundary fluxes).
 from __future__ import annotations
 
 import ctypes as C
+import json
 import os
 
 import numpy as np
@@ -200,6 +201,34 @@ def model_desc(p: dict) -> ModelDesc:
         d.bottom_flux[n] = float(p.get("bottom_flux", {}).get(name, 0.0))
     d.fp64_pivots = int(p.get("fp64_pivots", -1))
     return d
+
+
+def shape_key(p: dict) -> list:
+    """What a tendency tile choice depends on: grid size, precision, order, closure, tracer count."""
+    return [int(p["Nx"]), int(p["Ny"]), int(p["Nz"]), int(p.get("precision", 32)), int(p.get("weno_order", 5)),
+            str(p.get("closure", "none")), len(p.get("tracers", ["b"]))]
+
+
+def _tuning_cache(path: str, key: str, value=None):
+    """Read (value None) or write one entry of a JSON tuning cache; the file maps keys to choices."""
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except (OSError, ValueError):
+        data = {}
+    if value is None:
+        return data.get(key)
+    data[key] = value
+    tmp = f"{path}.{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+    return value
+
+
+def _device_name(device) -> str:
+    import torch
+    return torch.cuda.get_device_name(device)
 
 
 def grid_desc(p: dict):
@@ -456,12 +485,22 @@ class Model:
         _check(lib().ocn_kernel_times(self._h, counts, ms), "ocn_kernel_times")
         return {k: (counts[i], ms[i]) for i, k in enumerate(KERNEL_CLASSES)}
 
-    def autotune(self):
+    def autotune(self, cache: str = None):
         """Time every tendency tile variant on the current state, keep the fastest.
-        Returns (best index, [ms per launch of each variant])."""
+        Returns (best index, [ms per launch of each variant]).  With ``cache`` (a JSON file path)
+        a choice stored there for this device and model shape is applied without timing (ms is
+        then None), and a new choice is stored."""
+        key = json.dumps(["model", lib().ocn_abi_version(), _device_name(self.device), shape_key(self.params)])
+        if cache:
+            v = _tuning_cache(cache, key)
+            if v is not None:
+                self.set_option(OCN_OPT_TENDENCY_VARIANT, int(v))
+                return int(v), None
         best = C.c_int()
         ms = (C.c_double * TENDENCY_VARIANTS)()
         _check(lib().ocn_autotune(self._h, C.byref(best), ms), "ocn_autotune")
+        if cache:
+            _tuning_cache(cache, key, best.value)
         return best.value, list(ms)
 
     def synchronize(self):
@@ -486,6 +525,7 @@ class Ensemble:
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (the library has no CPU path)")
         self.params = [dict(p) for p in params_list]
+        self._mode, self._branches = "concurrent", 4
         n = len(self.params)
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         grids = (GridDesc * n)()
@@ -537,14 +577,29 @@ class Ensemble:
             raise ValueError(f"unknown ensemble mode {mode!r}")
         _check(lib().ocn_ensemble_set_option(self._h, OCN_OPT_ENSEMBLE_MODE, ENSEMBLE_MODES[mode]),
                "ocn_ensemble_set_option")
+        self._mode = mode
 
     def set_branches(self, n: int):
         """Batched mode: split each group of members into n graph branches (1..64)."""
         _check(lib().ocn_ensemble_set_option(self._h, OCN_OPT_ENSEMBLE_BRANCHES, int(n)), "ocn_ensemble_set_option")
+        self._branches = int(n)
 
-    def autotune(self):
+    def autotune(self, cache: str = None):
+        """Choose the members' tendency tile variants in context (see ocn_ensemble_autotune); returns
+        them.  With ``cache`` (a JSON file path) the choices stored there for this device, mode,
+        branch count and member list are applied without timing, and new choices are stored."""
+        key = json.dumps(["ensemble", lib().ocn_abi_version(), _device_name(self.device), self._mode, self._branches,
+                          [shape_key(p) for p in self.params]])
+        if cache:
+            v = _tuning_cache(cache, key)
+            if v is not None and len(v) == len(self.members):
+                for m, x in zip(self.members, v):
+                    m.set_option(OCN_OPT_TENDENCY_VARIANT, int(x))
+                return [int(x) for x in v]
         v = (C.c_int * len(self.members))()
         _check(lib().ocn_ensemble_autotune(self._h, v), "ocn_ensemble_autotune")
+        if cache:
+            _tuning_cache(cache, key, list(v))
         return list(v)
 
     def launches_per_step(self) -> int:

@@ -103,3 +103,20 @@ def test_batched_learned_closure_shared_and_distinct_networks(ocn):
     for i in range(4):
         d = B.members[i].diagnostics()
         assert np.isfinite(d["max_div"])
+
+
+def test_autotune_json_cache(ocn, tmp_path):
+    cache = str(tmp_path / "tuning.json")
+    ps = inputs.ensemble_configs(n=3, sizes=(16, 32), depths=(8, 16))
+    E = ocn.Ensemble(ps)
+    E.set_mode("batched")
+    for i, q in enumerate(ps):
+        E.members[i].set(**inputs.initial_state(q, seed=inputs.SEED + i))
+    v1 = E.autotune(cache=cache)
+    v2 = E.autotune(cache=cache)                # applied from the file, not re-timed
+    assert v1 == v2 and all(0 <= x < ocn.TENDENCY_VARIANTS for x in v1)
+    m = ocn.Model(ps[0])
+    m.set(**inputs.initial_state(ps[0]))
+    b1, ms1 = m.autotune(cache=cache)
+    b2, ms2 = m.autotune(cache=cache)
+    assert b1 == b2 and ms1 is not None and ms2 is None
