@@ -26,8 +26,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "batch.cuh"
 #include "ocn_internal.cuh"
+#include "weno_coeffs.h"
 
 namespace ocn {
 
@@ -57,22 +60,43 @@ static cudaError_t upload_tables_here(const WenoTables<double>& t) {
   return cudaMemcpyToSymbol(cWf, &f, sizeof(f));
 }
 
-template <typename T> struct Tab;
-template <> struct Tab<float> {
-  static __device__ __forceinline__ float sub(int r, int s, int n) { return cWf.sub[r][s][n]; }
-  static __device__ __forceinline__ float d(int r, int s) { return cWf.d[r][s]; }
-  static __device__ __forceinline__ float beta(int r, int s, int a, int b) { return cWf.beta[r][s][a][b]; }
-  static __device__ __forceinline__ float cen(int p, int n) { return cWf.cen[p][n]; }
-  static __device__ __forceinline__ float gq(int r, int s, int a) { return cWf.gq[r][s][a]; }
-  static __device__ __forceinline__ float db(int r, int s, int a, int b) { return cWf.dbeta[r][s][a][b]; }
+// f(std::integral_constant<int, i>) for i = 0 .. N-1: loops whose index must be a compile-time
+// constant (the reconstruction coefficients below are selected by it).
+template <class F, int... I>
+__device__ __forceinline__ void sfor_seq(F&& f, std::integer_sequence<int, I...>) {
+  (f(std::integral_constant<int, I>()), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void sfor(F&& f) {
+  sfor_seq(f, std::make_integer_sequence<int, N>());
+}
+
+// Reconstruction coefficients by compile-time index: FP32 as immediates (weno_coeffs.h), FP64
+// from the long-double tables in constant memory.
+template <typename T> struct Coef;
+template <> struct Coef<float> {
+  template <int r, int s, int a> static __device__ __forceinline__ float gq() {
+    constexpr float v = WenoGq<float, r, s, a>::value;
+    return v;
+  }
+  template <int r, int s, int a, int b> static __device__ __forceinline__ float db() {
+    constexpr float v = WenoDb<float, r, s, a, b>::value;
+    return v;
+  }
+  template <int r, int s> static __device__ __forceinline__ float d() {
+    constexpr float v = WenoD<float, r, s>::value;
+    return v;
+  }
+  template <int p, int n> static __device__ __forceinline__ float cen() {
+    constexpr float v = WenoCen<float, p, n>::value;
+    return v;
+  }
 };
-template <> struct Tab<double> {
-  static __device__ __forceinline__ double sub(int r, int s, int n) { return cWd.sub[r][s][n]; }
-  static __device__ __forceinline__ double d(int r, int s) { return cWd.d[r][s]; }
-  static __device__ __forceinline__ double beta(int r, int s, int a, int b) { return cWd.beta[r][s][a][b]; }
-  static __device__ __forceinline__ double cen(int p, int n) { return cWd.cen[p][n]; }
-  static __device__ __forceinline__ double gq(int r, int s, int a) { return cWd.gq[r][s][a]; }
-  static __device__ __forceinline__ double db(int r, int s, int a, int b) { return cWd.dbeta[r][s][a][b]; }
+template <> struct Coef<double> {
+  template <int r, int s, int a> static __device__ __forceinline__ double gq() { return cWd.gq[r][s][a]; }
+  template <int r, int s, int a, int b> static __device__ __forceinline__ double db() { return cWd.dbeta[r][s][a][b]; }
+  template <int r, int s> static __device__ __forceinline__ double d() { return cWd.d[r][s]; }
+  template <int p, int n> static __device__ __forceinline__ double cen() { return cWd.cen[p][n]; }
 };
 
 __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
@@ -101,31 +125,35 @@ __device__ __forceinline__ T weno(const T* s, T vel) {
     const T ref = pos ? s[r - 1] : s[r];
     const T sgn = pos ? T(1) : T(-1);
     T q[r], b[r];
-#pragma unroll
-    for (int k = 0; k < r; ++k) {
-      T acc = Tab<T>::gq(r, k, 0) * d[k];
-#pragma unroll
-      for (int a = 1; a < r - 1; ++a) acc = fma(Tab<T>::gq(r, k, a), d[k + a], acc);
+    sfor<r>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      T acc = Coef<T>::template gq<r, k, 0>() * d[k];
+      sfor<r - 2>([&](auto ac) {
+        constexpr int a = decltype(ac)::value + 1;
+        acc = fma(Coef<T>::template gq<r, k, a>(), d[k + a], acc);
+      });
       q[k] = acc;
       T bb = T(0);
-#pragma unroll
-      for (int a = 0; a < r - 1; ++a) {
-        T inner = Tab<T>::db(r, k, a, a) * d[k + a];
-#pragma unroll
-        for (int c = a + 1; c < r - 1; ++c) inner = fma(Tab<T>::db(r, k, a, c), d[k + c], inner);
+      sfor<r - 1>([&](auto ac) {
+        constexpr int a = decltype(ac)::value;
+        T inner = Coef<T>::template db<r, k, a, a>() * d[k + a];
+        sfor<r - 2 - a>([&](auto cc) {
+          constexpr int c = decltype(cc)::value + a + 1;
+          inner = fma(Coef<T>::template db<r, k, a, c>(), d[k + c], inner);
+        });
         bb = fma(inner, d[k + a], bb);
-      }
+      });
       b[k] = bb;
-    }
+    });
     const T tau = fabs(b[0] - b[r - 1]);
     T num = T(0), den = T(0);
-#pragma unroll
-    for (int k = 0; k < r; ++k) {
+    sfor<r>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
       const T ratio = tau * rcp(b[k] + T(1e-8));
-      const T alpha = Tab<T>::d(r, k) * fma(ratio, ratio, T(1));
+      const T alpha = Coef<T>::template d<r, k>() * fma(ratio, ratio, T(1));
       num = fma(alpha, q[k], num);
       den += alpha;
-    }
+    });
     return fma(sgn, num * rcp(den), ref);
   }
 }
@@ -156,8 +184,10 @@ template <typename T> __device__ __forceinline__ T rstrain(T x, T y, T r, T g) {
 template <typename T, int p>
 __device__ __forceinline__ T centered(const T* s) {
   T acc = T(0);
-#pragma unroll
-  for (int n = 0; n < p; ++n) acc = fma(Tab<T>::cen(p, n), s[n] + s[2 * p - 1 - n], acc);
+  sfor<p>([&](auto nc) {
+    constexpr int n = decltype(nc)::value;
+    acc = fma(Coef<T>::template cen<p, n>(), s[n] + s[2 * p - 1 - n], acc);
+  });
   return acc;
 }
 
