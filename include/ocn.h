@@ -186,7 +186,9 @@ ocn_status ocn_compute_tendencies(ocn_model* model);
 ocn_status ocn_diagnostics(ocn_model* model, double dt, double* out, int nout);
 
 /* Options.  OCN_OPT_GRAPHS: 1 (default) replays each time step from a CUDA
- * graph captured on first use per dt; 0 launches kernels directly.
+ * graph captured on first use per dt (at most 32 kept per model or ensemble: a
+ * run with many distinct dt values starts the cache over); 0 launches kernels
+ * directly.
  * OCN_OPT_SYNC_CHECK: 1 synchronises and checks for errors after every kernel.
  * OCN_OPT_KERNEL_TIMING: 1 launches directly and brackets every kernel with
  * CUDA events on the model stream (read with ocn_kernel_times); 0 (default) off. */

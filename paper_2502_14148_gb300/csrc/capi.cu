@@ -28,6 +28,9 @@
 using namespace ocn;
 
 namespace ocn {
+// step graphs kept per model or ensemble (keyed by time step, buffer parity, stepper state)
+constexpr size_t kGraphCacheMax = 32;
+
 LaunchRecorder*& active_recorder() {
   static thread_local LaunchRecorder* r = nullptr;
   return r;
@@ -518,6 +521,8 @@ cudaError_t enqueue_step(ocn_model* m, double dt, int* which, int* nlaunch) {
   return cudaSuccess;
 }
 
+void drop_graphs(ocn_model* m);
+
 template <typename T>
 ocn_status time_step_t(ocn_model* m, double dt, int nsteps) {
   const bool use_graph = m->graphs && m->stream != nullptr && !m->sync_check && !m->timing;
@@ -538,6 +543,11 @@ ocn_status time_step_t(ocn_model* m, double dt, int nsteps) {
     cudaGraphExec_t exec = nullptr;
     int w = m->cur;
     if (it == m->graph_cache.end()) {
+      if (m->graph_cache.size() >= kGraphCacheMax) {   // many time steps (adaptive dt): start over
+        cudaError_t es = cudaStreamSynchronize(m->stream);
+        if (es != cudaSuccess) return cuda_fail(es, "graph cache reset");
+        drop_graphs(m);
+      }
       cudaGraph_t graph = nullptr;
       cudaError_t e = cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) return cuda_fail(e, "begin capture");
@@ -1461,6 +1471,11 @@ ocn_status ensemble_step_t(ocn_ensemble* e, double dt, int nsteps) {
     }
     auto it = e->graphs.find(key);
     std::vector<int> w(e->n);
+    if (it == e->graphs.end() && e->graphs.size() >= kGraphCacheMax) {   // many time steps: start over
+      cudaError_t es = cudaStreamSynchronize(e->stream);
+      if (es != cudaSuccess) return cuda_fail(es, "graph cache reset");
+      clear_graphs(e);
+    }
     if (it == e->graphs.end() && e->mode == OCN_ENSEMBLE_BATCHED) {
       cudaGraphExec_t exec = nullptr;
       void* tables = nullptr;

@@ -120,3 +120,25 @@ def test_autotune_json_cache(ocn, tmp_path):
     b1, ms1 = m.autotune(cache=cache)
     b2, ms2 = m.autotune(cache=cache)
     assert b1 == b2 and ms1 is not None and ms2 is None
+
+
+def test_graph_caches_bounded_with_varying_dt(ocn):
+    """Forty distinct time steps (each a new step graph) pass the cache bound; results equal direct launches."""
+    torch = pytest.importorskip("torch")
+    p = inputs.config("cbl_256", Nx=32, Ny=32, Nz=16)
+    st = inputs.initial_state(p)
+    a, b = ocn.Model(p), ocn.Model(p)
+    a.set(**st)
+    b.set(**st)
+    b.set_option(ocn.OCN_OPT_GRAPHS, 0)
+    ps = inputs.ensemble_configs(n=2, sizes=(16,), depths=(8,))
+    E, S = _pair(ocn, ps)
+    for i in range(40):
+        dt = 2.0 + 0.05 * i
+        a.time_step(dt, 1)
+        b.time_step(dt, 1)
+        E.time_step(dt, 1)
+        S.time_step(dt, 1)
+    for n in ("u", "v", "w", "b"):
+        assert torch.equal(a.get(n), b.get(n)), n
+    _assert_equal(E, S)
