@@ -66,6 +66,27 @@ __device__ __forceinline__ void dft(C* v, int s) {
   }
 }
 
+// Division by a divisor that is fixed for a whole loop: a shift and a mask when it is a power of
+// two, else a float reciprocal with one correction step (exact for 0 <= x < 2^22; larger x divide).
+struct IDiv {
+  int d, sh;
+  float inv;
+  bool p2;
+  __device__ __forceinline__ explicit IDiv(int d_) : d(d_), sh(0), inv(1.0f / (float)d_), p2((d_ & (d_ - 1)) == 0) {
+    while ((1 << sh) < d_) ++sh;
+  }
+  __device__ __forceinline__ int div(int x) const {
+    if (p2) return x >> sh;
+    if (x >= (1 << 22)) return x / d;
+    int q = __float2int_rz((float)x * inv);
+    const int r = x - q * d;
+    if (r >= d) ++q;
+    else if (r < 0) --q;
+    return q;
+  }
+  __device__ __forceinline__ int mod(int x) const { return p2 ? (x & (d - 1)) : x - div(x) * d; }
+};
+
 // One Stockham pass of radix R over `nlines` lines of length N held in `src`,
 // written to `dst`.  Element e of line l lives at l*sl + e*se.  The twiddle
 // table holds e^{-2 pi i t / (N*tws)} for t < N*tws (tws = stride into it).
@@ -75,25 +96,26 @@ __device__ __forceinline__ void stockham_pass(const C* src, C* dst, int N, int N
   const int nb = N / R;
   const int total = nlines * nb;
   const int twstep = N / (Ns * R);
+  const IDiv dl(line_fast ? nlines : nb), dns(Ns);
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     int l, j;
-    if (line_fast) { l = idx % nlines; j = idx / nlines; }
-    else { j = idx % nb; l = idx / nb; }
+    if (line_fast) { j = dl.div(idx); l = idx - j * nlines; }
+    else { l = dl.div(idx); j = idx - l * nb; }
     C v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = src[l * sl + (j + r * nb) * se];
-    const int k = j % Ns;
+    const int jq = dns.div(j), k = j - jq * Ns;
     if (Ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        int t = (r * k * twstep) % N;
+        const int t = r * k * twstep;           // < N: k < Ns, r < R, twstep = N / (Ns R)
         C w = tw[t * tws];
         if (s > 0) w.y = -w.y;
         v[r] = cmul(v[r], w);
       }
     }
     dft<C, T, R>(v, s);
-    const int base = (j / Ns) * Ns * R + k;
+    const int base = jq * Ns * R + k;
 #pragma unroll
     for (int r = 0; r < R; ++r) dst[l * sl + (base + r * Ns) * se] = v[r];
   }
@@ -131,10 +153,11 @@ __device__ __forceinline__ void div_fftx_body(const PoissonArgs<T>& a, int LR, c
   const size_t plane = (size_t)Nx * Ny;
   const int row0 = bid.x * LR;
   const int nrows = min(LR, Ny * Nz - row0);
+  const IDiv dM(M), dNy(Ny);
   for (int idx = threadIdx.x; idx < nrows * M; idx += blockDim.x) {
-    const int l = idx / M, n = idx % M;
+    const int l = dM.div(idx), n = idx - l * M;
     const int row = row0 + l;
-    const int j = row % Ny, k = row / Ny;
+    const int k = dNy.div(row), j = row - k * Ny;
     const int jp = (j + 1 == Ny) ? 0 : j + 1;
     const T rdz = __ldg(a.rdzc + k);
     T val[2];
@@ -153,14 +176,15 @@ __device__ __forceinline__ void div_fftx_body(const PoissonArgs<T>& a, int LR, c
   C* Z = block_fft<C, T>(A, B, a.px, nrows, M, 1, reinterpret_cast<const C*>(a.twx), 2, -1, false);
   // split: X[kx] = E + W^kx O, E = (Z[kx] + conj Z[M-kx])/2, O = (Z[kx] - conj Z[M-kx])/(2i)
   const int S = M + 1;
+  const IDiv dS(S);
   for (int idx = threadIdx.x; idx < nrows * S; idx += blockDim.x) {
-    const int l = idx / S, kx = idx % S;
-    const C z1 = Z[l * M + (kx % M)];
-    const C z2 = cconj(Z[l * M + ((M - kx) % M)]);
+    const int l = dS.div(idx), kx = idx - l * S;          // kx = 0 .. M
+    const C z1 = Z[l * M + (kx == M ? 0 : kx)];
+    const C z2 = cconj(Z[l * M + (kx == 0 ? 0 : M - kx)]);
     const C E = cscale(cadd(z1, z2), T(0.5));
     const C D = cscale(csub(z1, z2), T(0.5));
     const C O = {D.y, -D.x};                   // D / i
-    const C w = reinterpret_cast<const C*>(a.twx)[kx % Nx];
+    const C w = reinterpret_cast<const C*>(a.twx)[kx];    // kx <= M < Nx
     const C X = cadd(E, cmul(w, O));
     const int row = row0 + l;
     reinterpret_cast<C*>(a.spec)[(size_t)row * S + kx] = X;
@@ -180,8 +204,9 @@ __device__ __forceinline__ void ifftx_body(const PoissonArgs<T>& a, int LR, cons
   const int nrows = min(LR, Ny * Nz - row0);
   const C* spec = reinterpret_cast<const C*>(a.spec);
   const C* tw = reinterpret_cast<const C*>(a.twx);
+  const IDiv dM(M);
   for (int idx = threadIdx.x; idx < nrows * M; idx += blockDim.x) {
-    const int l = idx / M, kx = idx % M;
+    const int l = dM.div(idx), kx = idx - l * M;
     const size_t ro = (size_t)(row0 + l) * S;
     const C x1 = spec[ro + kx];
     const C x2 = cconj(spec[ro + (M - kx)]);
@@ -197,7 +222,7 @@ __device__ __forceinline__ void ifftx_body(const PoissonArgs<T>& a, int LR, cons
   const size_t plane = (size_t)Nx * Ny;
   (void)plane;
   for (int idx = threadIdx.x; idx < nrows * M; idx += blockDim.x) {
-    const int l = idx / M, n = idx % M;
+    const int l = dM.div(idx), n = idx - l * M;
     const int row = row0 + l;
     const C v = z[l * M + n];
     a.p[(size_t)row * Nx + 2 * n] = v.x;
@@ -216,14 +241,15 @@ __device__ __forceinline__ void fft_y_body(const PoissonArgs<T>& a, int CW, int 
   const int kx0 = bid.x * CW, k = bid.y;
   const int ncol = min(CW, S - kx0);
   C* spec = reinterpret_cast<C*>(a.spec) + (size_t)k * Ny * S;
+  const IDiv dCW(CW);
   for (int idx = threadIdx.x; idx < Ny * CW; idx += blockDim.x) {
-    const int c = idx % CW, j = idx / CW;
+    const int j = dCW.div(idx), c = idx - j * CW;
     if (c < ncol) A[j * CW + c] = spec[(size_t)j * S + kx0 + c];
   }
   __syncthreads();
   C* r = block_fft<C, T>(A, B, a.py, CW, 1, CW, reinterpret_cast<const C*>(a.twy), 1, sign, true);
   for (int idx = threadIdx.x; idx < Ny * CW; idx += blockDim.x) {
-    const int c = idx % CW, j = idx / CW;
+    const int j = dCW.div(idx), c = idx - j * CW;
     if (c < ncol) spec[(size_t)j * S + kx0 + c] = r[j * CW + c];
   }
 }
