@@ -230,7 +230,8 @@ __device__ __forceinline__ void ifftx_body(const PoissonArgs<T>& a, int LR, cons
   }
 }
 
-// FFT along y of a tile of CW kx-columns in one z-plane, in place.
+// FFT along y of a tile of CW kx-columns in one z-plane, in place; the Ny twiddles are staged in
+// shared memory after the two data buffers.
 template <typename T>
 __device__ __forceinline__ void fft_y_body(const PoissonArgs<T>& a, int CW, int sign, const uint3 bid) {
   typedef typename CT<T>::type C;
@@ -238,16 +239,19 @@ __device__ __forceinline__ void fft_y_body(const PoissonArgs<T>& a, int CW, int 
   C* A = reinterpret_cast<C*>(sm_raw);
   const int Ny = a.Ny, S = a.Mx + 1;
   C* B = A + Ny * CW;
+  C* sTw = B + Ny * CW;
   const int kx0 = bid.x * CW, k = bid.y;
   const int ncol = min(CW, S - kx0);
   C* spec = reinterpret_cast<C*>(a.spec) + (size_t)k * Ny * S;
+  const C* twy = reinterpret_cast<const C*>(a.twy);
+  for (int t = threadIdx.x; t < Ny; t += blockDim.x) sTw[t] = twy[t];
   const IDiv dCW(CW);
   for (int idx = threadIdx.x; idx < Ny * CW; idx += blockDim.x) {
     const int j = dCW.div(idx), c = idx - j * CW;
     if (c < ncol) A[j * CW + c] = spec[(size_t)j * S + kx0 + c];
   }
   __syncthreads();
-  C* r = block_fft<C, T>(A, B, a.py, CW, 1, CW, reinterpret_cast<const C*>(a.twy), 1, sign, true);
+  C* r = block_fft<C, T>(A, B, a.py, CW, 1, CW, sTw, 1, sign, true);
   for (int idx = threadIdx.x; idx < Ny * CW; idx += blockDim.x) {
     const int j = dCW.div(idx), c = idx - j * CW;
     if (c < ncol) spec[(size_t)j * S + kx0 + c] = r[j * CW + c];
@@ -528,7 +532,7 @@ cudaError_t launch_projection(const PoissonArgs<T>& a, cudaStream_t s, int* nlau
   // about 2048 (FP32) / 1024 (FP64) values, but not beyond the spectrum's width
   int CW = (sizeof(T) == 4) ? 8 : 4;
   while (CW * a.Ny < (sizeof(T) == 4 ? 2048 : 1024) && CW < a.Mx + 1) CW *= 2;
-  const size_t smy = 2 * (size_t)a.Ny * CW * sizeof(C);
+  const size_t smy = (2 * (size_t)a.Ny * CW + a.Ny) * sizeof(C);
   e = raise_smem_limit(k_fft_y<T>, smy);
   if (e != cudaSuccess) return e;
   dim3 gy((a.Mx + 1 + CW - 1) / CW, a.Nz);
