@@ -111,16 +111,20 @@ __device__ __forceinline__ void closure_body(const ClosureArgs<T>& a, const uint
     } else {  // AMD
       const T G[3][3] = {{ux, uy, uz}, {vx, vy, vz}, {wx, wy, wz}};
       const T D2[3] = {a.dx * a.dx, a.dy * a.dy, dz * dz};
+      // num = sum_m D2_m g_m^T S g_m over the columns g_m = G[.][m]; with S the symmetric part of G,
+      // g^T S g = g^T G g, so each term is one matrix-vector product and a dot product
       T num = T(0), den = T(0);
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        T h = T(0);
+#pragma unroll
+        for (int p = 0; p < 3; ++p) h += G[p][m] * (G[p][0] * G[0][m] + G[p][1] * G[1][m] + G[p][2] * G[2][m]);
+        num += D2[m] * h;
+      }
 #pragma unroll
       for (int p = 0; p < 3; ++p)
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          const T Spq = T(0.5) * (G[p][q] + G[q][p]);
-#pragma unroll
-          for (int m = 0; m < 3; ++m) num += D2[m] * G[p][m] * G[q][m] * Spq;
-          den += G[p][q] * G[p][q];
-        }
+        for (int q = 0; q < 3; ++q) den += G[p][q] * G[p][q];
       T nu = (den > T(0)) ? -a.C_amd * num / den : T(0);
       a.nu[id] = nu > T(0) ? nu : T(0);
       for (int t = 0; t < a.nt; ++t) {
@@ -132,11 +136,10 @@ __device__ __forceinline__ void closure_body(const ClosureArgs<T>& a, const uint
         const T dcb = (k >= 1) ? ((c0 - __ldg(c + id - plane)) + (cref(t, k) - cref(t, k - 1))) * __ldg(a.rdzf + k) : T(0);
         const T dct = (k + 1 < Nz) ? ((__ldg(c + id + plane) - c0) + (cref(t, k + 1) - cref(t, k))) * rdzf1 : T(0);
         dc[2] = T(0.5) * (dcb + dct);
+        // cn = sum_m D2_m dc_m (sum_p G[p][m] dc_p)
         T cn = T(0), cd = T(0);
 #pragma unroll
-        for (int m = 0; m < 3; ++m)
-#pragma unroll
-          for (int p = 0; p < 3; ++p) cn += D2[m] * G[p][m] * dc[m] * dc[p];
+        for (int m = 0; m < 3; ++m) cn += D2[m] * dc[m] * (G[0][m] * dc[0] + G[1][m] * dc[1] + G[2][m] * dc[2]);
 #pragma unroll
         for (int p = 0; p < 3; ++p) cd += dc[p] * dc[p];
         T kap = (cd > T(0)) ? -a.C_amd * cn / cd : T(0);
