@@ -206,9 +206,10 @@ def max_over_ranks(x: float, world: int) -> float:
 
 
 # ------------------------------------------------------------------ oracle legs
-def oracle_rate(workload: str, steps: int, warmup: int = 0, cores: int = None, sample=CPU_SAMPLE):
+def oracle_rate(workload: str, steps: int, warmup: int = 0, cores: int = None, sample=CPU_SAMPLE, keep=None):
     """Time the FP64 oracle (as it stands) on the bounded sample with `cores` threads (default:
-    all host cores); returns (cell-substeps/s, s/step, cores, sample description)."""
+    all host cores); returns (cell-substeps/s, s/step, cores, sample description).  `keep` (a
+    dict) receives the sample's parameters and the oracle model after the timed steps."""
     from oracle import oracle
     from paper_2502_14148_gb300 import inputs
     cores = cores or os.cpu_count() or 1
@@ -223,6 +224,8 @@ def oracle_rate(workload: str, steps: int, warmup: int = 0, cores: int = None, s
     m.time_step(p["dt"], steps)
     dt = time.perf_counter() - t0
     cells = p["Nx"] * p["Ny"] * p["Nz"]
+    if keep is not None:
+        keep.update(params=p, model=m, steps=warmup + steps)
     return cells * 3 * steps / dt, dt / steps, cores, f"{p['Nx']}x{p['Ny']}x{p['Nz']} cells of the {workload} physics and spacing, {steps} RK3 step(s), FP64 oracle"
 
 
@@ -421,11 +424,23 @@ def run_ours(args, world, rank, local):
     if args.size:
         line["config"]["workload"] += " (resized for profiling, not a bench line)"
     if world == 1 and not args.no_cpu_baseline and not qab2 and args.vertical == "none":
-        rate, sps, cores, sample = oracle_rate(args.workload, 1)
+        kept = {}
+        rate, sps, cores, sample = oracle_rate(args.workload, 1, keep=kept)
         r1, _, _, sample1 = oracle_rate(args.workload, 1, cores=1, sample=CPU_SAMPLE_1CORE)
         line["cpu_baseline"] = {"value": rate, "unit": "cell-substeps/s", "cores": cores, "kind": "oracle",
                                 "sample": sample,
                                 "single_core": {"value": r1, "unit": "cell-substeps/s", "cores": 1, "sample": sample1}}
+        # the same sample stepped by the library, against the oracle's result (relative L2 per field)
+        ps, om = kept["params"], kept["model"]
+        gm = ocn.Model(ps, device=dev)
+        gm.set(**inputs.initial_state(ps))
+        gm.time_step(ps["dt"], kept["steps"])
+        err = {}
+        for n in ["u", "v", "w"] + gm.tracers:
+            ref = om.get(n)
+            err[n] = float(np.linalg.norm(gm.get_numpy(n).astype(np.float64) - ref) / max(np.linalg.norm(ref), 1e-300))
+        line["oracle_error"] = {"rel_l2": err, "sample": sample, "precision": f"FP{ps['precision']} vs the FP64 oracle"}
+        del gm
     print(json.dumps(line), flush=True)
     return 0
 
