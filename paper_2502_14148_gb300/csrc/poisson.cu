@@ -156,6 +156,10 @@ __device__ __forceinline__ void div_fftx_body(const PoissonArgs<T>& a, int LR, c
   const int row0 = bid.x * LR;
   const int nrows = min(LR, Ny * Nz - row0);
   const IDiv dM(M), dNy(Ny);
+  // pairs of cells as 2-vectors when the fields are aligned to them (the no-allocation projection
+  // takes the caller's arrays)
+  const bool pairs = ((reinterpret_cast<uintptr_t>(a.u) | reinterpret_cast<uintptr_t>(a.v) |
+                       reinterpret_cast<uintptr_t>(a.w)) & (2 * sizeof(T) - 1)) == 0;
   for (int idx = threadIdx.x; idx < nrows * M; idx += blockDim.x) {
     const int l = dM.div(idx), n = idx - l * M;
     const int row = row0 + l;
@@ -163,14 +167,25 @@ __device__ __forceinline__ void div_fftx_body(const PoissonArgs<T>& a, int LR, c
     const int jp = (j + 1 == Ny) ? 0 : j + 1;
     const T rdz = __ldg(a.rdzc + k);
     T val[2];
+    const size_t o = (size_t)k * plane + (size_t)j * Nx;
+    if (pairs) {                        // cells 2n, 2n+1 as one vector per field and level
+      const C u01 = *reinterpret_cast<const C*>(a.u + o + 2 * n);
+      const T u2 = a.u[o + (2 * n + 2 == Nx ? 0 : 2 * n + 2)];
+      const C vj = *reinterpret_cast<const C*>(a.v + o + 2 * n);
+      const C vp = *reinterpret_cast<const C*>(a.v + (size_t)k * plane + (size_t)jp * Nx + 2 * n);
+      const C wk = *reinterpret_cast<const C*>(a.w + o + 2 * n);
+      const C wt = *reinterpret_cast<const C*>(a.w + o + plane + 2 * n);
+      val[0] = ((u01.y - u01.x) * a.rdx + (vp.x - vj.x) * a.rdy + (wt.x - wk.x) * rdz) * a.inv_dt;
+      val[1] = ((u2 - u01.y) * a.rdx + (vp.y - vj.y) * a.rdy + (wt.y - wk.y) * rdz) * a.inv_dt;
+    } else {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int i = 2 * n + h;
-      const int ip = (i + 1 == Nx) ? 0 : i + 1;
-      const size_t o = (size_t)k * plane + (size_t)j * Nx;
-      const T div = (a.u[o + ip] - a.u[o + i]) * a.rdx + (a.v[(size_t)k * plane + (size_t)jp * Nx + i] - a.v[o + i]) * a.rdy +
-                    (a.w[o + plane + i] - a.w[o + i]) * rdz;
-      val[h] = div * a.inv_dt;
+      for (int h = 0; h < 2; ++h) {
+        const int i = 2 * n + h;
+        const int ip = (i + 1 == Nx) ? 0 : i + 1;
+        const T div = (a.u[o + ip] - a.u[o + i]) * a.rdx + (a.v[(size_t)k * plane + (size_t)jp * Nx + i] - a.v[o + i]) * a.rdy +
+                      (a.w[o + plane + i] - a.w[o + i]) * rdz;
+        val[h] = div * a.inv_dt;
+      }
     }
     A[l * M + n] = C{val[0], val[1]};
   }
@@ -221,14 +236,19 @@ __device__ __forceinline__ void ifftx_body(const PoissonArgs<T>& a, int LR, cons
   }
   __syncthreads();
   C* z = block_fft<C, T>(A, B, a.px, nrows, M, 1, tw, 2, +1, false);
+  const bool pairs = (reinterpret_cast<uintptr_t>(a.p) & (2 * sizeof(T) - 1)) == 0;   // p as 2-vectors
   const size_t plane = (size_t)Nx * Ny;
   (void)plane;
   for (int idx = threadIdx.x; idx < nrows * M; idx += blockDim.x) {
     const int l = dM.div(idx), n = idx - l * M;
     const int row = row0 + l;
     const C v = z[l * M + n];
-    a.p[(size_t)row * Nx + 2 * n] = v.x;
-    a.p[(size_t)row * Nx + 2 * n + 1] = v.y;
+    if (pairs) {
+      *reinterpret_cast<C*>(a.p + (size_t)row * Nx + 2 * n) = v;
+    } else {
+      a.p[(size_t)row * Nx + 2 * n] = v.x;
+      a.p[(size_t)row * Nx + 2 * n + 1] = v.y;
+    }
   }
 }
 
