@@ -34,9 +34,9 @@
 
 namespace ocn {
 
-// Each translation unit that includes this header owns its copy of the tables
-// (no relocatable device code), uploaded by its own upload function.
-static __constant__ WenoTables<float> cWf;
+// Each translation unit that includes this header owns its copy of the FP64 tables
+// (no relocatable device code), uploaded by its own upload function; the FP32 kernels
+// take their coefficients as compile-time constants (weno_coeffs.h).
 static __constant__ WenoTables<double> cWd;
 
 static cudaError_t upload_tables_here(const WenoTables<double>& t) {
@@ -50,14 +50,7 @@ static cudaError_t upload_tables_here(const WenoTables<double>& t) {
         for (int b = 0; b < r - 1; ++b)
           d.dbeta[r][s][a][b] = (b > a) ? 2.0 * t.dbeta[r][s][a][b] : (b == a ? t.dbeta[r][s][a][b] : 0.0);
     }
-  WenoTables<float> f;
-  const double* src = reinterpret_cast<const double*>(&d);
-  float* dst = reinterpret_cast<float*>(&f);
-  static_assert(sizeof(WenoTables<double>) == 2 * sizeof(WenoTables<float>), "table layout");
-  for (size_t n = 0; n < sizeof(WenoTables<float>) / sizeof(float); ++n) dst[n] = (float)src[n];
-  cudaError_t e = cudaMemcpyToSymbol(cWd, &d, sizeof(d));
-  if (e != cudaSuccess) return e;
-  return cudaMemcpyToSymbol(cWf, &f, sizeof(f));
+  return cudaMemcpyToSymbol(cWd, &d, sizeof(d));
 }
 
 // f(std::integral_constant<int, i>) for i = 0 .. N-1: loops whose index must be a compile-time
