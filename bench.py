@@ -96,7 +96,7 @@ def measured_peaks() -> dict:
 MLP_FLOPS_PER_SAMPLE = 2 * (32 * 128 + 128 * 128 + 128 * 128 + 128 * 16)
 
 
-PROFILED_SOURCES = {"tendency": ["tendency_kernel.cuh", "tendency_f32_r5.cu", "tendency_f32_r3.cu"],
+PROFILED_SOURCES = {"tendency": ["tendency_kernel.cuh", "weno_coeffs.h", "tendency_f32_r5.cu", "tendency_f32_r5_smag.cu"],
                     "mlp_closure": ["mlp.cu", "column.cuh"]}
 
 

@@ -18,8 +18,9 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libocn.so")
-SOURCES = ["capi.cu", "coeffs.cpp", "tendency_f32_r5.cu", "tendency_f32_r3.cu", "tendency_f64.cu", "tendency_f32_r5_batch.cu",
-           "tendency_f32_r3_batch.cu", "tendency_f64_batch.cu", "closure.cu",
+SOURCES = ["capi.cu", "coeffs.cpp", "tendency_f64.cu", "tendency_f64_batch.cu"] + \
+          [f"tendency_f32_r{r}{part}.cu" for r in (5, 3)
+           for part in ("", "_smag", "_amd", "_batch", "_batch_smag", "_batch_amd")] + ["closure.cu",
            "poisson.cu", "reduce.cu", "noalloc.cu", "mlp.cu", "column.cu", "vertical.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -30,11 +30,7 @@ struct WenoTables {
 void derive_weno_tables(WenoTables<double>* out);
 // Upload to the constant memory of every tendency translation unit.
 cudaError_t upload_weno_tables(const WenoTables<double>& t);
-cudaError_t upload_tables_f32_r5(const WenoTables<double>& t);
-cudaError_t upload_tables_f32_r3(const WenoTables<double>& t);
 cudaError_t upload_tables_f64(const WenoTables<double>& t);
-cudaError_t upload_tables_f32_r5_batch(const WenoTables<double>& t);
-cudaError_t upload_tables_f32_r3_batch(const WenoTables<double>& t);
 cudaError_t upload_tables_f64_batch(const WenoTables<double>& t);
 
 // Fields of one prognostic state.

@@ -5,7 +5,7 @@ namespace ocn {
 
 template <int R, int NTR>
 static cudaError_t launch_f64_rn(const TendencyArgs<double>& a, cudaStream_t s) {
-  return launch_tendency_variant<double, R, NTR, 32, 8, 1>(a, s);
+  return launch_tendency_variant<double, R, NTR, 32, 8, 1, kClAny>(a, s);
 }
 
 cudaError_t launch_tendency_f64(const TendencyArgs<double>& a, int weno_r, cudaStream_t s) {
@@ -29,11 +29,8 @@ cudaError_t launch_tendency<double>(const TendencyArgs<double>& a, int weno_r, c
 }
 
 cudaError_t upload_weno_tables(const WenoTables<double>& t) {
-  cudaError_t e = upload_tables_f32_r5(t);
-  if (e == cudaSuccess) e = upload_tables_f32_r3(t);
-  if (e == cudaSuccess) e = upload_tables_f64(t);
-  if (e == cudaSuccess) e = upload_tables_f32_r5_batch(t);
-  if (e == cudaSuccess) e = upload_tables_f32_r3_batch(t);
+  // only the FP64 kernels read the tables (the FP32 kernels use compile-time coefficients)
+  cudaError_t e = upload_tables_f64(t);
   if (e == cudaSuccess) e = upload_tables_f64_batch(t);
   return e;
 }

@@ -219,13 +219,21 @@ __device__ __forceinline__ T buoyancy(const TendencyArgs<T>& a, T c0, T c1) {
   return a.eos == OCN_EOS_LINEAR_TS ? a.g_alpha * (c0 - a.T0) - a.g_beta * (c1 - a.S0) : c0;
 }
 
+// Closure classes the FP32 kernels are compiled for: fluxes of a constant diffusivity (or none),
+// Smagorinsky-Lilly, AMD; the FP64 kernels choose at run time (kClAny).  A fixed class lets the
+// compiler drop the other closures' branches.
+constexpr int kClAny = 0, kClScalar = 1, kClSmag = 2, kClAmd = 3;
+inline int closure_class(int closure) {
+  return closure == OCN_CLOSURE_SMAGORINSKY ? kClSmag : (closure == OCN_CLOSURE_AMD ? kClAmd : kClScalar);
+}
+
 template <int TX, int TY>
 struct TileGeom {
   static constexpr int NMAIN = TX * TY;
   static constexpr int NTHREADS = ((TX * TY + TX + TY) + 31) / 32 * 32;
 };
 
-template <typename T, int R, int NTR, int TX, int TY>
+template <typename T, int R, int NTR, int TX, int TY, int CL>
 __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const uint3 bid) {
   constexpr int P = R - 1;          // advecting-velocity half width
   constexpr int H = R;              // plane halo
@@ -240,9 +248,10 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
   constexpr int nt = NTR;
   constexpr int nf = 3 + nt;
   const size_t plane = (size_t)Nx * Ny;
-  const bool stress = (a.closure == OCN_CLOSURE_SMAGORINSKY || a.closure == OCN_CLOSURE_AMD);
-  const bool amd = (a.closure == OCN_CLOSURE_AMD);
-  const bool scalar = (a.closure == OCN_CLOSURE_SCALAR);
+  const bool stress = (CL == kClAny) ? (a.closure == OCN_CLOSURE_SMAGORINSKY || a.closure == OCN_CLOSURE_AMD)
+                                      : (CL == kClSmag || CL == kClAmd);
+  const bool amd = (CL == kClAny) ? (a.closure == OCN_CLOSURE_AMD) : (CL == kClAmd);
+  const bool scalar = (CL == kClAny || CL == kClScalar) ? (a.closure == OCN_CLOSURE_SCALAR) : false;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
@@ -706,24 +715,30 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
   }
 }
 
-template <typename T, int R, int NTR, int TX, int TY, int MINB>
+template <typename T, int R, int NTR, int TX, int TY, int MINB, int CL>
 struct TendencyK {
   typedef TendencyArgs<T> Payload;
   static constexpr int kThreads = TileGeom<TX, TY>::NTHREADS, kMinBlocks = MINB;
   static __device__ __forceinline__ void run(const Payload& a, uint3 bid, uint3) {
-    tendency_body<T, R, NTR, TX, TY>(a, bid);
+    tendency_body<T, R, NTR, TX, TY, CL>(a, bid);
   }
 };
 
-template <typename T, int R, int NTR, int TX, int TY, int MINB>
+template <typename T, int R, int NTR, int TX, int TY, int MINB, int CL>
 __global__ void __launch_bounds__(TileGeom<TX, TY>::NTHREADS, MINB) k_tendency(const TendencyArgs<T> a) {
-  tendency_body<T, R, NTR, TX, TY>(a, blockIdx);
+  tendency_body<T, R, NTR, TX, TY, CL>(a, blockIdx);
 }
 
-// The batched twin of k_tendency<T, R, NTR, TX, TY, MINB> (k_batched over TendencyK), instantiated
-// in the *_batch translation units so that the plain and batched kernels compile in parallel.
-template <typename T, int R, int NTR, int TX, int TY, int MINB>
+// The batched twin of k_tendency<T, R, NTR, TX, TY, MINB, CL> (k_batched over TendencyK),
+// instantiated in the *_batch translation units so that the plain and batched kernels compile in
+// parallel.
+template <typename T, int R, int NTR, int TX, int TY, int MINB, int CL>
 const void* tendency_batched_kernel();
+
+// The FP32 tile variants (TX, TY, CTAs per SM), in the order of the variant index.
+#define OCN_F32_TILE_VARIANTS(X, R, NTR, CL) \
+  X(R, NTR, 32, 8, 1, CL) X(R, NTR, 32, 8, 2, CL) X(R, NTR, 32, 16, 1, CL) X(R, NTR, 32, 4, 3, CL) \
+  X(R, NTR, 32, 14, 1, CL) X(R, NTR, 32, 12, 1, CL) X(R, NTR, 16, 16, 2, CL)
 
 template <typename T, int R, int TX, int TY>
 static size_t tendency_smem(const TendencyArgs<T>& a) {
@@ -739,10 +754,11 @@ static size_t tendency_smem(const TendencyArgs<T>& a) {
   return bytes;
 }
 
-// Launch one tile variant (TX x TY columns per CTA, at least MINB CTAs per SM).
-template <typename T, int R, int NTR, int TX, int TY, int MINB>
-static cudaError_t launch_tendency_variant(const TendencyArgs<T>& a, cudaStream_t s) {
-  auto kern = k_tendency<T, R, NTR, TX, TY, MINB>;
+// Launch one tile variant (TX x TY columns per CTA, at least MINB CTAs per SM) of closure class
+// CL.  Instantiated explicitly, one closure class per translation unit.
+template <typename T, int R, int NTR, int TX, int TY, int MINB, int CL>
+cudaError_t launch_tendency_variant(const TendencyArgs<T>& a, cudaStream_t s) {
+  auto kern = k_tendency<T, R, NTR, TX, TY, MINB, CL>;
   size_t smem = tendency_smem<T, R, TX, TY>(a);
   cudaError_t e = raise_smem_limit(kern, smem);
   if (e != cudaSuccess) return e;
@@ -753,7 +769,7 @@ static cudaError_t launch_tendency_variant(const TendencyArgs<T>& a, cudaStream_
   dim3 grid((a.Nx + TX - 1) / TX, (a.Ny + TY - 1) / TY);
   if (LaunchRecorder* r = active_recorder()) {
     LaunchRecord rec;
-    rec.fn = tendency_batched_kernel<T, R, NTR, TX, TY, MINB>();
+    rec.fn = tendency_batched_kernel<T, R, NTR, TX, TY, MINB, CL>();
     rec.grid = grid;
     rec.block = dim3(TileGeom<TX, TY>::NTHREADS);
     rec.smem = smem;
