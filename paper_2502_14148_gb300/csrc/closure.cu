@@ -14,7 +14,8 @@ namespace ocn {
 // costs about twenty loads (horizontal neighbours come through L1).  The march is
 // latency-bound, so residency matters most: in FP32, four 256-thread CTAs per SM
 // (registers capped at 64) measured 1.5x faster than three; more CTAs spill.
-template <typename T>
+// SMAG: compiled for Smagorinsky-Lilly (true) or AMD (false).
+template <typename T, bool SMAG>
 __device__ __forceinline__ void closure_body(const ClosureArgs<T>& a, const uint3 bid, const uint3 gdim) {
   const int i = bid.x * blockDim.x + threadIdx.x;
   const int j = bid.y * blockDim.y + threadIdx.y;
@@ -59,7 +60,7 @@ __device__ __forceinline__ void closure_body(const ClosureArgs<T>& a, const uint
     dvdz_lo0 = (v0 - __ldg(V + Lm + c00)) * r;
     dvdz_lo1 = (v1 - __ldg(V + Lm + c0p)) * r;
   }
-  const bool smag = (a.closure == OCN_CLOSURE_SMAGORINSKY);
+  constexpr bool smag = SMAG;
   T b_prev = (smag && kb > 0) ? buoy(kb - 1) : T(0), b_cur = smag ? buoy(kb) : T(0);
   for (int k = kb; k < ke; ++k) {
     const size_t L = (size_t)k * plane, L1 = L + plane;
@@ -90,7 +91,7 @@ __device__ __forceinline__ void closure_body(const ClosureArgs<T>& a, const uint
     const T wx = T(0.25) * ((w00 - wm0) + (wp0 - w00) + (w01 - wm1) + (wp1 - w01)) * rdx;
     const T wy = T(0.25) * ((w00 - w0m) + (w0p - w00) + (w01 - w0m1) + (w0p1 - w01)) * rdy;
     const size_t id = L + c00;
-    if (a.closure == OCN_CLOSURE_SMAGORINSKY) {
+    if constexpr (SMAG) {
       const T b_next = (k + 1 < Nz) ? buoy(k + 1) : T(0);
       const T S12 = T(0.5) * (uy + vx), S13 = T(0.5) * (uz + wx), S23 = T(0.5) * (vz + wy);
       const T SS = T(2) * (ux * ux + vy * vy + wz * wz + T(2) * (S12 * S12 + S13 * S13 + S23 * S23));
@@ -153,16 +154,18 @@ __device__ __forceinline__ void closure_body(const ClosureArgs<T>& a, const uint
   }
 }
 
-template <typename T>
+template <typename T, bool SMAG>
 struct ClosureK {
   typedef ClosureArgs<T> Payload;
   static constexpr int kThreads = 256, kMinBlocks = sizeof(T) == 4 ? 4 : 2;
-  static __device__ __forceinline__ void run(const Payload& a, uint3 bid, uint3 gdim) { closure_body<T>(a, bid, gdim); }
+  static __device__ __forceinline__ void run(const Payload& a, uint3 bid, uint3 gdim) {
+    closure_body<T, SMAG>(a, bid, gdim);
+  }
 };
 
-template <typename T>
-__global__ void __launch_bounds__(ClosureK<T>::kThreads, ClosureK<T>::kMinBlocks) k_closure(const ClosureArgs<T> a) {
-  closure_body<T>(a, blockIdx, gridDim);
+template <typename T, bool SMAG>
+__global__ void __launch_bounds__(ClosureK<T, SMAG>::kThreads, ClosureK<T, SMAG>::kMinBlocks) k_closure(const ClosureArgs<T> a) {
+  closure_body<T, SMAG>(a, blockIdx, gridDim);
 }
 
 template <typename T>
@@ -177,8 +180,13 @@ cudaError_t launch_closure(const ClosureArgs<T>& a, cudaStream_t s) {
   int nch = (int)((1000000 + cols - 1) / cols);
   nch = std::max(1, std::min(nch, a.Nz / 16));
   dim3 grid((a.Nx + blk.x - 1) / blk.x, (a.Ny + blk.y - 1) / blk.y, nch);
-  if (record_launch<ClosureK<T>>(a, grid, blk, 0, OCN_K_CLOSURE)) return cudaSuccess;
-  k_closure<T><<<grid, blk, 0, s>>>(a);
+  if (a.closure == OCN_CLOSURE_SMAGORINSKY) {
+    if (record_launch<ClosureK<T, true>>(a, grid, blk, 0, OCN_K_CLOSURE)) return cudaSuccess;
+    k_closure<T, true><<<grid, blk, 0, s>>>(a);
+  } else {
+    if (record_launch<ClosureK<T, false>>(a, grid, blk, 0, OCN_K_CLOSURE)) return cudaSuccess;
+    k_closure<T, false><<<grid, blk, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
