@@ -187,11 +187,10 @@ def test_les_fp32_100_steps(ocn, oracle_mod):
     assert rel_l2(g.get_numpy("T") - T0, o.get("T") - T0) < 1e-4
 
 
-def test_les_512_full_size_sampled(ocn, oracle_mod):
-    """The benchmark workload at full size (512x512x256 FP32, WENO9, Smagorinsky-Lilly, T,S):
-    tendencies at 300 sampled points against the oracle's pointwise evaluation, and the projection
-    checked by properties that hold at any size (div u = 0, u_new = u - grad p, lap p = div u)."""
-    p = inputs.config("les_512")
+def _full_size_sampled(ocn, oracle_mod, p, names, tol):
+    """Tendencies at 300 sampled points against the oracle's pointwise evaluation, and the
+    projection checked by properties that hold at any size (div u = 0, u_new = u - grad p,
+    lap p = div u), on the workload's full grid."""
     st = rounded(inputs.initial_state(p), 32)
     g = ocn.Model(p)
     g.set(project=False, **st)
@@ -202,30 +201,43 @@ def test_les_512_full_size_sampled(ocn, oracle_mod):
     Nx, Ny, Nz = p["Nx"], p["Ny"], p["Nz"]
     pts = [(int(rng.integers(Nx)), int(rng.integers(Ny)), int(k)) for k in
            list(rng.integers(0, Nz, 240)) + [0, 1, 2, 3, 4, 5, Nz - 6, Nz - 5, Nz - 4, Nz - 3, Nz - 2, Nz - 1] * 5]
-    for name in ("u", "v", "w", "T", "S"):
+    for name in names:
         ref = np.array([o.tendency_at(name, i, j, k) for (i, j, k) in pts])
         got = np.array([G[name][k, j, i] for (i, j, k) in pts])
         scale = max(np.abs(ref).max(), 1e-30)
-        assert np.abs(got - ref).max() / scale < 2e-4, name
+        assert np.abs(got - ref).max() / scale < tol, name
     # projection properties
     u0, v0, w0 = (st[x] for x in "uvw")
     g.project()
     u1, v1, w1, pr = (g.get_numpy(x).astype(np.float64) for x in ("u", "v", "w", "p"))
     d = g.diagnostics()
-    assert d["max_div"] < 1e-5 * np.abs(u0).max()
-    zf = p["z_faces"]; zc = 0.5 * (zf[1:] + zf[:-1]); dzc = np.diff(zf)
+    assert d["max_div"] < 1e-5 * np.abs(u0).max() * max(Nx / p["Lx"], 1.0)
+    dx, dy = p["Lx"] / Nx, p["Ly"] / Ny
+    zf = np.asarray(p["z_faces"]); zc = 0.5 * (zf[1:] + zf[:-1]); dzc = np.diff(zf)
+    us = max(np.abs(u0).max(), 1e-30)
     for (i, j, k) in pts[:100]:
-        assert abs(u1[k, j, i] - (u0[k, j, i] - (pr[k, j, i] - pr[k, j, i - 1]))) < 1e-5
-        assert abs(v1[k, j, i] - (v0[k, j, i] - (pr[k, j, i] - pr[k, j - 1, i]))) < 1e-5
+        assert abs(u1[k, j, i] - (u0[k, j, i] - (pr[k, j, i] - pr[k, j, i - 1]) / dx)) < 1e-5 * max(us, 1.0)
+        assert abs(v1[k, j, i] - (v0[k, j, i] - (pr[k, j, i] - pr[k, j - 1, i]) / dy)) < 1e-5 * max(us, 1.0)
         if 0 < k < Nz:
-            assert abs(w1[k, j, i] - (w0[k, j, i] - (pr[k, j, i] - pr[k - 1, j, i]) / (zc[k] - zc[k - 1]))) < 1e-5
+            assert abs(w1[k, j, i] - (w0[k, j, i] - (pr[k, j, i] - pr[k - 1, j, i]) / (zc[k] - zc[k - 1]))) < 1e-5 * max(us, 1.0)
         ip, jp = (i + 1) % Nx, (j + 1) % Ny
-        div0 = (u0[k, j, ip] - u0[k, j, i]) + (v0[k, jp, i] - v0[k, j, i]) + (w0[k + 1, j, i] - w0[k, j, i]) / dzc[k]
-        lap = (pr[k, j, ip] - 2 * pr[k, j, i] + pr[k, j, i - 1]) + (pr[k, jp, i] - 2 * pr[k, j, i] + pr[k, j - 1, i])
+        div0 = (u0[k, j, ip] - u0[k, j, i]) / dx + (v0[k, jp, i] - v0[k, j, i]) / dy + (w0[k + 1, j, i] - w0[k, j, i]) / dzc[k]
+        lap = (pr[k, j, ip] - 2 * pr[k, j, i] + pr[k, j, i - 1]) / dx ** 2 + (pr[k, jp, i] - 2 * pr[k, j, i] + pr[k, j - 1, i]) / dy ** 2
         up = (pr[k + 1, j, i] - pr[k, j, i]) / (zc[k + 1] - zc[k]) if k + 1 < Nz else 0.0
         dn = (pr[k, j, i] - pr[k - 1, j, i]) / (zc[k] - zc[k - 1]) if k > 0 else 0.0
         lap += (up - dn) / dzc[k]
         assert abs(lap - div0) < 1e-4 * max(1.0, abs(div0)), (i, j, k)
+
+
+def test_les_512_full_size_sampled(ocn, oracle_mod):
+    """The benchmark workload at full size (512x512x256 FP32, WENO9, Smagorinsky-Lilly, T,S)."""
+    _full_size_sampled(ocn, oracle_mod, inputs.config("les_512"), ("u", "v", "w", "T", "S"), 2e-4)
+
+
+def test_cbl_256_full_size_sampled(ocn, oracle_mod):
+    """The convective-boundary-layer configuration at full size (256x256x128 FP32, 2 m spacing,
+    tanh-stretched z, WENO5, AMD, f = 1e-4, surface buoyancy flux)."""
+    _full_size_sampled(ocn, oracle_mod, inputs.config("cbl_256"), ("u", "v", "w", "b"), 2e-4)
 
 
 # ----------------------------------------------------------------------------- behaviour
