@@ -15,6 +15,15 @@ namespace ocn {
 // latency-bound, so residency matters most: in FP32, four 256-thread CTAs per SM
 // (registers capped at 64) measured 1.5x faster than three; more CTAs spill.
 // SMAG: compiled for Smagorinsky-Lilly (true) or AMD (false).
+//
+// Each level's new values come from HBM with nothing else in flight for that warp, so the
+// march also asks L2 for the column's values kPrefetch levels ahead (prefetch.global.L2: no
+// register, no wait); the loads of those levels then hit L2.
+constexpr int kPrefetch = 3;
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 template <typename T, bool SMAG>
 __device__ __forceinline__ void closure_body(const ClosureArgs<T>& a, const uint3 bid, const uint3 gdim) {
   const int i = bid.x * blockDim.x + threadIdx.x;
@@ -64,6 +73,17 @@ __device__ __forceinline__ void closure_body(const ClosureArgs<T>& a, const uint
   T b_prev = (smag && kb > 0) ? buoy(kb - 1) : T(0), b_cur = smag ? buoy(kb) : T(0);
   for (int k = kb; k < ke; ++k) {
     const size_t L = (size_t)k * plane, L1 = L + plane;
+    {
+      const int kp = k + 1 + kPrefetch;      // level (and face) kp, in bounds only
+      const size_t o = (size_t)kp * plane + c00;
+      if (kp <= Nz) prefetch_l2(W + o);
+      if (kp < Nz) {
+        prefetch_l2(U + o);
+        prefetch_l2(V + o);
+        const int ntp = SMAG ? min(a.nt, a.eos == OCN_EOS_LINEAR_TS ? 2 : 1) : a.nt;
+        for (int t = 0; t < ntp; ++t) prefetch_l2(a.cur.c[t] + o);
+      }
+    }
     const T rdzc = __ldg(a.rdzc + k);
     const T rdzf1 = (k + 1 < Nz) ? __ldg(a.rdzf + k + 1) : T(0);
     const T dz = __ldg(a.dzc + k);
@@ -102,9 +122,9 @@ __device__ __forceinline__ void closure_body(const ClosureArgs<T>& a, const uint
         const T N2 = T(0.5) * (dbb + dbt);
         const T Delta = cbrt(a.dx * a.dy * dz);
         const T CD = a.Cs * Delta;
-        T stab = T(1) - a.Cb * N2 * a.inv_Pr / SS;
-        stab = stab > T(0) ? stab : T(0);
-        nu = CD * CD * sqrt(SS) * sqrt(stab);
+        // (C_s Delta)^2 sqrt(SS) sqrt(max(1 - C_b N2 / (Pr SS), 0)), written for SS > 0 without the division
+        const T e = SS - a.Cb * N2 * a.inv_Pr;
+        nu = e > T(0) ? CD * CD * sqrt(e) : T(0);
       }
       a.nu[id] = nu;
       b_prev = b_cur;

@@ -89,8 +89,17 @@ struct IDiv {
   __device__ __forceinline__ int mod(int x) const { return p2 ? (x & (d - 1)) : x - div(x) * d; }
 };
 
+// Shared-memory layout of the FFT buffers: one padding element after every 128 bytes of data.
+// A Stockham pass writes element j*R + r from the thread of butterfly j, a stride of R elements
+// across the threads of a warp; unpadded, the first pass of a radix-8 x line puts a half-warp's
+// sixteen 8-byte stores on two bank pairs (8-way conflict).  Padded, they fall on sixteen.
+template <typename C> __host__ __device__ constexpr int spad_shift() { return sizeof(C) == 8 ? 4 : 3; }
+template <typename C> __device__ __forceinline__ int spad(int i) { return i + (i >> spad_shift<C>()); }
+// elements a buffer of n padded elements spans
+template <typename C> __host__ __device__ constexpr size_t spad_size(size_t n) { return n + (n >> spad_shift<C>()); }
+
 // One Stockham pass of radix R over `nlines` lines of length N held in `src`,
-// written to `dst`.  Element e of line l lives at l*sl + e*se.  The twiddle
+// written to `dst`.  Element e of line l lives at spad(l*sl + e*se).  The twiddle
 // table holds e^{-2 pi i t / (N*tws)} for t < N*tws (tws = stride into it).
 template <typename C, typename T, int R>
 __device__ __forceinline__ void stockham_pass(const C* src, C* dst, int N, int Ns, int nlines, int sl, int se,
@@ -105,7 +114,7 @@ __device__ __forceinline__ void stockham_pass(const C* src, C* dst, int N, int N
     else { l = dl.div(idx); j = idx - l * nb; }
     C v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = src[l * sl + (j + r * nb) * se];
+    for (int r = 0; r < R; ++r) v[r] = src[spad<C>(l * sl + (j + r * nb) * se)];
     const int jq = dns.div(j), k = j - jq * Ns;
     if (Ns > 1) {
 #pragma unroll
@@ -119,7 +128,7 @@ __device__ __forceinline__ void stockham_pass(const C* src, C* dst, int N, int N
     dft<C, T, R>(v, s);
     const int base = jq * Ns * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) dst[l * sl + (base + r * Ns) * se] = v[r];
+    for (int r = 0; r < R; ++r) dst[spad<C>(l * sl + (base + r * Ns) * se)] = v[r];
   }
 }
 
@@ -151,7 +160,7 @@ __device__ __forceinline__ void div_fftx_body(const PoissonArgs<T>& a, int LR, c
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C* A = reinterpret_cast<C*>(sm_raw);
   const int M = a.Mx, Nx = a.Nx, Ny = a.Ny, Nz = a.Nz;
-  C* B = A + LR * M;
+  C* B = A + spad_size<C>((size_t)LR * M);
   const size_t plane = (size_t)Nx * Ny;
   const int row0 = bid.x * LR;
   const int nrows = min(LR, Ny * Nz - row0);
@@ -160,34 +169,47 @@ __device__ __forceinline__ void div_fftx_body(const PoissonArgs<T>& a, int LR, c
   // takes the caller's arrays)
   const bool pairs = ((reinterpret_cast<uintptr_t>(a.u) | reinterpret_cast<uintptr_t>(a.v) |
                        reinterpret_cast<uintptr_t>(a.w)) & (2 * sizeof(T) - 1)) == 0;
-  for (int idx = threadIdx.x; idx < nrows * M; idx += blockDim.x) {
-    const int l = dM.div(idx), n = idx - l * M;
-    const int row = row0 + l;
-    const int k = dNy.div(row), j = row - k * Ny;
-    const int jp = (j + 1 == Ny) ? 0 : j + 1;
-    const T rdz = __ldg(a.rdzc + k);
-    T val[2];
-    const size_t o = (size_t)k * plane + (size_t)j * Nx;
-    if (pairs) {                        // cells 2n, 2n+1 as one vector per field and level
-      const C u01 = *reinterpret_cast<const C*>(a.u + o + 2 * n);
-      const T u2 = a.u[o + (2 * n + 2 == Nx ? 0 : 2 * n + 2)];
-      const C vj = *reinterpret_cast<const C*>(a.v + o + 2 * n);
-      const C vp = *reinterpret_cast<const C*>(a.v + (size_t)k * plane + (size_t)jp * Nx + 2 * n);
-      const C wk = *reinterpret_cast<const C*>(a.w + o + 2 * n);
-      const C wt = *reinterpret_cast<const C*>(a.w + o + plane + 2 * n);
-      val[0] = ((u01.y - u01.x) * a.rdx + (vp.x - vj.x) * a.rdy + (wt.x - wk.x) * rdz) * a.inv_dt;
-      val[1] = ((u2 - u01.y) * a.rdx + (vp.y - vj.y) * a.rdy + (wt.y - wk.y) * rdz) * a.inv_dt;
-    } else {
+  // two elements per thread and trip, their loads issued before either is stored (the index of
+  // the second is clamped into range; a clamped duplicate is not stored)
+  const int ne = nrows * M;
+  for (int b0 = threadIdx.x; b0 < ne; b0 += 2 * blockDim.x) {
+    C out[2];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int i = 2 * n + h;
-        const int ip = (i + 1 == Nx) ? 0 : i + 1;
-        const T div = (a.u[o + ip] - a.u[o + i]) * a.rdx + (a.v[(size_t)k * plane + (size_t)jp * Nx + i] - a.v[o + i]) * a.rdy +
-                      (a.w[o + plane + i] - a.w[o + i]) * rdz;
-        val[h] = div * a.inv_dt;
+    for (int u = 0; u < 2; ++u) {
+      const int idx = min(b0 + u * (int)blockDim.x, ne - 1);
+      const int l = dM.div(idx), n = idx - l * M;
+      const int row = row0 + l;
+      const int k = dNy.div(row), j = row - k * Ny;
+      const int jp = (j + 1 == Ny) ? 0 : j + 1;
+      const T rdz = __ldg(a.rdzc + k);
+      T val[2];
+      const size_t o = (size_t)k * plane + (size_t)j * Nx;
+      if (pairs) {                        // cells 2n, 2n+1 as one vector per field and level
+        const C u01 = *reinterpret_cast<const C*>(a.u + o + 2 * n);
+        const T u2 = a.u[o + (2 * n + 2 == Nx ? 0 : 2 * n + 2)];
+        const C vj = *reinterpret_cast<const C*>(a.v + o + 2 * n);
+        const C vp = *reinterpret_cast<const C*>(a.v + (size_t)k * plane + (size_t)jp * Nx + 2 * n);
+        const C wk = *reinterpret_cast<const C*>(a.w + o + 2 * n);
+        const C wt = *reinterpret_cast<const C*>(a.w + o + plane + 2 * n);
+        val[0] = ((u01.y - u01.x) * a.rdx + (vp.x - vj.x) * a.rdy + (wt.x - wk.x) * rdz) * a.inv_dt;
+        val[1] = ((u2 - u01.y) * a.rdx + (vp.y - vj.y) * a.rdy + (wt.y - wk.y) * rdz) * a.inv_dt;
+      } else {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int i = 2 * n + h;
+          const int ip = (i + 1 == Nx) ? 0 : i + 1;
+          const T div = (a.u[o + ip] - a.u[o + i]) * a.rdx + (a.v[(size_t)k * plane + (size_t)jp * Nx + i] - a.v[o + i]) * a.rdy +
+                        (a.w[o + plane + i] - a.w[o + i]) * rdz;
+          val[h] = div * a.inv_dt;
+        }
       }
+      out[u] = C{val[0], val[1]};
     }
-    A[l * M + n] = C{val[0], val[1]};
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int idx = b0 + u * (int)blockDim.x;
+      if (idx < ne) A[spad<C>(idx)] = out[u];       // idx = l * M + n
+    }
   }
   __syncthreads();
   C* Z = block_fft<C, T>(A, B, a.px, nrows, M, 1, reinterpret_cast<const C*>(a.twx), 2, -1, false);
@@ -196,8 +218,8 @@ __device__ __forceinline__ void div_fftx_body(const PoissonArgs<T>& a, int LR, c
   const IDiv dS(S);
   for (int idx = threadIdx.x; idx < nrows * S; idx += blockDim.x) {
     const int l = dS.div(idx), kx = idx - l * S;          // kx = 0 .. M
-    const C z1 = Z[l * M + (kx == M ? 0 : kx)];
-    const C z2 = cconj(Z[l * M + (kx == 0 ? 0 : M - kx)]);
+    const C z1 = Z[spad<C>(l * M + (kx == M ? 0 : kx))];
+    const C z2 = cconj(Z[spad<C>(l * M + (kx == 0 ? 0 : M - kx))]);
     const C E = cscale(cadd(z1, z2), T(0.5));
     const C D = cscale(csub(z1, z2), T(0.5));
     const C O = {D.y, -D.x};                   // D / i
@@ -215,24 +237,38 @@ __device__ __forceinline__ void ifftx_body(const PoissonArgs<T>& a, int LR, cons
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C* A = reinterpret_cast<C*>(sm_raw);
   const int M = a.Mx, Nx = a.Nx, Ny = a.Ny, Nz = a.Nz;
-  C* B = A + LR * M;
+  C* B = A + spad_size<C>((size_t)LR * M);
   const int S = M + 1;
   const int row0 = bid.x * LR;
   const int nrows = min(LR, Ny * Nz - row0);
   const C* spec = reinterpret_cast<const C*>(a.spec);
   const C* tw = reinterpret_cast<const C*>(a.twx);
   const IDiv dM(M);
-  for (int idx = threadIdx.x; idx < nrows * M; idx += blockDim.x) {
-    const int l = dM.div(idx), kx = idx - l * M;
-    const size_t ro = (size_t)(row0 + l) * S;
-    const C x1 = spec[ro + kx];
-    const C x2 = cconj(spec[ro + (M - kx)]);
-    const C E = cscale(cadd(x1, x2), T(0.5));
-    C w = tw[kx];
-    w.y = -w.y;                                 // e^{+2 pi i kx / Nx}
-    const C O = cmul(cscale(csub(x1, x2), T(0.5)), w);
-    const C Zk = cscale(cadd(E, cmuli(O, 1)), a.scale);
-    A[l * M + kx] = Zk;
+  // four elements per thread and trip, their spectrum loads issued together (indices clamped into
+  // range; clamped duplicates are not stored)
+  constexpr int kU = 4;
+  const int ne = nrows * M;
+  for (int b0 = threadIdx.x; b0 < ne; b0 += kU * blockDim.x) {
+    C x1[kU], x2[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int idx = min(b0 + u * (int)blockDim.x, ne - 1);
+      const int l = dM.div(idx), kx = idx - l * M;
+      const size_t ro = (size_t)(row0 + l) * S;
+      x1[u] = spec[ro + kx];
+      x2[u] = cconj(spec[ro + (M - kx)]);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int idx = b0 + u * (int)blockDim.x;
+      if (idx >= ne) break;
+      const int l = dM.div(idx), kx = idx - l * M;
+      const C E = cscale(cadd(x1[u], x2[u]), T(0.5));
+      C w = tw[kx];
+      w.y = -w.y;                                 // e^{+2 pi i kx / Nx}
+      const C O = cmul(cscale(csub(x1[u], x2[u]), T(0.5)), w);
+      A[spad<C>(idx)] = cscale(cadd(E, cmuli(O, 1)), a.scale);   // idx = l * M + kx
+    }
   }
   __syncthreads();
   C* z = block_fft<C, T>(A, B, a.px, nrows, M, 1, tw, 2, +1, false);
@@ -242,7 +278,7 @@ __device__ __forceinline__ void ifftx_body(const PoissonArgs<T>& a, int LR, cons
   for (int idx = threadIdx.x; idx < nrows * M; idx += blockDim.x) {
     const int l = dM.div(idx), n = idx - l * M;
     const int row = row0 + l;
-    const C v = z[l * M + n];
+    const C v = z[spad<C>(l * M + n)];
     if (pairs) {
       *reinterpret_cast<C*>(a.p + (size_t)row * Nx + 2 * n) = v;
     } else {
@@ -260,23 +296,38 @@ __device__ __forceinline__ void fft_y_body(const PoissonArgs<T>& a, int CW, int 
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C* A = reinterpret_cast<C*>(sm_raw);
   const int Ny = a.Ny, S = a.Mx + 1;
-  C* B = A + Ny * CW;
-  C* sTw = B + Ny * CW;
+  C* B = A + spad_size<C>((size_t)Ny * CW);
+  C* sTw = B + spad_size<C>((size_t)Ny * CW);
   const int kx0 = bid.x * CW, k = bid.y;
   const int ncol = min(CW, S - kx0);
   C* spec = reinterpret_cast<C*>(a.spec) + (size_t)k * Ny * S;
   const C* twy = reinterpret_cast<const C*>(a.twy);
   for (int t = threadIdx.x; t < Ny; t += blockDim.x) sTw[t] = twy[t];
   const IDiv dCW(CW);
-  for (int idx = threadIdx.x; idx < Ny * CW; idx += blockDim.x) {
-    const int j = dCW.div(idx), c = idx - j * CW;
-    if (c < ncol) A[j * CW + c] = spec[(size_t)j * S + kx0 + c];
+  // eight elements per thread and trip, their loads issued together (columns past the spectrum's
+  // edge are neither loaded nor stored)
+  constexpr int kU = 8;
+  const int ne = Ny * CW;
+  for (int b0 = threadIdx.x; b0 < ne; b0 += kU * blockDim.x) {
+    C v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int idx = b0 + u * (int)blockDim.x;
+      const int j = dCW.div(idx), c = idx - j * CW;
+      if (idx < ne && c < ncol) v[u] = spec[(size_t)j * S + kx0 + c];
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int idx = b0 + u * (int)blockDim.x;
+      const int c = idx - dCW.div(idx) * CW;
+      if (idx < ne && c < ncol) A[spad<C>(idx)] = v[u];      // idx = j * CW + c
+    }
   }
   __syncthreads();
   C* r = block_fft<C, T>(A, B, a.py, CW, 1, CW, sTw, 1, sign, true);
-  for (int idx = threadIdx.x; idx < Ny * CW; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < ne; idx += blockDim.x) {
     const int j = dCW.div(idx), c = idx - j * CW;
-    if (c < ncol) spec[(size_t)j * S + kx0 + c] = r[j * CW + c];
+    if (c < ncol) spec[(size_t)j * S + kx0 + c] = r[spad<C>(idx)];
   }
 }
 
@@ -583,7 +634,7 @@ cudaError_t launch_projection(const PoissonArgs<T>& a, cudaStream_t s, int* nlau
   int n = 0;
   const int M = a.Mx;
   const int LR = rows_per_block(M);
-  const size_t smx = 2 * (size_t)LR * M * sizeof(C);
+  const size_t smx = 2 * spad_size<C>((size_t)LR * M) * sizeof(C);
   const int rows = a.Ny * a.Nz;
   e = raise_smem_limit(k_div_fftx<T>, smx);
   if (e != cudaSuccess) return e;
@@ -599,7 +650,7 @@ cudaError_t launch_projection(const PoissonArgs<T>& a, cudaStream_t s, int* nlau
   // about 2048 (FP32) / 1024 (FP64) values, but not beyond the spectrum's width
   int CW = (sizeof(T) == 4) ? 8 : 4;
   while (CW * a.Ny < (sizeof(T) == 4 ? 2048 : 1024) && CW < a.Mx + 1) CW *= 2;
-  const size_t smy = (2 * (size_t)a.Ny * CW + a.Ny) * sizeof(C);
+  const size_t smy = (2 * spad_size<C>((size_t)a.Ny * CW) + a.Ny) * sizeof(C);
   e = raise_smem_limit(k_fft_y<T>, smy);
   if (e != cudaSuccess) return e;
   dim3 gy((a.Mx + 1 + CW - 1) / CW, a.Nz);
