@@ -18,7 +18,9 @@ namespace ocn {
 //
 // Each level's new values come from HBM with nothing else in flight for that warp, so the
 // march also asks L2 for the column's values kPrefetch levels ahead (prefetch.global.L2: no
-// register, no wait); the loads of those levels then hit L2.
+// register, no wait); the loads of those levels then hit L2.  (Unrolling the march by two levels,
+// so that both levels' loads are issued together, spills under the 64-register cap and measured
+// slower.)
 constexpr int kPrefetch = 3;
 __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));

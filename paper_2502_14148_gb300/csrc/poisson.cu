@@ -34,6 +34,13 @@ template <typename C> __device__ __forceinline__ C csub(C a, C b) { return {a.x 
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
 template <typename C> __device__ __forceinline__ C cconj(C a) { return {a.x, -a.y}; }
 template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) { return {a.x * s, a.y * s}; }
+// a * s with each product rounded on its own (never fused into a later add): the first FFT pass
+// feeds values formed on the way in straight into the DFT's additions, and a product the code
+// generator was free to contract there could be fused differently in the plain and the batched
+// instantiation of a kernel, which must agree bit for bit
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+template <typename C, typename T> __device__ __forceinline__ C cscale_rn(C a, T s) { return {mul_rn(a.x, s), mul_rn(a.y, s)}; }
 // multiply by s*i
 template <typename C> __device__ __forceinline__ C cmuli(C a, int s) { return s > 0 ? C{-a.y, a.x} : C{a.y, -a.x}; }
 
@@ -98,12 +105,13 @@ template <typename C> __device__ __forceinline__ int spad(int i) { return i + (i
 // elements a buffer of n padded elements spans
 template <typename C> __host__ __device__ constexpr size_t spad_size(size_t n) { return n + (n >> spad_shift<C>()); }
 
-// One Stockham pass of radix R over `nlines` lines of length N held in `src`,
-// written to `dst`.  Element e of line l lives at spad(l*sl + e*se).  The twiddle
-// table holds e^{-2 pi i t / (N*tws)} for t < N*tws (tws = stride into it).
-template <typename C, typename T, int R>
-__device__ __forceinline__ void stockham_pass(const C* src, C* dst, int N, int Ns, int nlines, int sl, int se,
-                                              const C* tw, int tws, int s, bool line_fast) {
+// One Stockham pass of radix R over `nlines` lines of length N: ld(l, e) supplies element e of
+// line l, st(l, e, v) takes output element e of line l.  The twiddle table holds
+// e^{-2 pi i t / (N*tws)} for t < N*tws (tws = stride into it).  A thread's R loads are issued
+// together, before any of its stores.
+template <typename C, typename T, int R, class Ld, class St>
+__device__ __forceinline__ void stockham_pass(const Ld& ld, const St& st, int N, int Ns, int nlines, const C* tw,
+                                              int tws, int s, bool line_fast) {
   const int nb = N / R;
   const int total = nlines * nb;
   const int twstep = N / (Ns * R);
@@ -114,7 +122,7 @@ __device__ __forceinline__ void stockham_pass(const C* src, C* dst, int N, int N
     else { l = dl.div(idx); j = idx - l * nb; }
     C v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = src[spad<C>(l * sl + (j + r * nb) * se)];
+    for (int r = 0; r < R; ++r) v[r] = ld(l, j + r * nb);
     const int jq = dns.div(j), k = j - jq * Ns;
     if (Ns > 1) {
 #pragma unroll
@@ -128,32 +136,56 @@ __device__ __forceinline__ void stockham_pass(const C* src, C* dst, int N, int N
     dft<C, T, R>(v, s);
     const int base = jq * Ns * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) dst[spad<C>(l * sl + (base + r * Ns) * se)] = v[r];
+    for (int r = 0; r < R; ++r) st(l, base + r * Ns, v[r]);
   }
 }
 
-// Full FFT; the data start in a and the result ends in a or b (returned).
-template <typename C, typename T>
-__device__ C* block_fft(C* a, C* b, const FftPlan& plan, int nlines, int sl, int se, const C* tw, int tws, int s,
-                        bool line_fast) {
+// A pass whose input and output are each either the transform's own (ld / st: global memory or a
+// computed value) or a padded shared buffer (element e of line l at spad(l*sl + e*se)).
+template <typename C, typename T, int R, class Ld, class St>
+__device__ __forceinline__ void stockham_pass_at(bool first, bool last, const Ld& ld, const St& st, const C* src,
+                                                 C* dst, int sl, int se, int N, int Ns, int nlines, const C* tw,
+                                                 int tws, int s, bool line_fast) {
+  auto sld = [&](int l, int e) -> C { return src[spad<C>(l * sl + e * se)]; };
+  auto sst = [&](int l, int e, C v) { dst[spad<C>(l * sl + e * se)] = v; };
+  if (first && last) stockham_pass<C, T, R>(ld, st, N, Ns, nlines, tw, tws, s, line_fast);
+  else if (first) stockham_pass<C, T, R>(ld, sst, N, Ns, nlines, tw, tws, s, line_fast);
+  else if (last) stockham_pass<C, T, R>(sld, st, N, Ns, nlines, tw, tws, s, line_fast);
+  else stockham_pass<C, T, R>(sld, sst, N, Ns, nlines, tw, tws, s, line_fast);
+}
+
+// Full FFT of `nlines` lines.  The first pass reads its input through ld(l, e) and the last pass
+// writes its output through st(l, e, v), straight from and to global memory (or values computed
+// on the way in), so only the passes in between go through shared memory: pass p writes buffer a
+// for even p and b for odd p.  A one-pass transform touches no shared memory.  The last pass
+// writes into the buffer the last pass of a transform through shared memory would use,
+// (npass - 1) even ? a : b, when st stores there.
+template <typename C, typename T, class Ld, class St>
+__device__ __forceinline__ void block_fft(C* a, C* b, const FftPlan& plan, int nlines, int sl, int se, const C* tw,
+                                          int tws, int s, bool line_fast, const Ld& ld, const St& st) {
   int Ns = 1;
-  for (int p = 0; p < plan.npass; ++p) {
+  const int np = plan.npass;
+  for (int p = 0; p < np; ++p) {
     const int R = plan.radix[p];
+    const bool first = (p == 0), last = (p == np - 1);
+    const C* src = (p & 1) ? a : b;      // written by pass p - 1
+    C* dst = (p & 1) ? b : a;
     switch (R) {
-      case 8: stockham_pass<C, T, 8>(a, b, plan.n, Ns, nlines, sl, se, tw, tws, s, line_fast); break;
-      case 4: stockham_pass<C, T, 4>(a, b, plan.n, Ns, nlines, sl, se, tw, tws, s, line_fast); break;
-      case 3: stockham_pass<C, T, 3>(a, b, plan.n, Ns, nlines, sl, se, tw, tws, s, line_fast); break;
-      default: stockham_pass<C, T, 2>(a, b, plan.n, Ns, nlines, sl, se, tw, tws, s, line_fast); break;
+      case 8: stockham_pass_at<C, T, 8>(first, last, ld, st, src, dst, sl, se, plan.n, Ns, nlines, tw, tws, s, line_fast); break;
+      case 4: stockham_pass_at<C, T, 4>(first, last, ld, st, src, dst, sl, se, plan.n, Ns, nlines, tw, tws, s, line_fast); break;
+      case 3: stockham_pass_at<C, T, 3>(first, last, ld, st, src, dst, sl, se, plan.n, Ns, nlines, tw, tws, s, line_fast); break;
+      default: stockham_pass_at<C, T, 2>(first, last, ld, st, src, dst, sl, se, plan.n, Ns, nlines, tw, tws, s, line_fast); break;
     }
-    __syncthreads();
+    if (!last) __syncthreads();
     Ns *= R;
-    C* t = a; a = b; b = t;
   }
-  return a;
 }
 
 // ---------------------------------------------------------------------------
-// divergence + real FFT along x.  Each block handles LR consecutive rows.
+// divergence + real FFT along x.  Each block handles LR consecutive rows.  The divergence goes to
+// shared memory first, two elements per thread and trip with their loads issued together (taking
+// it inside the first pass instead holds the six loads of each of a butterfly's eight elements at
+// once: 64 registers and fewer blocks per SM, measured slower).
 template <typename T>
 __device__ __forceinline__ void div_fftx_body(const PoissonArgs<T>& a, int LR, const uint3 bid) {
   typedef typename CT<T>::type C;
@@ -169,8 +201,8 @@ __device__ __forceinline__ void div_fftx_body(const PoissonArgs<T>& a, int LR, c
   // takes the caller's arrays)
   const bool pairs = ((reinterpret_cast<uintptr_t>(a.u) | reinterpret_cast<uintptr_t>(a.v) |
                        reinterpret_cast<uintptr_t>(a.w)) & (2 * sizeof(T) - 1)) == 0;
-  // two elements per thread and trip, their loads issued before either is stored (the index of
-  // the second is clamped into range; a clamped duplicate is not stored)
+  // element n of line l: div(u)/dt at cells 2n and 2n+1 of row row0 + l (index of the second
+  // element of a trip clamped into range; a clamped duplicate is not stored)
   const int ne = nrows * M;
   for (int b0 = threadIdx.x; b0 < ne; b0 += 2 * blockDim.x) {
     C out[2];
@@ -212,7 +244,13 @@ __device__ __forceinline__ void div_fftx_body(const PoissonArgs<T>& a, int LR, c
     }
   }
   __syncthreads();
-  C* Z = block_fft<C, T>(A, B, a.px, nrows, M, 1, reinterpret_cast<const C*>(a.twx), 2, -1, false);
+  // the transform reads A in its first pass, so its passes write B first (block_fft(B, A, ..)),
+  // and its output stays in shared memory for the split
+  auto ld = [&](int l, int e) -> C { return A[spad<C>(l * M + e)]; };
+  C* Z = ((a.px.npass - 1) & 1) ? A : B;
+  auto st = [&](int l, int e, C v) { Z[spad<C>(l * M + e)] = v; };
+  block_fft<C, T>(B, A, a.px, nrows, M, 1, reinterpret_cast<const C*>(a.twx), 2, -1, false, ld, st);
+  __syncthreads();
   // split: X[kx] = E + W^kx O, E = (Z[kx] + conj Z[M-kx])/2, O = (Z[kx] - conj Z[M-kx])/(2i)
   const int S = M + 1;
   const IDiv dS(S);
@@ -230,7 +268,8 @@ __device__ __forceinline__ void div_fftx_body(const PoissonArgs<T>& a, int LR, c
   }
 }
 
-// complex-to-real inverse FFT along x -> p (scaled by a.scale).
+// complex-to-real inverse FFT along x -> p (scaled by a.scale).  The first pass forms its
+// elements from the half spectrum; the last pass writes p.
 template <typename T>
 __device__ __forceinline__ void ifftx_body(const PoissonArgs<T>& a, int LR, const uint3 bid) {
   typedef typename CT<T>::type C;
@@ -243,53 +282,35 @@ __device__ __forceinline__ void ifftx_body(const PoissonArgs<T>& a, int LR, cons
   const int nrows = min(LR, Ny * Nz - row0);
   const C* spec = reinterpret_cast<const C*>(a.spec);
   const C* tw = reinterpret_cast<const C*>(a.twx);
-  const IDiv dM(M);
-  // four elements per thread and trip, their spectrum loads issued together (indices clamped into
-  // range; clamped duplicates are not stored)
-  constexpr int kU = 4;
-  const int ne = nrows * M;
-  for (int b0 = threadIdx.x; b0 < ne; b0 += kU * blockDim.x) {
-    C x1[kU], x2[kU];
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int idx = min(b0 + u * (int)blockDim.x, ne - 1);
-      const int l = dM.div(idx), kx = idx - l * M;
-      const size_t ro = (size_t)(row0 + l) * S;
-      x1[u] = spec[ro + kx];
-      x2[u] = cconj(spec[ro + (M - kx)]);
-    }
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int idx = b0 + u * (int)blockDim.x;
-      if (idx >= ne) break;
-      const int l = dM.div(idx), kx = idx - l * M;
-      const C E = cscale(cadd(x1[u], x2[u]), T(0.5));
-      C w = tw[kx];
-      w.y = -w.y;                                 // e^{+2 pi i kx / Nx}
-      const C O = cmul(cscale(csub(x1[u], x2[u]), T(0.5)), w);
-      A[spad<C>(idx)] = cscale(cadd(E, cmuli(O, 1)), a.scale);   // idx = l * M + kx
-    }
-  }
-  __syncthreads();
-  C* z = block_fft<C, T>(A, B, a.px, nrows, M, 1, tw, 2, +1, false);
+  // element kx of line l: Z_kx = E + i e^{+2 pi i kx / Nx} O from X[kx] and conj X[M - kx]
+  auto ld = [&](int l, int kx) -> C {
+    const size_t ro = (size_t)(row0 + l) * S;
+    const C x1 = spec[ro + kx];
+    const C x2 = cconj(spec[ro + (M - kx)]);
+    const C E = cscale(cadd(x1, x2), T(0.5));
+    C w = tw[kx];
+    w.y = -w.y;                                 // e^{+2 pi i kx / Nx}
+    const C O = cmul(cscale(csub(x1, x2), T(0.5)), w);
+    return cscale_rn(cadd(E, cmuli(O, 1)), a.scale);
+  };
   const bool pairs = (reinterpret_cast<uintptr_t>(a.p) & (2 * sizeof(T) - 1)) == 0;   // p as 2-vectors
-  const size_t plane = (size_t)Nx * Ny;
-  (void)plane;
-  for (int idx = threadIdx.x; idx < nrows * M; idx += blockDim.x) {
-    const int l = dM.div(idx), n = idx - l * M;
-    const int row = row0 + l;
-    const C v = z[spad<C>(l * M + n)];
+  // output element n of line l: p at cells 2n and 2n+1 of row row0 + l
+  auto st = [&](int l, int n, C v) {
+    const size_t o = (size_t)(row0 + l) * Nx + 2 * n;
     if (pairs) {
-      *reinterpret_cast<C*>(a.p + (size_t)row * Nx + 2 * n) = v;
+      *reinterpret_cast<C*>(a.p + o) = v;
     } else {
-      a.p[(size_t)row * Nx + 2 * n] = v.x;
-      a.p[(size_t)row * Nx + 2 * n + 1] = v.y;
+      a.p[o] = v.x;
+      a.p[o + 1] = v.y;
     }
-  }
+  };
+  block_fft<C, T>(A, B, a.px, nrows, M, 1, tw, 2, +1, false, ld, st);
 }
 
-// FFT along y of a tile of CW kx-columns in one z-plane, in place; the Ny twiddles are staged in
-// shared memory after the two data buffers.
+// FFT along y of a tile of CW kx-columns in one z-plane, in place: the first pass reads the
+// spectrum, the last pass writes it back (columns past the spectrum's edge are neither read nor
+// written).  The Ny twiddles are staged in shared memory after the two data buffers; the first
+// pass uses none (N_s = 1), and the barrier after it publishes them to the others.
 template <typename T>
 __device__ __forceinline__ void fft_y_body(const PoissonArgs<T>& a, int CW, int sign, const uint3 bid) {
   typedef typename CT<T>::type C;
@@ -303,32 +324,9 @@ __device__ __forceinline__ void fft_y_body(const PoissonArgs<T>& a, int CW, int 
   C* spec = reinterpret_cast<C*>(a.spec) + (size_t)k * Ny * S;
   const C* twy = reinterpret_cast<const C*>(a.twy);
   for (int t = threadIdx.x; t < Ny; t += blockDim.x) sTw[t] = twy[t];
-  const IDiv dCW(CW);
-  // eight elements per thread and trip, their loads issued together (columns past the spectrum's
-  // edge are neither loaded nor stored)
-  constexpr int kU = 8;
-  const int ne = Ny * CW;
-  for (int b0 = threadIdx.x; b0 < ne; b0 += kU * blockDim.x) {
-    C v[kU];
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int idx = b0 + u * (int)blockDim.x;
-      const int j = dCW.div(idx), c = idx - j * CW;
-      if (idx < ne && c < ncol) v[u] = spec[(size_t)j * S + kx0 + c];
-    }
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int idx = b0 + u * (int)blockDim.x;
-      const int c = idx - dCW.div(idx) * CW;
-      if (idx < ne && c < ncol) A[spad<C>(idx)] = v[u];      // idx = j * CW + c
-    }
-  }
-  __syncthreads();
-  C* r = block_fft<C, T>(A, B, a.py, CW, 1, CW, sTw, 1, sign, true);
-  for (int idx = threadIdx.x; idx < ne; idx += blockDim.x) {
-    const int j = dCW.div(idx), c = idx - j * CW;
-    if (c < ncol) spec[(size_t)j * S + kx0 + c] = r[spad<C>(idx)];
-  }
+  auto ld = [&](int l, int e) -> C { return (l < ncol) ? spec[(size_t)e * S + kx0 + l] : C{T(0), T(0)}; };
+  auto st = [&](int l, int e, C v) { if (l < ncol) spec[(size_t)e * S + kx0 + l] = v; };
+  block_fft<C, T>(A, B, a.py, CW, 1, CW, sTw, 1, sign, true, ld, st);
 }
 
 // Thomas algorithm per horizontal wavenumber.  a_k p_{k-1} + b_k p_k + c_k p_{k+1} = r_k,
