@@ -81,8 +81,13 @@ struct IDiv {
   int d, sh;
   float inv;
   bool p2;
-  __device__ __forceinline__ explicit IDiv(int d_) : d(d_), sh(0), inv(1.0f / (float)d_), p2((d_ & (d_ - 1)) == 0) {
-    while ((1 << sh) < d_) ++sh;
+  // built once per thread and pass, for a handful of elements: the shift from a count of leading
+  // zeros, the reciprocal (a division) only for divisors that need it
+  __device__ __forceinline__ explicit IDiv(int d_) : d(d_), sh(0), inv(0.0f), p2((d_ & (d_ - 1)) == 0) {
+#ifdef __CUDA_ARCH__
+    if (p2) sh = 31 - __clz(d_);
+    else inv = 1.0f / (float)d_;
+#endif
   }
   __device__ __forceinline__ int div(int x) const {
     if (p2) return x >> sh;
@@ -106,15 +111,14 @@ template <typename C> __device__ __forceinline__ int spad(int i) { return i + (i
 template <typename C> __host__ __device__ constexpr size_t spad_size(size_t n) { return n + (n >> spad_shift<C>()); }
 
 // One Stockham pass of radix R over `nlines` lines of length N: ld(l, e) supplies element e of
-// line l, st(l, e, v) takes output element e of line l.  The twiddle table holds
-// e^{-2 pi i t / (N*tws)} for t < N*tws (tws = stride into it).  A thread's R loads are issued
+// line l, st(l, e, v) takes output element e of line l; twstep = N / (Ns R).  The twiddle table
+// holds e^{-2 pi i t / (N*tws)} for t < N*tws (tws = stride into it).  A thread's R loads are issued
 // together, before any of its stores.
 template <typename C, typename T, int R, class Ld, class St>
-__device__ __forceinline__ void stockham_pass(const Ld& ld, const St& st, int N, int Ns, int nlines, const C* tw,
-                                              int tws, int s, bool line_fast) {
+__device__ __forceinline__ void stockham_pass(const Ld& ld, const St& st, int N, int Ns, int twstep, int nlines,
+                                              const C* tw, int tws, int s, bool line_fast) {
   const int nb = N / R;
   const int total = nlines * nb;
-  const int twstep = N / (Ns * R);
   const IDiv dl(line_fast ? nlines : nb), dns(Ns);
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     int l, j;
@@ -144,14 +148,14 @@ __device__ __forceinline__ void stockham_pass(const Ld& ld, const St& st, int N,
 // computed value) or a padded shared buffer (element e of line l at spad(l*sl + e*se)).
 template <typename C, typename T, int R, class Ld, class St>
 __device__ __forceinline__ void stockham_pass_at(bool first, bool last, const Ld& ld, const St& st, const C* src,
-                                                 C* dst, int sl, int se, int N, int Ns, int nlines, const C* tw,
-                                                 int tws, int s, bool line_fast) {
+                                                 C* dst, int sl, int se, int N, int Ns, int twstep, int nlines,
+                                                 const C* tw, int tws, int s, bool line_fast) {
   auto sld = [&](int l, int e) -> C { return src[spad<C>(l * sl + e * se)]; };
   auto sst = [&](int l, int e, C v) { dst[spad<C>(l * sl + e * se)] = v; };
-  if (first && last) stockham_pass<C, T, R>(ld, st, N, Ns, nlines, tw, tws, s, line_fast);
-  else if (first) stockham_pass<C, T, R>(ld, sst, N, Ns, nlines, tw, tws, s, line_fast);
-  else if (last) stockham_pass<C, T, R>(sld, st, N, Ns, nlines, tw, tws, s, line_fast);
-  else stockham_pass<C, T, R>(sld, sst, N, Ns, nlines, tw, tws, s, line_fast);
+  if (first && last) stockham_pass<C, T, R>(ld, st, N, Ns, twstep, nlines, tw, tws, s, line_fast);
+  else if (first) stockham_pass<C, T, R>(ld, sst, N, Ns, twstep, nlines, tw, tws, s, line_fast);
+  else if (last) stockham_pass<C, T, R>(sld, st, N, Ns, twstep, nlines, tw, tws, s, line_fast);
+  else stockham_pass<C, T, R>(sld, sst, N, Ns, twstep, nlines, tw, tws, s, line_fast);
 }
 
 // Full FFT of `nlines` lines.  The first pass reads its input through ld(l, e) and the last pass
@@ -164,17 +168,18 @@ template <typename C, typename T, class Ld, class St>
 __device__ __forceinline__ void block_fft(C* a, C* b, const FftPlan& plan, int nlines, int sl, int se, const C* tw,
                                           int tws, int s, bool line_fast, const Ld& ld, const St& st) {
   int Ns = 1;
+  int rem = plan.n;                      // N / Ns
   const int np = plan.npass;
   for (int p = 0; p < np; ++p) {
     const int R = plan.radix[p];
     const bool first = (p == 0), last = (p == np - 1);
     const C* src = (p & 1) ? a : b;      // written by pass p - 1
     C* dst = (p & 1) ? b : a;
-    switch (R) {
-      case 8: stockham_pass_at<C, T, 8>(first, last, ld, st, src, dst, sl, se, plan.n, Ns, nlines, tw, tws, s, line_fast); break;
-      case 4: stockham_pass_at<C, T, 4>(first, last, ld, st, src, dst, sl, se, plan.n, Ns, nlines, tw, tws, s, line_fast); break;
-      case 3: stockham_pass_at<C, T, 3>(first, last, ld, st, src, dst, sl, se, plan.n, Ns, nlines, tw, tws, s, line_fast); break;
-      default: stockham_pass_at<C, T, 2>(first, last, ld, st, src, dst, sl, se, plan.n, Ns, nlines, tw, tws, s, line_fast); break;
+    switch (R) {                         // rem / R = N / (Ns R), the pass's twiddle step
+      case 8: rem /= 8; stockham_pass_at<C, T, 8>(first, last, ld, st, src, dst, sl, se, plan.n, Ns, rem, nlines, tw, tws, s, line_fast); break;
+      case 4: rem /= 4; stockham_pass_at<C, T, 4>(first, last, ld, st, src, dst, sl, se, plan.n, Ns, rem, nlines, tw, tws, s, line_fast); break;
+      case 3: rem /= 3; stockham_pass_at<C, T, 3>(first, last, ld, st, src, dst, sl, se, plan.n, Ns, rem, nlines, tw, tws, s, line_fast); break;
+      default: rem /= 2; stockham_pass_at<C, T, 2>(first, last, ld, st, src, dst, sl, se, plan.n, Ns, rem, nlines, tw, tws, s, line_fast); break;
     }
     if (!last) __syncthreads();
     Ns *= R;
