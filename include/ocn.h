@@ -94,7 +94,7 @@ enum {
 /* Grid (paper listing "RectilinearGrid(...)"): x in [0,Lx), y in [0,Ly) periodic,
  * uniform; z bounded with Nz+1 ascending face heights. */
 typedef struct {
-  int Nx, Ny, Nz;            /* Nx, Ny even and of the form 2^a 3^b, >= 4; Nz >= 1 */
+  int Nx, Ny, Nz;            /* Nx, Ny even and of the form 2^a 3^b, >= 4, Nx*Ny < 2^31; Nz >= 1 */
   double Lx, Ly;             /* > 0 */
   const double* z_faces;     /* Nz+1 strictly ascending heights; copied by ocn_grid_create */
 } ocn_grid_desc;
@@ -127,8 +127,8 @@ int ocn_abi_version(void);
 const char* ocn_last_error(void);
 
 /* Create a grid from *desc.  *out receives a new handle (free with ocn_grid_destroy).
- * Errors: OCN_ERR_ARG for a null pointer, a size that is not even 2^a 3^b >= 4,
- * non-positive lengths or non-ascending faces; OCN_ERR_OOM. */
+ * Errors: OCN_ERR_ARG for a null pointer, a size that is not even 2^a 3^b >= 4, a level of
+ * 2^31 cells or more, non-positive lengths or non-ascending faces; OCN_ERR_OOM. */
 ocn_status ocn_grid_create(const ocn_grid_desc* desc, ocn_grid** out);
 void ocn_grid_destroy(ocn_grid* grid);
 

@@ -626,6 +626,8 @@ ocn_status ocn_grid_create(const ocn_grid_desc* desc, ocn_grid** out) {
   *out = nullptr;
   if (desc->Nx < 4 || desc->Ny < 4 || (desc->Nx % 2) || (desc->Ny % 2) || !is_2a3b(desc->Nx) || !is_2a3b(desc->Ny))
     return fail(OCN_ERR_ARG, "Nx and Ny must be even, >= 4 and of the form 2^a 3^b");
+  if ((long long)desc->Nx * desc->Ny > 2147483647LL)
+    return fail(OCN_ERR_ARG, "Nx * Ny must be below 2^31 (kernels index a level with 32-bit offsets)");
   if (desc->Nz < 1) return fail(OCN_ERR_ARG, "Nz must be >= 1");
   if (!(desc->Lx > 0) || !(desc->Ly > 0)) return fail(OCN_ERR_ARG, "Lx and Ly must be positive");
   if (!desc->z_faces) return fail(OCN_ERR_ARG, "z_faces is null");

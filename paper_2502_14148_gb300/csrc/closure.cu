@@ -35,55 +35,70 @@ __device__ __forceinline__ void closure_body(const ClosureArgs<T>& a, const uint
   const size_t plane = (size_t)Nx * Ny;
   const int ip = (i + 1 == Nx) ? 0 : i + 1, im = (i == 0) ? Nx - 1 : i - 1;
   const int jp = (j + 1 == Ny) ? 0 : j + 1, jm = (j == 0) ? Ny - 1 : j - 1;
-  // column offsets inside a level
-  const size_t c00 = (size_t)j * Nx + i, cp0 = (size_t)j * Nx + ip, cm0 = (size_t)j * Nx + im;
-  const size_t c0p = (size_t)jp * Nx + i, c0m = (size_t)jm * Nx + i;
-  const size_t cpp = (size_t)jp * Nx + ip, cpm = (size_t)jm * Nx + ip, cmp = (size_t)jp * Nx + im;
+  // column offsets inside a level, 32-bit (grids are created with Nx Ny < 2^31): the march keeps
+  // one pointer per field to its current level, so a load adds a 32-bit offset to it instead of
+  // forming a 64-bit level-plus-column index
+  const int c00 = j * Nx + i, cp0 = j * Nx + ip, cm0 = j * Nx + im;
+  const int c0p = jp * Nx + i, c0m = jm * Nx + i;
+  const int cpp = jp * Nx + ip, cpm = jm * Nx + ip, cmp = jp * Nx + im;
   const T rdx = a.rdx, rdy = a.rdy;
-  const T* U = a.cur.u;
-  const T* V = a.cur.v;
-  const T* W = a.cur.w;
+  const bool ts = (a.eos == OCN_EOS_LINEAR_TS);
+  const T* cr0 = a.cref[0];
+  const T* cr1 = a.cref[1];
   auto cref = [&](int t, int kk) -> T { return a.cref[t] ? __ldg(a.cref[t] + kk) : T(0); };
-  auto buoy = [&](int kk) -> T {   // b at (i, j, kk), tracers stored about their profiles
-    const size_t o = (size_t)kk * plane + c00;
-    if (a.eos == OCN_EOS_LINEAR_TS)
-      return a.g_alpha * (__ldg(a.cur.c[0] + o) + cref(0, kk) - a.T0) - a.g_beta * (__ldg(a.cur.c[1] + o) + cref(1, kk) - a.S0);
-    return __ldg(a.cur.c[0] + o) + cref(0, kk);
+  // b at (i, j) from the tracers of a level (pointers to it) and level kk's reference profiles
+  auto buoy = [&](const T* c0, const T* c1, int kk) -> T {
+    const T t0 = __ldg(c0 + c00) + (cr0 ? __ldg(cr0 + kk) : T(0));
+    if (ts) return a.g_alpha * (t0 - a.T0) - a.g_beta * (__ldg(c1 + c00) + (cr1 ? __ldg(cr1 + kk) : T(0)) - a.S0);
+    return t0;
   };
   // this CTA's chunk of levels [kb, ke) (block z); the march state is set up at kb from the level
   // below, so chunks are independent
   const int nch = gdim.z, per = (Nz + nch - 1) / nch;
   const int kb = bid.z * per, ke = min(Nz, kb + per);
   if (kb >= ke) return;
-  const size_t Lb = (size_t)kb * plane;
+  // level-kb pointers (w: face kb); tracer pointers are only formed for the tracers a kernel reads
+  const T* Uk = a.cur.u + (size_t)kb * plane;
+  const T* Vk = a.cur.v + (size_t)kb * plane;
+  const T* Wk = a.cur.w + (size_t)kb * plane;
+  const T* C0k = SMAG ? a.cur.c[0] + (size_t)kb * plane : nullptr;
+  const T* C1k = (SMAG && ts) ? a.cur.c[1] + (size_t)kb * plane : nullptr;
   // carried from level to level: u at (i|ip, j) and v at (i, j|jp) on the current level, w on face k,
   // the two lower-face z-derivatives, b below
-  T u0 = __ldg(U + Lb + c00), u1 = __ldg(U + Lb + cp0);
-  T v0 = __ldg(V + Lb + c00), v1 = __ldg(V + Lb + c0p);
-  T w00 = __ldg(W + Lb + c00), wm0 = __ldg(W + Lb + cm0), wp0 = __ldg(W + Lb + cp0), w0m = __ldg(W + Lb + c0m),
-    w0p = __ldg(W + Lb + c0p);
+  T u0 = __ldg(Uk + c00), u1 = __ldg(Uk + cp0);
+  T v0 = __ldg(Vk + c00), v1 = __ldg(Vk + c0p);
+  T w00 = __ldg(Wk + c00), wm0 = __ldg(Wk + cm0), wp0 = __ldg(Wk + cp0), w0m = __ldg(Wk + c0m), w0p = __ldg(Wk + c0p);
   T dudz_lo0 = T(0), dudz_lo1 = T(0), dvdz_lo0 = T(0), dvdz_lo1 = T(0);   // faces at k (walls: 0)
   if (kb > 0) {
-    const size_t Lm = Lb - plane;
     const T r = __ldg(a.rdzf + kb);
-    dudz_lo0 = (u0 - __ldg(U + Lm + c00)) * r;
-    dudz_lo1 = (u1 - __ldg(U + Lm + cp0)) * r;
-    dvdz_lo0 = (v0 - __ldg(V + Lm + c00)) * r;
-    dvdz_lo1 = (v1 - __ldg(V + Lm + c0p)) * r;
+    dudz_lo0 = (u0 - __ldg(Uk - plane + c00)) * r;
+    dudz_lo1 = (u1 - __ldg(Uk - plane + cp0)) * r;
+    dvdz_lo0 = (v0 - __ldg(Vk - plane + c00)) * r;
+    dvdz_lo1 = (v1 - __ldg(Vk - plane + c0p)) * r;
   }
-  constexpr bool smag = SMAG;
-  T b_prev = (smag && kb > 0) ? buoy(kb - 1) : T(0), b_cur = smag ? buoy(kb) : T(0);
+  T b_prev = T(0), b_cur = T(0);
+  if constexpr (SMAG) {
+    if (kb > 0) b_prev = buoy(C0k - plane, ts ? C1k - plane : nullptr, kb - 1);
+    b_cur = buoy(C0k, C1k, kb);
+  }
   for (int k = kb; k < ke; ++k) {
-    const size_t L = (size_t)k * plane, L1 = L + plane;
+    const T* U1 = Uk + plane;               // level k+1 (face k+1 for w)
+    const T* V1 = Vk + plane;
+    const T* W1 = Wk + plane;
     {
-      const int kp = k + 1 + kPrefetch;      // level (and face) kp, in bounds only
-      const size_t o = (size_t)kp * plane + c00;
-      if (kp <= Nz) prefetch_l2(W + o);
+      // level (and face) k+1+kPrefetch, in bounds only
+      const int kp = k + 1 + kPrefetch;
+      const size_t ahead = (size_t)kPrefetch * plane;
+      if (kp <= Nz) prefetch_l2(W1 + ahead + c00);
       if (kp < Nz) {
-        prefetch_l2(U + o);
-        prefetch_l2(V + o);
-        const int ntp = SMAG ? min(a.nt, a.eos == OCN_EOS_LINEAR_TS ? 2 : 1) : a.nt;
-        for (int t = 0; t < ntp; ++t) prefetch_l2(a.cur.c[t] + o);
+        prefetch_l2(U1 + ahead + c00);
+        prefetch_l2(V1 + ahead + c00);
+        if constexpr (SMAG) {
+          prefetch_l2(C0k + plane + ahead + c00);
+          if (ts) prefetch_l2(C1k + plane + ahead + c00);
+        } else {
+          for (int t = 0; t < a.nt; ++t) prefetch_l2(a.cur.c[t] + (size_t)kp * plane + c00);
+        }
       }
     }
     const T rdzc = __ldg(a.rdzc + k);
@@ -91,12 +106,12 @@ __device__ __forceinline__ void closure_body(const ClosureArgs<T>& a, const uint
     const T dz = __ldg(a.dzc + k);
     // next level (k+1) of the carried columns, and face k+1 of w
     T un0 = T(0), un1 = T(0), vn0 = T(0), vn1 = T(0);
-    if (k + 1 < Nz) { un0 = __ldg(U + L1 + c00); un1 = __ldg(U + L1 + cp0); vn0 = __ldg(V + L1 + c00); vn1 = __ldg(V + L1 + c0p); }
-    const T w01 = __ldg(W + L1 + c00), wm1 = __ldg(W + L1 + cm0), wp1 = __ldg(W + L1 + cp0);
-    const T w0m1 = __ldg(W + L1 + c0m), w0p1 = __ldg(W + L1 + c0p);
+    if (k + 1 < Nz) { un0 = __ldg(U1 + c00); un1 = __ldg(U1 + cp0); vn0 = __ldg(V1 + c00); vn1 = __ldg(V1 + c0p); }
+    const T w01 = __ldg(W1 + c00), wm1 = __ldg(W1 + cm0), wp1 = __ldg(W1 + cp0);
+    const T w0m1 = __ldg(W1 + c0m), w0p1 = __ldg(W1 + c0p);
     // horizontal neighbours on level k
-    const T u_0m = __ldg(U + L + c0m), u_1m = __ldg(U + L + cpm), u_0p = __ldg(U + L + c0p), u_1p = __ldg(U + L + cpp);
-    const T v_m0 = __ldg(V + L + cm0), v_p0 = __ldg(V + L + cp0), v_mp = __ldg(V + L + cmp), v_pp = __ldg(V + L + cpp);
+    const T u_0m = __ldg(Uk + c0m), u_1m = __ldg(Uk + cpm), u_0p = __ldg(Uk + c0p), u_1p = __ldg(Uk + cpp);
+    const T v_m0 = __ldg(Vk + cm0), v_p0 = __ldg(Vk + cp0), v_mp = __ldg(Vk + cmp), v_pp = __ldg(Vk + cpp);
     const T ux = (u1 - u0) * rdx;
     const T vy = (v1 - v0) * rdy;
     const T wz = (w01 - w00) * rdzc;
@@ -112,9 +127,9 @@ __device__ __forceinline__ void closure_body(const ClosureArgs<T>& a, const uint
     const T vz = T(0.25) * (dvdz_lo0 + dvdz_lo1 + dvdz_hi0 + dvdz_hi1);
     const T wx = T(0.25) * ((w00 - wm0) + (wp0 - w00) + (w01 - wm1) + (wp1 - w01)) * rdx;
     const T wy = T(0.25) * ((w00 - w0m) + (w0p - w00) + (w01 - w0m1) + (w0p1 - w01)) * rdy;
-    const size_t id = L + c00;
+    const size_t id = (size_t)k * plane + c00;
     if constexpr (SMAG) {
-      const T b_next = (k + 1 < Nz) ? buoy(k + 1) : T(0);
+      const T b_next = (k + 1 < Nz) ? buoy(C0k + plane, ts ? C1k + plane : nullptr, k + 1) : T(0);
       const T S12 = T(0.5) * (uy + vx), S13 = T(0.5) * (uz + wx), S23 = T(0.5) * (vz + wy);
       const T SS = T(2) * (ux * ux + vy * vy + wz * wz + T(2) * (S12 * S12 + S13 * S13 + S23 * S23));
       T nu = T(0);
@@ -131,6 +146,8 @@ __device__ __forceinline__ void closure_body(const ClosureArgs<T>& a, const uint
       a.nu[id] = nu;
       b_prev = b_cur;
       b_cur = b_next;
+      C0k += plane;
+      if (ts) C1k += plane;
     } else {  // AMD
       const T G[3][3] = {{ux, uy, uz}, {vx, vy, vz}, {wx, wy, wz}};
       const T D2[3] = {a.dx * a.dx, a.dy * a.dy, dz * dz};
@@ -151,13 +168,13 @@ __device__ __forceinline__ void closure_body(const ClosureArgs<T>& a, const uint
       T nu = (den > T(0)) ? -a.C_amd * num / den : T(0);
       a.nu[id] = nu > T(0) ? nu : T(0);
       for (int t = 0; t < a.nt; ++t) {
-        const T* c = a.cur.c[t];
-        const T c0 = __ldg(c + id);
+        const T* c = a.cur.c[t] + (size_t)k * plane;      // level k of tracer t
+        const T c0 = __ldg(c + c00);
         T dc[3];
-        dc[0] = T(0.5) * ((c0 - __ldg(c + L + cm0)) + (__ldg(c + L + cp0) - c0)) * rdx;
-        dc[1] = T(0.5) * ((c0 - __ldg(c + L + c0m)) + (__ldg(c + L + c0p) - c0)) * rdy;
-        const T dcb = (k >= 1) ? ((c0 - __ldg(c + id - plane)) + (cref(t, k) - cref(t, k - 1))) * __ldg(a.rdzf + k) : T(0);
-        const T dct = (k + 1 < Nz) ? ((__ldg(c + id + plane) - c0) + (cref(t, k + 1) - cref(t, k))) * rdzf1 : T(0);
+        dc[0] = T(0.5) * ((c0 - __ldg(c + cm0)) + (__ldg(c + cp0) - c0)) * rdx;
+        dc[1] = T(0.5) * ((c0 - __ldg(c + c0m)) + (__ldg(c + c0p) - c0)) * rdy;
+        const T dcb = (k >= 1) ? ((c0 - __ldg(c - plane + c00)) + (cref(t, k) - cref(t, k - 1))) * __ldg(a.rdzf + k) : T(0);
+        const T dct = (k + 1 < Nz) ? ((__ldg(c + plane + c00) - c0) + (cref(t, k + 1) - cref(t, k))) * rdzf1 : T(0);
         dc[2] = T(0.5) * (dcb + dct);
         // cn = sum_m D2_m dc_m (sum_p G[p][m] dc_p)
         T cn = T(0), cd = T(0);
@@ -173,6 +190,7 @@ __device__ __forceinline__ void closure_body(const ClosureArgs<T>& a, const uint
     u0 = un0; u1 = un1; v0 = vn0; v1 = vn1;
     w00 = w01; wm0 = wm1; wp0 = wp1; w0m = w0m1; w0p = w0p1;
     dudz_lo0 = dudz_hi0; dudz_lo1 = dudz_hi1; dvdz_lo0 = dvdz_hi0; dvdz_lo1 = dvdz_hi1;
+    Uk = U1; Vk = V1; Wk = W1;
   }
 }
 

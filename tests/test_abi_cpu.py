@@ -48,6 +48,10 @@ def test_abi_version_and_grid_validation(libocn):
     with pytest.raises(ocn.OcnError):
         ocn.Grid(16, 12, 8, 1.0, 1.0, zf[::-1])       # descending faces
     assert "ascending" in libocn.ocn_last_error().decode()
+    with pytest.raises(ocn.OcnError) as ei:           # a level of 2^32 cells: beyond 32-bit level offsets
+        ocn.Grid(65536, 65536, 8, 1.0, 1.0, zf)
+    assert ei.value.status == -1 and "2^31" in libocn.ocn_last_error().decode()
+    assert ocn.Grid(32768, 49152, 1, 1.0, 1.0, np.linspace(-1, 0, 2))._h   # 1.6e9 cells per level: allowed
 
 
 def test_no_oracle_in_the_product_path():
