@@ -233,7 +233,15 @@ struct TileGeom {
   static constexpr int NTHREADS = ((TX * TY + TX + TY) + 31) / 32 * 32;
 };
 
-template <typename T, int R, int NTR, int TX, int TY, int CL>
+// PREG: keep this thread's gather offsets in registers for the whole march (FP32 launches whose
+// register budget, 65536 / (threads x blocks per SM), is at least 128 a thread; below that, and in
+// the FP64 kernels, the extra registers spill and the offsets are formed per level instead).
+template <typename T, int TX, int TY, int MINB>
+struct GatherInRegisters {
+  static constexpr bool value = sizeof(T) == 4 && 65536 / (TileGeom<TX, TY>::NTHREADS * MINB) >= 128;
+};
+
+template <typename T, int R, int NTR, int TX, int TY, int CL, bool PREG>
 __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const uint3 bid) {
   constexpr int P = R - 1;          // advecting-velocity half width
   constexpr int H = R;              // plane halo
@@ -283,11 +291,34 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
   for (int e = tid; e < PH; e += NT_) { int g = (j0 + e - H) % Ny; gj_tab[e] = g < 0 ? g + Ny : g; }
   __syncthreads();
 
+  // With PREG, this thread's gather offsets (plane elements tid + q NT_, periodic wrap through the
+  // tables; the same for every field and level; 32-bit, as grids are created with Nx Ny < 2^31) are
+  // formed once, so that a level's cp.async issue costs one add each; otherwise they are formed per
+  // element and level.
+  constexpr int NIT = (PLANE + NT_ - 1) / NT_;
+  int goff[PREG ? NIT : 1];
+#pragma unroll
+  for (int q = 0; q < (PREG ? NIT : 1); ++q) {
+    const int e = tid + q * NT_;
+    goff[q] = 0;
+    if (PREG && e < PLANE) {
+      const int yy = e / PW, xx = e - yy * PW;
+      goff[q] = gj_tab[yy] * Nx + gi_tab[xx];
+    }
+  }
   auto load_plane = [&](T* dst, const T* field, int level) {
     const T* base = field + (size_t)level * plane;
-    for (int e = tid; e < PLANE; e += NT_) {
-      const int yy = e / PW, xx = e - yy * PW;
-      cp_async(dst + e, base + (size_t)gj_tab[yy] * Nx + gi_tab[xx], (int)sizeof(T));
+    if constexpr (PREG) {
+#pragma unroll
+      for (int q = 0; q < NIT; ++q) {
+        const int e = tid + q * NT_;
+        if (e < PLANE) cp_async(dst + e, base + goff[q], (int)sizeof(T));
+      }
+    } else {
+      for (int e = tid; e < PLANE; e += NT_) {
+        const int yy = e / PW, xx = e - yy * PW;
+        cp_async(dst + e, base + (size_t)gj_tab[yy] * Nx + gi_tab[xx], (int)sizeof(T));
+      }
     }
   };
   auto load_level = [&](int k) {  // u, v, tracers at level k (slot k&1)
@@ -720,13 +751,13 @@ struct TendencyK {
   typedef TendencyArgs<T> Payload;
   static constexpr int kThreads = TileGeom<TX, TY>::NTHREADS, kMinBlocks = MINB;
   static __device__ __forceinline__ void run(const Payload& a, uint3 bid, uint3) {
-    tendency_body<T, R, NTR, TX, TY, CL>(a, bid);
+    tendency_body<T, R, NTR, TX, TY, CL, GatherInRegisters<T, TX, TY, MINB>::value>(a, bid);
   }
 };
 
 template <typename T, int R, int NTR, int TX, int TY, int MINB, int CL>
 __global__ void __launch_bounds__(TileGeom<TX, TY>::NTHREADS, MINB) k_tendency(const TendencyArgs<T> a) {
-  tendency_body<T, R, NTR, TX, TY, CL>(a, blockIdx);
+  tendency_body<T, R, NTR, TX, TY, CL, GatherInRegisters<T, TX, TY, MINB>::value>(a, blockIdx);
 }
 
 // The batched twin of k_tendency<T, R, NTR, TX, TY, MINB, CL> (k_batched over TendencyK),
