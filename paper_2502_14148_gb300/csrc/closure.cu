@@ -12,8 +12,9 @@ namespace ocn {
 // One thread per (i, j) column marching up in z: the values on face / level
 // k+1 loaded for one level are reused as the k values of the next, so each cell
 // costs about twenty loads (horizontal neighbours come through L1).  The march is
-// latency-bound, so residency matters most: in FP32, four 256-thread CTAs per SM
-// (registers capped at 64) measured 1.5x faster than three; more CTAs spill.
+// bound by load latency and instruction issue together, so residency matters: in FP32,
+// four 256-thread CTAs per SM (registers capped at 64) measured 1.5x faster than three;
+// more CTAs spill.
 // SMAG: compiled for Smagorinsky-Lilly (true) or AMD (false).
 //
 // Each level's new values come from HBM with nothing else in flight for that warp, so the
