@@ -63,3 +63,17 @@ def test_no_oracle_in_the_product_path():
             if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
                 txt = open(os.path.join(dirpath, f), encoding="utf-8").read()
                 assert not pat.search(txt), f
+
+
+def test_no_cpu_fallback_without_a_gpu():
+    """Without a CUDA device every compute object refuses to be created: there is no CPU path."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_2502_14148_gb300 import inputs, ocn
+    p = inputs.config("cbl_256", Nx=16, Ny=16, Nz=8)
+    for make in (lambda: ocn.Model(p),
+                 lambda: ocn.Ensemble(inputs.ensemble_configs(n=2, sizes=(16,), depths=(8,))),
+                 lambda: ocn.MLP(inputs.MLP_SIZES, max_batch=128)):
+        with pytest.raises(RuntimeError, match="no CPU path"):
+            make()
