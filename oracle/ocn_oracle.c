@@ -19,8 +19,9 @@
  *   - RK3, Eq. rk3 (gamma, zeta); pressure correction, Eqs. predictor-velocity,
  *     pressure-correction, pressure-poisson; FFT + tridiagonal Poisson solve
  *     (Appendix A.2 and the eigenfunction expansion described there).
- * Parity unpinned: WENO-Z epsilon and tau, closure constants and averaging
- * stencils, the Coriolis 4-point average, EOS constants, the flux sign
+ * Parity unpinned: WENO-Z epsilon and tau, the closures' constants and
+ * averaging stencils (their formulas are pinned in closed form on linear
+ * fields), the Coriolis 4-point average, EOS constants, the flux sign
  * convention (decisions, see ocn_oracle.h).
  */
 #include "ocn_oracle.h"

@@ -13,9 +13,13 @@
  * described by ascending face heights zf[0..Nz].
  *
  * Parity unpinned (fixed by decision, checked only oracle-vs-GPU): the WENO-Z
- * constants (epsilon = 1e-8, tau = |beta_0 - beta_{r-1}|), the AMD and
- * Smagorinsky-Lilly constants and averaging stencils, the Coriolis 4-point
- * average, the linear-EOS constants and the flux-BC sign convention.
+ * constants (epsilon = 1e-8, tau = |beta_0 - beta_{r-1}|), the values of the
+ * AMD and Smagorinsky-Lilly constants, which edges are averaged onto a centre
+ * (linear fields cannot tell averaging stencils apart), the Coriolis 4-point
+ * average, the linear-EOS constants and the flux-BC sign convention.  The two
+ * closure formulas themselves (Smagorinsky-Lilly with its stratification
+ * factor, AMD viscosity and tracer diffusivity) are pinned by closed forms on
+ * linear velocity and tracer fields.
  */
 #ifndef OCN_ORACLE_H
 #define OCN_ORACLE_H

@@ -384,6 +384,148 @@ def test_amd_zero_on_pure_shear_and_nonnegative(oracle_mod):
         assert min(vals) >= 0.0 and max(vals) > 0.0
 
 
+# Linear fields on the staggered grid.  Away from the periodic wrap and from the
+# walls every discrete difference of a linear field is its exact derivative and
+# every average of a constant is that constant, so the closures' values there
+# have closed forms, expanded by hand below for each field (Sec. 3.1.1 closure
+# equation; Smagorinsky-Lilly with Lilly's stratification factor, and the
+# anisotropic minimum-dissipation model of Rozema et al. 2015 with the tracer
+# form of Vreugdenhil & Taylor 2018).  The grid is anisotropic (dx = 2, dy = 1)
+# and tanh-stretched in z, so a transposed gradient index or a swapped grid
+# spacing changes the value.
+_LIN_N = dict(Nx=12, Ny=12, Nz=10, Lx=24.0, Ly=12.0, Lz=10.0, stretch=1.5)
+
+
+def _linear_fields(p, u=(0, 0, 0), v=(0, 0, 0), w=(0, 0, 0), tracers=None):
+    """u = u0 x + u1 y + u2 z (and likewise v, w, each tracer) sampled at each
+    field's own staggered location; w is zero on the two walls."""
+    Nx, Ny, Nz = p["Nx"], p["Ny"], p["Nz"]
+    dx, dy = p["Lx"] / Nx, p["Ly"] / Ny
+    zf = np.asarray(p["z_faces"])
+    zc = 0.5 * (zf[1:] + zf[:-1])
+    xf, xc = np.arange(Nx) * dx, (np.arange(Nx) + 0.5) * dx
+    yf, yc = np.arange(Ny) * dy, (np.arange(Ny) + 0.5) * dy
+
+    def lin(g, x, y, z):
+        return g[0] * x[None, None, :] + g[1] * y[None, :, None] + g[2] * z[:, None, None]
+
+    out = {"u": lin(u, xf, yc, zc), "v": lin(v, xc, yf, zc), "w": lin(w, xc, yc, zf)}
+    out["w"][0] = 0.0
+    out["w"][-1] = 0.0
+    for name, g in (tracers or {}).items():
+        out[name] = lin(g, xc, yc, zc)
+    return {k: np.ascontiguousarray(a) for k, a in out.items()}, zc, dx, dy, np.diff(zf)
+
+
+# interior cells: two cells from the periodic wrap in x and y, one from each wall
+_LIN_CELLS = [(i, j, k) for i in (2, 5, 9) for j in (3, 8) for k in (1, 4, 8)]
+
+
+@pytest.mark.parametrize("S,T,N2,expect_zero", [(0.3, -0.2, 0.01, False),    # weakly stable shear
+                                                 (0.3, 0.4, 0.11, False),     # close to the cut-off
+                                                 (0.3, 0.1, 0.2, True),       # Richardson number past the cut-off
+                                                 (0.3, 0.0, -0.05, False)])   # unstable: the factor exceeds 1
+def test_smagorinsky_lilly_stratified_shear(oracle_mod, S, T, N2, expect_zero):
+    """u = S z, v = T z, b = N^2 z:  |S|^2 = S^2 + T^2 and
+    nu_e = (C_s Delta)^2 |S| sqrt(max(0, 1 - C_b N^2 / (Pr |S|^2))), kappa_e = nu_e / Pr,
+    Delta = (dx dy dz_k)^(1/3) with the stretched dz_k of the cell."""
+    Cs, Cb, Pr = 0.16, 1.3, 0.7
+    p = small_params(closure="smagorinsky", Cs=Cs, Cb=Cb, Pr=Pr, **_LIN_N)
+    f, zc, dx, dy, dzc = _linear_fields(p, u=(0, 0, S), v=(0, 0, T), tracers={"b": (0, 0, N2)})
+    m = oracle_mod.OracleModel(p)
+    m.set(**f)
+    SS = S * S + T * T
+    factor = 1.0 - Cb * N2 / (Pr * SS)
+    assert (factor <= 0.0) == expect_zero
+    for (i, j, k) in _LIN_CELLS:
+        Delta = (dx * dy * dzc[k]) ** (1.0 / 3.0)
+        nu = (Cs * Delta) ** 2 * math.sqrt(SS) * math.sqrt(max(0.0, factor))
+        assert abs(m.diffusivity_at(0, i, j, k) - nu) <= 1e-14 * (Cs * Delta) ** 2 * math.sqrt(SS)
+        assert abs(m.diffusivity_at(1, i, j, k) - nu / Pr) <= 1e-14 * (Cs * Delta) ** 2 * math.sqrt(SS) / Pr
+        if expect_zero:
+            assert m.diffusivity_at(0, i, j, k) == 0.0
+
+
+def test_smagorinsky_lilly_horizontal_strain_and_linear_eos(oracle_mod):
+    """u = E x + S z, v = -E y with a linear equation of state T = T0 + G z,
+    S = S0 + s z:  |S|^2 = 2 (E^2 + E^2 + 2 (S/2)^2) = 4 E^2 + S^2 and
+    N^2 = g (alpha G - beta s)."""
+    E, S, G, s = -0.05, 0.08, 2.0, 0.05
+    Cs, Cb, Pr, g, alpha, beta = 0.2, 1.0, 0.9, 9.81, 2e-4, 8e-4
+    p = small_params(closure="smagorinsky", Cs=Cs, Cb=Cb, Pr=Pr, tracers=["T", "S"], eos="linear_ts",
+                     g=g, alpha=alpha, beta=beta, T0=20.0, S0=35.0, **_LIN_N)
+    f, zc, dx, dy, dzc = _linear_fields(p, u=(E, 0, S), v=(0, -E, 0), tracers={"T": (0, 0, G), "S": (0, 0, s)})
+    f["T"] += 20.0
+    f["S"] += 35.0
+    m = oracle_mod.OracleModel(p)
+    m.set(**f)
+    SS = 4 * E * E + S * S
+    N2 = g * (alpha * G - beta * s)
+    factor = 1.0 - Cb * N2 / (Pr * SS)
+    assert 0.05 < factor < 0.95
+    for (i, j, k) in _LIN_CELLS:
+        Delta = (dx * dy * dzc[k]) ** (1.0 / 3.0)
+        nu = (Cs * Delta) ** 2 * math.sqrt(SS * factor)
+        assert abs(m.diffusivity_at(0, i, j, k) - nu) <= 1e-13 * nu
+        for n in (1, 2):
+            assert abs(m.diffusivity_at(n, i, j, k) - nu / Pr) <= 1e-13 * nu / Pr
+
+
+@pytest.mark.parametrize("E,S,T", [(-0.05, 0.08, 0.03), (0.05, 0.08, 0.03), (-0.1, 0.0, 0.2)])
+def test_amd_viscosity_linear_flow(oracle_mod, E, S, T):
+    """u = E x + S z, v = T x - E y (gradient G = [[E,0,S],[T,-E,0],[0,0,0]]):
+    sum_k D_k^2 (d_k u_i)(d_k u_j) S_ij = E^3 (dx^2 - dy^2) + dz^2 S^2 E (the T terms
+    cancel), |grad u|^2 = 2 E^2 + S^2 + T^2, nu_e = max(0, -C num / den)."""
+    C = 1.0 / 12.0
+    p = small_params(closure="amd", C_amd=C, **_LIN_N)
+    f, zc, dx, dy, dzc = _linear_fields(p, u=(E, 0, S), v=(T, -E, 0), tracers={"b": (0, 0, 0)})
+    m = oracle_mod.OracleModel(p)
+    m.set(**f)
+    nonzero = 0
+    for (i, j, k) in _LIN_CELLS:
+        num = E ** 3 * (dx * dx - dy * dy) + dzc[k] ** 2 * S * S * E
+        den = 2 * E * E + S * S + T * T
+        nu = max(0.0, -C * num / den)
+        scale = C * abs(num) / den + 1e-300
+        assert abs(m.diffusivity_at(0, i, j, k) - nu) <= 1e-13 * scale
+        nonzero += nu > 0
+    assert nonzero == (len(_LIN_CELLS) if E < 0 else 0)
+
+
+@pytest.mark.parametrize("a,b,S", [(0.2, 0.5, 0.3), (0.2, -0.5, 0.3), (-0.7, 0.1, -0.4)])
+def test_amd_diffusivity_shear_and_tilted_tracer(oracle_mod, a, b, S):
+    """u = S z, c = a x + b z: the only non-zero term of sum_k D_k^2 (d_k u_i)(d_k c)(d_i c)
+    is k = z, i = x, so kappa_e = max(0, -C dz^2 S a b / (a^2 + b^2))."""
+    C = 1.0 / 12.0
+    p = small_params(closure="amd", C_amd=C, **_LIN_N)
+    f, zc, dx, dy, dzc = _linear_fields(p, u=(0, 0, S), tracers={"b": (a, 0, b)})
+    m = oracle_mod.OracleModel(p)
+    m.set(**f)
+    for (i, j, k) in _LIN_CELLS:
+        kap = max(0.0, -C * dzc[k] ** 2 * S * a * b / (a * a + b * b))
+        scale = C * dzc[k] ** 2 * abs(S * a * b) / (a * a + b * b)
+        assert abs(m.diffusivity_at(1, i, j, k) - kap) <= 1e-13 * scale
+        assert (kap > 0) == (S * a * b < 0)
+
+
+@pytest.mark.parametrize("E,T,a,d", [(0.06, 0.1, 0.3, -0.4), (-0.06, 0.1, 0.3, 0.4), (0.02, -0.3, 0.5, 0.2)])
+def test_amd_diffusivity_horizontal_gradients(oracle_mod, E, T, a, d):
+    """u = E x, v = T x - E y, c = a x + d y (two tracers, the second with the
+    gradient reversed, which leaves kappa_e unchanged):
+    num = dx^2 (E a^2 + T a d) - dy^2 E d^2, kappa_e = max(0, -C num / (a^2 + d^2))."""
+    C = 1.0 / 12.0
+    p = small_params(closure="amd", C_amd=C, tracers=["b", "c"], **_LIN_N)
+    f, zc, dx, dy, dzc = _linear_fields(p, u=(E, 0, 0), v=(T, -E, 0), tracers={"b": (a, d, 0), "c": (-a, -d, 0)})
+    m = oracle_mod.OracleModel(p)
+    m.set(**f)
+    num = dx * dx * (E * a * a + T * a * d) - dy * dy * E * d * d
+    kap = max(0.0, -C * num / (a * a + d * d))
+    scale = C * (dx * dx * (abs(E) * a * a + abs(T * a * d)) + dy * dy * abs(E) * d * d) / (a * a + d * d)
+    for (i, j, k) in _LIN_CELLS:
+        for n in (1, 2):
+            assert abs(m.diffusivity_at(n, i, j, k) - kap) <= 1e-13 * scale
+
+
 # ----------------------------------------------------------------------------- solutions
 def test_resting_stratified_state_stays_at_rest(oracle_mod):
     p = small_params(stretch=1.5, Nx=8, Ny=8, Nz=10, closure="amd", f=1e-4)
