@@ -188,8 +188,8 @@ def test_les_fp32_100_steps(ocn, oracle_mod):
 
 
 def _full_size_sampled(ocn, oracle_mod, p, names, tol):
-    """Tendencies at 300 sampled points against the oracle's pointwise evaluation, and the
-    projection checked by properties that hold at any size (div u = 0, u_new = u - grad p,
+    """Tendencies at 300 sampled points against the oracle's pointwise evaluation (the one-call
+    FP32 bar: max|a-o| / max|o| over the samples), and the projection checked by properties that hold at any size (div u = 0, u_new = u - grad p,
     lap p = div u), on the workload's full grid."""
     st = rounded(inputs.initial_state(p), 32)
     g = ocn.Model(p)
@@ -205,6 +205,7 @@ def _full_size_sampled(ocn, oracle_mod, p, names, tol):
         ref = np.array([o.tendency_at(name, i, j, k) for (i, j, k) in pts])
         got = np.array([G[name][k, j, i] for (i, j, k) in pts])
         scale = max(np.abs(ref).max(), 1e-30)
+        print(p["name"], "sampled tendency", name, f"{np.abs(got - ref).max() / scale:.2e}")
         assert np.abs(got - ref).max() / scale < tol, name
     # projection properties
     u0, v0, w0 = (st[x] for x in "uvw")
@@ -231,13 +232,13 @@ def _full_size_sampled(ocn, oracle_mod, p, names, tol):
 
 def test_les_512_full_size_sampled(ocn, oracle_mod):
     """The benchmark workload at full size (512x512x256 FP32, WENO9, Smagorinsky-Lilly, T,S)."""
-    _full_size_sampled(ocn, oracle_mod, inputs.config("les_512"), ("u", "v", "w", "T", "S"), 2e-4)
+    _full_size_sampled(ocn, oracle_mod, inputs.config("les_512"), ("u", "v", "w", "T", "S"), 2e-5)
 
 
 def test_cbl_256_full_size_sampled(ocn, oracle_mod):
     """The convective-boundary-layer configuration at full size (256x256x128 FP32, 2 m spacing,
     tanh-stretched z, WENO5, AMD, f = 1e-4, surface buoyancy flux)."""
-    _full_size_sampled(ocn, oracle_mod, inputs.config("cbl_256"), ("u", "v", "w", "b"), 2e-4)
+    _full_size_sampled(ocn, oracle_mod, inputs.config("cbl_256"), ("u", "v", "w", "b"), 2e-5)
 
 
 # ----------------------------------------------------------------------------- behaviour
