@@ -96,7 +96,8 @@ def measured_peaks() -> dict:
 MLP_FLOPS_PER_SAMPLE = 2 * (32 * 128 + 128 * 128 + 128 * 128 + 128 * 16)
 
 
-PROFILED_SOURCES = {"tendency": ["tendency_kernel.cuh", "weno_coeffs.h", "tendency_f32_r5.cu", "tendency_f32_r5_smag.cu"],
+PROFILED_SOURCES = {"tendency": ["tendency_kernel.cuh", "weno_coeffs.h", "tendency_f32_r5.cu", "tendency_f32_r5_smag.cu",
+                                 "ocn_internal.cuh"],
                     "mlp_closure": ["mlp.cu", "column.cuh"]}
 
 
@@ -108,9 +109,9 @@ def source_hash(kernel: str) -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, valid only while the kernel
-    source hash recorded there matches the current sources (else None)."""
+def profiled_field(kernel: str, workload: str, key: str):
+    """A number from the committed ncu summary of a kernel, valid only while the kernel source
+    hash recorded there matches the current sources (else None)."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
     try:
         fields = {}
@@ -120,9 +121,26 @@ def profiled_traffic(kernel: str, workload: str):
                 fields[k.strip()] = v.strip()
         if fields.get("source_sha256_16") != source_hash(kernel):
             return None
-        return float(fields["dram_bytes_per_full_launch"])
+        return float(fields[key].split()[0])
     except Exception:
         return None
+
+
+def profiled_traffic(kernel: str, workload: str):
+    """DRAM bytes per full-size launch from the committed ncu summary (None when stale)."""
+    return profiled_field(kernel, workload, "dram_bytes_per_full_launch")
+
+
+def tendency_bytes_per_cell(p: dict, first_substage: bool = False) -> int:
+    """Algorithmic HBM bytes of the fused tendency + RK update per cell: the state in and out, G^m
+    out and G^{m-1} in (not in an RK3 first substage, zeta = 0), nu_e out when it is computed in
+    the kernel (FP32 Smagorinsky-Lilly) or in with the other closures."""
+    n = 3 + len(p["tracers"])
+    w = 4 if p.get("precision", 32) == 32 else 8
+    words = 3 * n + (0 if first_substage else n)
+    if p.get("closure") in ("smagorinsky", "amd"):
+        words += 1
+    return words * w
 
 
 # ------------------------------------------------------------------ clocks
@@ -365,22 +383,35 @@ def run_ours(args, world, rank, local):
     per_class = {k: {"launches": c, "ms_total": t, "ms_per_launch": (t / c if c else None),
                      "share": (t / sum(x for _, x in ktimes.values()))} for k, (c, t) in ktimes.items() if c}
     dom = max(per_class, key=lambda k: per_class[k]["ms_total"])
-    flops_cell = tendency_flops_per_cell(p)
+    model_flops = tendency_flops_per_cell(p)
+    exec_flops = profiled_field("tendency", p["name"], "fp32_flops_per_cell_executed")
     clock_mhz = peaks["sm_max_mhz"]
     if dom == "tendency":
         t_launch = per_class["tendency"]["ms_per_launch"] * 1e-3
+        flops_cell = exec_flops if exec_flops else model_flops
         achieved = flops_cell * cells / t_launch / 1e12
         nominal = SMS * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
         peak = fma_peak
         traffic = profiled_traffic("tendency", p["name"])
+        # the HBM view of the same launch: 2 of 3 substages read G^{m-1}
+        tb = (tendency_bytes_per_cell(p, True) + 2 * tendency_bytes_per_cell(p)) / 3.0
         roof = {"bound": "alu", "kernel": "k_tendency", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "traffic_source": "profiles/tendency_les_512.txt: an RK3 first-substage launch (no G_prev read), "
                                   "scaled from 256x256x128 by the cell count",
-                "algorithmic": f"{flops_cell} FP32 flops per cell (FMA = 2) x {cells} cells per launch",
+                "algorithmic": (f"{flops_cell:.0f} FP32 flops per cell executed (ncu FFMA x 2 + FMUL + FADD per cell, "
+                                "profiles/tendency_les_512.txt)" if exec_flops else
+                                f"{flops_cell} FP32 flops per cell from the WENO cost model (the ncu instruction count "
+                                "is stale for these sources)") + f" x {cells} cells per launch",
+                "cost_model_flops_per_cell": model_flops,
+                "executed_flops_per_cell": exec_flops,
                 "peak_source": "measured FP32 FMA throughput (ocn_fp32_fma_peak, this run)",
                 "nominal_peak": nominal, "frac_of_nominal": achieved / nominal,
-                "nominal_source": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 x {clock_mhz:.0f} MHz"}
+                "nominal_source": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 x {clock_mhz:.0f} MHz",
+                "hbm_view": {"achieved": tb * cells / t_launch / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                             "frac": tb * cells / t_launch / 1e9 / peaks["hbm_gbs"],
+                             "algorithmic": f"{tb:.1f} B per cell (state in/out, G out, G_prev in on 2 of 3 "
+                                            "substages, nu_e)"}}
     else:
         roof = None
     sub_bytes = substep_bytes_per_cell(p) * cells
@@ -529,8 +560,12 @@ def run_closure(args, world, rank, local):
     res = closure.experiment(n_members=32, n_train=24, t_end=3 * 3600.0, dt=10.0, every=180, train_steps=2000,
                              log=lambda *a: None)
     t_exp = time.time() - t0
-    net, mu, sigma, scale, ysc = res["nets"]["mlp"]
-    cl = closure.closure_for(net, mu, sigma, scale, ysc)
+    net, mu, sigma, scale, ysc, form = res["nets"]["mlp"]
+    cl = closure.closure_for(net, mu, sigma, scale, ysc, form)
+
+    def attach(model, p):
+        c = cl(p) if callable(cl) else cl
+        model.set_column_closure(c[0], c[1], c[2], c[3], p["N2"], mode=c[4])
     fine = inputs.ensemble_configs(n=args.members, seed=inputs.SEED + 7, dt=10.0)
     ps = [closure.coarse_config(p) for p in fine]
     cells = sum(p["Nx"] * p["Ny"] * p["Nz"] for p in ps)
@@ -543,7 +578,7 @@ def run_closure(args, world, rank, local):
         for i, p in enumerate(ps):
             E.members[i].set(**inputs.initial_state(p, seed=inputs.SEED + i + 1000 * rank))
             if mode == "learned":
-                E.members[i].set_column_closure(*cl(p), p["N2"])
+                attach(E.members[i], p)
         E.autotune()
         E.time_step(dt, args.warmup)
         E.synchronize()
@@ -565,7 +600,7 @@ def run_closure(args, world, rank, local):
     q = closure.coarse_config(dict(fine[0], Nz=nz, z_faces=inputs.tanh_faces(nz, fine[0]["Lz"])), side, side)
     big = ocn.Model(q, device=dev)
     big.set(**inputs.initial_state(q, seed=inputs.SEED))
-    big.set_column_closure(*cl(q), q["N2"])
+    attach(big, q)
     nsamp = side * side * (nz + 1)
     F = torch.empty((3, nz + 1, side, side), dtype=torch.float32, device=dev)
     reps = 20

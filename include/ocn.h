@@ -413,6 +413,21 @@ typedef struct {
   double N2_background;      /* background stratification (feature 17 and the depth estimate) */
 } ocn_column_closure_desc;
 ocn_status ocn_set_column_closure(ocn_model* model, const ocn_mlp* mlp, const ocn_column_closure_desc* desc);
+/* How the learned column closure enters the step.  mode 0 (the default): the network's outputs
+ * are face fluxes F_b, F_ubar, F_vbar, applied explicitly as above.  mode 1: outputs 0 and 1 are
+ * eddy diffusivities kappa = max(0, out_scale[0] y_0) and nu = max(0, out_scale[1] y_1) at every
+ * interior w-face of every column (output 2 is unused); in each substage, after the stage update,
+ * their horizontal means over the grid become the vertical diffusivity profiles (kappa for the
+ * tracers, nu for u, v and w; zero at the walls) of the semi-implicit column solve of
+ * ocn_set_vertical_diffusivity (Eq. tracer-time-discretization, Eq. predictor-velocity),
+ * (I - dtau d/dz K d/dz) q = q~, so a large learned diffusivity cannot make the step unstable.
+ * The network's fluxes are then -kappa db/dz, -nu dubar/dz, -nu dvbar/dz.  A tendency evaluation
+ * (ocn_compute_tendencies) takes nothing from the closure in this mode, as with any implicit
+ * vertical diffusion.  Mode 1 needs an FP32 buoyancy-tracer model without profiles of its own
+ * (ocn_set_vertical_diffusivity refuses them while it is active).  The mode is kept when the
+ * network is replaced or removed.  Errors: OCN_ERR_ARG (mode not 0 or 1), OCN_ERR_UNSUPPORTED,
+ * OCN_ERR_STATE. */
+ocn_status ocn_set_column_closure_mode(ocn_model* model, int mode);
 ocn_status ocn_closure_features(ocn_model* model, double N2_background, float* X);
 ocn_status ocn_column_fluxes(ocn_model* model, int which, float* F);
 ocn_status ocn_coarse_grain(ocn_model* model, int cx, int cy, double* out, size_t nout);

@@ -100,3 +100,11 @@ def closure_fluxes(params, X, mu, sigma, scale, shape):
     F[:, 0] = 0.0
     F[:, -1] = 0.0
     return F
+
+
+def closure_diffusivities(params, X, mu, sigma, scale, shape):
+    """The learned column closure in diffusivity form: K_q = max(0, scale_q * y_q) for q = 0
+    (tracers), 1 (momentum) at every w-face, [3][Nz+1][Ny][Nx] (K[2] = 0, walls 0)."""
+    K = np.maximum(closure_fluxes(params, X, mu, sigma, scale, shape), 0.0)
+    K[2] = 0.0
+    return K

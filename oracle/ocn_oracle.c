@@ -51,6 +51,8 @@ struct orc_model {
   int ab_started;                                   /* QAB2: a previous tendency exists */
   orc_face_flux_fn flux_fn;                         /* column closure hook (or NULL) */
   void* flux_ctx;
+  orc_face_flux_fn diff_fn;                         /* learned-diffusivity hook (or NULL) */
+  void* diff_ctx;
   double* Fcol;                                     /* [3][Nz+1][Ny][Nx] face fluxes of b, ubar, vbar */
 };
 
@@ -705,8 +707,11 @@ static void hydrostatic_split(orc_model* M, double* Hu, double* Hv, double* Hw) 
       }
 }
 
+static void learned_profiles(orc_model* M);
+
 static void stage(orc_model* M, double dt, double g, double z, double dtau) {
   size_t plane = (size_t)M->Nx * M->Ny, N = plane * M->Nz;
+  if (M->diff_fn) learned_profiles(M);          /* from the stage's initial state */
   all_tendencies(M, M->Hu, M->Hv, M->Hw, M->Hc);
   hydrostatic_split(M, M->Hu, M->Hv, M->Hw);
 #pragma omp parallel for schedule(static)
@@ -1015,6 +1020,31 @@ void orc_set_face_flux(orc_model* M, orc_face_flux_fn fn, void* ctx) {
   M->flux_fn = fn;
   M->flux_ctx = ctx;
   if (fn && !M->Fcol) M->Fcol = (double*)calloc((size_t)3 * (M->Nz + 1) * M->Nx * M->Ny, sizeof(double));
+}
+
+void orc_set_face_diffusivity(orc_model* M, orc_face_flux_fn fn, void* ctx) {
+  M->diff_fn = fn;
+  M->diff_ctx = ctx;
+  if (!fn) return;
+  if (!M->Fcol) M->Fcol = (double*)calloc((size_t)3 * (M->Nz + 1) * M->Nx * M->Ny, sizeof(double));
+  if (!M->nuz) M->nuz = (double*)calloc((size_t)M->Nz + 1, sizeof(double));
+  if (!M->kapz) M->kapz = (double*)calloc((size_t)M->Nz + 1, sizeof(double));
+  M->p.nu_z = M->nuz; M->p.kappa_z = M->kapz;
+  M->p.vertical_implicit = 1;
+}
+
+/* kappa_z, nu_z <- the horizontal means of the hook's diffusivities at the interior faces. */
+static void learned_profiles(orc_model* M) {
+  int Nx = M->Nx, Ny = M->Ny, Nz = M->Nz;
+  size_t plane = (size_t)Nx * Ny, NW = plane * (Nz + 1);
+  M->diff_fn(M->diff_ctx, M, M->Fcol);
+  for (int k = 0; k <= Nz; ++k) {
+    double s0 = 0.0, s1 = 0.0;
+    if (k > 0 && k < Nz)
+      for (size_t c = 0; c < plane; ++c) { s0 += M->Fcol[(size_t)k * plane + c]; s1 += M->Fcol[NW + (size_t)k * plane + c]; }
+    M->kapz[k] = s0 / (double)plane;
+    M->nuz[k] = s1 / (double)plane;
+  }
 }
 
 /* G_b -= dF_b/dz at centres; G_u, G_v -= dF/dz of the face flux averaged onto the u and v columns.

@@ -133,6 +133,15 @@ void orc_coarse_grain(orc_model* m, int cx, int cy, double* out);
  * and v columns to G_u and G_v (buoyancy-tracer models).  fn = NULL removes it. */
 typedef void (*orc_face_flux_fn)(void* ctx, orc_model* m, double* F);
 void orc_set_face_flux(orc_model* m, orc_face_flux_fn fn, void* ctx);
+/* Hook of a learned closure in diffusivity form: at the start of every stage of the time stepper,
+ * fn(ctx, m, K) with the stage's initial state in m fills K [3][Nz+1][Ny][Nx] with the eddy
+ * diffusivity of the tracers (K[0]) and of momentum (K[1]) at every w-face of every column (K[2]
+ * unused); their horizontal means over the grid at the interior faces (0 at the walls) become the
+ * vertical diffusivity profiles of that stage's semi-implicit column solve (Eq.
+ * tracer-time-discretization, Eq. predictor-velocity): kappa for every tracer, nu for u, v, w.
+ * Setting it makes the model's vertical diffusion implicit; fn = NULL removes it (the profiles
+ * of the last stage stay). */
+void orc_set_face_diffusivity(orc_model* m, orc_face_flux_fn fn, void* ctx);
 
 /* Vertical diffusion operator D(q) = d/dz (kappa dq/dz) of one column with no flux through the walls,
  * second order (fluxes -kappa_f (q_k - q_{k-1})/dz_f at the interior faces, divergence over dz_c):

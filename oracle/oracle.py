@@ -95,6 +95,7 @@ def lib():
         L.orc_column_sgs_flux.argtypes = [C.c_void_p, dp]
         L.orc_coarse_grain.argtypes = [C.c_void_p, C.c_int, C.c_int, dp]
         L.orc_set_face_flux.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        L.orc_set_face_diffusivity.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         L.orc_vertical_diffusion.argtypes = [C.c_void_p, C.c_int, dp, dp, dp]
         L.orc_vertical_implicit_solve.argtypes = [C.c_void_p, C.c_int, dp, C.c_double, dp, dp]
         _lib = L
@@ -320,6 +321,23 @@ class OracleModel:
 
         self._flux_cb = FACE_FLUX_FN(cb)
         lib().orc_set_face_flux(self._h, C.cast(self._flux_cb, C.c_void_p), None)
+
+    def set_face_diffusivity(self, fn):
+        """fn(model) -> K [3][Nz+1][Ny][Nx] (tracer and momentum diffusivities at every w-face of
+        every column) called at the start of every stage; their horizontal means become that
+        stage's implicit vertical diffusivity profiles.  None removes the hook."""
+        if fn is None:
+            lib().orc_set_face_diffusivity(self._h, None, None)
+            self._diff_cb = None
+            return
+        shape = (3, self.Nz + 1, self.Ny, self.Nx)
+
+        def cb(ctx, h, F):
+            out = np.ctypeslib.as_array(F, shape=shape)
+            out[...] = fn(self)
+
+        self._diff_cb = FACE_FLUX_FN(cb)
+        lib().orc_set_face_diffusivity(self._h, C.cast(self._diff_cb, C.c_void_p), None)
 
     def vertical_diffusion(self, q, kappa_faces, staggering: int = 0) -> np.ndarray:
         """D(q) = d/dz(kappa dq/dz) of one column (staggering 0: centres, 1: faces)."""

@@ -105,21 +105,50 @@ def normalisation(X):
 
 
 NONLOCAL = (15, 16, 17, 18, 19)      # Jb, f, N2, depth, mixed-layer depth: no local gradients
+LOCAL = tuple(range(17))             # db/dz, dubar/dz, dvbar/dz at the five faces k-2..k+2, Jb, f
 # The trained closure: the buoyancy flux (momentum stays with AMD), non-dimensionalised by the
 # surface buoyancy flux, from the non-local features only, fitted to the member-mean residual.
 # Feeding the local gradients as well fits the training data better but feeds grid-scale
 # gradients back into the explicit flux and degrades the coupled runs.
 DEFAULT_VARIANT = dict(target="mean", outputs=(0,), features="nonlocal", scale="Jb")
+# The closure on the inputs the configuration states (local gradients of b, ubar, vbar over five
+# faces, the surface buoyancy flux and f) in diffusivity form: the network predicts eddy
+# diffusivities kappa (tracers) and nu (momentum) >= 0 at every face, whose column means the
+# coarse model applies through its semi-implicit vertical solve.
+DIFFUSIVITY_VARIANT = dict(target="mean", outputs=(0, 1), features="local", form="diffusivity")
+KAPPA_MAX = 1.0                      # m^2/s: cap of the diffusivity targets
+
+
+def diffusivity_targets(X, Y, ncol: int, kmax: float = KAPPA_MAX):
+    """Per-sample diffusivity targets and least-squares weights from the member-mean residual
+    fluxes Y [N][3] (one value per face, repeated over the ncol columns of a snapshot) and the
+    column-mean gradients at the face (features 2, 7, 12): the flux -K g with the smallest
+    squared error is K = -F g / g^2, clipped to [0, kmax]; its weight is g^2 (so that sampling
+    in proportion to it makes the mean-square error of K the flux error)."""
+    import torch
+    gm = X[:, [2, 7, 12]].double().reshape(-1, ncol, 3).mean(dim=1)          # per face and snapshot
+    gm = gm.repeat_interleave(ncol, dim=0)
+    Yd = Y.double()
+    gb = gm[:, 0]
+    gb2 = gb * gb
+    kap = torch.where(gb2 > 0, -Yd[:, 0] * gb / gb2.clamp_min(1e-300), torch.zeros_like(gb)).clamp(0.0, kmax)
+    gu2 = gm[:, 1] ** 2 + gm[:, 2] ** 2
+    nu = torch.where(gu2 > 0, -(Yd[:, 1] * gm[:, 1] + Yd[:, 2] * gm[:, 2]) / gu2.clamp_min(1e-300),
+                     torch.zeros_like(gb)).clamp(0.0, kmax)
+    T = torch.stack([kap, nu, torch.zeros_like(kap)], dim=1).float()
+    w = gb2 / gb2.mean().clamp_min(1e-300) + gu2 / gu2.mean().clamp_min(1e-300)
+    return T, w
 
 
 def train(X, Y, steps: int = 3000, batch: int = 16384, lr: float = 1e-3, seed: int = inputs.SEED, log_every=0,
-          outputs=(0, 1, 2), features=None, yscale=None):
+          outputs=(0, 1, 2), features=None, yscale=None, weights=None):
     """Train a 32-128-128-128-16 network on (X raw features, Y targets [N][3]); only the flux
     components in `outputs` enter the loss (the others get out_scale 0: the closure leaves them
     to the model's own closure); `features` (indices) restricts the inputs (the others are
     normalised to zero by an infinite scale); yscale [N][3] divides the targets per sample
-    (e.g. by the member's surface buoyancy flux).  Returns the network, the feature
-    normalisation, the output scales and the loss history."""
+    (e.g. by the member's surface buoyancy flux); weights [N] (or None) sets the probability
+    with which a sample enters a batch, so that the mean-square loss is weighted by it.  Returns
+    the network, the feature normalisation, the output scales and the loss history."""
     import torch
     mu, sigma = normalisation(X)
     if features is not None:
@@ -147,7 +176,10 @@ def train(X, Y, steps: int = 3000, batch: int = 16384, lr: float = 1e-3, seed: i
     hist = []
     for s in range(steps):
         lr_s = lr * 0.5 * (1.0 + math.cos(math.pi * s / steps))        # cosine decay
-        idx = torch.randint(0, Xn.shape[0], (batch,), device=dev, generator=g)
+        if weights is None:
+            idx = torch.randint(0, Xn.shape[0], (batch,), device=dev, generator=g)
+        else:
+            idx = torch.multinomial(weights, batch, replacement=True, generator=g)
         loss = net.train_step(Xn[idx], Yn[idx], mask, lr_s)
         hist.append(loss)
         if log_every and s % log_every == 0:
@@ -170,16 +202,17 @@ def predict(net, mu, sigma, out_scale, X, chunk: int = 0):
 
 
 def coarse_run(members, init_states, t_end: float, dt: float, every: int, closure=None):
-    """Coarse ensemble from the given initial states; closure = (net, mu, sigma, out_scale) or
-    a function p -> that tuple (per-member scales), or None (plain AMD).  Returns per-member
-    profile series at the snapshot steps."""
+    """Coarse ensemble from the given initial states; closure = (net, mu, sigma, out_scale[, mode])
+    or a function p -> that tuple (per-member scales), or None (plain AMD); mode "flux" (default)
+    or "diffusivity".  Returns per-member profile series at the snapshot steps."""
     ens = ocn.Ensemble(members)
     ens.set_mode("batched")        # coarse instances are small: one launch per kernel for all of them
     for p, m, st in zip(members, ens.members, init_states):
         m.set(project=False, **st)
         if closure is not None:
-            net, mu, sigma, scale = closure(p) if callable(closure) else closure
-            m.set_column_closure(net, mu, sigma, scale, p["N2"])
+            c = closure(p) if callable(closure) else closure
+            net, mu, sigma, scale = c[:4]
+            m.set_column_closure(net, mu, sigma, scale, p["N2"], mode=c[4] if len(c) > 4 else "flux")
     ens.autotune()
     n = _time_steps(t_end, dt)
     series = [[] for _ in members]
@@ -210,12 +243,12 @@ def profile_errors(p: dict, coarse_series, fine_series) -> dict:
     return {"b": math.sqrt(db / max(nb, 1e-300)), "Fb": math.sqrt(df / max(nf, 1e-300))}
 
 
-def closure_for(net, mu, sigma, scale, yscale=None):
+def closure_for(net, mu, sigma, scale, yscale=None, mode="flux"):
     """The per-member closure arguments: with yscale "Jb" the output scales carry the member's
     surface buoyancy flux."""
     if yscale == "Jb":
-        return lambda q: (net, mu, sigma, np.asarray(scale) * q["top_flux"]["b"])
-    return (net, mu, sigma, scale)
+        return lambda q: (net, mu, sigma, np.asarray(scale) * q["top_flux"]["b"], mode)
+    return (net, mu, sigma, scale, mode)
 
 
 def apriori_errors(pred, Y, G, n_members, Nz_of, cy, cx):
@@ -281,21 +314,28 @@ def experiment(n_members: int = 64, n_train: int = 48, t_end: float = 6 * 3600.0
         tr = G < n_train
         t1 = time.time()
         outputs = tuple(v.get("outputs", (0, 1, 2)))
-        feats = NONLOCAL if v.get("features") == "nonlocal" else None
+        feats = {"nonlocal": NONLOCAL, "local": LOCAL}.get(v.get("features"))
         jb = torch.tensor([p["top_flux"]["b"] for p in members], dtype=torch.float64, device=X.device)
         ysc = None
         if v.get("scale") == "Jb":
             ysc = jb[G.long()][:, None].expand(-1, 3).contiguous()
-        net, mu, sigma, scale, hist = train(X[tr], Y[tr], steps=train_steps, batch=batch, lr=lr, outputs=outputs,
-                                            features=feats, yscale=None if ysc is None else ysc[tr])
+        diffusive = v.get("form") == "diffusivity"
+        Yt, wts = (diffusivity_targets(X, Y, cx * cy) if diffusive else (Y, None))
+        net, mu, sigma, scale, hist = train(X[tr], Yt[tr], steps=train_steps, batch=batch, lr=lr, outputs=outputs,
+                                            features=feats, yscale=None if ysc is None else ysc[tr],
+                                            weights=None if wts is None else wts[tr])
         t_train = time.time() - t1
         pred = predict(net, mu, sigma, scale, X)
         if ysc is not None:
             pred = pred * ysc
+        if diffusive:        # the fluxes -K dq/dz of the predicted diffusivities, column by column
+            K = pred.clamp_min(0.0)
+            g3 = X[:, [2, 7, 12]].double()
+            pred = torch.stack([-K[:, 0] * g3[:, 0], -K[:, 1] * g3[:, 1], -K[:, 1] * g3[:, 2]], dim=1)
         # a priori skill against the column-mean target of every member
         Xm, Ym, Gm = data["mean"] if "mean" in data else (Xs, Ys, Gs)
         ap = apriori_errors(pred, torch.cat(Ym), torch.cat(Gm), n_members, None, cy, cx)
-        closure_fn = closure_for(net, mu, sigma, scale, v.get("scale"))
+        closure_fn = closure_for(net, mu, sigma, scale, v.get("scale"), "diffusivity" if diffusive else "flux")
         _, learned = coarse_run(coarse_members, init_states, t_end, dt, every, closure_fn)
         for i, p in enumerate(members):
             e = profile_errors(p, learned[i], fine_series[i])
@@ -307,7 +347,7 @@ def experiment(n_members: int = 64, n_train: int = 48, t_end: float = 6 * 3600.0
         summary[f"{name}_loss"] = [float(hist[0]), float(np.mean(hist[-50:]))]
         summary[f"{name}_samples"] = int(tr.sum())
         summary[f"{name}_train_seconds"] = t_train
-        nets[name] = (net, mu, sigma, scale, v.get("scale"))
+        nets[name] = (net, mu, sigma, scale, v.get("scale"), "diffusivity" if diffusive else "flux")
         log(f"{name}: loss {hist[0]:.4f} -> {np.mean(hist[-50:]):.4f} ({t_train:.1f} s); test b {summary[name + '_b']:.3f} "
             f"Fb {summary[name + '_Fb']:.3f} apriori {summary[name + '_apriori_b']:.3f} | amd b {summary['amd_b']:.3f} "
             f"Fb {summary['amd_Fb']:.3f}")

@@ -166,6 +166,7 @@ struct ocn_model {
   float colc_mu[kColumnFeatures] = {0}, colc_isig[kColumnFeatures] = {0}, colc_scale[3] = {0, 0, 0};
   double colc_N2 = 0.0;
   int colc_version = 0;
+  int colc_mode = 0;                // 0: face fluxes, explicit; 1: diffusivities through the implicit step
   // time stepper (Eq. rk3 or Eq. qab2) and vertical diffusivity profiles (explicit or semi-implicit)
   int stepper = OCN_STEPPER_RK3;
   double chi = 0.1;
@@ -337,10 +338,19 @@ PoissonArgs<T> poisson_args(const ocn_model* m, int which, double dts) {
   return a;
 }
 
+// FP32 Smagorinsky-Lilly models compute nu_e inside the tendency kernel (and write it to the arena
+// as they go), so a time step or a tendency evaluation launches no closure kernel for them.
+inline bool tendency_computes_nu(const ocn_model* m) {
+  return m->es == 4 && m->d.closure == OCN_CLOSURE_SMAGORINSKY;
+}
+
+// The eddy-diffusivity kernel; with before_tendency, nothing when the tendency kernel that
+// follows computes nu_e itself.
 template <typename T>
-cudaError_t enqueue_closure(ocn_model* m, int which) {
+cudaError_t enqueue_closure(ocn_model* m, int which, bool before_tendency = false) {
   const ocn_grid* g = m->g;
   if (!(m->d.closure == OCN_CLOSURE_SMAGORINSKY || m->d.closure == OCN_CLOSURE_AMD)) return cudaSuccess;
+  if (before_tendency && tendency_computes_nu(m)) return cudaSuccess;
   ClosureArgs<T> c;
   memset(&c, 0, sizeof(c));
   c.cur = state_ptrs<T>(m, which);
@@ -383,6 +393,10 @@ cudaError_t enqueue_tendency(ocn_model* m, int which, double dt_gamma, double dt
   a.dt_gamma = (T)dt_gamma; a.dt_zeta = (T)dt_zeta;
   a.mode = mode;
   a.variant = m->variant;
+  a.nu_out = m->off_nu ? at<T>(m, m->off_nu) : nullptr;
+  a.dzc = at<T>(m, m->off_dzc);
+  a.dx = (T)(g->Lx / g->Nx); a.dy = (T)(g->Ly / g->Ny);
+  a.Cs = (T)m->d.Cs; a.Cb = (T)m->d.Cb;
   m->hook.pre(OCN_K_TENDENCY);
   cudaError_t e = launch_tendency<T>(a, m->R, m->stream);
   m->hook.post(OCN_K_TENDENCY);
@@ -415,6 +429,7 @@ cudaError_t enqueue_learned_flux(ocn_model* m, int which, float* F, int* nlaunch
   if (!mlp_closure_layers(m->colc, a.W, a.bias)) return cudaErrorInvalidValue;
   for (int q = 0; q < kColumnFeatures; ++q) { a.mu[q] = m->colc_mu[q]; a.inv_sigma[q] = m->colc_isig[q]; }
   for (int q = 0; q < 3; ++q) a.scale[q] = m->colc_scale[q];
+  a.relu = (m->colc_mode == 1) ? 1 : 0;
   a.F = F;
   a.status = at<int>(m, m->off_status);
   m->hook.pre(OCN_K_COLUMN_CLOSURE);
@@ -434,6 +449,24 @@ cudaError_t enqueue_column_closure(ocn_model* m, int which, double dt_gamma, int
   } else {
     if (!m->colc) return cudaSuccess;
     float* F = at<float>(m, m->off_colF);
+    if (m->colc_mode == 1) {
+      // diffusivities: their column means become the vertical diffusivity profiles of this
+      // substage (tracers: output 0; momentum: output 1), applied by the implicit step that
+      // follows; a tendency evaluation alone (mode 1) takes nothing from them
+      if (mode == 1) return cudaSuccess;
+      cudaError_t e = enqueue_learned_flux(m, which, F, nlaunch);
+      if (e != cudaSuccess) return e;
+      FaceMeanArgs fm;
+      fm.F = F;
+      fm.p0 = at<float>(m, m->off_kapz);
+      fm.p1 = at<float>(m, m->off_nuz);
+      fm.Nx = m->g->Nx; fm.Ny = m->g->Ny; fm.Nz = m->g->Nz;
+      m->hook.pre(OCN_K_COLUMN_CLOSURE);
+      e = launch_face_mean(fm, m->stream);
+      m->hook.post(OCN_K_COLUMN_CLOSURE);
+      if (nlaunch) *nlaunch += 1;
+      return e;
+    }
     cudaError_t e = enqueue_learned_flux(m, which, F, nlaunch);
     if (e != cudaSuccess) return e;
     FaceFluxArgs f;
@@ -458,8 +491,11 @@ cudaError_t enqueue_column_closure(ocn_model* m, int which, double dt_gamma, int
 // explicit term to G and skips the implicit step.
 template <typename T>
 cudaError_t enqueue_vertical(ocn_model* m, int which, double dt_gamma, double dtau, int mode, int* nlaunch) {
-  if (!m->vnu && !m->vkap) return cudaSuccess;
-  if (m->vimplicit && mode == 1) return cudaSuccess;
+  // a learned closure in diffusivity mode supplies both profiles every substage, applied implicitly
+  const bool learned = m->colc && m->colc_mode == 1;
+  const bool vnu = m->vnu || learned, vkap = m->vkap || learned, vimplicit = m->vimplicit || learned;
+  if (!vnu && !vkap) return cudaSuccess;
+  if (vimplicit && mode == 1) return cudaSuccess;
   VDiffArgs<T> a;
   memset(&a, 0, sizeof(a));
   StatePtrs<T> cur = state_ptrs<T>(m, which), nxt = state_ptrs<T>(m, 1 - which), G = g_ptrs<T>(m);
@@ -473,11 +509,11 @@ cudaError_t enqueue_vertical(ocn_model* m, int which, double dt_gamma, double dt
   a.nuz = at<T>(m, m->off_nuz); a.kapz = at<T>(m, m->off_kapz);
   a.dzc = at<T>(m, m->off_dzc); a.dzf = at<T>(m, m->off_dzf);
   a.Nx = m->g->Nx; a.Ny = m->g->Ny; a.Nz = m->g->Nz; a.nt = m->d.n_tracers;
-  a.fields = (m->vnu ? 7 : 0) | (m->vkap ? (((1 << m->d.n_tracers) - 1) << 3) : 0);
+  a.fields = (vnu ? 7 : 0) | (vkap ? (((1 << m->d.n_tracers) - 1) << 3) : 0);
   a.mode = mode;
   a.dt_gamma = (T)dt_gamma; a.dtau = (T)dtau;
   m->hook.pre(OCN_K_VERTICAL);
-  cudaError_t e = launch_vertical_diffusion<T>(a, m->vimplicit, m->stream);
+  cudaError_t e = launch_vertical_diffusion<T>(a, vimplicit, m->stream);
   m->hook.post(OCN_K_VERTICAL);
   if (nlaunch) *nlaunch += 1;
   return e;
@@ -501,9 +537,9 @@ cudaError_t enqueue_step(ocn_model* m, double dt, int* which, int* nlaunch) {
   for (int st = 0; st < nst; ++st) {
     const double g = qab2 ? 1.5 + chi : gam[st], z = qab2 ? 0.5 + chi : zet[st];
     const double dtau = (g - z) * dt;
-    cudaError_t e = check_sync(m, enqueue_closure<T>(m, *which));
+    cudaError_t e = check_sync(m, enqueue_closure<T>(m, *which, true));
     if (e != cudaSuccess) return e;
-    if (m->off_nu) ++n;
+    if (m->off_nu && !tendency_computes_nu(m)) ++n;
     e = check_sync(m, enqueue_tendency<T>(m, *which, g * dt, z * dt, 0));
     if (e != cudaSuccess) return e;
     ++n;
@@ -839,7 +875,7 @@ ocn_status ocn_compute_tendencies(ocn_model* m) {
   DeviceGuard dg(m->dev);
   cudaError_t e;
   if (m->es == 4) {
-    e = check_sync(m, enqueue_closure<float>(m, m->cur));
+    e = check_sync(m, enqueue_closure<float>(m, m->cur, true));
     if (e == cudaSuccess) e = check_sync(m, enqueue_tendency<float>(m, m->cur, 0.0, 0.0, 1));
     if (e == cudaSuccess) e = check_sync(m, enqueue_column_closure<float>(m, m->cur, 0.0, 1, nullptr));
     if (e == cudaSuccess) e = check_sync(m, enqueue_vertical<float>(m, m->cur, 0.0, 0.0, 1, nullptr));
@@ -973,7 +1009,7 @@ ocn_status ocn_profiles(ocn_model* m, double* out, int nout) {
   cudaError_t e;
   auto run = [&](auto tag) -> cudaError_t {
     typedef decltype(tag) T;
-    cudaError_t err = enqueue_closure<T>(m, m->cur);
+    cudaError_t err = enqueue_closure<T>(m, m->cur, true);
     if (err == cudaSuccess) err = enqueue_tendency<T>(m, m->cur, 0.0, 0.0, 1);   // unsplit G, state untouched
     if (err == cudaSuccess) err = enqueue_column_closure<T>(m, m->cur, 0.0, 1, nullptr);
     if (err == cudaSuccess) err = enqueue_vertical<T>(m, m->cur, 0.0, 0.0, 1, nullptr);
@@ -1040,6 +1076,8 @@ ocn_status ocn_set_vertical_diffusivity(ocn_model* m, const double* nu_faces, co
       for (int k = 0; k < n; ++k)
         if (!(p[k] >= 0.0) || !isfinite(p[k])) return fail(OCN_ERR_ARG, "diffusivities must be finite and >= 0");
   if (implicit && 4 * (size_t)m->es * m->g->Nz > 48 * 1024) return fail(OCN_ERR_UNSUPPORTED, "Nz too large for the implicit solver");
+  if (m->colc_mode == 1 && (nu_faces || kappa_faces))
+    return fail(OCN_ERR_STATE, "the learned column closure (diffusivity mode) sets the profiles");
   DeviceGuard dg(m->dev);
   std::vector<char> buf((size_t)n * m->es);
   auto upload = [&](const double* p, size_t off) -> cudaError_t {
@@ -1080,6 +1118,20 @@ ocn_status ocn_set_column_closure(ocn_model* m, const ocn_mlp* mlp, const ocn_co
   m->colc = mlp;
   m->colc_version += 1;
   drop_graphs(m);
+  return OCN_OK;
+}
+
+ocn_status ocn_set_column_closure_mode(ocn_model* m, int mode) {
+  if (!m) return fail(OCN_ERR_ARG, "null argument");
+  if (mode != 0 && mode != 1) return fail(OCN_ERR_ARG, "mode must be 0 (face fluxes) or 1 (diffusivities)");
+  if (mode == 1 && !m->off_colF) return fail(OCN_ERR_UNSUPPORTED, "the learned column closure needs an FP32 buoyancy-tracer model");
+  if (mode == 1 && (m->vnu || m->vkap)) return fail(OCN_ERR_STATE, "the model has its own vertical diffusivity profiles");
+  DeviceGuard dg(m->dev);
+  if (mode != m->colc_mode) {
+    m->colc_mode = mode;
+    m->colc_version += 1;
+    drop_graphs(m);
+  }
   return OCN_OK;
 }
 

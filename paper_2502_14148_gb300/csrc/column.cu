@@ -156,6 +156,41 @@ struct ApplyFaceFluxK {
   static constexpr int kThreads = 256, kMinBlocks = 1;
   static __device__ __forceinline__ void run(const Payload& a, uint3 bid, uint3 g) { apply_face_flux_body(a, bid, g); }
 };
+// One block per face k: the plane means of F[0][k] and F[1][k] (FP64 sums), 0 at the walls.
+constexpr int kFaceMeanThreads = 256;
+__device__ __forceinline__ void face_mean_body(const FaceMeanArgs& a, const uint3 bid) {
+  const int k = bid.x;
+  const size_t plane = (size_t)a.Nx * a.Ny, NW = plane * (a.Nz + 1);
+  double s0 = 0.0, s1 = 0.0;
+  if (k > 0 && k < a.Nz) {
+    const float* f0 = a.F + (size_t)k * plane;
+    const float* f1 = f0 + NW;
+    for (size_t i = threadIdx.x; i < plane; i += kFaceMeanThreads) {
+      s0 += (double)f0[i];
+      s1 += (double)f1[i];
+    }
+  }
+  __shared__ double r0[kFaceMeanThreads / 32], r1[kFaceMeanThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_down_sync(0xffffffffu, s0, o);
+    s1 += __shfl_down_sync(0xffffffffu, s1, o);
+  }
+  if ((threadIdx.x & 31) == 0) { r0[threadIdx.x >> 5] = s0; r1[threadIdx.x >> 5] = s1; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t0 = 0.0, t1 = 0.0;
+    for (int w = 0; w < kFaceMeanThreads / 32; ++w) { t0 += r0[w]; t1 += r1[w]; }
+    a.p0[k] = (float)(t0 / (double)plane);
+    a.p1[k] = (float)(t1 / (double)plane);
+  }
+}
+struct FaceMeanK {
+  typedef FaceMeanArgs Payload;
+  static constexpr int kThreads = kFaceMeanThreads, kMinBlocks = 1;
+  static __device__ __forceinline__ void run(const Payload& a, uint3 bid, uint3) { face_mean_body(a, bid); }
+};
+__global__ void __launch_bounds__(kFaceMeanThreads) k_face_mean(const FaceMeanArgs a) { face_mean_body(a, blockIdx); }
+
 __global__ void k_column_h(const ColumnArgs a) { column_h_body(a, blockIdx); }
 __global__ void k_apply_face_flux(const FaceFluxArgs a) { apply_face_flux_body(a, blockIdx, gridDim); }
 
@@ -189,6 +224,13 @@ cudaError_t launch_coarse_grain(const ColumnArgs& a, int cx, int cy, double* out
   if (cx < 1 || cy < 1 || a.Nx % cx || a.Ny % cy) return cudaErrorInvalidValue;
   const size_t n = (size_t)cx * cy * (a.Nz + 1);
   k_coarse_grain<<<(int)((n + 127) / 128), 128, 0, s>>>(a, cx, cy, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_face_mean(const FaceMeanArgs& a, cudaStream_t s) {
+  const dim3 grid(a.Nz + 1);
+  if (record_launch<FaceMeanK>(a, grid, dim3(kFaceMeanThreads), 0, OCN_K_COLUMN_CLOSURE)) return cudaSuccess;
+  k_face_mean<<<grid, kFaceMeanThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 

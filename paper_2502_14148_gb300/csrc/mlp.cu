@@ -580,7 +580,10 @@ __device__ __forceinline__ void mlp_closure_body(const MlpClosureArgs& a, const 
           const bool wall = (k == 0 || k == c.Nz);
           const float* b4 = sbias + 3 * kCH;
 #pragma unroll
-          for (int q = 0; q < 3; ++q) cur.m->F[(size_t)q * NW + sidx] = wall ? 0.0f : cur.m->scale[q] * (v[q] + b4[q]);
+          for (int q = 0; q < 3; ++q) {
+            const float y = cur.m->scale[q] * (v[q] + b4[q]);
+            cur.m->F[(size_t)q * NW + sidx] = wall ? 0.0f : (cur.m->relu ? fmaxf(y, 0.0f) : y);
+          }
         }
       }
     }

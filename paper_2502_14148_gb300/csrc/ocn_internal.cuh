@@ -66,6 +66,11 @@ struct TendencyArgs {
   int mode;               // 0: RK update + G;  1: G only
   int variant;            // tile variant of the FP32 kernel (0: 32x8 one CTA/SM, 1: 32x8 two, 2: 32x16, 3: 32x4 three,
                           // 4: 32x14, 5: 32x12, 6: 16x16 two CTAs/SM for grids under 32 columns wide)
+  // FP32 Smagorinsky-Lilly kernels compute the eddy viscosity of the stage state themselves (in the
+  // same z march, from the staged planes) and write it here for other readers; nu above is unused then.
+  T* nu_out;
+  const T* dzc;           // dz_c[k]
+  T dx, dy, Cs, Cb;       // grid spacing, Smagorinsky and stratification constants
 };
 
 template <typename T>
@@ -257,11 +262,20 @@ struct MlpClosureArgs {
   ColumnArgs col;
   const void* W[4]; const float* bias[4];  // BF16 weights [n_out][n_in], FP32 biases (32-128-128-128-16)
   float mu[kColumnFeatures], inv_sigma[kColumnFeatures];
+  int relu;                                // 1: outputs are diffusivities, max(0, scale * y)
   float scale[3];
   float* F;                                // [3][Nz+1][Ny][Nx]
   int* status;                             // set to 1 if a bounded wait gave up
 };
 cudaError_t launch_mlp_closure(const MlpClosureArgs& a, cudaStream_t s);
+// Horizontal means of face quantities 0 and 1 of F ([3][Nz+1][Ny][Nx]) per face, into p0 and p1
+// ([Nz+1]; 0 at the walls): the learned diffusivities' column-mean profiles.
+struct FaceMeanArgs {
+  const float* F;
+  float* p0; float* p1;
+  int Nx, Ny, Nz;
+};
+cudaError_t launch_face_mean(const FaceMeanArgs& a, cudaStream_t s);
 // Layer pointers of a network (mlp.cu): returns false unless its shape is 32-128-128-128-16.
 bool mlp_closure_layers(const ocn_mlp* n, const void** W, const float** bias);
 

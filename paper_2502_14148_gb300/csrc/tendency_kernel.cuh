@@ -22,6 +22,12 @@
 //    face flux is reconstructed exactly once.
 //  * The epilogue forms G, applies u~ = u + dt (gamma G - zeta G_prev) and
 //    writes the new state and G (the G_prev of the next substage).
+//  * FP32 Smagorinsky-Lilly kernels also compute the eddy viscosity: the ghost
+//    warps, which have no epilogue and a third of the main warps' flux work,
+//    evaluate nu_e two levels ahead of the march on the tile and a one-cell
+//    ring around it, from planes staged four levels ahead; no separate
+//    closure kernel and no nu_e round trip through HBM (it is still written
+//    out, for readers outside the step).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -68,8 +74,8 @@ __device__ __forceinline__ void sfor(F&& f) {
 // from the long-double tables in constant memory.
 template <typename T> struct Coef;
 template <> struct Coef<float> {
-  template <int r, int s, int a> static __device__ __forceinline__ float gq() {
-    constexpr float v = WenoGq<float, r, s, a>::value;
+  template <int r, int s, int a> static __device__ __forceinline__ float gqd() {
+    constexpr float v = WenoGqD<float, r, s, a>::value;
     return v;
   }
   template <int r, int s, int a, int b> static __device__ __forceinline__ float db() {
@@ -86,7 +92,7 @@ template <> struct Coef<float> {
   }
 };
 template <> struct Coef<double> {
-  template <int r, int s, int a> static __device__ __forceinline__ double gq() { return cWd.gq[r][s][a]; }
+  template <int r, int s, int a> static __device__ __forceinline__ double gqd() { return cWd.gq[r][s][a] * cWd.d[r][s]; }
   template <int r, int s, int a, int b> static __device__ __forceinline__ double db() { return cWd.dbeta[r][s][a][b]; }
   template <int r, int s> static __device__ __forceinline__ double d() { return cWd.d[r][s]; }
   template <int p, int n> static __device__ __forceinline__ double cen() { return cWd.cen[p][n]; }
@@ -102,7 +108,10 @@ __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 // each Jiang-Shu indicator a quadratic form in them (both exact rewritings of
 // the cell-value forms, the tables derived on the host).  Mirroring the
 // stencil for vel < 0 reverses and negates the differences; the indicators are
-// even in d, so only the final correction carries the sign.
+// even in d, so only the final correction carries the sign.  The substencil
+// values are formed already multiplied by their linear weights d_k, so that the
+// WENO-Z weight alpha_k = d_k (1 + (tau / (beta_k + eps))^2) enters the
+// numerator as (1 + ratio^2) q_k d_k and the denominator as one FMA.
 template <typename T, int r>
 __device__ __forceinline__ T weno(const T* s, T vel) {
   const bool pos = vel >= T(0);
@@ -120,10 +129,10 @@ __device__ __forceinline__ T weno(const T* s, T vel) {
     T q[r], b[r];
     sfor<r>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
-      T acc = Coef<T>::template gq<r, k, 0>() * d[k];
+      T acc = Coef<T>::template gqd<r, k, 0>() * d[k];
       sfor<r - 2>([&](auto ac) {
         constexpr int a = decltype(ac)::value + 1;
-        acc = fma(Coef<T>::template gq<r, k, a>(), d[k + a], acc);
+        acc = fma(Coef<T>::template gqd<r, k, a>(), d[k + a], acc);
       });
       q[k] = acc;
       T bb = T(0);
@@ -143,9 +152,9 @@ __device__ __forceinline__ T weno(const T* s, T vel) {
     sfor<r>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
       const T ratio = tau * rcp(b[k] + T(1e-8));
-      const T alpha = Coef<T>::template d<r, k>() * fma(ratio, ratio, T(1));
-      num = fma(alpha, q[k], num);
-      den += alpha;
+      const T a1 = fma(ratio, ratio, T(1));         // alpha_k / d_k
+      num = fma(a1, q[k], num);
+      den = fma(Coef<T>::template d<r, k>(), a1, den);
     });
     return fma(sgn, num * rcp(den), ref);
   }
@@ -233,6 +242,17 @@ struct TileGeom {
   static constexpr int NTHREADS = ((TX * TY + TX + TY) + 31) / 32 * 32;
 };
 
+// Staging depth of the z march: levels (u, v, tracers) and w faces are prefetched LAL and LAW
+// ahead of the level being computed, into LAL + 1 and LAW + 1 rotating plane slots.  The fused
+// eddy viscosity (FP32 Smagorinsky-Lilly) is computed two levels ahead and needs the levels on
+// either side of that, hence the deeper staging.
+template <typename T, int CL>
+struct MarchSlots {
+  static constexpr bool FUSE = sizeof(T) == 4 && CL == kClSmag;
+  static constexpr int LAL = FUSE ? 4 : 1, LAW = FUSE ? 4 : 2;
+  static constexpr int NSL = LAL + 1, NSW = LAW + 1;
+};
+
 // PREG: keep this thread's gather offsets in registers for the whole march (FP32 launches whose
 // register budget, 65536 / (threads x blocks per SM), is at least 128 a thread; below that, and in
 // the FP64 kernels, the extra registers spill and the offsets are formed per level instead).
@@ -251,6 +271,9 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
   constexpr int NT_ = TileGeom<TX, TY>::NTHREADS;
   constexpr int FXS = TY * (TX + 1);
   constexpr int FYS = (TY + 1) * TX;
+  typedef MarchSlots<T, CL> MS;
+  constexpr bool FUSE = MS::FUSE;
+  constexpr int LAL = MS::LAL, LAW = MS::LAW, NSL = MS::NSL, NSW = MS::NSW;
 
   const int Nx = a.Nx, Ny = a.Ny, Nz = a.Nz;
   constexpr int nt = NTR;
@@ -263,17 +286,19 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
-  T* sU = sm;                             // 2 slots
-  T* sV = sU + 2 * PLANE;                 // 2 slots
-  T* sW = sV + 2 * PLANE;                 // 3 slots (faces k, k+1, prefetch)
-  T* sC = sW + 3 * PLANE;                 // nt x 2 slots
-  T* sNu = sC + 2 * nt * PLANE;           // 4 slots (levels k-1, k, k+1, prefetch) if stress
+  T* sU = sm;                             // NSL slots (level k, prefetch; with FUSE levels k .. k+3, prefetch)
+  T* sV = sU + NSL * PLANE;               // NSL slots
+  T* sW = sV + NSL * PLANE;               // NSW slots (faces k, k+1, prefetch; with FUSE faces k .. k+3, prefetch)
+  T* sC = sW + NSW * PLANE;               // nt x NSL slots
+  T* sNu = sC + NSL * nt * PLANE;         // 4 slots (levels k-1, k, k+1, prefetch or, with FUSE, computed) if stress
   T* sK = sNu + (stress ? 4 : 0) * PLANE; // nt x 3 slots if amd
   T* FX = sK + (amd ? 3 * nt : 0) * PLANE;
   T* FY = FX + nf * FXS;
   T* PHs = FY + nf * FYS;                 // hydrostatic pressure anomaly, [TY+1][TX+1] (offset -1)
   int* gi_tab = reinterpret_cast<int*>(PHs + (TY + 1) * (TX + 1));
   int* gj_tab = gi_tab + PW;
+  // with FUSE, per level l <= Nz: (C_s Delta_l)^2, 1/dz_c[l], 1/(4 dz_f[l]) (0 at the walls), unused
+  T* sLev = reinterpret_cast<T*>(gj_tab + PH);
 
   const int tid = threadIdx.x;
   const int i0 = bid.x * TX, j0 = bid.y * TY;
@@ -321,16 +346,17 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
       }
     }
   };
-  auto load_level = [&](int k) {  // u, v, tracers at level k (slot k&1)
+  auto load_level = [&](int k) {  // u, v, tracers at level k (slot k % NSL)
     if (k >= Nz) return;
-    load_plane(sU + (k & 1) * PLANE, a.cur.u, k);
-    load_plane(sV + (k & 1) * PLANE, a.cur.v, k);
-    for (int n = 0; n < nt; ++n) load_plane(sC + (2 * n + (k & 1)) * PLANE, a.cur.c[n], k);
+    const int sl = k % NSL;
+    load_plane(sU + sl * PLANE, a.cur.u, k);
+    load_plane(sV + sl * PLANE, a.cur.v, k);
+    for (int n = 0; n < nt; ++n) load_plane(sC + (n * NSL + sl) * PLANE, a.cur.c[n], k);
   };
-  auto load_wface = [&](int f) { if (f <= Nz) load_plane(sW + (f % 3) * PLANE, a.cur.w, f); };
+  auto load_wface = [&](int f) { if (f <= Nz) load_plane(sW + (f % NSW) * PLANE, a.cur.w, f); };
   auto load_diff = [&](int l) {
     if (l < 0 || l >= Nz) return;
-    if (stress) load_plane(sNu + (l & 3) * PLANE, a.nu, l);
+    if (stress && !FUSE) load_plane(sNu + (l & 3) * PLANE, a.nu, l);
     if (amd) for (int n = 0; n < nt; ++n) load_plane(sK + (3 * n + l % 3) * PLANE, a.kap[n], l);
   };
 
@@ -347,6 +373,7 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
   auto cref_at = [&](int t, int level) -> T { return a.cref[t] ? __ldg(a.cref[t] + level) : T(0); };
   auto ld_w = [&](int face) -> T { return (face >= 0 && face <= Nz) ? __ldg(a.cur.w + (size_t)face * plane + col) : T(0); };
 
+
   // register rings: level (or face) k+1-R+n at index n
   T ru[2 * R], rv[2 * R], rw[2 * R], rc[NTR][2 * R];
 #pragma unroll
@@ -360,14 +387,131 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
 #pragma unroll
     for (int n = 0; n < 2 * R; ++n) rc[t][n] = ld_tr(t, 1 - R + n);
 
-  load_level(0);
-  load_wface(0);
-  load_wface(1);
+  // Smagorinsky-Lilly eddy viscosity (Sec. 3.1.1 closure equation, with Lilly's stratification
+  // factor) of level L, from the staged planes of levels L-1 .. L+1 and w faces L, L+1:
+  //   nu_e = (C_s Delta)^2 sqrt(max(|S|^2 - C_b N^2 / Pr, 0)),  |S|^2 = 2 S_ij S_ij,
+  //   Delta = (dx dy dz_L)^(1/3); each off-diagonal velocity gradient is the mean of its four edge
+  //   differences (wall edges 0), N^2 the mean of the two face gradients of b (wall faces 0).
+  // The mean of four edge differences telescopes to half-sums of centred differences.  A main
+  // thread computes its own cell, taking the point's own column (u, v, w, tracers at the levels
+  // L-1 .. L+1) from its register rings; the ghost warps compute the ring of cells around the tile
+  // from the planes, with the tracers' full values (stored anomaly + reference profile, the same
+  // rounding as the rings).  Multiply-adds are explicit (never left to contraction), so that every
+  // thread and every tile variant computes the same bits for the same point.
+  struct NuCol { T u0, um, up, v0, vm, vp, w0, w1, c0, cm, cp, d0, dm, dp; };
+  auto nu_point = [&](int L, int e, const NuCol& o) -> T {
+    T nu = T(0);
+    if constexpr (FUSE) {
+      const bool lo = L >= 1, hi = L + 1 < Nz;
+      const int s0 = L % NSL;
+      const T* U0 = sU + s0 * PLANE; const T* V0 = sV + s0 * PLANE;
+      const T* W0 = sW + (L % NSW) * PLANE; const T* W1 = sW + ((L + 1) % NSW) * PLANE;
+      const T* Um = sU + ((L + NSL - 1) % NSL) * PLANE; const T* Up = sU + ((L + 1) % NSL) * PLANE;
+      const T* Vm = sV + ((L + NSL - 1) % NSL) * PLANE; const T* Vp = sV + ((L + 1) % NSL) * PLANE;
+      const T* lc = sLev + 4 * L;                  // (C_s Delta)^2, 1/dz_c, 1/(4 dz_f) of faces L, L+1
+      const T CD2 = lc[0], rdzc = lc[1], rzl4 = lo ? lc[2] : T(0), rzh4 = hi ? lc[4 + 2] : T(0);
+      const T qx = T(0.25) * a.rdx, qy = T(0.25) * a.rdy;
+      const T u1 = U0[e + 1], v1 = V0[e + PW];
+      const T ux = (u1 - o.u0) * a.rdx, vy = (v1 - o.v0) * a.rdy, wz = (o.w1 - o.w0) * rdzc;
+      const T uy = __fmul_rn(qy, (U0[e + PW] - U0[e - PW]) + (U0[e + 1 + PW] - U0[e + 1 - PW]));
+      const T vx = __fmul_rn(qx, (V0[e + 1] - V0[e - 1]) + (V0[e + 1 + PW] - V0[e - 1 + PW]));
+      const T wx = __fmul_rn(qx, (W0[e + 1] - W0[e - 1]) + (W1[e + 1] - W1[e - 1]));
+      const T wy = __fmul_rn(qy, (W0[e + PW] - W0[e - PW]) + (W1[e + PW] - W1[e - PW]));
+      const T su = o.u0 + u1, sv = o.v0 + v1;
+      const T ul = lo ? su - (o.um + Um[e + 1]) : T(0), uh = hi ? (o.up + Up[e + 1]) - su : T(0);
+      const T vl = lo ? sv - (o.vm + Vm[e + PW]) : T(0), vh = hi ? (o.vp + Vp[e + PW]) - sv : T(0);
+      const T uz = __fmaf_rn(rzl4, ul, __fmul_rn(rzh4, uh));
+      const T vz = __fmaf_rn(rzl4, vl, __fmul_rn(rzh4, vh));
+      T bl = lo ? o.c0 - o.cm : T(0), bh = hi ? o.cp - o.c0 : T(0);
+      if (a.eos == OCN_EOS_LINEAR_TS) {
+        const T dl = lo ? o.d0 - o.dm : T(0), dh = hi ? o.dp - o.d0 : T(0);
+        bl = __fmaf_rn(a.g_alpha, bl, -__fmul_rn(a.g_beta, dl));
+        bh = __fmaf_rn(a.g_alpha, bh, -__fmul_rn(a.g_beta, dh));
+      }
+      // N^2 = (bl rdzf_L + bh rdzf_{L+1}) / 2, with the quarter-scaled reciprocals doubled
+      const T N2 = __fmul_rn(T(2), __fmaf_rn(rzl4, bl, __fmul_rn(rzh4, bh)));
+      const T a12 = uy + vx, a13 = uz + wx, a23 = vz + wy;       // 2 S_12, 2 S_13, 2 S_23
+      const T dg = __fmaf_rn(wz, wz, __fmaf_rn(vy, vy, __fmul_rn(ux, ux)));
+      const T od = __fmaf_rn(a23, a23, __fmaf_rn(a13, a13, __fmul_rn(a12, a12)));
+      const T SS = __fmaf_rn(T(2), dg, od);                          // 2 S_ij S_ij
+      const T ex = __fmaf_rn(-a.Cb * a.inv_Pr, N2, SS);
+      float r;
+      asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(ex));
+      nu = (SS > T(0) && ex > T(0)) ? CD2 * r : T(0);
+    }
+    return nu;
+  };
+  // nu_e of level L at this thread's share of the tile and the one-cell ring around it: a main
+  // thread its own cell (written to the arena too when it is inside the grid), its column from the
+  // ring entries RI-1, RI, RI+1 (levels L-1, L, L+1; w faces L, L+1 at RI, RI+1); the ghost threads
+  // share the ring's 2 (TX + 2) + 2 TY points from index r0 in steps of nr.
+  auto smag_nu = [&](int L, auto RIc, int r0, int nr) {
+    if constexpr (FUSE) {
+      constexpr int RI = decltype(RIc)::value;
+      constexpr int t1 = NTR > 1 ? 1 : 0;
+      T* nuS = sNu + (L & 3) * PLANE;
+      if (role == 0) {
+        const int e = (ly + H) * PW + (lx + H);
+        NuCol o;
+        o.u0 = ru[RI]; o.um = ru[RI - 1]; o.up = ru[RI + 1];
+        o.v0 = rv[RI]; o.vm = rv[RI - 1]; o.vp = rv[RI + 1];
+        o.w0 = rw[RI]; o.w1 = rw[RI + 1];
+        o.c0 = rc[0][RI]; o.cm = rc[0][RI - 1]; o.cp = rc[0][RI + 1];
+        o.d0 = rc[t1][RI]; o.dm = rc[t1][RI - 1]; o.dp = rc[t1][RI + 1];
+        const T nu = nu_point(L, e, o);
+        nuS[e] = nu;
+        if (a.nu_out && active) a.nu_out[(size_t)L * plane + col] = nu;
+      } else {
+        const int s0 = L % NSL, sm = (L + NSL - 1) % NSL, sp = (L + 1) % NSL;
+        const T r00 = cref_at(0, L), r0m = L >= 1 ? cref_at(0, L - 1) : T(0), r0p = L + 1 < Nz ? cref_at(0, L + 1) : T(0);
+        const T r10 = cref_at(t1, L), r1m = L >= 1 ? cref_at(t1, L - 1) : T(0), r1p = L + 1 < Nz ? cref_at(t1, L + 1) : T(0);
+        const T* W0 = sW + (L % NSW) * PLANE; const T* W1 = sW + ((L + 1) % NSW) * PLANE;
+        constexpr int NR = 2 * (TX + 2) + 2 * TY;
+#pragma unroll 1
+        for (int q = r0; q < NR; q += nr) {
+          int qx, qy;
+          if (q < TX + 2) { qx = q - 1; qy = -1; }
+          else if (q < 2 * (TX + 2)) { qx = q - (TX + 2) - 1; qy = TY; }
+          else if (q < 2 * (TX + 2) + TY) { qx = -1; qy = q - 2 * (TX + 2); }
+          else { qx = TX; qy = q - 2 * (TX + 2) - TY; }
+          const int e = (qy + H) * PW + (qx + H);
+          NuCol o;
+          o.u0 = sU[s0 * PLANE + e]; o.um = sU[sm * PLANE + e]; o.up = sU[sp * PLANE + e];
+          o.v0 = sV[s0 * PLANE + e]; o.vm = sV[sm * PLANE + e]; o.vp = sV[sp * PLANE + e];
+          o.w0 = W0[e]; o.w1 = W1[e];
+          o.c0 = sC[s0 * PLANE + e] + r00; o.cm = sC[sm * PLANE + e] + r0m; o.cp = sC[sp * PLANE + e] + r0p;
+          o.d0 = sC[(t1 * NSL + s0) * PLANE + e] + r10; o.dm = sC[(t1 * NSL + sm) * PLANE + e] + r1m;
+          o.dp = sC[(t1 * NSL + sp) * PLANE + e] + r1p;
+          nuS[e] = nu_point(L, e, o);
+        }
+      }
+    }
+  };
+
+  for (int l = 0; l < LAL; ++l) load_level(l);
+  for (int f = 0; f < LAW; ++f) load_wface(f);
   load_diff(0);
   load_diff(1);
   cp_async_commit();
+  if constexpr (FUSE) {
+    for (int l = tid; l <= Nz; l += NT_) {
+      T cd2 = T(0), rz = T(0), rf = T(0);
+      if (l < Nz) {
+        const T cd = a.Cs * cbrtf(a.dx * a.dy * __ldg(a.dzc + l));
+        cd2 = cd * cd;
+        rz = __ldg(a.rdzc + l);
+      }
+      if (l >= 1 && l < Nz) rf = T(0.25) * __ldg(a.rdzf + l);
+      sLev[4 * l] = cd2; sLev[4 * l + 1] = rz; sLev[4 * l + 2] = rf; sLev[4 * l + 3] = T(0);
+    }
+  }
   cp_async_wait_all();
   __syncthreads();
+  if constexpr (FUSE) {             // nu_e of the first two levels (rings hold levels 1-R .. R)
+    smag_nu(0, std::integral_constant<int, R - 1>(), tid - TX * TY, NT_ - TX * TY);
+    if (1 < Nz) smag_nu(1, std::integral_constant<int, R>(), tid - TX * TY, NT_ - TX * TY);
+    __syncthreads();
+  }
 
   // carried z fluxes through the bottom face of the current control volumes
   T fz_u = a.bot[0], fz_v = a.bot[1], fz_w = T(0);
@@ -403,11 +547,18 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
   const int k0 = (seg == 0) ? 0 : (seg == 1 ? kb : ke);
   const int k1 = (seg == 0) ? kb : (seg == 1 ? ke : Nz);
   for (int k = k0; k < k1; ++k) {
-    // ---- prefetch the next level's planes
-    load_level(k + 1);
-    load_wface(k + 2);
+    // ---- prefetch the planes LAL (levels) and LAW (faces) ahead
+    load_level(k + LAL);
+    load_wface(k + LAW);
     load_diff(k + 2);
     cp_async_commit();
+    const int sk = k % NSL;                      // slot of level k
+    // nu_e two levels ahead, for the fluxes of levels k+1 and k+2 (each main thread its own cell,
+    // the ghost warps the ring around the tile); slot (k+2) & 3 held nu_e of level k-2, which no
+    // thread reads at level k
+    if constexpr (FUSE) {
+      if (k + 2 < Nz) smag_nu(k + 2, std::integral_constant<int, R + 1>(), tid - TX * TY, NT_ - TX * TY);
+    }
     // next ring entries (level k+1+R)
     T nu_ = ld_c(a.cur.u, k + 1 + R), nv_ = ld_c(a.cur.v, k + 1 + R), nw_ = ld_w(k + 1 + R);
     T nc_[NTR];
@@ -427,10 +578,10 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
 #pragma unroll
     for (int t = 0; t < NTR; ++t) crk[t] = cref_at(t, k);
 
-    const T* pU = sU + (k & 1) * PLANE;
-    const T* pV = sV + (k & 1) * PLANE;
-    const T* pW0 = sW + (k % 3) * PLANE;        // face k
-    const T* pW1 = sW + ((k + 1) % 3) * PLANE;  // face k+1
+    const T* pU = sU + sk * PLANE;
+    const T* pV = sV + sk * PLANE;
+    const T* pW0 = sW + (k % NSW) * PLANE;        // face k
+    const T* pW1 = sW + ((k + 1) % NSW) * PLANE;  // face k+1
     const T* pNm = sNu + ((k + 3) & 3) * PLANE; // level k-1
     const T* pN0 = sNu + (k & 3) * PLANE;       // level k
     const T* pN1 = sNu + ((k + 1) & 3) * PLANE; // level k+1
@@ -495,7 +646,7 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
       // tracers at face i: U = u, advected WENO_x(c)
 #pragma unroll
       for (int t = 0; t < NTR; ++t) {
-        const T* pC = sC + (2 * t + (k & 1)) * PLANE;
+        const T* pC = sC + (t * NSL + sk) * PLANE;
         T sc[2 * R];
 #pragma unroll
         for (int n = 0; n < 2 * R; ++n) sc[n] = pC[rowc - R + n];
@@ -564,7 +715,7 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
       }
 #pragma unroll
       for (int t = 0; t < NTR; ++t) {
-        const T* pC = sC + (2 * t + (k & 1)) * PLANE;
+        const T* pC = sC + (t * NSL + sk) * PLANE;
         T sc[2 * R];
 #pragma unroll
         for (int n = 0; n < 2 * R; ++n) sc[n] = pC[rowc + (n - R) * PW];
@@ -647,8 +798,8 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
     }
 
     if (split && hidx >= 0) {
-      const T* pC0 = sC + (k & 1) * PLANE;
-      const T* pC1 = sC + (2 * (NTR > 1 ? 1 : 0) + (k & 1)) * PLANE;
+      const T* pC0 = sC + sk * PLANE;
+      const T* pC1 = sC + ((NTR > 1 ? 1 : 0) * NSL + sk) * PLANE;
       constexpr int t1 = NTR > 1 ? 1 : 0;
       const T bref = buoyancy(a, __ldg(a.cur.c[0] + (size_t)k * plane) + crk[0], __ldg(a.cur.c[t1] + (size_t)k * plane) + crk[t1]);
       const T bhere = (role == 0) ? buoyancy(a, rc[0][R - 1], rc[t1][R - 1])
@@ -719,7 +870,7 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
         T G = -(FXu[(3 + t) * FXS + 1] - FXu[(3 + t) * FXS]) * rdx - (FYu[(3 + t) * FYS + TX] - FYu[(3 + t) * FYS]) * rdy
               - (nz_c[t] - fz_c[t]) * rdzc_k;
         if (a.mode == 0) {
-          T upd = fma(a.dt_gamma, G, sC[(2 * t + (k & 1)) * PLANE + rowc]);   // the stored anomaly
+          T upd = fma(a.dt_gamma, G, sC[(t * NSL + sk) * PLANE + rowc]);   // the stored anomaly
           if (a.dt_zeta != T(0)) upd = fma(-a.dt_zeta, gp_c[t], upd);
           a.nxt.c[t][id] = upd;
         }
@@ -771,17 +922,19 @@ const void* tendency_batched_kernel();
   X(R, NTR, 32, 8, 1, CL) X(R, NTR, 32, 8, 2, CL) X(R, NTR, 32, 16, 1, CL) X(R, NTR, 32, 4, 3, CL) \
   X(R, NTR, 32, 14, 1, CL) X(R, NTR, 32, 12, 1, CL) X(R, NTR, 16, 16, 2, CL)
 
-template <typename T, int R, int TX, int TY>
+template <typename T, int R, int TX, int TY, int CL>
 static size_t tendency_smem(const TendencyArgs<T>& a) {
   constexpr int H = R;
   constexpr int PLANE = (TX + 2 * H) * (TY + 2 * H);
+  typedef MarchSlots<T, CL> MS;
   const bool stress = (a.closure == OCN_CLOSURE_SMAGORINSKY || a.closure == OCN_CLOSURE_AMD);
   const bool amd = (a.closure == OCN_CLOSURE_AMD);
   const int nf = 3 + a.nt;
-  size_t planes = 2 + 2 + 3 + 2 * a.nt + (stress ? 4 : 0) + (amd ? 3 * a.nt : 0);
+  size_t planes = MS::NSL * (2 + a.nt) + MS::NSW + (stress ? 4 : 0) + (amd ? 3 * a.nt : 0);
   size_t bytes = sizeof(T) * (planes * PLANE + (size_t)nf * (TY * (TX + 1) + (TY + 1) * TX));
   bytes += sizeof(T) * (TY + 1) * (TX + 1);
   bytes += sizeof(int) * ((TX + 2 * H) + (TY + 2 * H));
+  if (MS::FUSE) bytes += sizeof(T) * 4 * ((size_t)a.Nz + 1);
   return bytes;
 }
 
@@ -790,7 +943,7 @@ static size_t tendency_smem(const TendencyArgs<T>& a) {
 template <typename T, int R, int NTR, int TX, int TY, int MINB, int CL>
 cudaError_t launch_tendency_variant(const TendencyArgs<T>& a, cudaStream_t s) {
   auto kern = k_tendency<T, R, NTR, TX, TY, MINB, CL>;
-  size_t smem = tendency_smem<T, R, TX, TY>(a);
+  size_t smem = tendency_smem<T, R, TX, TY, CL>(a);
   cudaError_t e = raise_smem_limit(kern, smem);
   if (e != cudaSuccess) return e;
   if (MINB > 1) {

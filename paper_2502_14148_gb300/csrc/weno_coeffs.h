@@ -175,6 +175,12 @@ template <typename T, int r, int s, int a>
 struct WenoGq {
   static constexpr T value = (T)wc::kTables.gq[r][s][a];
 };
+// substencil coefficients times the substencil's linear weight d_s (the weighted sum of the
+// substencil values then needs no separate multiplication by d_s)
+template <typename T, int r, int s, int a>
+struct WenoGqD {
+  static constexpr T value = (T)(wc::kTables.gq[r][s][a] * wc::kTables.d[r][s]);
+};
 template <typename T, int r, int s, int a, int b>
 struct WenoDb {
   static constexpr T value = (T)wc::kTables.dbeta[r][s][a][b];

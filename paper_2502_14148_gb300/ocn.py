@@ -48,7 +48,7 @@ EXPORTS = ["ocn_abi_version", "ocn_last_error", "ocn_grid_create", "ocn_grid_des
            "ocn_mlp_get_params", "ocn_mlp_forward", "ocn_mlp_gradients", "ocn_mlp_adam", "ocn_mlp_train_step",
            "ocn_gemm_bf16", "ocn_set_column_closure", "ocn_closure_features", "ocn_column_fluxes",
            "ocn_coarse_grain", "ocn_set_time_stepper", "ocn_set_vertical_diffusivity", "ocn_gemm_timeout_test",
-           "ocn_fp32_fma_peak"]
+           "ocn_fp32_fma_peak", "ocn_set_column_closure_mode"]
 OCN_OPT_ENSEMBLE_MODE, OCN_ENSEMBLE_CONCURRENT, OCN_ENSEMBLE_SEQUENTIAL, OCN_ENSEMBLE_BATCHED = 5, 0, 1, 2
 OCN_OPT_ENSEMBLE_BRANCHES = 6
 ENSEMBLE_MODES = {"concurrent": OCN_ENSEMBLE_CONCURRENT, "sequential": OCN_ENSEMBLE_SEQUENTIAL,
@@ -143,6 +143,7 @@ def lib(path: str = LIB_PATH):
     L.ocn_mlp_adam.argtypes = [vp, vp, C.c_double, C.c_double, C.c_double, C.c_double]
     L.ocn_mlp_train_step.argtypes = [vp, vp, vp, vp, C.c_int, C.c_double, dp]
     L.ocn_set_column_closure.argtypes = [vp, vp, C.POINTER(ColumnClosureDesc)]
+    L.ocn_set_column_closure_mode.argtypes = [vp, C.c_int]
     L.ocn_set_time_stepper.argtypes = [vp, C.c_int, C.c_double]
     L.ocn_set_vertical_diffusivity.argtypes = [vp, dp, dp, C.c_int]
     L.ocn_closure_features.argtypes = [vp, C.c_double, vp]
@@ -421,9 +422,15 @@ class Model:
                 "Fb": F[:Nz + 1], "Fu": F[Nz + 1:2 * (Nz + 1)], "Fv": F[2 * (Nz + 1):]}
 
     # ------------------------------------------------------------ learned column closure
-    def set_column_closure(self, mlp, mu=None, sigma=None, out_scale=(1.0, 1.0, 1.0), N2_background=0.0):
+    def set_column_closure(self, mlp, mu=None, sigma=None, out_scale=(1.0, 1.0, 1.0), N2_background=0.0,
+                           mode=None):
         """Attach a trained network (an MLP of shape 32-128-128-128-16) as the learned column closure;
-        mlp=None removes it (the model's own closure remains)."""
+        mlp=None removes it (the model's own closure remains).  mode "flux" (explicit face fluxes)
+        or "diffusivity" (outputs 0, 1 are eddy diffusivities applied by the implicit column solve);
+        None keeps the current mode."""
+        if mode is not None:
+            _check(lib().ocn_set_column_closure_mode(self._h, {"flux": 0, "diffusivity": 1}[mode]),
+                   "ocn_set_column_closure_mode")
         if mlp is None:
             _check(lib().ocn_set_column_closure(self._h, None, None), "ocn_set_column_closure")
             self._colc = None

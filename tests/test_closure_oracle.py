@@ -207,3 +207,59 @@ def test_closure_fluxes_linear_network_and_walls():
         expect = scale[q] * y[:, q].reshape(5, 2, 3)
         expect[0] = 0; expect[-1] = 0
         np.testing.assert_allclose(F[q], expect, rtol=1e-14)
+
+
+def test_face_diffusivity_hook_equals_implicit_profiles(oracle_mod):
+    """The diffusivity hook's column means become the implicit profiles of every stage: per-column
+    diffusivities kappa_k (1 + r_ij), nu_k (1 - r_ij) with sum_ij r_ij = 0 step exactly like a model
+    given the profiles kappa, nu directly (pinned in tests/test_timestep_oracle.py), for RK3 and
+    QAB2; the hook sees each stage's initial state (three calls per RK3 step, the first with the
+    state the step starts from)."""
+    Nz, Ny, Nx = 10, 6, 8
+    zf = inputs.tanh_faces(Nz, 20.0, 1.5)
+    kap = 0.2 * np.exp(zf / 8.0); kap[0] = kap[-1] = 0.0
+    nu = 0.1 * np.exp(zf / 5.0); nu[0] = nu[-1] = 0.0
+    r = np.random.default_rng(8).standard_normal((Ny, Nx)) * 0.3
+    r -= r.mean()
+    K = np.zeros((3, Nz + 1, Ny, Nx))
+    K[0] = kap[:, None, None] * (1.0 + r)
+    K[1] = nu[:, None, None] * (1.0 - r)
+    for stepper in ("rk3", "qab2"):
+        m, p = _model(oracle_mod, closure="amd", timestepper=stepper)
+        _random_divfree(m, p)
+        st = {n: m.get(n) for n in ("u", "v", "w", "b")}
+        seen = []
+
+        def hook(model):
+            seen.append(model.get("b").copy())
+            return K
+        m.set_face_diffusivity(hook)
+        m.time_step(7.0, 2)
+        ref, _ = _model(oracle_mod, closure="amd", timestepper=stepper, kappa_z=kap, nu_z=nu, vertical_implicit=True)
+        ref.set(**st)
+        ref.time_step(7.0, 2)
+        for n in ("u", "v", "w", "b"):
+            a, b = m.get(n), ref.get(n)
+            assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max(), (stepper, n)
+        assert len(seen) == (6 if stepper == "rk3" else 2)
+        assert np.array_equal(seen[0], st["b"])
+        # the diffusion acted: the run differs from one without it
+        plain, _ = _model(oracle_mod, closure="amd", timestepper=stepper)
+        plain.set(**st)
+        plain.time_step(7.0, 2)
+        assert np.abs(plain.get("b") - m.get("b")).max() > 1e-6 * np.abs(m.get("b")).max()
+
+
+def test_closure_diffusivities_relu_and_walls():
+    rng = np.random.default_rng(10)
+    W = rng.standard_normal((16, 32)); b = rng.standard_normal(16)
+    X = rng.standard_normal((5 * 2 * 3, 32))
+    mu, sigma = rng.standard_normal(32), 1.0 + rng.random(32)
+    scale = np.array([2.0, 3.0, 5.0])
+    K = omlp.closure_diffusivities([(W, b)], X, mu, sigma, scale, (5, 2, 3))
+    y = ((X - mu) / sigma) @ W.T + b
+    for q in range(2):
+        expect = np.maximum(scale[q] * y[:, q].reshape(5, 2, 3), 0.0)
+        expect[0] = 0; expect[-1] = 0
+        np.testing.assert_allclose(K[q], expect, rtol=1e-14)
+    assert (K[:2] >= 0).all() and (K[:2] == 0).any() and (K[2] == 0).all()

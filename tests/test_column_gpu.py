@@ -198,6 +198,95 @@ def test_coupled_steps_match_oracle(oracle_mod):
         assert err <= bound, (name, err, bound, effect)
 
 
+def test_coupled_steps_diffusivity_mode_match_oracle(oracle_mod):
+    """The closure in diffusivity form: per stage, the column means of max(0, scale y) at each face
+    become the implicit vertical diffusivity profiles (kappa: tracers, nu: momentum).  The oracle
+    does the same with its FP64 network through its diffusivity hook."""
+    _need_gpu()
+    p = _params(32, 24, 20)
+    o, f = _state(p, oracle_mod)
+    X = o.closure_features(p["N2"])
+    net, params, mu, sigma = _network(X)
+    scale = np.array([0.05, 0.02, 0.0])                 # m^2/s per unit network output
+    shape = (p["Nz"] + 1, p["Ny"], p["Nx"])
+    dt, n = 5.0, 3
+    o_plain = oracle_mod.OracleModel(p)
+    o_plain.set(**f)
+    o_plain.time_step(dt, n)
+    o.set_face_diffusivity(lambda mod: omlp.closure_diffusivities(params, mod.closure_features(p["N2"]), mu, sigma,
+                                                                  scale, shape))
+    o.time_step(dt, n)
+    m = _gpu(p, f)
+    m.set_column_closure(net, mu, sigma, scale, p["N2"], mode="diffusivity")
+    m.time_step(dt, n)
+    m.synchronize()
+    assert m.diagnostics()["status"] == "OK"
+    moved = 0
+    for name in ("u", "v", "w", "b"):
+        g = m.get_numpy(name).astype(np.float64)
+        ref, plain = o.get(name), o_plain.get(name)
+        effect = np.linalg.norm(ref - plain)
+        moved += effect > 1e-3 * np.linalg.norm(ref - np.mean(ref))
+        err = np.linalg.norm(g - ref)
+        bound = 1e-4 * np.linalg.norm(ref) + 4 * TOL_BF16 * effect
+        assert err <= bound, (name, err, bound, effect)
+    assert moved >= 2                                   # the closure changed the state measurably
+    # a tendency evaluation takes nothing from an implicit closure
+    G0 = _gpu(p, f).compute_tendencies()
+    m2 = _gpu(p, f)
+    m2.set_column_closure(net, mu, sigma, scale, p["N2"], mode="diffusivity")
+    G1 = m2.compute_tendencies()
+    for name in G0:
+        assert np.array_equal(G0[name].cpu().numpy(), G1[name].cpu().numpy()), name
+
+
+def test_diffusivity_mode_batched_ensemble_equals_single_models(oracle_mod):
+    torch = _need_gpu()
+    from paper_2502_14148_gb300 import ocn
+    ps = [_params(16, 16, 12, top_flux={"b": 1e-8}), _params(24, 24, 16, top_flux={"b": 5e-8}, f=0.0)]
+    states = [_state(p, oracle_mod, seed=11 + i)[1] for i, p in enumerate(ps)]
+    X = oracle_mod.OracleModel(ps[0])
+    X.set(**states[0])
+    net, params, mu, sigma = _network(X.closure_features(ps[0]["N2"]))
+    scale = (0.05, 0.02, 0.0)
+    ens = ocn.Ensemble(ps)
+    ens.set_mode("batched")
+    singles = []
+    for p, st, mem in zip(ps, states, ens.members):
+        mem.set(project=False, **st)
+        mem.set_column_closure(net, mu, sigma, scale, p["N2"], mode="diffusivity")
+        s_ = _gpu(p, st)
+        s_.set_column_closure(net, mu, sigma, scale, p["N2"], mode="diffusivity")
+        singles.append(s_)
+    ens.time_step(5.0, 3)
+    ens.synchronize()
+    for s_ in singles:
+        s_.time_step(5.0, 3)
+        s_.synchronize()
+    for mem, s_ in zip(ens.members, singles):
+        for name in ("u", "v", "w", "b"):
+            assert torch.equal(mem.get(name), s_.get(name)), name
+
+
+def test_diffusivity_mode_validation():
+    _need_gpu()
+    from paper_2502_14148_gb300 import ocn
+    p = _params(16, 16, 8)
+    m = ocn.Model(p)
+    net = ocn.MLP(inputs.MLP_SIZES, max_batch=256)
+    with pytest.raises(ocn.OcnError) as ei:
+        ocn._check(ocn.lib().ocn_set_column_closure_mode(m._h, 2), "ocn_set_column_closure_mode")
+    assert ei.value.status == -1
+    m.set_vertical_diffusivity(np.full(9, 1e-3), np.full(9, 1e-3), implicit=True)
+    with pytest.raises(ocn.OcnError) as ei:            # the model's own profiles come first
+        m.set_column_closure(net, mode="diffusivity")
+    assert ei.value.status == -8
+    q = inputs.config("les_512", Nx=16, Ny=16, Nz=8)       # not a buoyancy-tracer model
+    with pytest.raises(ocn.OcnError) as ei:
+        ocn.Model(q).set_column_closure(None, mode="diffusivity")
+    assert ei.value.status == -7
+
+
 def test_ensemble_members_with_closure_match_single_models(oracle_mod):
     torch = _need_gpu()
     from paper_2502_14148_gb300 import ocn

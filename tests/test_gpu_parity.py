@@ -133,6 +133,53 @@ def test_tendency_parity_edge_sizes(ocn, oracle_mod, dims):
             assert rel_max(G[name], O[name]) < 1e-11, (order, name)
 
 
+@pytest.mark.parametrize("dims", [(4, 4, 1), (4, 4, 2), (6, 4, 3), (12, 8, 5), (72, 36, 24)])
+@pytest.mark.parametrize("order", [5, 9])
+def test_tendency_parity_fp32_smagorinsky_edge_sizes(ocn, oracle_mod, dims, order):
+    """The FP32 Smagorinsky-Lilly kernels compute nu_e in their own z march (two levels ahead of
+    the fluxes, from planes staged four levels ahead): one to five levels, fewer levels than the
+    staging depth, tiles that wrap the periodic domain, ragged multi-tile grids."""
+    Nx, Ny, Nz = dims
+    case = dict(weno_order=order, closure="smagorinsky", tracers=["T", "S"], eos="linear_ts",
+                top_flux={"u": 1e-2, "T": 2e-3})
+    G, O, _ = _tendency_pair(ocn, oracle_mod, case, 32, Nx=Nx, Ny=Ny, Nz=Nz, Lx=float(Nx), Ly=float(Ny), Lz=float(Nz))
+    for name in O:
+        assert rel_max(G[name], O[name]) < 2e-5, (order, name)
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+@pytest.mark.parametrize("eos", ["linear_ts", "buoyancy_tracer"])
+def test_smagorinsky_nu_field_matches_oracle(ocn, oracle_mod, precision, eos):
+    """nu_e left in the arena by a tendency evaluation (computed inside the FP32 tendency kernel,
+    by the closure kernel in FP64) against the oracle's diffusivity at every cell of a stratified,
+    stretched, ragged grid."""
+    tracers = ["T", "S"] if eos == "linear_ts" else ["b"]
+    p = params(Nx=24, Ny=18, Nz=9, precision=precision, closure="smagorinsky", tracers=tracers, eos=eos, Cb=1.0,
+               Pr=0.7)
+    # velocity amplitudes that put about half of the cells past the stratification cut-off
+    st = inputs.random_state(p, seed=61, amp=0.01 if eos == "linear_ts" else 0.2)
+    zc = 0.5 * (p["z_faces"][1:] + p["z_faces"][:-1])
+    if eos == "linear_ts":
+        st["T"] = 20.0 + 0.3 * zc[:, None, None] + 0.005 * st["T"]
+        st["S"] = 35.0 + 0.001 * st["S"]
+    else:
+        st["b"] = 0.2 * zc[:, None, None] + 0.005 * st["b"]
+    st = rounded(st, precision)
+    g = ocn.Model(p)
+    g.set(project=False, **st)
+    g.compute_tendencies()
+    nu = g.get_numpy("nu_e").astype(np.float64)
+    o = oracle_mod.OracleModel(p)
+    o.set(**st)
+    ref = np.array([[[o.diffusivity_at(0, i, j, k) for i in range(p["Nx"])] for j in range(p["Ny"])]
+                    for k in range(p["Nz"])])
+    assert 0.3 < (ref > 0).mean() < 0.7                       # both sides of the stratification cut-off
+    # nu_e^2 = (C_s Delta)^4 max(|S|^2 - C_b N^2 / Pr, 0) is linear in the rounded quantities; nu_e itself
+    # has an infinite slope at the cut-off, where a rounding-level change of the argument moves it by
+    # the square root of the rounding unit
+    assert rel_max(nu ** 2, ref ** 2) < (1e-11 if precision == 64 else 1e-5)
+
+
 # ----------------------------------------------------------------------------- time stepping
 def _run_pair(ocn, oracle_mod, p, steps, seed=inputs.SEED):
     st = rounded(inputs.initial_state(p, seed=seed), p["precision"])
