@@ -649,9 +649,9 @@ cudaError_t launch_projection(const PoissonArgs<T>& a, cudaStream_t s, int* nlau
     k_div_fftx<T><<<(rows + LR - 1) / LR, 256, smx, s>>>(a, LR);
   hook.post(OCN_K_DIV_FFTX);
   ++n;
-  // kx columns per block: 8 (FP32) / 4 (FP64), widened for short y lines so that a block holds
-  // about 2048 (FP32) / 1024 (FP64) values, but not beyond the spectrum's width
-  int CW = (sizeof(T) == 4) ? 8 : 4;
+  // kx columns per block: four (32 bytes of each row in FP32, a whole sector), widened for short y
+  // lines so that a block holds about 2048 (FP32) / 1024 (FP64) values, not beyond the spectrum
+  int CW = 4;
   while (CW * a.Ny < (sizeof(T) == 4 ? 2048 : 1024) && CW < a.Mx + 1) CW *= 2;
   const size_t smy = (2 * spad_size<C>((size_t)a.Ny * CW) + a.Ny) * sizeof(C);
   e = raise_smem_limit(k_fft_y<T>, smy);

@@ -12,6 +12,7 @@ boundary fluxes).
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import json
 import os
@@ -158,6 +159,26 @@ def lib(path: str = LIB_PATH):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
+
+
+@contextlib.contextmanager
+def _stream_scope(device, stream):
+    """Run the enclosed launches on the library's stream, ordered after everything the caller has
+    already queued on its current stream (inputs it produced are ready), and order the caller's
+    later work after them (outputs are ready for it)."""
+    import torch
+    caller = torch.cuda.current_stream(device)
+    stream.wait_stream(caller)
+    with torch.cuda.device(device), torch.cuda.stream(stream):
+        yield caller
+    caller.wait_stream(stream)
+
+
+def _hand_over(t, caller):
+    """A tensor made on the library's stream and returned: its memory is not reused before the
+    caller's stream is done with it."""
+    t.record_stream(caller)
+    return t
 
 
 def _check(st: int, where: str):
@@ -337,7 +358,7 @@ class Model:
     def set(self, project: bool = True, **fields):
         """set!: copy fields in (numpy or torch); projects the velocity unless project=False."""
         import torch
-        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+        with _stream_scope(self.device, self.stream) as caller:
             for name, arr in fields.items():
                 t = torch.as_tensor(arr).to(device=self.device, dtype=self.dtype).contiguous()
                 assert tuple(t.shape) == self.shape(name), (name, tuple(t.shape))
@@ -350,12 +371,12 @@ class Model:
     def get(self, name: str):
         """A device tensor copy of a field."""
         import torch
-        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+        with _stream_scope(self.device, self.stream) as caller:
             out = torch.empty(self.shape(name), dtype=self.dtype, device=self.device)
             _check(lib().ocn_get_field(self._h, self.fid(name), C.c_void_p(out.data_ptr()),
                                        out.numel() * out.element_size(), 1), "ocn_get_field")
         self.stream.synchronize()
-        return out
+        return _hand_over(out, caller)
 
     def get_numpy(self, name: str) -> np.ndarray:
         return self.get(name).cpu().numpy()
@@ -449,23 +470,23 @@ class Model:
     def closure_features(self, N2_background: float):
         """Raw column features of every w-face, a device tensor [(Nz+1)*Ny*Nx][32]."""
         import torch
-        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+        with _stream_scope(self.device, self.stream) as caller:
             X = torch.empty(((self.Nz + 1) * self.Ny * self.Nx, COLUMN_FEATURES), dtype=torch.float32,
                             device=self.device)
             _check(lib().ocn_closure_features(self._h, float(N2_background), C.c_void_p(X.data_ptr())),
                    "ocn_closure_features")
         self.stream.synchronize()
-        return X
+        return _hand_over(X, caller)
 
     def column_fluxes(self, learned: bool = False):
         """Face fluxes of b, ubar, vbar [3][Nz+1][Ny][Nx]: the model's closure (default) or the learned one."""
         import torch
-        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+        with _stream_scope(self.device, self.stream) as caller:
             F = torch.empty((3, self.Nz + 1, self.Ny, self.Nx), dtype=torch.float32, device=self.device)
             _check(lib().ocn_column_fluxes(self._h, 1 if learned else 0, C.c_void_p(F.data_ptr())),
                    "ocn_column_fluxes")
         self.stream.synchronize()
-        return F
+        return _hand_over(F, caller)
 
     def coarse_grain(self, cx: int, cy: int) -> dict:
         """Box filter onto cx x cy columns: coarse u, v, w, b and subfilter fluxes tau [3][Nz+1][cy][cx]
@@ -473,11 +494,12 @@ class Model:
         import torch
         Nz = self.Nz
         n = cx * cy
-        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+        with _stream_scope(self.device, self.stream) as caller:
             out = torch.empty(n * (7 * Nz + 4), dtype=torch.float64, device=self.device)
             _check(lib().ocn_coarse_grain(self._h, int(cx), int(cy), C.c_void_p(out.data_ptr()), out.numel()),
                    "ocn_coarse_grain")
         self.stream.synchronize()
+        _hand_over(out, caller)
         res, o = {}, 0
         for name, levels in (("u", Nz), ("v", Nz), ("w", Nz + 1), ("b", Nz)):
             res[name] = out[o:o + levels * n].view(levels, cy, cx); o += levels * n
@@ -699,29 +721,29 @@ class MLP:
 
     def forward(self, X):
         import torch
-        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+        with _stream_scope(self.device, self.stream) as caller:
             X = self._dev(X)
             Y = torch.empty((X.shape[0], self.sizes[-1]), dtype=torch.float32, device=self.device)
             _check(lib().ocn_mlp_forward(self._h, C.c_void_p(X.data_ptr()), X.shape[0], C.c_void_p(Y.data_ptr())),
                    "ocn_mlp_forward")
         self.stream.synchronize()
-        return Y
+        return _hand_over(Y, caller)
 
     def gradients(self, X, T, mask):
         """(loss, flat FP32 gradient tensor) of the masked mean-square loss."""
         import torch
-        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+        with _stream_scope(self.device, self.stream) as caller:
             X, T, m = self._dev(X), self._dev(T), self._dev(mask)
             g = torch.empty(self.nparams, dtype=torch.float32, device=self.device)
             loss = C.c_double()
             _check(lib().ocn_mlp_gradients(self._h, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()),
                                            C.c_void_p(m.data_ptr()), X.shape[0], C.c_void_p(g.data_ptr()),
                                            C.byref(loss)), "ocn_mlp_gradients")
-        return loss.value, g
+        return loss.value, _hand_over(g, caller)
 
     def adam(self, grads, lr, beta1=0.9, beta2=0.999, eps=1e-8):
         import torch
-        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+        with _stream_scope(self.device, self.stream) as caller:
             g = self._dev(grads)
             _check(lib().ocn_mlp_adam(self._h, C.c_void_p(g.data_ptr()), float(lr), float(beta1), float(beta2),
                                       float(eps)), "ocn_mlp_adam")
@@ -730,7 +752,7 @@ class MLP:
     def train_step(self, X, T, mask, lr) -> float:
         """One Adam step on (X, T) (device tensors or arrays); returns the loss before the step."""
         import torch
-        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+        with _stream_scope(self.device, self.stream) as caller:
             X, T, m = self._dev(X), self._dev(T), self._dev(mask)
             loss = C.c_double()
             _check(lib().ocn_mlp_train_step(self._h, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()),
