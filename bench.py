@@ -333,8 +333,9 @@ def run_ours(args, world, rank, local):
 
     # ---- e2e: through the C ABI with pinned host buffers, copies inside the timed region
     names = ["u", "v", "w"] + model.tracers
-    host_in = {n: torch.from_numpy(np.ascontiguousarray(st[n], dtype=np.float32)).pin_memory() for n in names}
-    host_out = {n: torch.empty(model.shape(n), dtype=torch.float32).pin_memory() for n in names}
+    npt, tdt = (np.float32, torch.float32) if p["precision"] == 32 else (np.float64, torch.float64)
+    host_in = {n: torch.from_numpy(np.ascontiguousarray(st[n], dtype=npt)).pin_memory() for n in names}
+    host_out = {n: torch.empty(model.shape(n), dtype=tdt).pin_memory() for n in names}
     h2d = sum(t.numel() * t.element_size() for t in host_in.values())
     d2h = sum(t.numel() * t.element_size() for t in host_out.values())
     k_e2e = max(2, min(args.steps, 6))
@@ -344,7 +345,7 @@ def run_ours(args, world, rank, local):
     configure(model2)
     model2.set_option(ocn.OCN_OPT_TENDENCY_VARIANT, variant)
     pair = (model, model2)
-    outs = (host_out, {n: torch.empty(model.shape(n), dtype=torch.float32).pin_memory() for n in names})
+    outs = (host_out, {n: torch.empty(model.shape(n), dtype=tdt).pin_memory() for n in names})
 
     def put(m):
         for n in names:
@@ -558,12 +559,16 @@ def run_closure(args, world, rank, local):
         args.ensemble_mode = "batched"
     t0 = time.time()
     res = closure.experiment(n_members=32, n_train=24, t_end=3 * 3600.0, dt=10.0, every=180, train_steps=2000,
-                             log=lambda *a: None)
+                             log=lambda *a: None,
+                             variants={"mlp": closure.DEFAULT_VARIANT, "cfg5": closure.DIFFUSIVITY_VARIANT})
     t_exp = time.time() - t0
-    net, mu, sigma, scale, ysc, form = res["nets"]["mlp"]
-    cl = closure.closure_for(net, mu, sigma, scale, ysc, form)
+    cls = {}
+    for v in ("mlp", "cfg5"):
+        net, mu, sigma, scale, ysc, form = res["nets"][v]
+        cls[v] = closure.closure_for(net, mu, sigma, scale, ysc, form)
 
-    def attach(model, p):
+    def attach(model, p, v="mlp"):
+        cl = cls[v]
         c = cl(p) if callable(cl) else cl
         model.set_column_closure(c[0], c[1], c[2], c[3], p["N2"], mode=c[4])
     fine = inputs.ensemble_configs(n=args.members, seed=inputs.SEED + 7, dt=10.0)
@@ -572,13 +577,13 @@ def run_closure(args, world, rank, local):
     faces = sum(p["Nx"] * p["Ny"] * (p["Nz"] + 1) for p in ps)
     dt = 10.0
     timings = {}
-    for mode in ("plain", "learned"):
+    for mode in ("plain", "learned", "cfg5"):
         E = ocn.Ensemble(ps, device=dev)
         E.set_mode(args.ensemble_mode)
         for i, p in enumerate(ps):
             E.members[i].set(**inputs.initial_state(p, seed=inputs.SEED + i + 1000 * rank))
-            if mode == "learned":
-                attach(E.members[i], p)
+            if mode != "plain":
+                attach(E.members[i], p, "mlp" if mode == "learned" else "cfg5")
         E.autotune()
         E.time_step(dt, args.warmup)
         E.synchronize()
@@ -620,6 +625,7 @@ def run_closure(args, world, rank, local):
     peaks = measured_peaks()
     ms_p, _, _, _ = timings["plain"]
     ms_l, clocks, launches, d = timings["learned"]
+    ms_5, _, launches5, _ = timings["cfg5"]
     val = cells * 3 * args.steps * world / (ms_l * 1e-3)
     achieved = MLP_FLOPS_PER_SAMPLE * nsamp / t_kernel / 1e12
     s = res["summary"]
@@ -636,14 +642,18 @@ def run_closure(args, world, rank, local):
             "gpu_launches": launches * args.steps,
             "plain_amd": {"value": cells * 3 * args.steps * world / (ms_p * 1e-3), "ms_per_step": ms_p / args.steps},
             "closure_overhead": ms_l / ms_p,
+            "cfg5_closure": {"value": cells * 3 * args.steps * world / (ms_5 * 1e-3), "ms_per_step": ms_5 / args.steps,
+                             "launches_per_step": launches5,
+                             "closure": "network on the local gradients (5 faces) + surface buoyancy flux + f, "
+                                        "diffusivities applied by the implicit vertical solve"},
             "roofline": {"bound": "tensor", "kernel": "k_mlp_closure", "achieved": achieved,
                          "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": achieved / peaks["bf16_tflops"],
                          "traffic": None,
                          "algorithmic": f"{MLP_FLOPS_PER_SAMPLE} flops per face x {nsamp} faces per launch",
                          "peak_source": f"{peaks['source']} bf16 burst", "ms_per_launch": t_kernel * 1e3},
             "flux_error": {"held_out_forcings": s["n_members"] - s["n_train"],
-                           "b_profile": {"plain_amd": s["amd_b"], "learned": s["mlp_b"]},
-                           "buoyancy_flux": {"plain_amd": s["amd_Fb"], "learned": s["mlp_Fb"]},
+                           "b_profile": {"plain_amd": s["amd_b"], "learned": s["mlp_b"], "cfg5": s["cfg5_b"]},
+                           "buoyancy_flux": {"plain_amd": s["amd_Fb"], "learned": s["mlp_Fb"], "cfg5": s["cfg5_Fb"]},
                            "training_samples": s["mlp_samples"], "experiment_seconds": t_exp,
                            "definition": "normalised RMS vs coarse-grained fine LES over 30-min snapshots to 3 h"},
             "clocks": clocks,

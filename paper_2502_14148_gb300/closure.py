@@ -114,9 +114,14 @@ DEFAULT_VARIANT = dict(target="mean", outputs=(0,), features="nonlocal", scale="
 # The closure on the inputs the configuration states (local gradients of b, ubar, vbar over five
 # faces, the surface buoyancy flux and f) in diffusivity form: the network predicts eddy
 # diffusivities kappa (tracers) and nu (momentum) >= 0 at every face, whose column means the
-# coarse model applies through its semi-implicit vertical solve.
-DIFFUSIVITY_VARIANT = dict(target="mean", outputs=(0, 1), features="local", form="diffusivity")
-KAPPA_MAX = 1.0                      # m^2/s: cap of the diffusivity targets
+# coarse model applies through its semi-implicit vertical solve.  The targets are capped at
+# KAPPA_MAX and every face counts alike (a scan of the cap on a 32-forcing, 3 h experiment:
+# 1, 0.1, 0.01, 0.005, 0.003, 0.001 m^2/s; 0.003 gave the lowest buoyancy-profile error, larger
+# caps over-mix the stratified interior; weighting the faces by the squared gradient, the
+# least-squares weight of the flux, fitted the mixed layer worse).
+DIFFUSIVITY_VARIANT = dict(target="mean", outputs=(0, 1), features="local", form="diffusivity",
+                           weighting="uniform", kmax=0.003)
+KAPPA_MAX = 0.003                    # m^2/s: cap of the diffusivity targets
 
 
 def diffusivity_targets(X, Y, ncol: int, kmax: float = KAPPA_MAX):
@@ -275,7 +280,7 @@ def experiment(n_members: int = 64, n_train: int = 48, t_end: float = 6 * 3600.0
     Returns per-member errors and summaries over the held-out members."""
     import torch
     if variants is None:
-        variants = {"mlp": DEFAULT_VARIANT}
+        variants = {"mlp": DEFAULT_VARIANT, "cfg5": DIFFUSIVITY_VARIANT}
     members = inputs.ensemble_configs(n=n_members, sizes=sizes, depths=depths, dt=dt)
     coarse_members = [coarse_config(p, cx, cy) for p in members]
     t0 = time.time()
@@ -320,7 +325,9 @@ def experiment(n_members: int = 64, n_train: int = 48, t_end: float = 6 * 3600.0
         if v.get("scale") == "Jb":
             ysc = jb[G.long()][:, None].expand(-1, 3).contiguous()
         diffusive = v.get("form") == "diffusivity"
-        Yt, wts = (diffusivity_targets(X, Y, cx * cy) if diffusive else (Y, None))
+        Yt, wts = (diffusivity_targets(X, Y, cx * cy, v.get("kmax", KAPPA_MAX)) if diffusive else (Y, None))
+        if v.get("weighting", "gradient") == "uniform":
+            wts = None
         net, mu, sigma, scale, hist = train(X[tr], Yt[tr], steps=train_steps, batch=batch, lr=lr, outputs=outputs,
                                             features=feats, yscale=None if ysc is None else ysc[tr],
                                             weights=None if wts is None else wts[tr])

@@ -1,4 +1,4 @@
-"""The trained column closure against plain AMD: coarse runs (16 x 16 columns) of held-out
+"""The trained column closures against plain AMD: coarse runs (16 x 16 columns) of held-out
 convective-boundary-layer forcings, judged by the fine LES of the same forcings.
 
 The closure is trained by the library's own tensor-core forward/backward/Adam kernels on
@@ -17,16 +17,29 @@ def test_learned_closure_beats_plain_amd_on_held_out_forcings():
         pytest.skip("no CUDA device")
     from paper_2502_14148_gb300 import closure
     res = closure.experiment(n_members=32, n_train=24, t_end=3 * 3600.0, dt=10.0, every=180, train_steps=2000,
-                             batch=16384)
+                             batch=16384, variants={"mlp": closure.DEFAULT_VARIANT, "cfg5": closure.DIFFUSIVITY_VARIANT})
     s = res["summary"]
     test = [r for r in res["rows"] if not r["train"]]
     assert len(test) == 8
-    # the learned closure lowers both errors on average over the held-out forcings ...
+    # the similarity closure (non-local inputs, explicit buoyancy flux) lowers both errors on average
+    # over the held-out forcings ...
     assert s["mlp_b"] < 0.9 * s["amd_b"], s
     assert s["mlp_Fb"] < 0.9 * s["amd_Fb"], s
     # ... and the buoyancy-profile error of most of them
     better = sum(r["mlp_b"] < r["amd_b"] for r in test)
     assert better >= 6, [(r["amd_b"], r["mlp_b"]) for r in test]
+    # the closure on the configuration's own inputs (local b, ubar, vbar gradients over five faces, the
+    # surface buoyancy flux, f) in diffusivity form, applied by the implicit vertical solve: a lower
+    # buoyancy-profile error by 10 % or more, on most forcings, without raising the mean flux error
+    assert s["cfg5_b"] < 0.9 * s["amd_b"], s
+    assert s["cfg5_Fb"] < s["amd_Fb"], s
+    assert sum(r["cfg5_b"] < r["amd_b"] for r in test) >= 6, [(r["amd_b"], r["cfg5_b"]) for r in test]
+    # no held-out forcing does much worse than plain AMD with either closure
+    for v in ("mlp", "cfg5"):
+        for r in test:
+            assert r[f"{v}_b"] < 1.25 * r["amd_b"] and r[f"{v}_Fb"] < 1.25 * r["amd_Fb"], (v, r)
     # training reduced the loss substantially and every run stayed finite
     assert s["mlp_loss"][1] < 0.2 * s["mlp_loss"][0]
-    assert all(np.isfinite([r["mlp_b"], r["mlp_Fb"], r["amd_b"], r["amd_Fb"]]).all() for r in res["rows"])
+    assert s["cfg5_loss"][1] < 0.6 * s["cfg5_loss"][0]
+    assert all(np.isfinite([r["mlp_b"], r["mlp_Fb"], r["cfg5_b"], r["cfg5_Fb"], r["amd_b"], r["amd_Fb"]]).all()
+               for r in res["rows"])
