@@ -338,10 +338,11 @@ PoissonArgs<T> poisson_args(const ocn_model* m, int which, double dts) {
   return a;
 }
 
-// FP32 Smagorinsky-Lilly models compute nu_e inside the tendency kernel (and write it to the arena
-// as they go), so a time step or a tendency evaluation launches no closure kernel for them.
+// FP32 Smagorinsky-Lilly and AMD models compute their eddy diffusivities inside the tendency kernel
+// (nu_e is written to the arena as they go), so a time step or a tendency evaluation launches no
+// closure kernel for them.
 inline bool tendency_computes_nu(const ocn_model* m) {
-  return m->es == 4 && m->d.closure == OCN_CLOSURE_SMAGORINSKY;
+  return m->es == 4 && (m->d.closure == OCN_CLOSURE_SMAGORINSKY || m->d.closure == OCN_CLOSURE_AMD);
 }
 
 // The eddy-diffusivity kernel; with before_tendency, nothing when the tendency kernel that
@@ -396,7 +397,7 @@ cudaError_t enqueue_tendency(ocn_model* m, int which, double dt_gamma, double dt
   a.nu_out = m->off_nu ? at<T>(m, m->off_nu) : nullptr;
   a.dzc = at<T>(m, m->off_dzc);
   a.dx = (T)(g->Lx / g->Nx); a.dy = (T)(g->Ly / g->Ny);
-  a.Cs = (T)m->d.Cs; a.Cb = (T)m->d.Cb;
+  a.Cs = (T)m->d.Cs; a.Cb = (T)m->d.Cb; a.C_amd = (T)m->d.C_amd;
   m->hook.pre(OCN_K_TENDENCY);
   cudaError_t e = launch_tendency<T>(a, m->R, m->stream);
   m->hook.post(OCN_K_TENDENCY);

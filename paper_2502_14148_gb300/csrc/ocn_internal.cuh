@@ -66,11 +66,12 @@ struct TendencyArgs {
   int mode;               // 0: RK update + G;  1: G only
   int variant;            // tile variant of the FP32 kernel (0: 32x8 one CTA/SM, 1: 32x8 two, 2: 32x16, 3: 32x4 three,
                           // 4: 32x14, 5: 32x12, 6: 16x16 two CTAs/SM for grids under 32 columns wide)
-  // FP32 Smagorinsky-Lilly kernels compute the eddy viscosity of the stage state themselves (in the
-  // same z march, from the staged planes) and write it here for other readers; nu above is unused then.
+  // FP32 Smagorinsky-Lilly and AMD kernels compute the eddy diffusivities of the stage state
+  // themselves (in the same z march, from the staged planes) and write nu_e here for other readers;
+  // nu and kap above are unused then.
   T* nu_out;
   const T* dzc;           // dz_c[k]
-  T dx, dy, Cs, Cb;       // grid spacing, Smagorinsky and stratification constants
+  T dx, dy, Cs, Cb, C_amd;  // grid spacing, Smagorinsky, stratification and AMD constants
 };
 
 template <typename T>

@@ -22,12 +22,12 @@
 //    face flux is reconstructed exactly once.
 //  * The epilogue forms G, applies u~ = u + dt (gamma G - zeta G_prev) and
 //    writes the new state and G (the G_prev of the next substage).
-//  * FP32 Smagorinsky-Lilly kernels also compute the eddy viscosity: the ghost
-//    warps, which have no epilogue and a third of the main warps' flux work,
-//    evaluate nu_e two levels ahead of the march on the tile and a one-cell
-//    ring around it, from planes staged four levels ahead; no separate
-//    closure kernel and no nu_e round trip through HBM (it is still written
-//    out, for readers outside the step).
+//  * FP32 Smagorinsky-Lilly and AMD kernels also compute the eddy
+//    diffusivities, two levels ahead of the march, from planes staged four
+//    levels ahead: each main thread its own cell (its column from its register
+//    rings), the ghost warps the one-cell ring around the tile; no separate
+//    closure kernel and no round trip through HBM (nu_e is still written out,
+//    for readers outside the step).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -244,11 +244,11 @@ struct TileGeom {
 
 // Staging depth of the z march: levels (u, v, tracers) and w faces are prefetched LAL and LAW
 // ahead of the level being computed, into LAL + 1 and LAW + 1 rotating plane slots.  The fused
-// eddy viscosity (FP32 Smagorinsky-Lilly) is computed two levels ahead and needs the levels on
-// either side of that, hence the deeper staging.
+// eddy diffusivities (FP32 Smagorinsky-Lilly and AMD) are computed two levels ahead and need the
+// levels on either side of that, hence the deeper staging.
 template <typename T, int CL>
 struct MarchSlots {
-  static constexpr bool FUSE = sizeof(T) == 4 && CL == kClSmag;
+  static constexpr bool FUSE = sizeof(T) == 4 && (CL == kClSmag || CL == kClAmd);
   static constexpr int LAL = FUSE ? 4 : 1, LAW = FUSE ? 4 : 2;
   static constexpr int NSL = LAL + 1, NSW = LAW + 1;
 };
@@ -297,7 +297,7 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
   T* PHs = FY + nf * FYS;                 // hydrostatic pressure anomaly, [TY+1][TX+1] (offset -1)
   int* gi_tab = reinterpret_cast<int*>(PHs + (TY + 1) * (TX + 1));
   int* gj_tab = gi_tab + PW;
-  // with FUSE, per level l <= Nz: (C_s Delta_l)^2, 1/dz_c[l], 1/(4 dz_f[l]) (0 at the walls), unused
+  // with FUSE, per level l <= Nz: (C_s Delta_l)^2, 1/dz_c[l], 1/(4 dz_f[l]) (0 at the walls), dz_c[l]^2
   T* sLev = reinterpret_cast<T*>(gj_tab + PH);
 
   const int tid = threadIdx.x;
@@ -356,7 +356,8 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
   auto load_wface = [&](int f) { if (f <= Nz) load_plane(sW + (f % NSW) * PLANE, a.cur.w, f); };
   auto load_diff = [&](int l) {
     if (l < 0 || l >= Nz) return;
-    if (stress && !FUSE) load_plane(sNu + (l & 3) * PLANE, a.nu, l);
+    if (FUSE) return;
+    if (stress) load_plane(sNu + (l & 3) * PLANE, a.nu, l);
     if (amd) for (int n = 0; n < nt; ++n) load_plane(sK + (3 * n + l % 3) * PLANE, a.kap[n], l);
   };
 
@@ -387,11 +388,14 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
 #pragma unroll
     for (int n = 0; n < 2 * R; ++n) rc[t][n] = ld_tr(t, 1 - R + n);
 
-  // Smagorinsky-Lilly eddy viscosity (Sec. 3.1.1 closure equation, with Lilly's stratification
-  // factor) of level L, from the staged planes of levels L-1 .. L+1 and w faces L, L+1:
-  //   nu_e = (C_s Delta)^2 sqrt(max(|S|^2 - C_b N^2 / Pr, 0)),  |S|^2 = 2 S_ij S_ij,
-  //   Delta = (dx dy dz_L)^(1/3); each off-diagonal velocity gradient is the mean of its four edge
-  //   differences (wall edges 0), N^2 the mean of the two face gradients of b (wall faces 0).
+  // Eddy diffusivities of level L (Sec. 3.1.1 closure equation) from the staged planes of levels
+  // L-1 .. L+1 and w faces L, L+1, with the velocity gradients at the centre as the closure kernel
+  // forms them (each off-diagonal gradient the mean of its four edge differences, wall edges 0):
+  //   Smagorinsky-Lilly  nu_e = (C_s Delta)^2 sqrt(max(|S|^2 - C_b N^2 / Pr, 0)), |S|^2 = 2 S_ij S_ij,
+  //                      Delta = (dx dy dz_L)^(1/3), N^2 the mean of the two face gradients of b;
+  //   AMD                nu_e = max(0, -C sum_m D_m^2 (d_m u_i)(d_m u_j) S_ij / |grad u|^2),
+  //                      kappa_e = max(0, -C sum_m D_m^2 (d_m u_i)(d_m c)(d_i c) / |grad c|^2) per tracer,
+  //                      tracer gradients centred (the mean of the two face differences).
   // The mean of four edge differences telescopes to half-sums of centred differences.  A main
   // thread computes its own cell, taking the point's own column (u, v, w, tracers at the levels
   // L-1 .. L+1) from its register rings; the ghost warps compute the ring of cells around the tile
@@ -399,7 +403,7 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
   // rounding as the rings).  Multiply-adds are explicit (never left to contraction), so that every
   // thread and every tile variant computes the same bits for the same point.
   struct NuCol { T u0, um, up, v0, vm, vp, w0, w1, c0, cm, cp, d0, dm, dp; };
-  auto nu_point = [&](int L, int e, const NuCol& o) -> T {
+  auto nu_point = [&](int L, int e, const NuCol& o, T* kap) -> T {
     T nu = T(0);
     if constexpr (FUSE) {
       const bool lo = L >= 1, hi = L + 1 < Nz;
@@ -408,8 +412,9 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
       const T* W0 = sW + (L % NSW) * PLANE; const T* W1 = sW + ((L + 1) % NSW) * PLANE;
       const T* Um = sU + ((L + NSL - 1) % NSL) * PLANE; const T* Up = sU + ((L + 1) % NSL) * PLANE;
       const T* Vm = sV + ((L + NSL - 1) % NSL) * PLANE; const T* Vp = sV + ((L + 1) % NSL) * PLANE;
-      const T* lc = sLev + 4 * L;                  // (C_s Delta)^2, 1/dz_c, 1/(4 dz_f) of faces L, L+1
-      const T CD2 = lc[0], rdzc = lc[1], rzl4 = lo ? lc[2] : T(0), rzh4 = hi ? lc[4 + 2] : T(0);
+      // (C_s Delta)^2, 1/dz_c, 1/(4 dz_f) of faces L (and L+1 in the next entry), dz_c^2
+      const T* lc = sLev + 4 * L;
+      const T rdzc = lc[1], rzl4 = lo ? lc[2] : T(0), rzh4 = hi ? lc[4 + 2] : T(0);
       const T qx = T(0.25) * a.rdx, qy = T(0.25) * a.rdy;
       const T u1 = U0[e + 1], v1 = V0[e + PW];
       const T ux = (u1 - o.u0) * a.rdx, vy = (v1 - o.v0) * a.rdy, wz = (o.w1 - o.w0) * rdzc;
@@ -422,35 +427,86 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
       const T vl = lo ? sv - (o.vm + Vm[e + PW]) : T(0), vh = hi ? (o.vp + Vp[e + PW]) - sv : T(0);
       const T uz = __fmaf_rn(rzl4, ul, __fmul_rn(rzh4, uh));
       const T vz = __fmaf_rn(rzl4, vl, __fmul_rn(rzh4, vh));
-      T bl = lo ? o.c0 - o.cm : T(0), bh = hi ? o.cp - o.c0 : T(0);
-      if (a.eos == OCN_EOS_LINEAR_TS) {
-        const T dl = lo ? o.d0 - o.dm : T(0), dh = hi ? o.dp - o.d0 : T(0);
-        bl = __fmaf_rn(a.g_alpha, bl, -__fmul_rn(a.g_beta, dl));
-        bh = __fmaf_rn(a.g_alpha, bh, -__fmul_rn(a.g_beta, dh));
+      if constexpr (CL == kClSmag) {
+        T bl = lo ? o.c0 - o.cm : T(0), bh = hi ? o.cp - o.c0 : T(0);
+        if (a.eos == OCN_EOS_LINEAR_TS) {
+          const T dl = lo ? o.d0 - o.dm : T(0), dh = hi ? o.dp - o.d0 : T(0);
+          bl = __fmaf_rn(a.g_alpha, bl, -__fmul_rn(a.g_beta, dl));
+          bh = __fmaf_rn(a.g_alpha, bh, -__fmul_rn(a.g_beta, dh));
+        }
+        // N^2 = (bl rdzf_L + bh rdzf_{L+1}) / 2, with the quarter-scaled reciprocals doubled
+        const T N2 = __fmul_rn(T(2), __fmaf_rn(rzl4, bl, __fmul_rn(rzh4, bh)));
+        const T a12 = uy + vx, a13 = uz + wx, a23 = vz + wy;       // 2 S_12, 2 S_13, 2 S_23
+        const T dg = __fmaf_rn(wz, wz, __fmaf_rn(vy, vy, __fmul_rn(ux, ux)));
+        const T od = __fmaf_rn(a23, a23, __fmaf_rn(a13, a13, __fmul_rn(a12, a12)));
+        const T SS = __fmaf_rn(T(2), dg, od);                          // 2 S_ij S_ij
+        const T ex = __fmaf_rn(-a.Cb * a.inv_Pr, N2, SS);
+        float r;
+        asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(ex));
+        nu = (SS > T(0) && ex > T(0)) ? lc[0] * r : T(0);
+      } else {                                                           // AMD
+        const T G[3][3] = {{ux, uy, uz}, {vx, vy, vz}, {wx, wy, wz}};
+        const T D2[3] = {a.dx * a.dx, a.dy * a.dy, lc[3]};
+        // (G G)[p][m], then num = sum_m D2_m sum_p G[p][m] (G G)[p][m] (g^T S g = g^T G g)
+        T num = T(0), den = T(0);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          T h = T(0);
+#pragma unroll
+          for (int p = 0; p < 3; ++p) {
+            const T gg = __fmaf_rn(G[p][2], G[2][m], __fmaf_rn(G[p][1], G[1][m], __fmul_rn(G[p][0], G[0][m])));
+            h = __fmaf_rn(G[p][m], gg, h);
+          }
+          num = __fmaf_rn(D2[m], h, num);
+        }
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+          for (int q = 0; q < 3; ++q) den = __fmaf_rn(G[p][q], G[p][q], den);
+        const T nv = __fdividef(-a.C_amd * num, den);
+        nu = (den > T(0) && nv > T(0)) ? nv : T(0);
+        const T rzl2 = T(2) * rzl4, rzh2 = T(2) * rzh4;                // 1/(2 dz_f) of the two faces
+        const T hx = T(0.5) * a.rdx, hy = T(0.5) * a.rdy;
+#pragma unroll
+        for (int t = 0; t < NTR; ++t) {
+          const T* C0 = sC + (t * NSL + s0) * PLANE;
+          const T c0 = t == 0 ? o.c0 : o.d0, cm = t == 0 ? o.cm : o.dm, cp = t == 0 ? o.cp : o.dp;
+          const T dc0 = __fmul_rn(hx, C0[e + 1] - C0[e - 1]);
+          const T dc1 = __fmul_rn(hy, C0[e + PW] - C0[e - PW]);
+          const T dc2 = __fmaf_rn(rzl2, lo ? c0 - cm : T(0), __fmul_rn(rzh2, hi ? cp - c0 : T(0)));
+          const T dc[3] = {dc0, dc1, dc2};
+          T cn = T(0);
+#pragma unroll
+          for (int m = 0; m < 3; ++m) {
+            const T gd = __fmaf_rn(G[2][m], dc2, __fmaf_rn(G[1][m], dc1, __fmul_rn(G[0][m], dc0)));
+            cn = __fmaf_rn(__fmul_rn(D2[m], dc[m]), gd, cn);
+          }
+          const T cd = __fmaf_rn(dc2, dc2, __fmaf_rn(dc1, dc1, __fmul_rn(dc0, dc0)));
+          const T kv = __fdividef(-a.C_amd * cn, cd);
+          kap[t] = (cd > T(0) && kv > T(0)) ? kv : T(0);
+        }
       }
-      // N^2 = (bl rdzf_L + bh rdzf_{L+1}) / 2, with the quarter-scaled reciprocals doubled
-      const T N2 = __fmul_rn(T(2), __fmaf_rn(rzl4, bl, __fmul_rn(rzh4, bh)));
-      const T a12 = uy + vx, a13 = uz + wx, a23 = vz + wy;       // 2 S_12, 2 S_13, 2 S_23
-      const T dg = __fmaf_rn(wz, wz, __fmaf_rn(vy, vy, __fmul_rn(ux, ux)));
-      const T od = __fmaf_rn(a23, a23, __fmaf_rn(a13, a13, __fmul_rn(a12, a12)));
-      const T SS = __fmaf_rn(T(2), dg, od);                          // 2 S_ij S_ij
-      const T ex = __fmaf_rn(-a.Cb * a.inv_Pr, N2, SS);
-      float r;
-      asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(ex));
-      nu = (SS > T(0) && ex > T(0)) ? CD2 * r : T(0);
     }
     return nu;
   };
-  // nu_e of level L at this thread's share of the tile and the one-cell ring around it: a main
-  // thread its own cell (written to the arena too when it is inside the grid), its column from the
-  // ring entries RI-1, RI, RI+1 (levels L-1, L, L+1; w faces L, L+1 at RI, RI+1); the ghost threads
-  // share the ring's 2 (TX + 2) + 2 TY points from index r0 in steps of nr.
+  // Eddy diffusivities of level L on the tile and the one-cell ring around it.  A main thread
+  // computes its own cell, its column from the ring entries RI-1, RI, RI+1 (levels L-1, L, L+1; w
+  // faces L, L+1 at RI, RI+1); the ghost threads compute the ring's 2 (TX + 2) + 2 TY points (from
+  // index r0 in steps of nr).  With 4 i + 2 main warps (32 x 14), the SM's schedulers 0 and 1 hold
+  // one main warp more than schedulers 2 and 3, which hold the two ghost warps (a third of the flux
+  // work, no epilogue); the cells of the main warps 4 i and 4 i + 1 then go to the ghost threads
+  // too (NDEL of them), which evens out the schedulers' work.  nu_e of cells inside the grid is
+  // written to the arena as well.
+  constexpr int MAINW = TX * TY / 32;
+  constexpr bool DELEG = FUSE && (TX * TY) % 32 == 0 && MAINW % 4 == 2;
+  constexpr int NDEL = DELEG ? 64 * ((MAINW + 2) / 4) : 0;
+  const bool delegated = DELEG && role == 0 && ((tid >> 5) & 3) < 2;
   auto smag_nu = [&](int L, auto RIc, int r0, int nr) {
     if constexpr (FUSE) {
       constexpr int RI = decltype(RIc)::value;
       constexpr int t1 = NTR > 1 ? 1 : 0;
       T* nuS = sNu + (L & 3) * PLANE;
-      if (role == 0) {
+      if (role == 0 && !delegated) {
         const int e = (ly + H) * PW + (lx + H);
         NuCol o;
         o.u0 = ru[RI]; o.um = ru[RI - 1]; o.up = ru[RI + 1];
@@ -458,22 +514,31 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
         o.w0 = rw[RI]; o.w1 = rw[RI + 1];
         o.c0 = rc[0][RI]; o.cm = rc[0][RI - 1]; o.cp = rc[0][RI + 1];
         o.d0 = rc[t1][RI]; o.dm = rc[t1][RI - 1]; o.dp = rc[t1][RI + 1];
-        const T nu = nu_point(L, e, o);
+        T kap[NTR];
+        const T nu = nu_point(L, e, o, kap);
         nuS[e] = nu;
+        if constexpr (CL == kClAmd) {
+#pragma unroll
+          for (int t = 0; t < NTR; ++t) sK[(3 * t + L % 3) * PLANE + e] = kap[t];
+        }
         if (a.nu_out && active) a.nu_out[(size_t)L * plane + col] = nu;
-      } else {
+      } else if (role != 0) {
         const int s0 = L % NSL, sm = (L + NSL - 1) % NSL, sp = (L + 1) % NSL;
         const T r00 = cref_at(0, L), r0m = L >= 1 ? cref_at(0, L - 1) : T(0), r0p = L + 1 < Nz ? cref_at(0, L + 1) : T(0);
         const T r10 = cref_at(t1, L), r1m = L >= 1 ? cref_at(t1, L - 1) : T(0), r1p = L + 1 < Nz ? cref_at(t1, L + 1) : T(0);
         const T* W0 = sW + (L % NSW) * PLANE; const T* W1 = sW + ((L + 1) % NSW) * PLANE;
         constexpr int NR = 2 * (TX + 2) + 2 * TY;
 #pragma unroll 1
-        for (int q = r0; q < NR; q += nr) {
+        for (int q = r0; q < NR + NDEL; q += nr) {
           int qx, qy;
           if (q < TX + 2) { qx = q - 1; qy = -1; }
           else if (q < 2 * (TX + 2)) { qx = q - (TX + 2) - 1; qy = TY; }
           else if (q < 2 * (TX + 2) + TY) { qx = -1; qy = q - 2 * (TX + 2); }
-          else { qx = TX; qy = q - 2 * (TX + 2) - TY; }
+          else if (q < NR) { qx = TX; qy = q - 2 * (TX + 2) - TY; }
+          else {                                   // a delegated cell of main warp 4 i or 4 i + 1
+            const int d = q - NR, mt = 128 * (d >> 6) + (d & 63);
+            qy = mt / TX; qx = mt - qy * TX;
+          }
           const int e = (qy + H) * PW + (qx + H);
           NuCol o;
           o.u0 = sU[s0 * PLANE + e]; o.um = sU[sm * PLANE + e]; o.up = sU[sp * PLANE + e];
@@ -482,7 +547,15 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
           o.c0 = sC[s0 * PLANE + e] + r00; o.cm = sC[sm * PLANE + e] + r0m; o.cp = sC[sp * PLANE + e] + r0p;
           o.d0 = sC[(t1 * NSL + s0) * PLANE + e] + r10; o.dm = sC[(t1 * NSL + sm) * PLANE + e] + r1m;
           o.dp = sC[(t1 * NSL + sp) * PLANE + e] + r1p;
-          nuS[e] = nu_point(L, e, o);
+          T kap[NTR];
+          const T nu = nu_point(L, e, o, kap);
+          nuS[e] = nu;
+          if constexpr (CL == kClAmd) {
+#pragma unroll
+            for (int t = 0; t < NTR; ++t) sK[(3 * t + L % 3) * PLANE + e] = kap[t];
+          }
+          if (q >= NR && a.nu_out && qx < Wt && qy < Ht)
+            a.nu_out[(size_t)L * plane + (size_t)(j0 + qy) * Nx + (i0 + qx)] = nu;
         }
       }
     }
@@ -502,7 +575,8 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
         rz = __ldg(a.rdzc + l);
       }
       if (l >= 1 && l < Nz) rf = T(0.25) * __ldg(a.rdzf + l);
-      sLev[4 * l] = cd2; sLev[4 * l + 1] = rz; sLev[4 * l + 2] = rf; sLev[4 * l + 3] = T(0);
+      const T dz = (l < Nz) ? __ldg(a.dzc + l) : T(0);
+      sLev[4 * l] = cd2; sLev[4 * l + 1] = rz; sLev[4 * l + 2] = rf; sLev[4 * l + 3] = dz * dz;
     }
   }
   cp_async_wait_all();

@@ -135,12 +135,13 @@ def test_tendency_parity_edge_sizes(ocn, oracle_mod, dims):
 
 @pytest.mark.parametrize("dims", [(4, 4, 1), (4, 4, 2), (6, 4, 3), (12, 8, 5), (72, 36, 24)])
 @pytest.mark.parametrize("order", [5, 9])
-def test_tendency_parity_fp32_smagorinsky_edge_sizes(ocn, oracle_mod, dims, order):
-    """The FP32 Smagorinsky-Lilly kernels compute nu_e in their own z march (two levels ahead of
-    the fluxes, from planes staged four levels ahead): one to five levels, fewer levels than the
-    staging depth, tiles that wrap the periodic domain, ragged multi-tile grids."""
+@pytest.mark.parametrize("closure", ["smagorinsky", "amd"])
+def test_tendency_parity_fp32_fused_closure_edge_sizes(ocn, oracle_mod, dims, order, closure):
+    """The FP32 Smagorinsky-Lilly and AMD kernels compute the eddy diffusivities in their own z march
+    (two levels ahead of the fluxes, from planes staged four levels ahead): one to five levels, fewer
+    levels than the staging depth, tiles that wrap the periodic domain, ragged multi-tile grids."""
     Nx, Ny, Nz = dims
-    case = dict(weno_order=order, closure="smagorinsky", tracers=["T", "S"], eos="linear_ts",
+    case = dict(weno_order=order, closure=closure, tracers=["T", "S"], eos="linear_ts",
                 top_flux={"u": 1e-2, "T": 2e-3})
     G, O, _ = _tendency_pair(ocn, oracle_mod, case, 32, Nx=Nx, Ny=Ny, Nz=Nz, Lx=float(Nx), Ly=float(Ny), Lz=float(Nz))
     for name in O:
@@ -149,12 +150,13 @@ def test_tendency_parity_fp32_smagorinsky_edge_sizes(ocn, oracle_mod, dims, orde
 
 @pytest.mark.parametrize("precision", [32, 64])
 @pytest.mark.parametrize("eos", ["linear_ts", "buoyancy_tracer"])
-def test_smagorinsky_nu_field_matches_oracle(ocn, oracle_mod, precision, eos):
+@pytest.mark.parametrize("closure", ["smagorinsky", "amd"])
+def test_eddy_viscosity_field_matches_oracle(ocn, oracle_mod, precision, eos, closure):
     """nu_e left in the arena by a tendency evaluation (computed inside the FP32 tendency kernel,
     by the closure kernel in FP64) against the oracle's diffusivity at every cell of a stratified,
     stretched, ragged grid."""
     tracers = ["T", "S"] if eos == "linear_ts" else ["b"]
-    p = params(Nx=24, Ny=18, Nz=9, precision=precision, closure="smagorinsky", tracers=tracers, eos=eos, Cb=1.0,
+    p = params(Nx=24, Ny=18, Nz=9, precision=precision, closure=closure, tracers=tracers, eos=eos, Cb=1.0,
                Pr=0.7)
     # velocity amplitudes that put about half of the cells past the stratification cut-off
     st = inputs.random_state(p, seed=61, amp=0.01 if eos == "linear_ts" else 0.2)
@@ -173,11 +175,14 @@ def test_smagorinsky_nu_field_matches_oracle(ocn, oracle_mod, precision, eos):
     o.set(**st)
     ref = np.array([[[o.diffusivity_at(0, i, j, k) for i in range(p["Nx"])] for j in range(p["Ny"])]
                     for k in range(p["Nz"])])
-    assert 0.3 < (ref > 0).mean() < 0.7                       # both sides of the stratification cut-off
-    # nu_e^2 = (C_s Delta)^4 max(|S|^2 - C_b N^2 / Pr, 0) is linear in the rounded quantities; nu_e itself
-    # has an infinite slope at the cut-off, where a rounding-level change of the argument moves it by
-    # the square root of the rounding unit
-    assert rel_max(nu ** 2, ref ** 2) < (1e-11 if precision == 64 else 1e-5)
+    assert 0.3 < (ref > 0).mean() < 0.7                       # both sides of the cut-off
+    if closure == "smagorinsky":
+        # nu_e^2 = (C_s Delta)^4 max(|S|^2 - C_b N^2 / Pr, 0) is linear in the rounded quantities; nu_e
+        # itself has an infinite slope at the cut-off, where a rounding-level change of the argument
+        # moves it by the square root of the rounding unit
+        assert rel_max(nu ** 2, ref ** 2) < (1e-11 if precision == 64 else 1e-5)
+    else:
+        assert rel_max(nu, ref) < (1e-11 if precision == 64 else 1e-5)
 
 
 # ----------------------------------------------------------------------------- time stepping
