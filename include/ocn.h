@@ -302,7 +302,10 @@ ocn_status ocn_ensemble_launches_per_step(const ocn_ensemble* ensemble, int* lau
  * else OCN_ERR_ARG (so are the grid rules of ocn_grid_create).
  * The call allocates no device memory (no cudaMalloc, cudaFree or allocating
  * library routine).  The first call on each device looks up the device address
- * of the array and keeps it; make that first call before any stream capture.
+ * of the array and keeps it.  Every call uploads its grid tables from a host
+ * array on the stream, so the call cannot be captured into a CUDA graph: a
+ * stream that is being captured is refused with OCN_ERR_UNSUPPORTED before
+ * anything is enqueued.
  * Every call on a device shares the one array and leaves its contents behind
  * (each call rewrites all it reads, so nothing needs clearing), so calls whose
  * work overlaps on the GPU, e.g. on two streams at once, race and must be

@@ -12,7 +12,8 @@
 // cudaGetSymbolAddress while that device is current and keeps it.  Calls share
 // the array: each call rewrites every part of it that it reads before reading
 // it, so nothing has to start at zero, but calls whose work overlaps on the GPU
-// (for example on two streams at once) race on it.
+// (for example on two streams at once) race on it.  Every call uploads its grid
+// tables from a host array, so a stream that is being captured is refused.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -133,7 +134,7 @@ Result project_t(int Nx, int Ny, int Nz, double Lx, double Ly, const double* zf,
   auto dat = [&](size_t word) { return reinterpret_cast<const T*>(dmet + word * 8); };
   a.dzc = dat(wDzc); a.rdzc = dat(wRdzc); a.rdzf = dat(wRdzf);
   a.lamx = dat(wLx); a.lamy = dat(wLy); a.twx = dat(wTx); a.twy = dat(wTy);
-  a.Nx = Nx; a.Ny = Ny; a.Nz = Nz; a.Mx = Nx / 2;
+  a.Nx = Nx; a.Ny = Ny; a.Nz = Nz; a.Mx = Nx / 2; a.Sp = Nx / 2 + 1;   // unpadded: the array's size limit
   a.rdx = (T)(Nx / Lx); a.rdy = (T)(Ny / Ly);
   a.inv_dt = (T)1; a.dt = (T)1;
   a.scale = (T)(1.0 / ((double)(Nx / 2) * Ny));
@@ -164,6 +165,16 @@ extern "C" ocn_status ocn_project_noalloc(int precision, int Nx, int Ny, int Nz,
   else {
     for (int k = 0; k < Nz; ++k)
       if (!(z_faces[k + 1] > z_faces[k])) { r = bad(OCN_ERR_ARG, "z_faces must be strictly ascending"); break; }
+  }
+  if (r.st == OCN_OK) {
+    // The metric tables are uploaded from a host array on every call, which a stream under
+    // capture cannot record (and a graph that replayed it would read whatever a later call left
+    // in that array), so a capturing stream is refused before anything is enqueued.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(reinterpret_cast<cudaStream_t>(stream), &cs) != cudaSuccess ||
+        cs != cudaStreamCaptureStatusNone)
+      r = bad(OCN_ERR_UNSUPPORTED, "the stream is being captured into a CUDA graph; ocn_project_noalloc "
+                                   "uploads its grid tables from host memory and cannot be captured");
   }
   if (r.st == OCN_OK) {
     std::lock_guard<std::mutex> lk(g_mu);

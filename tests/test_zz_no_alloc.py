@@ -84,3 +84,28 @@ def test_noalloc_rejects_sizes_above_its_limit(ocn):
                                        zf.ctypes.data_as(C.POINTER(C.c_double)),
                                        *(C.c_void_p(dummy.data_ptr()) for _ in range(4)), None, C.byref(err))
     assert st == -1 and b"OCN_NOALLOC_MAX_MODES" in err.value
+
+
+def test_noalloc_refuses_a_stream_under_capture(ocn):
+    """Every call uploads its grid tables from host memory, which a captured graph could not
+    replay faithfully; a stream that is being captured is refused before anything is enqueued,
+    and the capture itself still ends cleanly."""
+    import torch
+    p = _params(32)
+    dev = torch.device("cuda")
+    u, v, w, pr = (torch.zeros((p["Nz"], p["Ny"], p["Nx"]), device=dev) for _ in range(4))
+    x = torch.zeros(8, device=dev)
+    zf = np.ascontiguousarray(p["z_faces"], dtype=np.float64)
+    err = C.c_char_p()
+    stream = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        x.add_(1.0)
+        st = ocn.lib().ocn_project_noalloc(32, p["Nx"], p["Ny"], p["Nz"], p["Lx"], p["Ly"],
+                                           zf.ctypes.data_as(C.POINTER(C.c_double)),
+                                           *(C.c_void_p(t.data_ptr()) for t in (u, v, w, pr)),
+                                           C.c_void_p(stream.cuda_stream), C.byref(err))
+    assert st == -7 and b"captured" in err.value, (st, err.value)
+    g.replay()
+    torch.cuda.synchronize()
+    assert float(x[0]) == 1.0
