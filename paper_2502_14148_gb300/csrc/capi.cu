@@ -263,7 +263,7 @@ void layout(ocn_model* m) {
   m->off_nu = stress ? take(es * Nc) : 0;
   for (int t = 0; t < OCN_MAX_TRACERS; ++t)
     m->off_kap[t] = (m->d.closure == OCN_CLOSURE_AMD && t < m->d.n_tracers) ? take(es * Nc) : 0;
-  const size_t S = (size_t)(g->Nx / 2 + 1) * g->Ny * g->Nz;
+  const size_t S = (size_t)spec_row_stride(g->Nx / 2) * g->Ny * g->Nz;
   m->off_spec = take(2 * es * S);
   m->off_cpiv = take(es * S);
   m->off_pinv = take(es * S);
@@ -328,7 +328,7 @@ PoissonArgs<T> poisson_args(const ocn_model* m, int which, double dts) {
   a.rdzc = at<T>(m, m->off_rdzc); a.rdzf = at<T>(m, m->off_rdzf); a.dzc = at<T>(m, m->off_dzc);
   a.lamx = at<T>(m, m->off_lamx); a.lamy = at<T>(m, m->off_lamy);
   a.twx = at<T>(m, m->off_twx); a.twy = at<T>(m, m->off_twy);
-  a.Nx = g->Nx; a.Ny = g->Ny; a.Nz = g->Nz; a.Mx = g->Nx / 2;
+  a.Nx = g->Nx; a.Ny = g->Ny; a.Nz = g->Nz; a.Mx = g->Nx / 2; a.Sp = spec_row_stride(a.Mx);
   a.rdx = (T)(g->Nx / g->Lx); a.rdy = (T)(g->Ny / g->Ly);
   a.inv_dt = (T)(1.0 / dts); a.dt = (T)dts;
   a.scale = (T)(1.0 / ((double)(g->Nx / 2) * g->Ny));
@@ -513,10 +513,12 @@ cudaError_t enqueue_vertical(ocn_model* m, int which, double dt_gamma, double dt
   a.fields = (vnu ? 7 : 0) | (vkap ? (((1 << m->d.n_tracers) - 1) << 3) : 0);
   a.mode = mode;
   a.dt_gamma = (T)dt_gamma; a.dtau = (T)dtau;
+  // the spectral work space is free between projections
+  a.tab = at<T>(m, m->off_spec);
+  a.tab_cap = 2 * (size_t)spec_row_stride(m->g->Nx / 2) * m->g->Ny * m->g->Nz;
   m->hook.pre(OCN_K_VERTICAL);
-  cudaError_t e = launch_vertical_diffusion<T>(a, vimplicit, m->stream);
+  cudaError_t e = launch_vertical_diffusion<T>(a, vimplicit, m->stream, nlaunch);
   m->hook.post(OCN_K_VERTICAL);
-  if (nlaunch) *nlaunch += 1;
   return e;
 }
 

@@ -102,15 +102,16 @@ template <typename T>
 struct PoissonArgs {
   T* u; T* v; T* w;            // velocity to project (in place)
   T* p;                        // pressure out
-  T* spec;                     // complex [Nz][Ny][Nx/2+1] interleaved (re, im)
-  T* cpiv;                     // Thomas pivots c' [Nz][Ny][Nx/2+1]
-  T* pinv;                     // 1 / Thomas diagonal [Nz][Ny][Nx/2+1] when stored (else null: computed per solve)
+  T* spec;                     // complex [Nz][Ny][Sp] interleaved (re, im); kx = 0 .. Nx/2 used
+  T* cpiv;                     // Thomas pivots c' [Nz][Ny][Sp]
+  T* pinv;                     // 1 / Thomas diagonal [Nz][Ny][Sp] when stored (else null: computed per solve)
   const T* rdzc; const T* rdzf; const T* dzc;
   const T* lamx;               // [Nx/2+1]
   const T* lamy;               // [Ny]
   const T* twx;                // e^{-2 pi i t/Nx}, t < Nx (complex interleaved)
   const T* twy;                // e^{-2 pi i t/Ny}, t < Ny
   int Nx, Ny, Nz, Mx;          // Mx = Nx/2
+  int Sp;                      // row stride of the spectrum and pivots (>= Mx + 1)
   T rdx, rdy;
   T inv_dt;                    // 1 / (stage dt)
   T dt;                        // stage dt
@@ -119,6 +120,12 @@ struct PoissonArgs {
   int fp64_pivots;
   FftPlan px, py;
 };
+
+// Row stride of a model's spectrum: Nx/2 + 1 rounded up to a multiple of 8 complex values, so
+// that every row, and every tile of 4 or 8 kx columns that the y transform moves, starts on a
+// 32-byte sector (an odd stride would split most of the y transform's 32-byte row pieces over two
+// sectors).
+inline int spec_row_stride(int Mx) { return (Mx + 1 + 7) / 8 * 8; }
 
 template <typename T>
 struct DiagArgs {
@@ -198,8 +205,17 @@ struct VDiffArgs {
   int fields;
   int mode;
   T dt_gamma, dtau;
+  // work space of the segmented implicit solve ((3 + nt) (4 Nz + 16) values, written by its factor
+  // kernel and read by its solve kernel of the same call; nothing is kept between calls) and its
+  // capacity in elements; 0 selects the one-thread-per-column solve
+  T* tab;
+  size_t tab_cap;
+  int seg;                                 // rows per segment of the segmented solve (set by the launcher)
 };
-template <typename T> cudaError_t launch_vertical_diffusion(const VDiffArgs<T>& a, bool implicit, cudaStream_t s);
+// Enqueues the vertical diffusion kernels; *nlaunch (if not null) is increased by the number of
+// kernels launched or recorded.
+template <typename T>
+cudaError_t launch_vertical_diffusion(const VDiffArgs<T>& a, bool implicit, cudaStream_t s, int* nlaunch);
 
 // Tensor-core GEMM of the learned column closure (mlp.cu):  D = A . B^T with A [M][K] and
 // B [N][K] BF16 (K contiguous, lda/ldb multiples of 8 elements, 16-byte aligned bases),

@@ -7,7 +7,7 @@
 // Kernels:
 //   k_div_fftx : divergence of each x-row fused with its real-to-complex FFT
 //                (half-length complex FFT + split), written to the half
-//                spectrum [Nz][Ny][Nx/2+1];
+//                spectrum [Nz][Ny][Sp] (kx = 0 .. Nx/2 of rows of stride Sp);
 //   k_fft_y    : complex FFT along y for tiles of kx columns (forward/inverse);
 //   k_tridiag  : one thread per (kx, ky) column; coalesced across kx;
 //                Neumann walls; the (0,0) mode is pinned by p_0 = 0;
@@ -269,7 +269,7 @@ __device__ __forceinline__ void div_fftx_body(const PoissonArgs<T>& a, int LR, c
     const C w = reinterpret_cast<const C*>(a.twx)[kx];    // kx <= M < Nx
     const C X = cadd(E, cmul(w, O));
     const int row = row0 + l;
-    reinterpret_cast<C*>(a.spec)[(size_t)row * S + kx] = X;
+    reinterpret_cast<C*>(a.spec)[(size_t)row * a.Sp + kx] = X;
   }
 }
 
@@ -289,7 +289,7 @@ __device__ __forceinline__ void ifftx_body(const PoissonArgs<T>& a, int LR, cons
   const C* tw = reinterpret_cast<const C*>(a.twx);
   // element kx of line l: Z_kx = E + i e^{+2 pi i kx / Nx} O from X[kx] and conj X[M - kx]
   auto ld = [&](int l, int kx) -> C {
-    const size_t ro = (size_t)(row0 + l) * S;
+    const size_t ro = (size_t)(row0 + l) * a.Sp;
     const C x1 = spec[ro + kx];
     const C x2 = cconj(spec[ro + (M - kx)]);
     const C E = cscale(cadd(x1, x2), T(0.5));
@@ -321,16 +321,16 @@ __device__ __forceinline__ void fft_y_body(const PoissonArgs<T>& a, int CW, int 
   typedef typename CT<T>::type C;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C* A = reinterpret_cast<C*>(sm_raw);
-  const int Ny = a.Ny, S = a.Mx + 1;
+  const int Ny = a.Ny, S = a.Mx + 1, Sp = a.Sp;
   C* B = A + spad_size<C>((size_t)Ny * CW);
   C* sTw = B + spad_size<C>((size_t)Ny * CW);
   const int kx0 = bid.x * CW, k = bid.y;
   const int ncol = min(CW, S - kx0);
-  C* spec = reinterpret_cast<C*>(a.spec) + (size_t)k * Ny * S;
+  C* spec = reinterpret_cast<C*>(a.spec) + (size_t)k * Ny * Sp;
   const C* twy = reinterpret_cast<const C*>(a.twy);
   for (int t = threadIdx.x; t < Ny; t += blockDim.x) sTw[t] = twy[t];
-  auto ld = [&](int l, int e) -> C { return (l < ncol) ? spec[(size_t)e * S + kx0 + l] : C{T(0), T(0)}; };
-  auto st = [&](int l, int e, C v) { if (l < ncol) spec[(size_t)e * S + kx0 + l] = v; };
+  auto ld = [&](int l, int e) -> C { return (l < ncol) ? spec[(size_t)e * Sp + kx0 + l] : C{T(0), T(0)}; };
+  auto st = [&](int l, int e, C v) { if (l < ncol) spec[(size_t)e * Sp + kx0 + l] = v; };
   block_fft<C, T>(A, B, a.py, CW, 1, CW, sTw, 1, sign, true, ld, st);
 }
 
@@ -359,9 +359,9 @@ __device__ __forceinline__ void tridiag_body(const PoissonArgs<T>& a, const uint
   const int o_ = bid.x * blockDim.x + threadIdx.x;   // column ky * S + kx
   if (o_ >= S * Ny) return;
   const int ky = o_ / S, kx = o_ - ky * S;
-  const size_t pl = (size_t)Ny * S;
-  C* x = reinterpret_cast<C*>(a.spec) + (size_t)ky * S + kx;
-  T* cp = a.cpiv + (size_t)ky * S + kx;
+  const size_t pl = (size_t)Ny * a.Sp;
+  C* x = reinterpret_cast<C*>(a.spec) + (size_t)ky * a.Sp + kx;
+  T* cp = a.cpiv + (size_t)ky * a.Sp + kx;
   const P lam = (P)__ldg(a.lamx + kx) + (P)__ldg(a.lamy + ky);
   const bool gauge = (kx == 0 && ky == 0);
   P cprev = P(0);
@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(256) k_tridiag_factor(const PoissonArgs<T> a) 
   const int o_ = blockIdx.x * blockDim.x + threadIdx.x;   // column ky * S + kx
   if (o_ >= S * Ny) return;
   const int ky = o_ / S, kx = o_ - ky * S;
-  const size_t pl = (size_t)Ny * S, o = (size_t)ky * S + kx;
+  const size_t pl = (size_t)Ny * a.Sp, o = (size_t)ky * a.Sp + kx;
   const P lam = (P)__ldg(a.lamx + kx) + (P)__ldg(a.lamy + ky);
   const bool gauge = (kx == 0 && ky == 0);
   P cprev = P(0);
@@ -419,7 +419,7 @@ __device__ __forceinline__ void tridiag_solve_body(const PoissonArgs<T>& a, cons
   const int o_ = bid.x * blockDim.x + threadIdx.x;   // column ky * S + kx
   if (o_ >= S * Ny) return;
   const int ky = o_ / S, kx = o_ - ky * S;
-  const size_t pl = (size_t)Ny * S, o = (size_t)ky * S + kx;
+  const size_t pl = (size_t)Ny * a.Sp, o = (size_t)ky * a.Sp + kx;
   C* x = reinterpret_cast<C*>(a.spec) + o;
   const T* cp = a.cpiv + o;
   const T* pinv = a.pinv + o;
@@ -477,7 +477,7 @@ __device__ __forceinline__ void tridiag_solve_body(const PoissonArgs<T>& a, cons
 template <typename T>
 __device__ __forceinline__ void gauge_body(const PoissonArgs<T>& a) {
   typedef typename CT<T>::type C;
-  const size_t pl = (size_t)a.Ny * (a.Mx + 1);
+  const size_t pl = (size_t)a.Ny * a.Sp;
   C* x = reinterpret_cast<C*>(a.spec);
   double sr = 0.0, si = 0.0;
   for (int k = threadIdx.x; k < a.Nz; k += 32) {
