@@ -160,9 +160,10 @@ __device__ __forceinline__ T weno(const T* s, T vel) {
   }
 }
 
-// Closure-flux arithmetic with every operation rounded on its own.  Plain multiplies and adds
-// may be fused into FMAs by the code generator, and it makes that choice separately for every
-// tile variant; spelling the rounding out keeps all variants bit-identical.
+// Closure-flux arithmetic with every rounding spelled out (separate multiplies and adds, or
+// explicit FMAs).  Plain multiplies and adds may be fused into FMAs by the code generator, and it
+// makes that choice separately for every tile variant; spelling the rounding out keeps all
+// variants bit-identical.
 template <typename T> __device__ __forceinline__ T rmul(T a, T b);
 template <> __device__ __forceinline__ float rmul<float>(float a, float b) { return __fmul_rn(a, b); }
 template <> __device__ __forceinline__ double rmul<double>(double a, double b) { return __dmul_rn(a, b); }
@@ -170,17 +171,21 @@ template <typename T> __device__ __forceinline__ T radd(T a, T b);
 template <> __device__ __forceinline__ float radd<float>(float a, float b) { return __fadd_rn(a, b); }
 template <> __device__ __forceinline__ double radd<double>(double a, double b) { return __dadd_rn(a, b); }
 template <typename T> __device__ __forceinline__ T rsub(T a, T b) { return radd<T>(a, -b); }
-// F - c g
-template <typename T> __device__ __forceinline__ T rflux(T F, T c, T g) { return rsub<T>(F, rmul<T>(c, g)); }
+template <typename T> __device__ __forceinline__ T rfma(T a, T b, T c);
+template <> __device__ __forceinline__ float rfma<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <> __device__ __forceinline__ double rfma<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+// F - c g, one rounding
+template <typename T> __device__ __forceinline__ T rflux(T F, T c, T g) { return rfma<T>(-c, g, F); }
+// F - 2 nu S with the strain S = ((x - y) r + g) / 2 (a difference quotient and a gradient):
+// F - nu ((x - y) r + g)
+template <typename T> __device__ __forceinline__ T rstress(T F, T nu, T x, T y, T r, T g) {
+  return rfma<T>(-nu, rfma<T>(rsub<T>(x, y), r, g), F);
+}
 // (a + b + c + d) / 4 and (a + b) / 2
 template <typename T> __device__ __forceinline__ T ravg4(T a, T b, T c, T d) {
   return rmul<T>(T(0.25), radd<T>(radd<T>(radd<T>(a, b), c), d));
 }
 template <typename T> __device__ __forceinline__ T ravg2(T a, T b) { return rmul<T>(T(0.5), radd<T>(a, b)); }
-// half the sum of a difference quotient and a gradient: ((x - y) r + g) / 2
-template <typename T> __device__ __forceinline__ T rstrain(T x, T y, T r, T g) {
-  return rmul<T>(T(0.5), radd<T>(rmul<T>(rsub<T>(x, y), r), g));
-}
 
 // Centered reconstruction of order 2p at the interface between s[p-1] and s[p].
 template <typename T, int p>
@@ -283,6 +288,7 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
                                       : (CL == kClSmag || CL == kClAmd);
   const bool amd = (CL == kClAny) ? (a.closure == OCN_CLOSURE_AMD) : (CL == kClAmd);
   const bool scalar = (CL == kClAny || CL == kClScalar) ? (a.closure == OCN_CLOSURE_SCALAR) : false;
+  const T hPr = T(0.5) * a.inv_Pr;           // nu_e / (2 Pr) factor of a face-mean tracer diffusivity
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
@@ -692,8 +698,7 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
         if (scalar) F = rflux<T>(F, a.nu0, dvdx);
         else if (stress) {
           const T nuf = ravg4<T>(pN0[rowc - 1 - PW], pN0[rowc - PW], pN0[rowc - 1], pN0[rowc]);
-          const T S12 = rstrain<T>(pU[rowc], pU[rowc - PW], rdy, dvdx);
-          F = rflux<T>(F, rmul<T>(T(2), nuf), S12);
+          F = rstress<T>(F, nuf, pU[rowc], pU[rowc - PW], rdy, dvdx);
         }
         if (active) FX[1 * FXS + ly * (TX + 1) + lx] = F;
       }
@@ -711,8 +716,7 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
           if (scalar) F = rflux<T>(F, a.nu0, dwdx);
           else if (stress) {
             const T nuf = ravg4<T>(pNm[rowc - 1], pNm[rowc], pN0[rowc - 1], pN0[rowc]);
-            const T S13 = rstrain<T>(ru[R - 1], ru[R - 2], rdzf_k, dwdx);
-            F = rflux<T>(F, rmul<T>(T(2), nuf), S13);
+            F = rstress<T>(F, nuf, ru[R - 1], ru[R - 2], rdzf_k, dwdx);
           }
         }
         if (active) FX[2 * FXS + ly * (TX + 1) + lx] = F;
@@ -729,7 +733,7 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
         const T dc = (sc[R] - sc[R - 1]) * rdx;
         if (scalar) F = rflux<T>(F, a.kappa0, dc);
         else if (amd) { const T* pK = sK + (3 * t + k % 3) * PLANE; F = rflux<T>(F, ravg2<T>(pK[rowc - 1], pK[rowc]), dc); }
-        else if (stress) F = rflux<T>(F, rmul<T>(a.inv_Pr, ravg2<T>(pN0[rowc - 1], pN0[rowc])), dc);
+        else if (stress) F = rflux<T>(F, rmul<T>(hPr, radd<T>(pN0[rowc - 1], pN0[rowc])), dc);
         if (active) FX[(3 + t) * FXS + ly * (TX + 1) + lx] = F;
       }
     }
@@ -750,8 +754,7 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
         if (scalar) F = rflux<T>(F, a.nu0, dudy);
         else if (stress) {
           const T nuf = ravg4<T>(pN0[rowc - 1 - PW], pN0[rowc - PW], pN0[rowc - 1], pN0[rowc]);
-          const T S12 = rstrain<T>(pV[rowc], pV[rowc - 1], rdx, dudy);
-          F = rflux<T>(F, rmul<T>(T(2), nuf), S12);
+          F = rstress<T>(F, nuf, pV[rowc], pV[rowc - 1], rdx, dudy);
         }
         if (active) FY[0 * FYS + ly * TX + lx] = F;
       }
@@ -781,8 +784,7 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
           if (scalar) F = rflux<T>(F, a.nu0, dwdy);
           else if (stress) {
             const T nuf = ravg4<T>(pNm[rowc - PW], pNm[rowc], pN0[rowc - PW], pN0[rowc]);
-            const T S23 = rstrain<T>(rv[R - 1], rv[R - 2], rdzf_k, dwdy);
-            F = rflux<T>(F, rmul<T>(T(2), nuf), S23);
+            F = rstress<T>(F, nuf, rv[R - 1], rv[R - 2], rdzf_k, dwdy);
           }
         }
         if (active) FY[2 * FYS + ly * TX + lx] = F;
@@ -798,7 +800,7 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
         const T dc = (sc[R] - sc[R - 1]) * rdy;
         if (scalar) F = rflux<T>(F, a.kappa0, dc);
         else if (amd) { const T* pK = sK + (3 * t + k % 3) * PLANE; F = rflux<T>(F, ravg2<T>(pK[rowc - PW], pK[rowc]), dc); }
-        else if (stress) F = rflux<T>(F, rmul<T>(a.inv_Pr, ravg2<T>(pN0[rowc - PW], pN0[rowc])), dc);
+        else if (stress) F = rflux<T>(F, rmul<T>(hPr, radd<T>(pN0[rowc - PW], pN0[rowc])), dc);
         if (active) FY[(3 + t) * FYS + ly * TX + lx] = F;
       }
     }
@@ -823,8 +825,7 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
         if (scalar) F = rflux<T>(F, a.nu0, dudz);
         else if (stress) {
           const T nuf = ravg4<T>(pN0[rowc - 1], pN0[rowc], pN1[rowc - 1], pN1[rowc]);
-          const T S13 = rstrain<T>(pW1[rowc], pW1[rowc - 1], rdx, dudz);
-          F = rflux<T>(F, rmul<T>(T(2), nuf), S13);
+          F = rstress<T>(F, nuf, pW1[rowc], pW1[rowc - 1], rdx, dudz);
         }
         nz_u = F;
       }
@@ -839,8 +840,7 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
         if (scalar) F = rflux<T>(F, a.nu0, dvdz);
         else if (stress) {
           const T nuf = ravg4<T>(pN0[rowc - PW], pN0[rowc], pN1[rowc - PW], pN1[rowc]);
-          const T S23 = rstrain<T>(pW1[rowc], pW1[rowc - PW], rdy, dvdz);
-          F = rflux<T>(F, rmul<T>(T(2), nuf), S23);
+          F = rstress<T>(F, nuf, pW1[rowc], pW1[rowc - PW], rdy, dvdz);
         }
         nz_v = F;
       }
@@ -855,7 +855,7 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
           const T* pK0 = sK + (3 * t + k % 3) * PLANE;
           const T* pK1 = sK + (3 * t + (k + 1) % 3) * PLANE;
           F = rflux<T>(F, ravg2<T>(pK0[rowc], pK1[rowc]), dc);
-        } else if (stress) F = rflux<T>(F, rmul<T>(a.inv_Pr, ravg2<T>(pN0[rowc], pN1[rowc])), dc);
+        } else if (stress) F = rflux<T>(F, rmul<T>(hPr, radd<T>(pN0[rowc], pN1[rowc])), dc);
         nz_c[t] = F;
       }
       // w through centre k (w interface k+1; valid faces 0..Nz)
