@@ -181,16 +181,23 @@ __device__ __forceinline__ void vdiff_implicit_body(const VDiffArgs<T>& a, const
 // done the same way from the top (H_t the product of gamma over segment t).  The matrix is
 // diagonally dominant, so |alpha|, |gamma| < 1 and the products only decay.  k_vdiff_factor
 // computes the per-row coefficients (alpha, beta, dtau D(ref), gamma) and the segment products
-// once per call and field; a block copies its field's rows into shared memory.
+// once per call and field; a solve block copies its field's rows into shared memory.
 constexpr int kSegs = 8;
 constexpr int kMaxSeg = 64;
 // work-space elements per field: 4 per row, then (G_t, H_t) per segment
 __host__ __device__ constexpr size_t vtab_stride(int Nz) { return 4 * (size_t)Nz + 2 * kSegs; }
 
+// One block per field.  The rows' matrix entries and dtau D(ref) are formed in parallel (their
+// loads issued together), the pivot recurrence piv_r = diag_r - sub_r sup_{r-1} / piv_{r-1} runs
+// in one thread over shared memory, and the coefficients and segment products are written in
+// parallel again.
+constexpr int kFactorThreads = 256;
+
 template <typename T>
 __device__ __forceinline__ void vdiff_factor_body(const VDiffArgs<T>& a, const uint3 bid) {
+  __shared__ T s_sub[kSegs * kMaxSeg], s_sup[kSegs * kMaxSeg], s_dia[kSegs * kMaxSeg];
   const int f = bid.y;
-  if (!((a.fields >> f) & 1)) return;
+  if (!((a.fields >> f) & 1)) return;              // uniform over the block
   const int Nz = a.Nz;
   const bool faces = (f == 2);
   const int n0 = faces ? 1 : 0, n = faces ? Nz - 1 : Nz;
@@ -199,36 +206,44 @@ __device__ __forceinline__ void vdiff_factor_body(const VDiffArgs<T>& a, const u
   const T* kf = (f < 3) ? a.nuz : a.kapz;
   const T* ref = (f >= 3) ? a.cref[f - 3] : nullptr;
   const T dtau = a.dtau;
-  if (threadIdx.x == 0) {
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    const int k = n0 + r;
+    T lo, hi, h;
+    if (!faces) {
+      h = a.dzc[k];
+      lo = (k > 0) ? kf[k] / a.dzf[k] : T(0);
+      hi = (k < Nz - 1) ? kf[k + 1] / a.dzf[k + 1] : T(0);
+    } else {
+      h = a.dzf[k];
+      lo = T(0.5) * (kf[k - 1] + kf[k]) / a.dzc[k - 1];
+      hi = T(0.5) * (kf[k] + kf[k + 1]) / a.dzc[k];
+    }
+    s_sub[r] = (r > 0) ? -dtau * lo / h : T(0);
+    s_sup[r] = (r < n - 1) ? -dtau * hi / h : T(0);
+    s_dia[r] = T(1) + dtau * (lo + hi) / h;
+    T dr = T(0);
+    if (ref) {                                     // dtau D(ref) at centre k
+      const T Fb = (k > 0) ? -kf[k] * (ref[k] - ref[k - 1]) / a.dzf[k] : T(0);
+      const T Ft = (k < Nz - 1) ? -kf[k + 1] * (ref[k + 1] - ref[k]) / a.dzf[k + 1] : T(0);
+      dr = dtau * (-(Ft - Fb) / a.dzc[k]);
+    }
+    tb[4 * r + 2] = dr;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {                          // the pivots; s_dia becomes 1 / piv
     T cprev = T(0);
     for (int r = 0; r < n; ++r) {
-      const int k = n0 + r;
-      T lo, hi, h;
-      if (!faces) {
-        h = a.dzc[k];
-        lo = (k > 0) ? kf[k] / a.dzf[k] : T(0);
-        hi = (k < Nz - 1) ? kf[k + 1] / a.dzf[k + 1] : T(0);
-      } else {
-        h = a.dzf[k];
-        lo = T(0.5) * (kf[k - 1] + kf[k]) / a.dzc[k - 1];
-        hi = T(0.5) * (kf[k] + kf[k + 1]) / a.dzc[k];
-      }
-      const T sub = (r > 0) ? -dtau * lo / h : T(0);
-      const T sup = (r < n - 1) ? -dtau * hi / h : T(0);
-      const T diag = T(1) + dtau * (lo + hi) / h;
-      const T inv = T(1) / (diag - sub * cprev);
-      cprev = sup * inv;
-      T dr = T(0);
-      if (ref) {                                   // dtau D(ref) at centre k
-        const T Fb = (k > 0) ? -kf[k] * (ref[k] - ref[k - 1]) / a.dzf[k] : T(0);
-        const T Ft = (k < Nz - 1) ? -kf[k + 1] * (ref[k + 1] - ref[k]) / a.dzf[k + 1] : T(0);
-        dr = dtau * (-(Ft - Fb) / a.dzc[k]);
-      }
-      tb[4 * r] = -sub * inv;
-      tb[4 * r + 1] = inv;
-      tb[4 * r + 2] = dr;
-      tb[4 * r + 3] = -cprev;
+      const T inv = T(1) / (s_dia[r] - s_sub[r] * cprev);
+      cprev = s_sup[r] * inv;
+      s_dia[r] = inv;
     }
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    const T inv = s_dia[r];
+    tb[4 * r] = -s_sub[r] * inv;
+    tb[4 * r + 1] = inv;
+    tb[4 * r + 3] = -(s_sup[r] * inv);
   }
   __syncthreads();
   const int M = a.seg;
@@ -343,7 +358,7 @@ template <typename T> struct VDiffImplicitK {
 };
 template <typename T> struct VDiffFactorK {
   typedef VDiffArgs<T> Payload;
-  static constexpr int kThreads = 32, kMinBlocks = 1;
+  static constexpr int kThreads = kFactorThreads, kMinBlocks = 1;
   static __device__ __forceinline__ void run(const Payload& a, uint3 bid, uint3) { vdiff_factor_body<T>(a, bid); }
 };
 template <typename T, int M> struct VDiffSolveK {
@@ -352,7 +367,7 @@ template <typename T, int M> struct VDiffSolveK {
   static __device__ __forceinline__ void run(const Payload& a, uint3 bid, uint3) { vdiff_isolve_body<T, M>(a, bid); }
 };
 template <typename T>
-__global__ void __launch_bounds__(32) k_vdiff_factor(const VDiffArgs<T> a) { vdiff_factor_body<T>(a, blockIdx); }
+__global__ void __launch_bounds__(kFactorThreads) k_vdiff_factor(const VDiffArgs<T> a) { vdiff_factor_body<T>(a, blockIdx); }
 template <typename T, int M>
 __global__ void __launch_bounds__(32 * kSegs) k_vdiff_isolve(const VDiffArgs<T> a) { vdiff_isolve_body<T, M>(a, blockIdx); }
 template <typename T>
@@ -385,8 +400,8 @@ cudaError_t launch_vertical_diffusion(const VDiffArgs<T>& a_, bool implicit, cud
       a.seg = M;
       cudaError_t e = cudaSuccess;
       const dim3 fgrid(1, 3 + a.nt);
-      if (!record_launch<VDiffFactorK<T>>(a, fgrid, dim3(32), 0, OCN_K_VERTICAL)) {
-        k_vdiff_factor<T><<<fgrid, 32, 0, s>>>(a);
+      if (!record_launch<VDiffFactorK<T>>(a, fgrid, dim3(kFactorThreads), 0, OCN_K_VERTICAL)) {
+        k_vdiff_factor<T><<<fgrid, kFactorThreads, 0, s>>>(a);
         e = cudaGetLastError();
       }
       if (e != cudaSuccess) return e;
