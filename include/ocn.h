@@ -38,8 +38,9 @@
  * Streams: all work of a model is issued on the cudaStream_t given at
  * creation (NULL selects the legacy default stream; graph capture of the time
  * step then stays off).  Calls return after enqueueing, except
- * ocn_get_field to host memory and ocn_diagnostics, which synchronise the
- * stream.
+ * ocn_set_field from host memory (which waits for its copy), ocn_get_field to
+ * host memory (which waits for the data) and ocn_diagnostics, which
+ * synchronises the stream.
  *
  * Errors: every call returns an ocn_status.  OCN_OK is 0; failures are
  * negative.  ocn_last_error() returns a thread-local description of the last
@@ -153,9 +154,48 @@ ocn_status ocn_model_bind_arena(ocn_model* model, void* device_ptr, size_t bytes
  * the model precision.  src/dst is device memory when *_is_device != 0, host
  * memory otherwise.  Setting w forces w = 0 on the wall faces.  Setting a
  * field does not project the velocity (call ocn_project).
- * Errors: OCN_ERR_ARG, OCN_ERR_STATE (no arena), OCN_ERR_CUDA. */
+ * ocn_set_field from host memory returns once the host buffer has been copied;
+ * the rest of its work (for a tracer, the new reference profile and the
+ * anomaly) stays queued on the model stream.  ocn_get_field runs its copy (and,
+ * for a tracer, the kernel that adds the reference profile back) on an
+ * internal stream of the greatest priority, after the work queued on the model
+ * stream and before the model stream's later work, so that it does not wait
+ * behind the blocks of other work sharing the GPU; to host memory it returns
+ * when the data has arrived.
+ * Errors: OCN_ERR_ARG (also for *_is_device other than 0, 1, OCN_HOST_ASYNC),
+ * OCN_ERR_STATE (no arena), OCN_ERR_CUDA. */
 ocn_status ocn_set_field(ocn_model* model, int field, const void* src, size_t nbytes, int src_is_device);
 ocn_status ocn_get_field(ocn_model* model, int field, void* dst, size_t nbytes, int dst_is_device);
+
+/* *_is_device = OCN_HOST_ASYNC: host memory, and the call returns after
+ * enqueueing instead of waiting for its copies.  The caller keeps the host
+ * buffers valid (and, for a set, unchanged) until ocn_wait_transfers() has
+ * returned; the model stream's later work is ordered after the copies as for the
+ * waiting form.  Pinned host memory is needed for the copies to run
+ * asynchronously.  This lets a caller overlap a model's copies with its own or
+ * another model's steps and with copies in the other direction. */
+#define OCN_HOST_ASYNC 2
+/* Wait until every host transfer issued on the model so far (the copies of
+ * ocn_set_field(s) and everything of ocn_get_field(s)) has completed.
+ * Errors: OCN_ERR_ARG, OCN_ERR_CUDA. */
+ocn_status ocn_wait_transfers(ocn_model* model);
+
+/* Several fields in one call: fields[i], srcs[i] / dsts[i] and nbytes[i] for
+ * i < n, each as in ocn_set_field / ocn_get_field, applied in order.  All
+ * copies of a set are issued first, back to back, and the call returns once
+ * they are done (the follow-up work of tracers and of w stays queued on the
+ * model stream), so no copy waits for another field's kernels.  A get forms the
+ * full value of every requested tracer before the first copy, in the tracer's
+ * slot of the model's other state buffer (which holds the previous stage state,
+ * dead between steps and overwritten by the next one), then copies everything
+ * and returns when all data has arrived (to host memory).  This is the host
+ * transfer to use for a whole state: one wait per call instead of one per
+ * field.  Errors: as for the single-field calls; nothing is enqueued when an
+ * argument is invalid. */
+ocn_status ocn_set_fields(ocn_model* model, int n, const int* fields, const void* const* srcs, const size_t* nbytes,
+                          int src_is_device);
+ocn_status ocn_get_fields(ocn_model* model, int n, const int* fields, void* const* dsts, const size_t* nbytes,
+                          int dst_is_device);
 
 /* Enforce incompressibility of the current velocity: solve the discrete
  * Poisson problem lap p = div u (Eq. pressure-poisson with dt = 1) and set

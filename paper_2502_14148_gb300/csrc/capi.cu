@@ -151,6 +151,16 @@ struct ocn_model {
   // stratification.
   size_t off_cref[OCN_MAX_TRACERS] = {0, 0, 0, 0};
   std::vector<double> cref_host[OCN_MAX_TRACERS];
+  // Host transfers.  ocn_set_field waits only for its copies (copy_done): the reference-profile
+  // kernels of a tracer run afterwards on the model stream, and cref_host is read back from the
+  // device where it is used (cref_pending), not in the set call, so that no small copy to the host
+  // queues on the model stream behind the large copies of another model.  ocn_get_field runs on
+  // xfer, a stream of the greatest priority ordered after the model stream (xfer_in) and the model
+  // stream after it (xfer_out), so that its kernel is not queued behind the blocks of another
+  // model's step that shares the GPU.
+  cudaStream_t xfer = nullptr;
+  cudaEvent_t xfer_in = nullptr, xfer_out = nullptr, copy_done = nullptr;
+  bool cref_pending[OCN_MAX_TRACERS] = {false, false, false, false};
   // kernel timing (OCN_OPT_KERNEL_TIMING)
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -196,6 +206,41 @@ struct ocn_ensemble {
 };
 
 namespace {
+
+// The transfer stream and its events, created on first use.
+cudaError_t xfer_setup(ocn_model* m) {
+  if (m->xfer) return cudaSuccess;
+  int lo = 0, hi = 0;
+  cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->xfer_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->xfer_out, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->copy_done, cudaEventDisableTiming);
+  cudaStream_t s = nullptr;
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, hi);
+  if (e == cudaSuccess) m->xfer = s;
+  return e;
+}
+void xfer_release(ocn_model* m) {
+  if (m->xfer) cudaStreamDestroy(m->xfer);
+  if (m->xfer_in) cudaEventDestroy(m->xfer_in);
+  if (m->xfer_out) cudaEventDestroy(m->xfer_out);
+  if (m->copy_done) cudaEventDestroy(m->copy_done);
+  m->xfer = nullptr; m->xfer_in = m->xfer_out = m->copy_done = nullptr;
+}
+// Read back the reference profiles that ocn_set_field left pending into the host mirror (after the
+// model stream has been synchronised past the kernels that formed them).
+cudaError_t cref_refresh(ocn_model* m) {
+  for (int t = 0; t < m->d.n_tracers; ++t) {
+    if (!m->cref_pending[t]) continue;
+    std::vector<char> hb((size_t)m->g->Nz * m->es);
+    cudaError_t e = cudaMemcpy(hb.data(), m->arena + m->off_cref[t], hb.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return e;
+    for (int k = 0; k < m->g->Nz; ++k)
+      m->cref_host[t][k] = (m->es == 4) ? (double)reinterpret_cast<const float*>(hb.data())[k] : reinterpret_cast<const double*>(hb.data())[k];
+    m->cref_pending[t] = false;
+  }
+  return cudaSuccess;
+}
 
 cudaEvent_t take_event(ocn_model* m) {
   if (!m->ev_pool.empty()) { cudaEvent_t e = m->ev_pool.back(); m->ev_pool.pop_back(); return e; }
@@ -728,6 +773,8 @@ void ocn_model_destroy(ocn_model* model) {
     drop_events(model);
     for (cudaEvent_t e : model->ev_pool) cudaEventDestroy(e);
     model->ev_pool.clear();
+    if (model->xfer) cudaStreamSynchronize(model->xfer);
+    xfer_release(model);
   }
   delete model;
 }
@@ -748,7 +795,7 @@ ocn_status ocn_model_bind_arena(ocn_model* m, void* device_ptr, size_t bytes) {
   drop_graphs(m);
   m->arena = reinterpret_cast<char*>(device_ptr);
   m->cur = 0;
-  for (int t = 0; t < m->d.n_tracers; ++t) m->cref_host[t].assign(m->g->Nz, 0.0);
+  for (int t = 0; t < m->d.n_tracers; ++t) { m->cref_host[t].assign(m->g->Nz, 0.0); m->cref_pending[t] = false; }
   e = cudaMemsetAsync(m->arena, 0, m->bytes, m->stream);
   if (e != cudaSuccess) return cuda_fail(e, "clear arena");
   std::vector<char> blob = (m->es == 4) ? metrics_blob<float>(m) : metrics_blob<double>(m);
@@ -769,16 +816,15 @@ ocn_status ocn_model_bind_arena(ocn_model* m, void* device_ptr, size_t bytes) {
   return OCN_OK;
 }
 
-ocn_status ocn_set_field(ocn_model* m, int field, const void* src, size_t nbytes, int src_is_device) {
-  if (!m || !src) return fail(OCN_ERR_ARG, "null argument");
-  if (!m->arena) return fail(OCN_ERR_STATE, "arena not bound");
-  if (!field_valid(m, field) || field == OCN_FIELD_NU_E) return fail(OCN_ERR_ARG, "invalid field id for set");
-  DeviceGuard dg(m->dev);
-  size_t elems = 0;
-  char* dst = field_ptr(m, field, &elems);
-  if (nbytes != elems * (size_t)m->es) return fail(OCN_ERR_ARG, "byte count does not match the field size");
-  cudaError_t e = cudaMemcpyAsync(dst, src, nbytes, src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, m->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "set field copy");
+}  // extern "C"
+
+namespace {
+
+// The work of setting one field that follows its copy into dst: the QAB2 restart flag, the host
+// mirror of a reference profile set as is, the reference profile and anomaly of a tracer (its
+// profile read back into the pinned staging array), and the wall faces of w.
+ocn_status set_followup(ocn_model* m, int field, char* dst, size_t nbytes) {
+  cudaError_t e = cudaSuccess;
   // QAB2 restarts with an Euler step after the state is set, and continues when G^{m-1} is restored
   m->ab_started = (field >= OCN_FIELD_G && field < OCN_FIELD_G + 3 + OCN_MAX_TRACERS);
   const int tr = (field & OCN_FIELD_RAW) ? -1 : field - OCN_FIELD_TRACER0;
@@ -790,6 +836,7 @@ ocn_status ocn_set_field(ocn_model* m, int field, const void* src, size_t nbytes
     if (e != cudaSuccess) return cuda_fail(e, "reference profile read");
     for (int k = 0; k < m->g->Nz; ++k)
       m->cref_host[rf][k] = (m->es == 4) ? (double)reinterpret_cast<float*>(hb.data())[k] : reinterpret_cast<double*>(hb.data())[k];
+    m->cref_pending[rf] = false;
   }
   if (tr >= 0 && tr < m->d.n_tracers) {
     // new reference profile = the horizontal mean of each level; store the anomaly
@@ -803,12 +850,7 @@ ocn_status ocn_set_field(ocn_model* m, int field, const void* src, size_t nbytes
       if (e == cudaSuccess) e = launch_level_shift<double>(reinterpret_cast<double*>(dst), plane, m->g->Nz, reinterpret_cast<double*>(ref), -1.0, m->stream);
     }
     if (e != cudaSuccess) return cuda_fail(e, "tracer reference profile");
-    std::vector<char> hb((size_t)m->g->Nz * m->es);
-    e = cudaMemcpyAsync(hb.data(), ref, hb.size(), cudaMemcpyDeviceToHost, m->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "tracer reference profile read");
-    for (int k = 0; k < m->g->Nz; ++k)
-      m->cref_host[tr][k] = (m->es == 4) ? (double)reinterpret_cast<float*>(hb.data())[k] : reinterpret_cast<double*>(hb.data())[k];
+    m->cref_pending[tr] = true;      // the host mirror is read back where it is used
   }
   if (field == OCN_FIELD_W || field == OCN_FIELD_G + OCN_FIELD_W) {
     size_t pb = (size_t)m->g->Nx * m->g->Ny * m->es;
@@ -816,40 +858,132 @@ ocn_status ocn_set_field(ocn_model* m, int field, const void* src, size_t nbytes
     if (e == cudaSuccess) e = cudaMemsetAsync(dst + (size_t)m->g->Nz * pb, 0, pb, m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "wall faces");
   }
-  if (!src_is_device) {
-    e = cudaStreamSynchronize(m->stream);   // the host buffer is only borrowed for the call
+  return OCN_OK;
+}
+
+// Set n fields: every copy first, back to back on the model stream, then the follow-up work of
+// each field in order; from host memory the call returns once the copies are done (the host
+// buffers are borrowed for them only).
+ocn_status set_fields(ocn_model* m, int n, const int* fields, const void* const* srcs, const size_t* nbytes,
+                      int src_is_device) {
+  if (!m || n < 0 || (n > 0 && (!fields || !srcs || !nbytes))) return fail(OCN_ERR_ARG, "null argument");
+  if (src_is_device < 0 || src_is_device > OCN_HOST_ASYNC) return fail(OCN_ERR_ARG, "src_is_device must be 0, 1 or OCN_HOST_ASYNC");
+  if (!m->arena) return fail(OCN_ERR_STATE, "arena not bound");
+  std::vector<char*> dst(n);
+  for (int i = 0; i < n; ++i) {
+    if (!srcs[i]) return fail(OCN_ERR_ARG, "null argument");
+    if (!field_valid(m, fields[i]) || fields[i] == OCN_FIELD_NU_E) return fail(OCN_ERR_ARG, "invalid field id for set");
+    size_t elems = 0;
+    dst[i] = field_ptr(m, fields[i], &elems);
+    if (nbytes[i] != elems * (size_t)m->es) return fail(OCN_ERR_ARG, "byte count does not match the field size");
+  }
+  DeviceGuard dg(m->dev);
+  const bool host = src_is_device != 1;              // 0: host, waited for; OCN_HOST_ASYNC: host, not waited for
+  cudaError_t e = cudaSuccess;
+  if (host) {
+    e = xfer_setup(m);
+    if (e != cudaSuccess) return cuda_fail(e, "transfer stream");
+  }
+  for (int i = 0; i < n; ++i) {
+    e = cudaMemcpyAsync(dst[i], srcs[i], nbytes[i], host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "set field copy");
+  }
+  if (host) {
+    e = cudaEventRecord(m->copy_done, m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "set field copy event");
+  }
+  for (int i = 0; i < n; ++i) {
+    const ocn_status st = set_followup(m, fields[i], dst[i], nbytes[i]);
+    if (st != OCN_OK) return st;
+  }
+  if (src_is_device == 0) {
+    e = cudaEventSynchronize(m->copy_done);   // the host buffers are only borrowed for the copies
     if (e != cudaSuccess) return cuda_fail(e, "set field synchronise");
   }
   return OCN_OK;
 }
 
-ocn_status ocn_get_field(ocn_model* m, int field, void* dst, size_t nbytes, int dst_is_device) {
-  if (!m || !dst) return fail(OCN_ERR_ARG, "null argument");
+// Get n fields on the high-priority transfer stream, after the work queued on the model stream
+// so far (the model stream's later work waits for it).  A tracer's full value (stored anomaly +
+// reference profile) is formed in a work array first: the spectral work space for a single
+// field; for several fields, tracer t's slot of the state buffer that is not current (it holds
+// the stage state the last step no longer needs, and the next step overwrites it), so that every
+// tracer's kernel runs before any copy.
+ocn_status get_fields(ocn_model* m, int n, const int* fields, void* const* dsts, const size_t* nbytes,
+                      int dst_is_device) {
+  if (!m || n < 0 || (n > 0 && (!fields || !dsts || !nbytes))) return fail(OCN_ERR_ARG, "null argument");
+  if (dst_is_device < 0 || dst_is_device > OCN_HOST_ASYNC) return fail(OCN_ERR_ARG, "dst_is_device must be 0, 1 or OCN_HOST_ASYNC");
   if (!m->arena) return fail(OCN_ERR_STATE, "arena not bound");
-  if (!field_valid(m, field)) return fail(OCN_ERR_ARG, "invalid field id");
+  std::vector<char*> src(n);
+  for (int i = 0; i < n; ++i) {
+    if (!dsts[i]) return fail(OCN_ERR_ARG, "null argument");
+    if (!field_valid(m, fields[i])) return fail(OCN_ERR_ARG, "invalid field id");
+    size_t elems = 0;
+    src[i] = field_ptr(m, fields[i], &elems);
+    if (nbytes[i] != elems * (size_t)m->es) return fail(OCN_ERR_ARG, "byte count does not match the field size");
+  }
   DeviceGuard dg(m->dev);
-  size_t elems = 0;
-  char* src = field_ptr(m, field, &elems);
-  if (nbytes != elems * (size_t)m->es) return fail(OCN_ERR_ARG, "byte count does not match the field size");
-  const int tr = (field & OCN_FIELD_RAW) ? -1 : field - OCN_FIELD_TRACER0;
-  if (tr >= 0 && tr < m->d.n_tracers) {
-    // add the reference profile back in the spectral work space (larger than one field)
-    char* scratch = m->arena + m->off_spec;
+  cudaError_t e = xfer_setup(m);
+  if (e == cudaSuccess) e = cudaEventRecord(m->xfer_in, m->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(m->xfer, m->xfer_in, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "transfer stream");
+  for (int i = 0; i < n; ++i) {
+    const int tr = (fields[i] & OCN_FIELD_RAW) ? -1 : fields[i] - OCN_FIELD_TRACER0;
+    if (tr < 0 || tr >= m->d.n_tracers) continue;
+    // add the reference profile back in a work array
+    char* scratch = (n == 1) ? m->arena + m->off_spec : m->arena + m->off_state[1 - m->cur][OCN_FIELD_TRACER0 + tr];
     const size_t plane = (size_t)m->g->Nx * m->g->Ny;
     const char* ref = m->arena + m->off_cref[tr];
-    cudaError_t e = cudaMemcpyAsync(scratch, src, nbytes, cudaMemcpyDeviceToDevice, m->stream);
-    if (e == cudaSuccess)
-      e = (m->es == 4) ? launch_level_shift<float>(reinterpret_cast<float*>(scratch), plane, m->g->Nz, reinterpret_cast<const float*>(ref), 1.0f, m->stream)
-                       : launch_level_shift<double>(reinterpret_cast<double*>(scratch), plane, m->g->Nz, reinterpret_cast<const double*>(ref), 1.0, m->stream);
+    e = (m->es == 4) ? launch_level_add<float>(reinterpret_cast<float*>(scratch), reinterpret_cast<const float*>(src[i]), plane, m->g->Nz, reinterpret_cast<const float*>(ref), m->xfer)
+                     : launch_level_add<double>(reinterpret_cast<double*>(scratch), reinterpret_cast<const double*>(src[i]), plane, m->g->Nz, reinterpret_cast<const double*>(ref), m->xfer);
     if (e != cudaSuccess) return cuda_fail(e, "tracer reference profile");
-    src = scratch;
+    src[i] = scratch;
   }
-  cudaError_t e = cudaMemcpyAsync(dst, src, nbytes, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream);
+  for (int i = 0; i < n; ++i) {
+    e = cudaMemcpyAsync(dsts[i], src[i], nbytes[i], dst_is_device == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->xfer);
+    if (e != cudaSuccess) return cuda_fail(e, "get field copy");
+  }
+  e = cudaEventRecord(m->xfer_out, m->xfer);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(m->stream, m->xfer_out, 0);
   if (e != cudaSuccess) return cuda_fail(e, "get field copy");
-  if (!dst_is_device) {
-    e = cudaStreamSynchronize(m->stream);
+  if (dst_is_device == 0) {
+    e = cudaEventSynchronize(m->xfer_out);
     if (e != cudaSuccess) return cuda_fail(e, "get field synchronise");
   }
+  return OCN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ocn_status ocn_set_field(ocn_model* m, int field, const void* src, size_t nbytes, int src_is_device) {
+  if (!m || !src) return fail(OCN_ERR_ARG, "null argument");
+  return set_fields(m, 1, &field, &src, &nbytes, src_is_device);
+}
+
+ocn_status ocn_get_field(ocn_model* m, int field, void* dst, size_t nbytes, int dst_is_device) {
+  if (!m || !dst) return fail(OCN_ERR_ARG, "null argument");
+  return get_fields(m, 1, &field, &dst, &nbytes, dst_is_device);
+}
+
+ocn_status ocn_set_fields(ocn_model* m, int n, const int* fields, const void* const* srcs, const size_t* nbytes,
+                          int src_is_device) {
+  return set_fields(m, n, fields, srcs, nbytes, src_is_device);
+}
+
+ocn_status ocn_get_fields(ocn_model* m, int n, const int* fields, void* const* dsts, const size_t* nbytes,
+                          int dst_is_device) {
+  return get_fields(m, n, fields, dsts, nbytes, dst_is_device);
+}
+
+ocn_status ocn_wait_transfers(ocn_model* m) {
+  if (!m) return fail(OCN_ERR_ARG, "null argument");
+  if (!m->xfer) return OCN_OK;                      // no host transfer issued yet
+  DeviceGuard dg(m->dev);
+  cudaError_t e = cudaEventSynchronize(m->copy_done);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->xfer);
+  if (e != cudaSuccess) return cuda_fail(e, "wait for transfers");
   return OCN_OK;
 }
 
@@ -917,6 +1051,7 @@ ocn_status ocn_diagnostics(ocn_model* m, double dt, double* out, int nout) {
   double vals[OCN_MAX_TRACERS + 6];
   e = cudaMemcpyAsync(vals, m->arena + m->off_diag, sizeof(double) * (nt + 6), cudaMemcpyDeviceToHost, m->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e == cudaSuccess) e = cref_refresh(m);
   if (e != cudaSuccess) return cuda_fail(e, "diagnostics read");
   for (int v = 0; v < nt + 6; ++v) out[v] = vals[v];
   for (int t = 0; t < nt; ++t)

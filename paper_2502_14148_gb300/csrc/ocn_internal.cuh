@@ -181,6 +181,7 @@ template <typename T> cudaError_t launch_profile_means(const ProfileArgs<T>& a, 
 // and p[k][.] += sign * ref[k].
 template <typename T> cudaError_t launch_level_mean(const T* p, size_t plane, int Nz, T* ref, cudaStream_t s);
 template <typename T> cudaError_t launch_level_shift(T* p, size_t plane, int Nz, const T* ref, T sign, cudaStream_t s);
+template <typename T> cudaError_t launch_level_add(T* dst, const T* src, size_t plane, int Nz, const T* ref, cudaStream_t s);
 int diag_blocks();
 // Raise a kernel's dynamic shared memory limit to at least `bytes` on the current device (never
 // lowers it: graphs captured earlier may launch the kernel with more).

@@ -143,6 +143,13 @@ __global__ void k_level_shift(T* p, size_t plane, int Nz, const T* ref, T sign) 
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     p[i] += sign * ref[i / plane];
 }
+// dst = src + ref[level]: the same sum as a copy followed by k_level_shift with sign +1
+template <typename T>
+__global__ void k_level_add(T* __restrict__ dst, const T* __restrict__ src, size_t plane, int Nz, const T* ref) {
+  const size_t n = plane * (size_t)Nz;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = src[i] + ref[i / plane];
+}
 template <typename T>
 cudaError_t launch_level_mean(const T* p, size_t plane, int Nz, T* ref, cudaStream_t s) {
   k_level_mean<T><<<Nz, 256, 0, s>>>(p, plane, ref);
@@ -153,6 +160,13 @@ cudaError_t launch_level_shift(T* p, size_t plane, int Nz, const T* ref, T sign,
   k_level_shift<T><<<1216, 256, 0, s>>>(p, plane, Nz, ref, sign);
   return cudaGetLastError();
 }
+template <typename T>
+cudaError_t launch_level_add(T* dst, const T* src, size_t plane, int Nz, const T* ref, cudaStream_t s) {
+  k_level_add<T><<<1216, 256, 0, s>>>(dst, src, plane, Nz, ref);
+  return cudaGetLastError();
+}
+template cudaError_t launch_level_add<float>(float*, const float*, size_t, int, const float*, cudaStream_t);
+template cudaError_t launch_level_add<double>(double*, const double*, size_t, int, const double*, cudaStream_t);
 template cudaError_t launch_level_mean<float>(const float*, size_t, int, float*, cudaStream_t);
 template cudaError_t launch_level_mean<double>(const double*, size_t, int, double*, cudaStream_t);
 template cudaError_t launch_level_shift<float>(float*, size_t, int, const float*, float, cudaStream_t);

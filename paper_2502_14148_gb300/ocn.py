@@ -26,6 +26,7 @@ OCN_FIELD_U, OCN_FIELD_V, OCN_FIELD_W, OCN_FIELD_TRACER0 = 0, 1, 2, 3
 OCN_FIELD_P, OCN_FIELD_G, OCN_FIELD_NU_E = 10, 20, 30
 OCN_FIELD_TRACER_REF0, OCN_FIELD_RAW = 40, 0x100
 OCN_OPT_GRAPHS, OCN_OPT_SYNC_CHECK, OCN_OPT_KERNEL_TIMING, OCN_OPT_TENDENCY_VARIANT = 1, 2, 3, 4
+OCN_HOST_ASYNC = 2
 TENDENCY_VARIANTS = 7
 KERNEL_CLASSES = ["closure", "tendency", "div_fftx", "fft_y", "tridiag", "gauge", "ifftx", "correct", "column_closure",
                   "vertical"]
@@ -40,6 +41,7 @@ STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_NONFIN
 # Entry points declared in include/ocn.h (checked by the CPU test suite).
 EXPORTS = ["ocn_abi_version", "ocn_last_error", "ocn_grid_create", "ocn_grid_destroy", "ocn_model_create",
            "ocn_model_destroy", "ocn_model_arena_bytes", "ocn_model_bind_arena", "ocn_set_field", "ocn_get_field",
+           "ocn_set_fields", "ocn_get_fields", "ocn_wait_transfers",
            "ocn_project", "ocn_time_step", "ocn_compute_tendencies", "ocn_diagnostics", "ocn_set_option",
            "ocn_launches_per_step", "ocn_kernel_times", "ocn_project_noalloc", "ocn_autotune", "ocn_profiles",
            "ocn_regrid", "ocn_ensemble_create", "ocn_ensemble_destroy", "ocn_ensemble_arena_bytes",
@@ -107,6 +109,9 @@ def lib(path: str = LIB_PATH):
     L.ocn_model_bind_arena.argtypes = [vp, vp, sz]
     L.ocn_set_field.argtypes = [vp, C.c_int, vp, sz, C.c_int]
     L.ocn_get_field.argtypes = [vp, C.c_int, vp, sz, C.c_int]
+    L.ocn_set_fields.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(vp), C.POINTER(sz), C.c_int]
+    L.ocn_get_fields.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(vp), C.POINTER(sz), C.c_int]
+    L.ocn_wait_transfers.argtypes = [vp]
     L.ocn_project.argtypes = [vp]
     L.ocn_time_step.argtypes = [vp, C.c_double, C.c_int]
     L.ocn_compute_tendencies.argtypes = [vp]
@@ -389,6 +394,29 @@ class Model:
     def get_host(self, name: str, host_tensor):
         _check(lib().ocn_get_field(self._h, self.fid(name), C.c_void_p(host_tensor.data_ptr()),
                                    host_tensor.numel() * host_tensor.element_size(), 0), "ocn_get_field")
+
+    def _many(self, tensors: dict):
+        n = len(tensors)
+        fids = (C.c_int * n)(*[self.fid(k) for k in tensors])
+        ptrs = (C.c_void_p * n)(*[t.data_ptr() for t in tensors.values()])
+        nbytes = (C.c_size_t * n)(*[t.numel() * t.element_size() for t in tensors.values()])
+        return n, fids, ptrs, nbytes
+
+    def set_host_many(self, tensors: dict, wait: bool = True):
+        """Copy several fields from (pinned) host memory in one call (ocn_set_fields); with
+        wait=False the call only enqueues (OCN_HOST_ASYNC) and the tensors must stay unchanged
+        until wait_transfers()."""
+        n, fids, ptrs, nbytes = self._many(tensors)
+        _check(lib().ocn_set_fields(self._h, n, fids, ptrs, nbytes, 0 if wait else OCN_HOST_ASYNC), "ocn_set_fields")
+
+    def get_host_many(self, tensors: dict, wait: bool = True):
+        """Copy several fields into (pinned) host memory in one call (ocn_get_fields); with
+        wait=False the data is there once wait_transfers() has returned."""
+        n, fids, ptrs, nbytes = self._many(tensors)
+        _check(lib().ocn_get_fields(self._h, n, fids, ptrs, nbytes, 0 if wait else OCN_HOST_ASYNC), "ocn_get_fields")
+
+    def wait_transfers(self):
+        _check(lib().ocn_wait_transfers(self._h), "ocn_wait_transfers")
 
     def checkpoint(self) -> dict:
         """Device copies of everything a bitwise restart needs (state, raw tracer anomalies, profiles,
