@@ -98,9 +98,10 @@ template <> struct Coef<double> {
   template <int p, int n> static __device__ __forceinline__ double cen() { return cWd.cen[p][n]; }
 };
 
-// The reciprocals of the WENO weights: the hardware approximation (at most 1 ulp off; every
-// argument here is a positive indicator plus 1e-8, or a weight sum of at least 1, far from the
-// ranges where a division needs care), issued as the bare instruction.
+// The reciprocals of the WENO weights and of the AMD normalisations: the hardware approximation
+// (at most 1 ulp off), issued as the bare instruction.  Every WENO argument is a positive
+// indicator plus 1e-8 or a weight sum of at least 1; an AMD quotient is used only where its
+// denominator (a sum of squared gradients) is positive.
 __device__ __forceinline__ float rcp(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -476,7 +477,7 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
         for (int p = 0; p < 3; ++p)
 #pragma unroll
           for (int q = 0; q < 3; ++q) den = __fmaf_rn(G[p][q], G[p][q], den);
-        const T nv = __fdividef(-a.C_amd * num, den);
+        const T nv = (-a.C_amd * num) * rcp(den);      // used only where den > 0
         nu = (den > T(0) && nv > T(0)) ? nv : T(0);
         const T rzl2 = T(2) * rzl4, rzh2 = T(2) * rzh4;                // 1/(2 dz_f) of the two faces
         const T hx = T(0.5) * a.rdx, hy = T(0.5) * a.rdy;
@@ -495,7 +496,7 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
             cn = __fmaf_rn(__fmul_rn(D2[m], dc[m]), gd, cn);
           }
           const T cd = __fmaf_rn(dc2, dc2, __fmaf_rn(dc1, dc1, __fmul_rn(dc0, dc0)));
-          const T kv = __fdividef(-a.C_amd * cn, cd);
+          const T kv = (-a.C_amd * cn) * rcp(cd);      // used only where cd > 0
           kap[t] = (cd > T(0) && kv > T(0)) ? kv : T(0);
         }
       }
