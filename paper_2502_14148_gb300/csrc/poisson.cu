@@ -282,7 +282,6 @@ __device__ __forceinline__ void ifftx_body(const PoissonArgs<T>& a, int LR, cons
   C* A = reinterpret_cast<C*>(sm_raw);
   const int M = a.Mx, Nx = a.Nx, Ny = a.Ny, Nz = a.Nz;
   C* B = A + spad_size<C>((size_t)LR * M);
-  const int S = M + 1;
   const int row0 = bid.x * LR;
   const int nrows = min(LR, Ny * Nz - row0);
   const C* spec = reinterpret_cast<const C*>(a.spec);
