@@ -175,6 +175,19 @@ ocn_status ocn_get_field(ocn_model* model, int field, void* dst, size_t nbytes, 
  * asynchronously.  This lets a caller overlap a model's copies with its own or
  * another model's steps and with copies in the other direction. */
 #define OCN_HOST_ASYNC 2
+/* Bounds checks (a test aid, not a step of the method): in the library variant
+ * built with -DOCN_BOUNDS_CHECK=1 (libocn_checked.so: python -m
+ * paper_2502_14148_gb300.build --checked), the tendency kernel, the projection
+ * FFTs and the tridiagonal solve check their indices; an index outside its array
+ * sets a bit of the model's status word (1 stencil window outside the staged
+ * plane, 2 gather source, 4 face-flux slot, 8 state/tendency element, 16 FFT
+ * shared buffer, 32 spectrum/velocity/pressure element, 64 tridiagonal unknown)
+ * and is replaced by 0, so that nothing faults or traps.  Synchronises the model
+ * stream, returns the word in *status and clears it; *checked (if not null) is 1
+ * in the checked variant and 0 in the normal build (whose word stays 0).
+ * Errors: OCN_ERR_ARG, OCN_ERR_STATE (no arena), OCN_ERR_CUDA. */
+ocn_status ocn_bounds_status(ocn_model* model, unsigned* status, int* checked);
+
 /* Wait until every host transfer issued on the model so far (the copies of
  * ocn_set_field(s) and everything of ocn_get_field(s)) has completed.
  * Errors: OCN_ERR_ARG, OCN_ERR_CUDA. */

@@ -43,9 +43,13 @@ def _newer(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Build libocn.so; with checked=True the bounds-checked variant libocn_checked.so (every
+    translation unit compiled with -DOCN_BOUNDS_CHECK=1, objects in _build_checked/)."""
     nvcc = _nvcc()
-    os.makedirs(OBJ, exist_ok=True)
+    obj_dir = OBJ + "_checked" if checked else OBJ
+    lib_path = os.path.join(LIBDIR, "libocn_checked.so") if checked else LIB
+    os.makedirs(obj_dir, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     headers = [os.path.join(CSRC, "ocn_internal.cuh"), os.path.join(CSRC, "tendency_kernel.cuh"),
                os.path.join(CSRC, "column.cuh"), os.path.join(CSRC, "batch.cuh"),
@@ -54,10 +58,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
              "-I" + os.path.join(ROOT, "include")] + ARCH
     if verbose:
         flags += ["-Xptxas", "-v"]
+    if checked:
+        flags += ["-DOCN_BOUNDS_CHECK=1"]
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(OBJ, os.path.splitext(src)[0] + ".o")
+        o = os.path.join(obj_dir, os.path.splitext(src)[0] + ".o")
         if force or _newer(o, [s] + headers):
             jobs.append([nvcc] + flags + ["-c", s, "-o", o])
     if jobs:
@@ -69,18 +75,18 @@ def build(force: bool = False, verbose: bool = False) -> str:
                     sys.stderr.write(r.stdout + r.stderr)
                 if r.returncode != 0:
                     raise RuntimeError("nvcc failed: " + " ".join(j))
-    objs = [os.path.join(OBJ, os.path.splitext(s)[0] + ".o") for s in SOURCES]
-    if force or jobs or _newer(LIB, objs):
-        tmp = LIB + f".{os.getpid()}.tmp"
+    objs = [os.path.join(obj_dir, os.path.splitext(s)[0] + ".o") for s in SOURCES]
+    if force or jobs or _newer(lib_path, objs):
+        tmp = lib_path + f".{os.getpid()}.tmp"
         cmd = [nvcc, "-shared", "-cudart", "shared", "-o", tmp] + objs + ARCH + \
               ["-Xlinker", "-rpath=" + _cuda_lib_dir(nvcc)]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)
             raise RuntimeError("link failed")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

@@ -134,7 +134,7 @@ struct ocn_model {
   size_t off_G[3 + OCN_MAX_TRACERS];
   size_t off_p = 0, off_nu = 0, off_kap[OCN_MAX_TRACERS], off_spec = 0, off_cpiv = 0, off_pinv = 0;
   size_t off_dzc = 0, off_rdzc = 0, off_dzf = 0, off_rdzf = 0, off_lamx = 0, off_lamy = 0, off_twx = 0, off_twy = 0;
-  size_t off_partial = 0, off_diag = 0;
+  size_t off_partial = 0, off_diag = 0, off_oob = 0;
   char* arena = nullptr;
   int cur = 0;
   bool graphs = true, sync_check = false;
@@ -323,6 +323,7 @@ void layout(ocn_model* m) {
   for (int t = 0; t < OCN_MAX_TRACERS; ++t) m->off_cref[t] = (t < m->d.n_tracers) ? take(es * g->Nz) : 0;
   m->off_partial = take(sizeof(double) * (size_t)diag_blocks() * (OCN_MAX_TRACERS + 6));
   m->off_diag = take(sizeof(double) * 16);
+  m->off_oob = take(sizeof(unsigned));
   m->off_nuz = take(es * (g->Nz + 1));
   m->off_kapz = take(es * (g->Nz + 1));
   if (column_closure_capable(m)) {
@@ -374,6 +375,7 @@ PoissonArgs<T> poisson_args(const ocn_model* m, int which, double dts) {
   a.lamx = at<T>(m, m->off_lamx); a.lamy = at<T>(m, m->off_lamy);
   a.twx = at<T>(m, m->off_twx); a.twy = at<T>(m, m->off_twy);
   a.Nx = g->Nx; a.Ny = g->Ny; a.Nz = g->Nz; a.Mx = g->Nx / 2; a.Sp = spec_row_stride(a.Mx);
+  a.oob = at<unsigned>(m, m->off_oob);
   a.rdx = (T)(g->Nx / g->Lx); a.rdy = (T)(g->Ny / g->Ly);
   a.inv_dt = (T)(1.0 / dts); a.dt = (T)dts;
   a.scale = (T)(1.0 / ((double)(g->Nx / 2) * g->Ny));
@@ -443,6 +445,7 @@ cudaError_t enqueue_tendency(ocn_model* m, int which, double dt_gamma, double dt
   a.dzc = at<T>(m, m->off_dzc);
   a.dx = (T)(g->Lx / g->Nx); a.dy = (T)(g->Ly / g->Ny);
   a.Cs = (T)m->d.Cs; a.Cb = (T)m->d.Cb; a.C_amd = (T)m->d.C_amd;
+  a.oob = at<unsigned>(m, m->off_oob);
   m->hook.pre(OCN_K_TENDENCY);
   cudaError_t e = launch_tendency<T>(a, m->R, m->stream);
   m->hook.post(OCN_K_TENDENCY);
@@ -975,6 +978,20 @@ ocn_status ocn_set_fields(ocn_model* m, int n, const int* fields, const void* co
 ocn_status ocn_get_fields(ocn_model* m, int n, const int* fields, void* const* dsts, const size_t* nbytes,
                           int dst_is_device) {
   return get_fields(m, n, fields, dsts, nbytes, dst_is_device);
+}
+
+ocn_status ocn_bounds_status(ocn_model* m, unsigned* status, int* checked) {
+  if (!m || !status) return fail(OCN_ERR_ARG, "null argument");
+  if (!m->arena) return fail(OCN_ERR_STATE, "arena not bound");
+  if (checked) *checked = OCN_BOUNDS_CHECK;
+  DeviceGuard dg(m->dev);
+  unsigned v = 0;
+  cudaError_t e = cudaStreamSynchronize(m->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(&v, m->arena + m->off_oob, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->arena + m->off_oob, 0, sizeof(v), m->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bounds status");
+  *status = v;
+  return OCN_OK;
 }
 
 ocn_status ocn_wait_transfers(ocn_model* m) {

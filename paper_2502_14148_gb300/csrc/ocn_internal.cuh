@@ -42,6 +42,38 @@ struct StatePtrs {
   T* c[kMaxTracers];
 };
 
+// Bounds-checked builds (every translation unit compiled with -DOCN_BOUNDS_CHECK=1: the library
+// variant libocn_checked.so, for tests).  The tendency kernel, the projection FFTs and the
+// tridiagonal solve check their indices; one outside its array sets a bit of the model's status
+// word (the code below) and is replaced by 0, so the access stays inside the array and nothing
+// traps.  In the normal build a check is the index itself and costs nothing.
+enum : unsigned {
+  kOobPlane = 1u,        // a thread's stencil window or a ring point outside the staged plane
+  kOobGather = 2u,       // a staged plane's source element or level outside its field
+  kOobFlux = 4u,         // a face-flux slot outside the flux planes
+  kOobGlobal = 8u,       // a state, tendency or eddy-viscosity element outside its field
+  kOobFftShared = 16u,   // an FFT pass element outside its shared buffer
+  kOobFftGlobal = 32u,   // a spectrum, velocity or pressure element outside its array
+  kOobTridiag = 64u      // a tridiagonal unknown or factor outside the spectrum
+};
+#ifndef OCN_BOUNDS_CHECK
+#define OCN_BOUNDS_CHECK 0
+#endif
+#ifdef __CUDACC__
+__device__ __forceinline__ long long oob_index(long long i, long long n, unsigned* st, unsigned code) {
+  if (i < 0 || i >= n) {
+    if (st) atomicOr(st, code);
+    return 0;
+  }
+  return i;
+}
+#endif
+#if OCN_BOUNDS_CHECK
+#define OCN_CHK(i, n, st, code) ((decltype((i) + 0))::ocn::oob_index((long long)(i), (long long)(n), (st), (code)))
+#else
+#define OCN_CHK(i, n, st, code) (i)
+#endif
+
 template <typename T>
 struct TendencyArgs {
   StatePtrs<T> cur;       // state at the start of the substage (read)
@@ -72,6 +104,7 @@ struct TendencyArgs {
   T* nu_out;
   const T* dzc;           // dz_c[k]
   T dx, dy, Cs, Cb, C_amd;  // grid spacing, Smagorinsky, stratification and AMD constants
+  unsigned* oob;          // status word of the bounds-checked build (or null)
 };
 
 template <typename T>
@@ -119,6 +152,7 @@ struct PoissonArgs {
   T Htot;                      // total depth (for the gauge mean)
   int fp64_pivots;
   FftPlan px, py;
+  unsigned* oob;               // status word of the bounds-checked build (or null)
 };
 
 // Row stride of a model's spectrum: Nx/2 + 1 rounded up to a multiple of 8 complex values, so

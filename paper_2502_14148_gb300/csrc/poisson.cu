@@ -149,9 +149,12 @@ __device__ __forceinline__ void stockham_pass(const Ld& ld, const St& st, int N,
 template <typename C, typename T, int R, class Ld, class St>
 __device__ __forceinline__ void stockham_pass_at(bool first, bool last, const Ld& ld, const St& st, const C* src,
                                                  C* dst, int sl, int se, int N, int Ns, int twstep, int nlines,
-                                                 const C* tw, int tws, int s, bool line_fast) {
-  auto sld = [&](int l, int e) -> C { return src[spad<C>(l * sl + e * se)]; };
-  auto sst = [&](int l, int e, C v) { dst[spad<C>(l * sl + e * se)] = v; };
+                                                 const C* tw, int tws, int s, bool line_fast, unsigned* oob) {
+#if OCN_BOUNDS_CHECK
+  const int cap = (int)spad_size<C>((size_t)nlines * N);   // elements of each shared buffer in use
+#endif
+  auto sld = [&](int l, int e) -> C { return src[OCN_CHK(spad<C>(l * sl + e * se), cap, oob, kOobFftShared)]; };
+  auto sst = [&](int l, int e, C v) { dst[OCN_CHK(spad<C>(l * sl + e * se), cap, oob, kOobFftShared)] = v; };
   if (first && last) stockham_pass<C, T, R>(ld, st, N, Ns, twstep, nlines, tw, tws, s, line_fast);
   else if (first) stockham_pass<C, T, R>(ld, sst, N, Ns, twstep, nlines, tw, tws, s, line_fast);
   else if (last) stockham_pass<C, T, R>(sld, st, N, Ns, twstep, nlines, tw, tws, s, line_fast);
@@ -166,7 +169,8 @@ __device__ __forceinline__ void stockham_pass_at(bool first, bool last, const Ld
 // (npass - 1) even ? a : b, when st stores there.
 template <typename C, typename T, class Ld, class St>
 __device__ __forceinline__ void block_fft(C* a, C* b, const FftPlan& plan, int nlines, int sl, int se, const C* tw,
-                                          int tws, int s, bool line_fast, const Ld& ld, const St& st) {
+                                          int tws, int s, bool line_fast, const Ld& ld, const St& st,
+                                          unsigned* oob = nullptr) {
   int Ns = 1;
   int rem = plan.n;                      // N / Ns
   const int np = plan.npass;
@@ -176,10 +180,10 @@ __device__ __forceinline__ void block_fft(C* a, C* b, const FftPlan& plan, int n
     const C* src = (p & 1) ? a : b;      // written by pass p - 1
     C* dst = (p & 1) ? b : a;
     switch (R) {                         // rem / R = N / (Ns R), the pass's twiddle step
-      case 8: rem /= 8; stockham_pass_at<C, T, 8>(first, last, ld, st, src, dst, sl, se, plan.n, Ns, rem, nlines, tw, tws, s, line_fast); break;
-      case 4: rem /= 4; stockham_pass_at<C, T, 4>(first, last, ld, st, src, dst, sl, se, plan.n, Ns, rem, nlines, tw, tws, s, line_fast); break;
-      case 3: rem /= 3; stockham_pass_at<C, T, 3>(first, last, ld, st, src, dst, sl, se, plan.n, Ns, rem, nlines, tw, tws, s, line_fast); break;
-      default: rem /= 2; stockham_pass_at<C, T, 2>(first, last, ld, st, src, dst, sl, se, plan.n, Ns, rem, nlines, tw, tws, s, line_fast); break;
+      case 8: rem /= 8; stockham_pass_at<C, T, 8>(first, last, ld, st, src, dst, sl, se, plan.n, Ns, rem, nlines, tw, tws, s, line_fast, oob); break;
+      case 4: rem /= 4; stockham_pass_at<C, T, 4>(first, last, ld, st, src, dst, sl, se, plan.n, Ns, rem, nlines, tw, tws, s, line_fast, oob); break;
+      case 3: rem /= 3; stockham_pass_at<C, T, 3>(first, last, ld, st, src, dst, sl, se, plan.n, Ns, rem, nlines, tw, tws, s, line_fast, oob); break;
+      default: rem /= 2; stockham_pass_at<C, T, 2>(first, last, ld, st, src, dst, sl, se, plan.n, Ns, rem, nlines, tw, tws, s, line_fast, oob); break;
     }
     if (!last) __syncthreads();
     Ns *= R;
@@ -220,7 +224,7 @@ __device__ __forceinline__ void div_fftx_body(const PoissonArgs<T>& a, int LR, c
       const int jp = (j + 1 == Ny) ? 0 : j + 1;
       const T rdz = __ldg(a.rdzc + k);
       T val[2];
-      const size_t o = (size_t)k * plane + (size_t)j * Nx;
+      const size_t o = OCN_CHK((size_t)k * plane + (size_t)j * Nx, (size_t)Nz * plane, a.oob, kOobFftGlobal);
       if (pairs) {                        // cells 2n, 2n+1 as one vector per field and level
         const C u01 = *reinterpret_cast<const C*>(a.u + o + 2 * n);
         const T u2 = a.u[o + (2 * n + 2 == Nx ? 0 : 2 * n + 2)];
@@ -254,7 +258,7 @@ __device__ __forceinline__ void div_fftx_body(const PoissonArgs<T>& a, int LR, c
   auto ld = [&](int l, int e) -> C { return A[spad<C>(l * M + e)]; };
   C* Z = ((a.px.npass - 1) & 1) ? A : B;
   auto st = [&](int l, int e, C v) { Z[spad<C>(l * M + e)] = v; };
-  block_fft<C, T>(B, A, a.px, nrows, M, 1, reinterpret_cast<const C*>(a.twx), 2, -1, false, ld, st);
+  block_fft<C, T>(B, A, a.px, nrows, M, 1, reinterpret_cast<const C*>(a.twx), 2, -1, false, ld, st, a.oob);
   __syncthreads();
   // split: X[kx] = E + W^kx O, E = (Z[kx] + conj Z[M-kx])/2, O = (Z[kx] - conj Z[M-kx])/(2i)
   const int S = M + 1;
@@ -269,7 +273,7 @@ __device__ __forceinline__ void div_fftx_body(const PoissonArgs<T>& a, int LR, c
     const C w = reinterpret_cast<const C*>(a.twx)[kx];    // kx <= M < Nx
     const C X = cadd(E, cmul(w, O));
     const int row = row0 + l;
-    reinterpret_cast<C*>(a.spec)[(size_t)row * a.Sp + kx] = X;
+    reinterpret_cast<C*>(a.spec)[OCN_CHK((size_t)row * a.Sp + kx, (size_t)Ny * Nz * a.Sp, a.oob, kOobFftGlobal)] = X;
   }
 }
 
@@ -289,8 +293,9 @@ __device__ __forceinline__ void ifftx_body(const PoissonArgs<T>& a, int LR, cons
   // element kx of line l: Z_kx = E + i e^{+2 pi i kx / Nx} O from X[kx] and conj X[M - kx]
   auto ld = [&](int l, int kx) -> C {
     const size_t ro = (size_t)(row0 + l) * a.Sp;
-    const C x1 = spec[ro + kx];
-    const C x2 = cconj(spec[ro + (M - kx)]);
+    [[maybe_unused]] const size_t nspec = (size_t)Ny * Nz * a.Sp;
+    const C x1 = spec[OCN_CHK(ro + kx, nspec, a.oob, kOobFftGlobal)];
+    const C x2 = cconj(spec[OCN_CHK(ro + (M - kx), nspec, a.oob, kOobFftGlobal)]);
     const C E = cscale(cadd(x1, x2), T(0.5));
     C w = tw[kx];
     w.y = -w.y;                                 // e^{+2 pi i kx / Nx}
@@ -300,7 +305,7 @@ __device__ __forceinline__ void ifftx_body(const PoissonArgs<T>& a, int LR, cons
   const bool pairs = (reinterpret_cast<uintptr_t>(a.p) & (2 * sizeof(T) - 1)) == 0;   // p as 2-vectors
   // output element n of line l: p at cells 2n and 2n+1 of row row0 + l
   auto st = [&](int l, int n, C v) {
-    const size_t o = (size_t)(row0 + l) * Nx + 2 * n;
+    const size_t o = OCN_CHK((size_t)(row0 + l) * Nx + 2 * n, (size_t)Nx * Ny * Nz - 1, a.oob, kOobFftGlobal);
     if (pairs) {
       *reinterpret_cast<C*>(a.p + o) = v;
     } else {
@@ -308,7 +313,7 @@ __device__ __forceinline__ void ifftx_body(const PoissonArgs<T>& a, int LR, cons
       a.p[o + 1] = v.y;
     }
   };
-  block_fft<C, T>(A, B, a.px, nrows, M, 1, tw, 2, +1, false, ld, st);
+  block_fft<C, T>(A, B, a.px, nrows, M, 1, tw, 2, +1, false, ld, st, a.oob);
 }
 
 // FFT along y of a tile of CW kx-columns in one z-plane, in place: the first pass reads the
@@ -328,9 +333,12 @@ __device__ __forceinline__ void fft_y_body(const PoissonArgs<T>& a, int CW, int 
   C* spec = reinterpret_cast<C*>(a.spec) + (size_t)k * Ny * Sp;
   const C* twy = reinterpret_cast<const C*>(a.twy);
   for (int t = threadIdx.x; t < Ny; t += blockDim.x) sTw[t] = twy[t];
-  auto ld = [&](int l, int e) -> C { return (l < ncol) ? spec[(size_t)e * Sp + kx0 + l] : C{T(0), T(0)}; };
-  auto st = [&](int l, int e, C v) { if (l < ncol) spec[(size_t)e * Sp + kx0 + l] = v; };
-  block_fft<C, T>(A, B, a.py, CW, 1, CW, sTw, 1, sign, true, ld, st);
+  [[maybe_unused]] const size_t nlev = (size_t)Ny * Sp;
+  auto ld = [&](int l, int e) -> C {
+    return (l < ncol) ? spec[OCN_CHK((size_t)e * Sp + kx0 + l, nlev, a.oob, kOobFftGlobal)] : C{T(0), T(0)};
+  };
+  auto st = [&](int l, int e, C v) { if (l < ncol) spec[OCN_CHK((size_t)e * Sp + kx0 + l, nlev, a.oob, kOobFftGlobal)] = v; };
+  block_fft<C, T>(A, B, a.py, CW, 1, CW, sTw, 1, sign, true, ld, st, a.oob);
 }
 
 // Thomas algorithm per horizontal wavenumber.  a_k p_{k-1} + b_k p_k + c_k p_{k+1} = r_k,
@@ -419,6 +427,10 @@ __device__ __forceinline__ void tridiag_solve_body(const PoissonArgs<T>& a, cons
   if (o_ >= S * Ny) return;
   const int ky = o_ / S, kx = o_ - ky * S;
   const size_t pl = (size_t)Ny * a.Sp, o = (size_t)ky * a.Sp + kx;
+#if OCN_BOUNDS_CHECK
+  // the column's unknowns and factors, levels 0 .. Nz-1, inside the spectrum
+  (void)OCN_CHK(o + (size_t)(Nz - 1) * pl, pl * (size_t)Nz, a.oob, kOobTridiag);
+#endif
   C* x = reinterpret_cast<C*>(a.spec) + o;
   const T* cp = a.cpiv + o;
   const T* pinv = a.pinv + o;

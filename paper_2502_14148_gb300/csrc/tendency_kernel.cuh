@@ -325,6 +325,15 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
   else if (tid < TX * TY + TX + TY) { role = 2; lx = Wt; ly = tid - TX * TY - TX; }
   else { role = 3; lx = 0; ly = 0; }
   const bool active = (role == 0) ? (lx < Wt && ly < Ht) : (role == 1 ? lx < Wt : (role == 2 ? ly < Ht : false));
+#if OCN_BOUNDS_CHECK
+  if (role <= 2) {   // the stencil window of this thread's plane reads and its face-flux slots
+    const int rc = (ly + H) * PW + (lx + H);
+    (void)OCN_CHK(rc - R * PW - R, PLANE, a.oob, kOobPlane);
+    (void)OCN_CHK(rc + (R - 1) * PW + R - 1, PLANE, a.oob, kOobPlane);
+    if (active && role != 1) (void)OCN_CHK(ly * (TX + 1) + lx + (role == 0 ? 1 : 0), FXS, a.oob, kOobFlux);
+    if (active && role != 2) (void)OCN_CHK(ly * TX + lx + (role == 0 ? TX : 0), FYS, a.oob, kOobFlux);
+  }
+#endif
 
   for (int e = tid; e < PW; e += NT_) { int g = (i0 + e - H) % Nx; gi_tab[e] = g < 0 ? g + Nx : g; }
   for (int e = tid; e < PH; e += NT_) { int g = (j0 + e - H) % Ny; gj_tab[e] = g < 0 ? g + Ny : g; }
@@ -351,12 +360,12 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
 #pragma unroll
       for (int q = 0; q < NIT; ++q) {
         const int e = tid + q * NT_;
-        if (e < PLANE) cp_async(dst + e, base + goff[q], (int)sizeof(T));
+        if (e < PLANE) cp_async(dst + e, base + OCN_CHK(goff[q], plane, a.oob, kOobGather), (int)sizeof(T));
       }
     } else {
       for (int e = tid; e < PLANE; e += NT_) {
         const int yy = e / PW, xx = e - yy * PW;
-        cp_async(dst + e, base + (size_t)gj_tab[yy] * Nx + gi_tab[xx], (int)sizeof(T));
+        cp_async(dst + e, base + OCN_CHK((size_t)gj_tab[yy] * Nx + gi_tab[xx], plane, a.oob, kOobGather), (int)sizeof(T));
       }
     }
   };
@@ -554,6 +563,10 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
             qy = mt / TX; qx = mt - qy * TX;
           }
           const int e = (qy + H) * PW + (qx + H);
+#if OCN_BOUNDS_CHECK
+          (void)OCN_CHK(e - PW - 1, PLANE, a.oob, kOobPlane);
+          (void)OCN_CHK(e + PW + 1, PLANE, a.oob, kOobPlane);
+#endif
           NuCol o;
           o.u0 = sU[s0 * PLANE + e]; o.um = sU[sm * PLANE + e]; o.up = sU[sp * PLANE + e];
           o.v0 = sV[s0 * PLANE + e]; o.vm = sV[sm * PLANE + e]; o.vp = sV[sp * PLANE + e];
@@ -657,7 +670,7 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
 #pragma unroll
     for (int t = 0; t < NTR; ++t) gp_c[t] = T(0);
     if (a.mode == 0 && a.dt_zeta != T(0) && role == 0 && active) {
-      const size_t id = (size_t)k * plane + col;
+      const size_t id = OCN_CHK((size_t)k * plane + col, (size_t)Nz * plane, a.oob, kOobGlobal);
       gp_u = a.G.u[id]; gp_v = a.G.v[id]; gp_w = a.G.w[id];
 #pragma unroll
       for (int t = 0; t < NTR; ++t) gp_c[t] = a.G.c[t][id];
@@ -896,7 +909,7 @@ __device__ __forceinline__ void tendency_body(const TendencyArgs<T>& a, const ui
 
     // ================= tendencies and RK update
     if (role == 0 && active) {
-      const size_t id = (size_t)k * plane + col;
+      const size_t id = OCN_CHK((size_t)k * plane + col, (size_t)Nz * plane, a.oob, kOobGlobal);
       const T* FXu = FX + ly * (TX + 1) + lx;
       const T* FYu = FY + ly * TX + lx;
       // u

@@ -41,7 +41,7 @@ STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_NONFIN
 # Entry points declared in include/ocn.h (checked by the CPU test suite).
 EXPORTS = ["ocn_abi_version", "ocn_last_error", "ocn_grid_create", "ocn_grid_destroy", "ocn_model_create",
            "ocn_model_destroy", "ocn_model_arena_bytes", "ocn_model_bind_arena", "ocn_set_field", "ocn_get_field",
-           "ocn_set_fields", "ocn_get_fields", "ocn_wait_transfers",
+           "ocn_set_fields", "ocn_get_fields", "ocn_wait_transfers", "ocn_bounds_status",
            "ocn_project", "ocn_time_step", "ocn_compute_tendencies", "ocn_diagnostics", "ocn_set_option",
            "ocn_launches_per_step", "ocn_kernel_times", "ocn_project_noalloc", "ocn_autotune", "ocn_profiles",
            "ocn_regrid", "ocn_ensemble_create", "ocn_ensemble_destroy", "ocn_ensemble_arena_bytes",
@@ -90,11 +90,14 @@ class ColumnClosureDesc(C.Structure):
 _lib = None
 
 
-def lib(path: str = LIB_PATH):
-    """Load libocn.so (raises if it has not been built: there is no fallback)."""
+def lib(path: str = None):
+    """Load libocn.so (raises if it has not been built: there is no fallback).  The environment
+    variable OCN_LIBRARY selects another build of the same library (the bounds-checked
+    libocn_checked.so)."""
     global _lib
     if _lib is not None:
         return _lib
+    path = path or os.environ.get("OCN_LIBRARY") or LIB_PATH
     if not os.path.exists(path):
         raise RuntimeError(f"{path} is missing: build it with `python -m paper_2502_14148_gb300.build`")
     L = C.CDLL(path)
@@ -112,6 +115,7 @@ def lib(path: str = LIB_PATH):
     L.ocn_set_fields.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(vp), C.POINTER(sz), C.c_int]
     L.ocn_get_fields.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(vp), C.POINTER(sz), C.c_int]
     L.ocn_wait_transfers.argtypes = [vp]
+    L.ocn_bounds_status.argtypes = [vp, C.POINTER(C.c_uint), C.POINTER(C.c_int)]
     L.ocn_project.argtypes = [vp]
     L.ocn_time_step.argtypes = [vp, C.c_double, C.c_int]
     L.ocn_compute_tendencies.argtypes = [vp]
@@ -417,6 +421,14 @@ class Model:
 
     def wait_transfers(self):
         _check(lib().ocn_wait_transfers(self._h), "ocn_wait_transfers")
+
+    def bounds_status(self):
+        """(status word, checked): the out-of-range index bits recorded by the bounds-checked
+        library variant since the last call (cleared by the call), and whether the loaded library
+        is that variant."""
+        st, chk = C.c_uint(0), C.c_int(0)
+        _check(lib().ocn_bounds_status(self._h, C.byref(st), C.byref(chk)), "ocn_bounds_status")
+        return int(st.value), bool(chk.value)
 
     def checkpoint(self) -> dict:
         """Device copies of everything a bitwise restart needs (state, raw tracer anomalies, profiles,
