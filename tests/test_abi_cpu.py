@@ -77,3 +77,30 @@ def test_no_cpu_fallback_without_a_gpu():
                  lambda: ocn.MLP(inputs.MLP_SIZES, max_batch=128)):
         with pytest.raises(RuntimeError, match="no CPU path"):
             make()
+
+
+def test_transfer_and_bounds_calls_reject_bad_arguments(libocn):
+    """The batched transfer calls, the transfer wait and the bounds-status call refuse a null
+    model before touching the device (host-only paths)."""
+    vp = C.c_void_p
+    fids = (C.c_int * 1)(0)
+    ptrs = (vp * 1)(None)
+    nb = (C.c_size_t * 1)(4)
+    assert libocn.ocn_set_fields(None, 1, fids, ptrs, nb, 0) == -1
+    assert libocn.ocn_get_fields(None, 1, fids, ptrs, nb, 2) == -1
+    assert libocn.ocn_wait_transfers(None) == -1
+    st, chk = C.c_uint(7), C.c_int(7)
+    assert libocn.ocn_bounds_status(None, C.byref(st), C.byref(chk)) == -1
+    assert "null" in libocn.ocn_last_error().decode()
+
+
+def test_library_variant_is_selected_by_environment(tmp_path):
+    """OCN_LIBRARY names the build the binding loads (the bounds-checked variant in its GPU test); a
+    missing file is an error that names it, never a fallback to another build."""
+    import subprocess
+    import sys
+    missing = str(tmp_path / "libocn_missing.so")
+    code = "from paper_2502_14148_gb300 import ocn; ocn.lib()"
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=dict(os.environ, OCN_LIBRARY=missing),
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode != 0 and "libocn_missing.so is missing" in r.stderr
