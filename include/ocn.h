@@ -151,8 +151,9 @@ ocn_status ocn_model_arena_bytes(const ocn_model* model, size_t* bytes);
 ocn_status ocn_model_bind_arena(ocn_model* model, void* device_ptr, size_t bytes);
 
 /* Copy a field in (set) or out (get).  nbytes must equal the field's size in
- * the model precision.  src/dst is device memory when *_is_device != 0, host
- * memory otherwise.  Setting w forces w = 0 on the wall faces.  Setting a
+ * the model precision.  src/dst is device memory when *_is_device is 1, host
+ * memory when it is 0 (the call waits for its copies) or OCN_HOST_ASYNC (below:
+ * it does not).  Setting w forces w = 0 on the wall faces.  Setting a
  * field does not project the velocity (call ocn_project).
  * ocn_set_field from host memory returns once the host buffer has been copied;
  * the rest of its work (for a tracer, the new reference profile and the
